@@ -1,0 +1,260 @@
+"""FP64 CPU oracle of the Photon-Plasma particle step (arXiv:1211.4575).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product library never imports, links or calls it, and it imports nothing from
+the product package.
+
+The arithmetic lives in ``pp_oracle.c`` (plain C, one literal loop per
+definition of the paper, cited per function).  This module only compiles that
+file with gcc and marshals numpy arrays to it with ctypes.
+
+Array conventions: fields are numpy float64 arrays of shape (nz, ny, nx)
+(x fastest in memory), with the Yee staggering of the paper's Sec. III:
+E_x, J_x at (i+1/2, j, k), B_x at (i, j+1/2, k+1/2), cyclic for y and z.
+Positions are physical, in [0, n*dx).  c = eps0 = mu0 = 1.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pp_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+
+VAY, BORIS = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile pp_oracle.c into oracle/_build/liboracle.so (gcc -O2)."""
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
+        return _OUT
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    tmp = _OUT + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _OUT)
+    return _OUT
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double),
+                ("field_order", C.c_int), ("alpha", C.c_double), ("shape_order", C.c_int),
+                ("pusher", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double)]
+
+
+class Species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("w", C.c_double), ("n", C.c_int64),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("energy_E", C.c_double), ("energy_B", C.c_double), ("energy_Ex", C.c_double),
+                ("kinetic", C.c_double), ("charge", C.c_double), ("gauss_max", C.c_double),
+                ("rho_max", C.c_double), ("divB_max", C.c_double), ("relax_iters", C.c_int),
+                ("relax_residual", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        L.orc_weight.restype = C.c_double
+        L.orc_weight.argtypes = [C.c_int, C.c_double]
+        L.orc_fd_coeffs.argtypes = [C.c_int, P]
+        L.orc_diff.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, C.c_int, P, P]
+        L.orc_gather.argtypes = [C.POINTER(Grid), P, P, P, P, P]
+        L.orc_push_vay.argtypes = [C.c_double, P, P, P]
+        L.orc_push_boris.argtypes = [C.c_double, P, P, P]
+        L.orc_deposit_particle.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, P, P, P, P]
+        L.orc_current_from_drho.argtypes = [C.POINTER(Grid), P, P, P]
+        L.orc_field_update.argtypes = [C.POINTER(Grid), P, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.orc_particles_deposit.argtypes = [C.POINTER(Grid), P, P, C.POINTER(Species), C.c_int, P]
+        L.orc_step.argtypes = [C.POINTER(Grid), P, P, P, C.POINTER(Species), C.c_int,
+                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.orc_rho.argtypes = [C.POINTER(Grid), C.POINTER(Species), C.c_int, P]
+        L.orc_div_minus.argtypes = [C.POINTER(Grid), P, P]
+        L.orc_div_plus.argtypes = [C.POINTER(Grid), P, P]
+        L.orc_diagnostics.argtypes = [C.POINTER(Grid), P, P, C.POINTER(Species), C.c_int, C.POINTER(Diag)]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _ptr3(arrs):
+    """Array of three double* (for the C functions taking double *F[3])."""
+    t = (C.c_void_p * 3)(*[a.ctypes.data for a in arrs])
+    return t
+
+
+def make_grid(n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
+              relax_max_iter=200, relax_tol=1e-14) -> Grid:
+    g = Grid()
+    g.n[:] = list(n)
+    g.d[:] = [float(v) for v in d]
+    g.dt = float(dt)
+    g.field_order = int(field_order)
+    g.alpha = float(alpha)
+    g.shape_order = int(shape_order)
+    g.pusher = int(pusher)
+    g.relax_max_iter = int(relax_max_iter)
+    g.relax_tol = float(relax_tol)
+    return g
+
+
+def weight(order: int, delta: float) -> float:
+    """W^order(delta) exactly as printed in Sec. II."""
+    return lib().orc_weight(int(order), float(delta))
+
+
+def fd_coeffs(order: int) -> np.ndarray:
+    k = np.zeros(3)
+    lib().orc_fd_coeffs(int(order), _ptr(k))
+    return k
+
+
+def diff(g: Grid, f: np.ndarray, axis: int, direction: int, order: int | None = None) -> np.ndarray:
+    """Staggered derivative of a (nz, ny, nx) array along axis 0=x,1=y,2=z."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    lib().orc_diff(C.byref(g), int(order if order is not None else g.field_order), int(axis),
+                   int(direction), _ptr(f), _ptr(out))
+    return out
+
+
+def gather(g: Grid, E, B, xp):
+    xp = np.asarray(xp, dtype=np.float64)
+    Ep, Bp = np.zeros(3), np.zeros(3)
+    Ec = [np.ascontiguousarray(a, dtype=np.float64) for a in E]
+    Bc = [np.ascontiguousarray(a, dtype=np.float64) for a in B]
+    lib().orc_gather(C.byref(g), _ptr3(Ec), _ptr3(Bc), _ptr(xp), _ptr(Ep), _ptr(Bp))
+    return Ep, Bp
+
+
+def push(qmdt: float, E, B, u, pusher=VAY) -> np.ndarray:
+    E = np.asarray(E, dtype=np.float64).copy()
+    B = np.asarray(B, dtype=np.float64).copy()
+    u = np.asarray(u, dtype=np.float64).copy()
+    f = lib().orc_push_vay if pusher == VAY else lib().orc_push_boris
+    f(float(qmdt), _ptr(E), _ptr(B), _ptr(u))
+    return u
+
+
+def deposit_particle(g: Grid, q, w, x0, x1, Drho=None, lsum=None):
+    """Accumulate one particle's D rho (3 mesh arrays) and line sums."""
+    nx, ny, nz = g.n
+    if Drho is None:
+        Drho = [np.zeros((nz, ny, nx)) for _ in range(3)]
+    if lsum is None:
+        # lsum[a] is indexed [t_c, t_b] with b = a+1, c = a+2 (mod 3), t_b fastest
+        n = (nx, ny, nz)
+        lsum = [np.zeros((n[(a + 2) % 3], n[(a + 1) % 3])) for a in range(3)]
+    x0 = np.asarray(x0, dtype=np.float64)
+    x1 = np.asarray(x1, dtype=np.float64)
+    lib().orc_deposit_particle(C.byref(g), float(q), float(w), _ptr(x0), _ptr(x1), _ptr3(Drho), _ptr3(lsum))
+    return Drho, lsum
+
+
+def current_from_drho(g: Grid, Drho, lsum):
+    nx, ny, nz = g.n
+    J = [np.zeros((nz, ny, nx)) for _ in range(3)]
+    lib().orc_current_from_drho(C.byref(g), _ptr3(Drho), _ptr3(lsum), _ptr3(J))
+    return J
+
+
+def field_update(g: Grid, E, B, J):
+    """Advance E, B (lists of 3 arrays, modified in place). Returns (iters, residual)."""
+    it = C.c_int(0)
+    res = C.c_double(0.0)
+    lib().orc_field_update(C.byref(g), _ptr3(E), _ptr3(B), _ptr3(J), C.byref(it), C.byref(res))
+    return it.value, res.value
+
+
+def div_minus(g: Grid, F) -> np.ndarray:
+    out = np.zeros_like(F[0])
+    lib().orc_div_minus(C.byref(g), _ptr3(F), _ptr(out))
+    return out
+
+
+def div_plus(g: Grid, F) -> np.ndarray:
+    out = np.zeros_like(F[0])
+    lib().orc_div_plus(C.byref(g), _ptr3(F), _ptr(out))
+    return out
+
+
+class Simulation:
+    """The oracle's whole step over numpy-held state (one FP64 copy per array)."""
+
+    def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
+                 relax_max_iter=200, relax_tol=1e-14):
+        self.g = make_grid(n, d, dt, field_order, alpha, shape_order, pusher, relax_max_iter, relax_tol)
+        nx, ny, nz = n
+        self.E = [np.zeros((nz, ny, nx)) for _ in range(3)]
+        self.B = [np.zeros((nz, ny, nx)) for _ in range(3)]
+        self.J = [np.zeros((nz, ny, nx)) for _ in range(3)]
+        self.species: list[dict] = []
+        self.relax_iters = 0
+        self.relax_residual = 0.0
+        self.nstep = 0
+
+    def add_species(self, q, m, w, x, y, z, ux, uy, uz) -> int:
+        arrs = {k: np.ascontiguousarray(v, dtype=np.float64).copy()
+                for k, v in dict(x=x, y=y, z=z, ux=ux, uy=uy, uz=uz).items()}
+        self.species.append(dict(q=float(q), m=float(m), w=float(w), **arrs))
+        return len(self.species) - 1
+
+    def _sp(self):
+        arr = (Species * max(1, len(self.species)))()
+        for i, s in enumerate(self.species):
+            arr[i].q, arr[i].m, arr[i].w, arr[i].n = s["q"], s["m"], s["w"], len(s["x"])
+            for k in ("x", "y", "z", "ux", "uy", "uz"):
+                setattr(arr[i], k, s[k].ctypes.data)
+        return arr
+
+    def load_fields(self, E, B):
+        for a in range(3):
+            self.E[a][...] = E[a]
+            self.B[a][...] = B[a]
+
+    def deposit(self):
+        """Gather, push, move and deposit every particle; J receives J^{n+1}."""
+        lib().orc_particles_deposit(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), self._sp(),
+                                    len(self.species), _ptr3(self.J))
+
+    def field_update(self):
+        self.relax_iters, self.relax_residual = field_update(self.g, self.E, self.B, self.J)
+
+    def step(self, n: int = 1):
+        it = C.c_int(0)
+        res = C.c_double(0.0)
+        for _ in range(n):
+            lib().orc_step(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), _ptr3(self.J), self._sp(),
+                           len(self.species), C.byref(it), C.byref(res))
+            self.nstep += 1
+        self.relax_iters, self.relax_residual = it.value, res.value
+
+    def rho(self) -> np.ndarray:
+        nx, ny, nz = self.g.n
+        out = np.zeros((nz, ny, nx))
+        lib().orc_rho(C.byref(self.g), self._sp(), len(self.species), _ptr(out))
+        return out
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        lib().orc_diagnostics(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), self._sp(), len(self.species),
+                              C.byref(d))
+        out = {k: getattr(d, k) for k, _ in Diag._fields_}
+        out["relax_iters"] = self.relax_iters
+        out["relax_residual"] = self.relax_residual
+        return out

@@ -1,0 +1,238 @@
+"""Seeded synthetic plasma loads for the Photon-Plasma particle step.
+
+This module only draws random numbers (numpy ``Generator(PCG64(seed))``) and lays
+out particle arrays.  It contains none of the method's arithmetic, and it is the
+one module that both the FP64 oracle's tests and the CUDA path's tests and
+benchmark use, so that both sides see identical inputs.
+
+Normalisation: c = eps0 = mu0 = 1, electron charge -1 and mass 1, lengths in
+c/omega_pe where omega_pe is set by the TOTAL electron density n_e = 1.  The
+weight ``w`` of a macro-particle is its number density, n_s / ppc_s.
+
+Velocity recipe: proper velocity u = gamma*v.  A drifting thermal population
+has u = Gamma_d * beta_d * e_drift + u_th * N(0, 1)^3.  A relativistic cold beam
+(Gamma >= 2) draws the thermal part in its rest frame and is Lorentz-boosted
+along x.  Positions are uniform inside each cell (a fixed number per cell), and
+every negative particle is placed on top of a positive partner of the same
+population, so that the initial charge density is exactly zero and E = B = 0
+is a consistent initial condition.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+import numpy as np
+
+
+@dataclass
+class Population:
+    """One drifting Maxwellian population of a neutral pair of species."""
+    ppc: int                 # macro-particles per cell for each of the two species
+    density: float           # number density of each of the two species
+    beta_drift: float = 0.0  # drift 3-velocity along x (units of c)
+    u_th: float = 0.0        # thermal spread of the proper velocity per component
+    boost: bool = False      # draw thermal part in the rest frame, then boost along x
+
+
+@dataclass
+class Load:
+    n: tuple                 # cells (nx, ny, nz)
+    d: tuple                 # cell size
+    dt: float
+    species: list            # list of dicts: q, m, w, x, y, z, ux, uy, uz (float64 arrays)
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n_particles(self) -> int:
+        return int(sum(len(s["x"]) for s in self.species))
+
+
+def _draw_u(rng, n, pop: Population):
+    ux = rng.standard_normal(n) * pop.u_th
+    uy = rng.standard_normal(n) * pop.u_th
+    uz = rng.standard_normal(n) * pop.u_th
+    b = pop.beta_drift
+    if b == 0.0:
+        return ux, uy, uz
+    G = 1.0 / math.sqrt(1.0 - b * b)
+    if not pop.boost:
+        return ux + G * b, uy, uz
+    # rest-frame proper velocity -> lab frame, boost with velocity b along x
+    g_rest = np.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
+    return G * (ux + b * g_rest), uy, uz
+
+
+def pair_plasma(n, d, dt, populations, seed, masses=(1.0, 1.0), cells=None) -> Load:
+    """Neutral two-species load: species 0 has charge -1 and mass masses[0],
+    species 1 has charge +1 and mass masses[1].
+
+    ``cells`` optionally restricts the load to a subset of linear cell indices
+    (x fastest); the draws for a cell do not depend on which other cells are
+    loaded, so a subset equals the corresponding part of the full load.
+    """
+    nx, ny, nz = n
+    ncell = nx * ny * nz
+    cells = np.arange(ncell, dtype=np.int64) if cells is None else np.asarray(cells, dtype=np.int64)
+    parts = {0: [], 1: []}
+    for ip, pop in enumerate(populations):
+        # one independent stream per (population, cell block) keeps subsets reproducible
+        block = 4096
+        for b0 in range(0, ncell, block):
+            sel = cells[(cells >= b0) & (cells < b0 + block)]
+            if sel.size == 0:
+                continue
+            rng = np.random.Generator(np.random.PCG64([seed, ip, b0 // block]))
+            # draw the whole block so that the stream position of a cell is fixed
+            nb = min(block, ncell - b0)
+            c = np.arange(b0, b0 + nb, dtype=np.int64).repeat(pop.ppc)
+            ri = rng.random((3, c.size))
+            u0 = _draw_u(rng, c.size, pop)
+            u1 = _draw_u(rng, c.size, pop)
+            keep = np.isin(c, sel)
+            c = c[keep]
+            ix = c % nx
+            iy = (c // nx) % ny
+            iz = c // (nx * ny)
+            x = (ix + ri[0][keep]) * d[0]
+            y = (iy + ri[1][keep]) * d[1]
+            z = (iz + ri[2][keep]) * d[2]
+            for sp, u in ((0, u0), (1, u1)):
+                parts[sp].append((x, y, z, u[0][keep], u[1][keep], u[2][keep], pop))
+    species = []
+    for sp, q in ((0, -1.0), (1, 1.0)):
+        chunks = parts[sp]
+        if chunks:
+            cols = [np.concatenate([ch[k] for ch in chunks]) for k in range(6)]
+        else:
+            cols = [np.zeros(0) for _ in range(6)]
+        # weight: number density per macro-particle of the population it came from
+        w = populations[0].density / populations[0].ppc
+        for pop in populations:
+            if abs(pop.density / pop.ppc - w) > 1e-15 * w:
+                raise ValueError("populations of one species must share the macro-particle weight")
+        species.append(dict(q=q, m=float(masses[sp]), w=w, x=cols[0], y=cols[1], z=cols[2],
+                            ux=cols[3], uy=cols[4], uz=cols[5]))
+    return Load(n=tuple(n), d=tuple(float(v) for v in d), dt=float(dt), species=species)
+
+
+# --------------------------------------------------------------------------
+# The paper-style workloads (sizes and distributions of its test problems).
+# --------------------------------------------------------------------------
+
+def two_stream(n=(16, 16, 16), seed=1211, ppc=8, beta=0.2, u_th=0.05) -> Load:
+    """Counter-streaming neutral pair beams along x (+/-beta), TSC / 6th order,
+    dx = 0.5, dt = 0.25; ppc macro-particles per cell per species split evenly
+    between the two beams (16^3 cells, 65,536 particles at the defaults)."""
+    half = ppc // 2
+    pops = [Population(half, 0.5, +beta, u_th), Population(half, 0.5, -beta, u_th)]
+    L = pair_plasma(n, (0.5, 0.5, 0.5), 0.25, pops, seed)
+    L.params = dict(workload="two-stream", shape_order=2, field_order=6, alpha=0.55, beta=beta, u_th=u_th)
+    return L
+
+
+def thermal(n=(128, 128, 128), seed=1212, ppc=32, u_th=0.1, dx=0.1, dt=0.05, cells=None) -> Load:
+    """Drift-free isotropic pair plasma for the numerical-heating test: PCS /
+    6th order, dx = 0.1, dt = 0.05 (128^3 cells x 32 per cell per species =
+    134,217,728 particles at the defaults)."""
+    pops = [Population(ppc, 1.0, 0.0, u_th)]
+    L = pair_plasma(n, (dx, dx, dx), dt, pops, seed, cells=cells)
+    L.params = dict(workload="thermal", shape_order=3, field_order=6, alpha=0.55, u_th=u_th, sort_interval=20)
+    return L
+
+
+def weibel(n=(128, 128, 128), seed=1213, ppc=32, beta=0.5, u_th=0.1, dx=0.1, dt=0.05, cells=None) -> Load:
+    """Counter-streaming pair beams (+/-beta along x, half of the macro-particles
+    in each) for the filamentation variant."""
+    half = ppc // 2
+    pops = [Population(half, 0.5, +beta, u_th), Population(half, 0.5, -beta, u_th)]
+    L = pair_plasma(n, (dx, dx, dx), dt, pops, seed, cells=cells)
+    L.params = dict(workload="weibel", shape_order=3, field_order=6, alpha=0.55, beta=beta, u_th=u_th,
+                    sort_interval=20)
+    return L
+
+
+def beam_background(n=(256, 128, 128), seed=1214, ppc=16, gamma_b=10.0, u_th_bg=0.01, mass_ratio=25.0,
+                    cells=None) -> Load:
+    """Electron-ion plasma (m_i/m_e = 25): a cold Gamma = 10 beam along +x through
+    a background at rest with u_th = 0.01; each population has ppc macro-particles
+    per cell per species and half of the electron density."""
+    beta = math.sqrt(1.0 - 1.0 / (gamma_b * gamma_b))
+    pops = [Population(ppc, 0.5, 0.0, u_th_bg), Population(ppc, 0.5, beta, 0.0, boost=True)]
+    L = pair_plasma(n, (0.5, 0.5, 0.5), 0.25, pops, seed, masses=(1.0, mass_ratio), cells=cells)
+    L.params = dict(workload="beam-background", shape_order=3, field_order=6, alpha=0.55, gamma_b=gamma_b)
+    return L
+
+
+def single_particle(n, d, dt, x, u, q=-1.0, m=1.0, w=1.0) -> Load:
+    """One macro-particle (used by the deposit pins and the edge cases)."""
+    arr = lambda v: np.array([float(v)])
+    sp = dict(q=q, m=m, w=w, x=arr(x[0]), y=arr(x[1]), z=arr(x[2]), ux=arr(u[0]), uy=arr(u[1]), uz=arr(u[2]))
+    return Load(n=tuple(n), d=tuple(d), dt=dt, species=[sp])
+
+
+def random_particles(n, d, dt, count, seed, u_scale=0.3, q=-1.0, m=1.0, w=0.05) -> Load:
+    """Particles at uniform random positions with Gaussian proper velocities
+    (a generic, non-neutral load for ragged and edge-case parity tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = [n[a] * d[a] for a in range(3)]
+    sp = dict(q=q, m=m, w=w,
+              x=rng.random(count) * L[0], y=rng.random(count) * L[1], z=rng.random(count) * L[2],
+              ux=rng.standard_normal(count) * u_scale, uy=rng.standard_normal(count) * u_scale,
+              uz=rng.standard_normal(count) * u_scale)
+    for k in ("x", "y", "z"):
+        a = "xyz".index(k)
+        sp[k] = np.minimum(sp[k], np.nextafter(L[a], 0.0))
+    return Load(n=tuple(n), d=tuple(d), dt=dt, species=[sp])
+
+
+def random_fields(n, seed, amp=0.05):
+    """Random E and B, each component a sum of three random low Fourier modes
+    plus 10% white noise, shape (nz, ny, nx).  B is not divergence-free;
+    callers that need div B = 0 build B from a curl themselves."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny, nz = n
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    out = []
+    for _ in range(6):
+        f = np.zeros((nz, ny, nx))
+        for _m in range(3):
+            k = rng.integers(0, 3, size=3)
+            ph = rng.random() * 2 * np.pi
+            f += rng.standard_normal() * np.cos(2 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz) + ph)
+        f += 0.1 * rng.standard_normal((nz, ny, nx))
+        out.append(amp * f)
+    return out[:3], out[3:]
+
+
+def quiet_two_stream(nx=32, ntr=2, dx=0.25, dt=0.125, ppc=8, beta=0.2, mode=2, eps=1e-6) -> Load:
+    """Noise-free (quiet-start) cold two-stream load: four co-located populations
+    (electrons and positrons of a +beta and a -beta beam along x, density 1/2
+    each) on a regular lattice, ppc per cell along x and one per cell in y and z,
+    with a seeded velocity perturbation eps*sin(k x) on the +beta electrons,
+    k = 2*pi*mode/(nx*dx).  Transverse uniformity makes the problem
+    one-dimensional; the charge density starts exactly at zero."""
+    Lx = nx * dx
+    G = 1.0 / math.sqrt(1.0 - beta * beta)
+    i = np.arange(nx).repeat(ppc)
+    s = np.tile(np.arange(ppc), nx)
+    x1 = (i + (s + 0.5) / ppc) * dx
+    xs, ys, zs = [], [], []
+    for k in range(ntr):
+        for j in range(ntr):
+            xs.append(x1)
+            ys.append(np.full(x1.size, (j + 0.5) * dx))
+            zs.append(np.full(x1.size, (k + 0.5) * dx))
+    x = np.concatenate(xs); y = np.concatenate(ys); z = np.concatenate(zs)
+    kx = 2.0 * np.pi * mode / Lx
+    pert = eps * np.sin(kx * x)
+    zero = np.zeros_like(x)
+    w = 0.5 / ppc
+    species = []
+    for q in (-1.0, 1.0):
+        for sgn in (+1.0, -1.0):
+            ux = sgn * G * beta + (pert if (q < 0 and sgn > 0) else 0.0)
+            species.append(dict(q=q, m=1.0, w=w, x=x.copy(), y=y.copy(), z=z.copy(),
+                                ux=np.asarray(ux, dtype=np.float64) + zero, uy=zero.copy(), uz=zero.copy()))
+    L = Load(n=(nx, ntr, ntr), d=(dx, dx, dx), dt=dt, species=species)
+    L.params = dict(workload="quiet-two-stream", beta=beta, mode=mode, k=kx)
+    return L

@@ -1,0 +1,468 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms, exact invariants, brute force on tiny inputs, or an
+independent (spectral) solution of the defining equations.  A plausible slip in
+the oracle (a dropped term, a wrong sign, index or staggering, a transposed
+operand, the printed 6th-order coefficient) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from tests import theory
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append([float(v) for v in line.split()])
+    return rows
+
+
+# --------------------------------------------------------------------------
+# Weight functions (Sec. II)
+# --------------------------------------------------------------------------
+
+def test_weight_golden_values(orc):
+    for order, delta, w in _golden("weights.txt"):
+        assert orc.weight(int(order), delta) == pytest.approx(w, abs=1e-15), (order, delta)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_weight_partition_of_unity_and_linear_reproduction(orc, order):
+    rng = np.random.default_rng(5)
+    for xi in rng.random(200) * 10.0 + 3.0:
+        nodes = np.arange(int(xi) - 4, int(xi) + 6)
+        w = np.array([orc.weight(order, i - xi) for i in nodes])
+        assert w.min() >= 0.0
+        if order == 0 and abs((xi % 1.0) - 0.5) < 1e-12:
+            continue
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+        if order >= 1:
+            assert (nodes * w).sum() == pytest.approx(xi, abs=1e-12)
+        assert np.count_nonzero(w) <= order + 1
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_weight_continuity_symmetry_and_unit_integral(orc, order):
+    half = (order + 1) / 2.0
+    breaks = np.arange(-half, half + 1e-9, 1.0)
+    for b in breaks:
+        lo, hi = orc.weight(order, b - 1e-9), orc.weight(order, b + 1e-9)
+        assert lo == pytest.approx(hi, abs=1e-8)
+    xs = np.linspace(-3, 3, 60001)
+    w = np.array([orc.weight(order, x) for x in xs])
+    assert np.allclose(w, w[::-1], atol=1e-15)
+    assert np.trapezoid(w, xs) == pytest.approx(1.0, abs=1e-7)
+
+
+# --------------------------------------------------------------------------
+# Staggered difference operators (Sec. III)
+# --------------------------------------------------------------------------
+
+def test_fd_coefficients_printed_and_taylor(orc):
+    for order, a, b, c in _golden("fd_coeffs.txt"):
+        k = orc.fd_coeffs(int(order))
+        assert np.allclose(k, [a, b, c], atol=1e-16)
+        assert k[0] + 3 * k[1] + 5 * k[2] == pytest.approx(1.0, abs=1e-15)
+        if order >= 4:
+            assert k[0] + 27 * k[1] + 125 * k[2] == pytest.approx(0.0, abs=1e-14)
+        if order >= 6:
+            assert k[0] + 243 * k[1] + 3125 * k[2] == pytest.approx(0.0, abs=1e-13)
+    # the printed 25/21 violates the first condition
+    assert 25 / 21 + 3 * (-25 / 384) + 5 * (3 / 640) == pytest.approx(1.0186, abs=1e-4)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_fd_convergence_order(orc, order, axis):
+    """d^+ and d^- of sin(2 pi x / L) converge at the stated order, on the
+    staggered positions (a half-cell offset error would show as 1st order)."""
+    errs = {+1: [], -1: []}
+    for n in (16, 32):
+        shape = [4, 4, 4]
+        shape[axis] = n
+        d = [0.3, 0.3, 0.3]
+        d[axis] = 1.0 / n
+        g = orc.make_grid(shape, d, 0.1)
+        x = np.arange(n) * d[axis]
+        for direction in (+1, -1):
+            xin = x if direction > 0 else x + 0.5 * d[axis]     # sample positions of the input
+            xout = x + 0.5 * d[axis] if direction > 0 else x    # positions of the result
+            f1 = np.sin(2 * np.pi * xin)
+            exp1 = 2 * np.pi * np.cos(2 * np.pi * xout)
+            sh = [1, 1, 1]
+            sh[2 - axis] = n
+            f = np.broadcast_to(f1.reshape(sh), (shape[2], shape[1], shape[0])).copy()
+            out = orc.diff(g, f, axis, direction, order)
+            e = np.abs(out - np.broadcast_to(exp1.reshape(sh), out.shape)).max()
+            errs[direction].append(e)
+    for direction in (+1, -1):
+        rate = math.log2(errs[direction][0] / errs[direction][1])
+        assert rate == pytest.approx(order, abs=0.15), (direction, errs[direction])
+
+
+def test_div_of_curl_vanishes(orc):
+    g = orc.make_grid((6, 5, 4), (0.5, 0.4, 0.3), 0.1)
+    rng = np.random.default_rng(1)
+    F = [rng.standard_normal((4, 5, 6)) for _ in range(3)]
+
+    def curl(F, direction):
+        out = []
+        for a in range(3):
+            b, c = (a + 1) % 3, (a + 2) % 3
+            out.append(orc.diff(g, F[c], b, direction) - orc.diff(g, F[b], c, direction))
+        return out
+
+    assert np.abs(orc.div_plus(g, curl(F, +1))).max() < 1e-12
+    assert np.abs(orc.div_minus(g, curl(F, -1))).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Gather (eq:pfields)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_gather_uniform_and_linear_fields(orc, shape):
+    n = (12, 12, 12)
+    d = (0.5, 0.4, 0.3)
+    g = orc.make_grid(n, d, 0.1, shape_order=shape)
+    z, y, x = np.meshgrid(np.arange(12.0), np.arange(12.0), np.arange(12.0), indexing="ij")
+    idx = (x, y, z)
+    # E_a linear in its own coordinate, sampled at its staggered node (i+1/2);
+    # B_a linear in the next coordinate, sampled at half-integer positions there.
+    E = [(idx[a] + 0.5) * d[a] for a in range(3)]
+    B = [(idx[(a + 1) % 3] + 0.5) * d[(a + 1) % 3] for a in range(3)]
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        xp = (4.0 + 3.0 * rng.random(3)) * np.array(d)   # away from the periodic seam
+        Ep, Bp = orc.gather(g, E, B, xp)
+        for a in range(3):
+            assert Ep[a] == pytest.approx(xp[a], abs=1e-12)
+            assert Bp[a] == pytest.approx(xp[(a + 1) % 3], abs=1e-12)
+        Ec = [np.full((12, 12, 12), v) for v in (1.5, -2.0, 0.25)]
+        Ep, Bp = orc.gather(g, Ec, Ec, xp)
+        assert np.allclose(Ep, [1.5, -2.0, 0.25], atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Pushers (Sec. III "Particle motion")
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_pure_B_gyration_closes(orc, pusher):
+    u0 = np.array([0.8, 0.0, 0.3])
+    g0 = math.sqrt(1 + u0 @ u0)
+    dt, q, m = 0.2, -1.0, 1.0
+    Bz = 2 * m * g0 * math.tan(math.pi / 64) / (abs(q) * dt)   # rotation 2*pi/64 per step
+    u = u0.copy()
+    for _ in range(64):
+        u = orc.push(q * dt / m, [0, 0, 0], [0, 0, Bz], u, pusher)
+        assert math.sqrt(u @ u) == pytest.approx(math.sqrt(u0 @ u0), rel=1e-14)
+    assert np.allclose(u, u0, atol=1e-13)
+    # a quarter orbit turns u_perp by 90 degrees about -z for an electron in +B_z
+    u = u0.copy()
+    for _ in range(16):
+        u = orc.push(q * dt / m, [0, 0, 0], [0, 0, Bz], u, pusher)
+    assert np.allclose(u, [0.0, 0.8, 0.3], atol=1e-13)
+
+
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_pure_E_kick(orc, pusher):
+    u = np.array([0.1, -0.2, 0.05])
+    E = np.array([0.3, 0.7, -0.4])
+    qmdt = -0.25
+    for _ in range(10):
+        u_new = orc.push(qmdt, E, [0, 0, 0], u, pusher)
+        assert np.allclose(u_new - u, qmdt * E, atol=1e-15)
+        u = u_new
+
+
+def test_ExB_drift_vay_exact_boris_not(orc):
+    E = np.array([0.0, 0.6, 0.0])
+    B = np.array([0.0, 0.0, 1.0])
+    vD = np.cross(E, B) / (B @ B)
+    gD = 1 / math.sqrt(1 - vD @ vD)
+    u0 = gD * vD
+    u_v, u_b = u0.copy(), u0.copy()
+    for _ in range(50):
+        u_v = orc.push(-0.1, E, B, u_v, 0)
+        u_b = orc.push(-0.1, E, B, u_b, 1)
+    assert np.abs(u_v - u0).max() < 1e-13        # Vay: force-free drift is a fixed point
+    assert np.abs(u_b - u0).max() > 1e-4         # Boris: known spurious force
+
+
+# --------------------------------------------------------------------------
+# Charge-conserving deposit and high-order current (eq:cc1 .. eq:penta)
+# --------------------------------------------------------------------------
+
+def _one_particle(orc, shape, forder, x0, u, n=(8, 8, 8), d=(0.5, 0.4, 0.3), dt=0.1, q=-1.0, w=0.7):
+    sim = orc.Simulation(n, d, dt, field_order=forder, shape_order=shape)
+    sim.add_species(q, 1.0, w, [x0[0]], [x0[1]], [x0[2]], [u[0]], [u[1]], [u[2]])
+    rho0 = sim.rho()
+    sim.deposit()
+    rho1 = sim.rho()
+    sp = sim.species[0]
+    x1 = np.array([sp["x"][0], sp["y"][0], sp["z"][0]])
+    return sim, rho0, rho1, x1
+
+
+CASES = [((1.3, 1.7, 0.9), (0.4, -0.3, 0.2)),
+         ((3.99, 0.01, 2.2), (2.0, -2.5, 0.0)),      # crosses cell faces on two axes
+         ((0.05, 3.15, 0.02), (-1.5, 1.2, -3.0))]     # crosses the periodic seam
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("forder", [2, 4, 6])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_single_particle_continuity(orc, shape, forder, case):
+    x0, u = CASES[case]
+    sim, rho0, rho1, x1 = _one_particle(orc, shape, forder, x0, u)
+    dt = sim.g.dt
+    drho = (rho1 - rho0) / dt
+    res = drho + orc.div_minus(sim.g, sim.J)
+    assert np.abs(res).max() <= 1e-13 * np.abs(drho).max()
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("forder", [2, 4, 6])
+def test_single_particle_total_current(orc, shape, forder):
+    """Sum over cells of J_a equals q w (x1_a - x0_a)/dt (B-spline linear
+    reproduction), independent of the field order (the solve keeps the mean)."""
+    n, d, dt, q, w = (8, 8, 8), (0.5, 0.4, 0.3), 0.1, -1.0, 0.7
+    for x0, u in CASES:
+        sim, _, _, x1 = _one_particle(orc, shape, forder, x0, u, n, d, dt, q, w)
+        gam = math.sqrt(1 + np.dot(u, u))
+        # the particle's unwrapped displacement is dt * v
+        for a in range(3):
+            disp = dt * u[a] / gam
+            assert sim.J[a].sum() == pytest.approx(q * w * disp / dt, rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_motion_along_x_only_and_at_rest(orc, shape):
+    sim, _, _, _ = _one_particle(orc, shape, 6, (1.3, 1.7, 0.9), (0.9, 0.0, 0.0))
+    assert np.abs(sim.J[1]).max() == 0.0 and np.abs(sim.J[2]).max() == 0.0
+    assert np.abs(sim.J[0]).max() > 0.0
+    sim, _, _, _ = _one_particle(orc, shape, 6, (1.3, 1.7, 0.9), (0.0, 0.0, 0.0))
+    assert max(np.abs(sim.J[a]).max() for a in range(3)) == 0.0
+
+
+def test_cic_textbook_current(orc):
+    """CIC moving along x inside one cell, 2nd-order fields: the only current is
+    J_x on the face the particle sits on, q w v_x times the fixed transverse
+    CIC weights (the classic area-weighting result)."""
+    d, dt, q, w = (0.5, 0.4, 0.3), 0.1, -1.0, 0.7
+    x0 = (1.1, 1.7, 0.9)
+    u = (0.5, 0.0, 0.0)
+    sim, _, _, x1 = _one_particle(orc, 1, 2, x0, u, d=d, dt=dt, q=q, w=w)
+    vx = u[0] / math.sqrt(1 + u[0] ** 2)
+    assert int(x1[0] / d[0]) == int(x0[0] / d[0])
+    eta, zeta = x0[1] / d[1], x0[2] / d[2]
+    j0, k0 = int(eta), int(zeta)
+    expect = np.zeros((8, 8, 8))
+    for j, wy in ((j0, 1 - (eta - j0)), (j0 + 1, eta - j0)):
+        for k, wz in ((k0, 1 - (zeta - k0)), (k0 + 1, zeta - k0)):
+            expect[k, j, int(x0[0] / d[0])] = q * w * vx * wy * wz
+    assert np.allclose(sim.J[0], expect, atol=1e-14)
+
+
+@pytest.mark.parametrize("forder", [4, 6])
+def test_high_order_current_brute_force(orc, forder):
+    """J of order 4/6 for one particle equals the dense least-squares solution
+    of  d^-_{order} J = d^-_2 J_2  (both equal -D rho) with the line mean of the
+    2nd-order current J_2 (reading R4); the dense operator is assembled by
+    applying the oracle's own difference to unit vectors, independently of the
+    banded solve and prefix sum being checked."""
+    x0, u = CASES[1]
+    n = (8, 8, 8)
+    sim2, _, _, _ = _one_particle(orc, 3, 2, x0, u, n)
+    simh, _, _, _ = _one_particle(orc, 3, forder, x0, u, n)
+    g = simh.g
+    N = n[0]
+    D = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros((1, 1, N))
+        e[0, 0, i] = 1.0
+        gg = orc.make_grid((N, 1, 1), (g.d[0], 1, 1), g.dt, field_order=forder)
+        D[:, i] = orc.diff(gg, e, 0, -1, forder)[0, 0]
+    D2 = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros((1, 1, N))
+        e[0, 0, i] = 1.0
+        gg = orc.make_grid((N, 1, 1), (g.d[0], 1, 1), g.dt, field_order=2)
+        D2[:, i] = orc.diff(gg, e, 0, -1, 2)[0, 0]
+    for k in range(n[2]):
+        for j in range(n[1]):
+            J2 = sim2.J[0][k, j]
+            rhs = D2 @ J2
+            A = np.vstack([D, np.ones((1, N))])
+            b = np.concatenate([rhs, [J2.sum()]])
+            sol, *_ = np.linalg.lstsq(A, b, rcond=None)
+            assert np.allclose(simh.J[0][k, j], sol, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Implicit field update (eq:bnplus1, eq:enplus1, eq:EllipticB)
+# --------------------------------------------------------------------------
+
+def _symbols(g, order):
+    """Fourier symbols of d^+ and d^- per axis for arrays of shape (nz, ny, nx)."""
+    k3 = np.array(order)
+    kc = {6: (75 / 64, -25 / 384, 3 / 640), 4: (9 / 8, -1 / 24, 0.0), 2: (1.0, 0.0, 0.0)}[order]
+    Dp, Dm = [], []
+    for a in range(3):
+        n, h = g.n[a], g.d[a]
+        k = 2 * np.pi * np.fft.fftfreq(n, d=h)
+        K = (2 / h) * sum(kc[m] * np.sin((2 * m + 1) * k * h / 2) for m in range(3))
+        sh = [1, 1, 1]
+        sh[2 - a] = n
+        Dp.append((1j * K * np.exp(+0.5j * k * h)).reshape(sh))
+        Dm.append((1j * K * np.exp(-0.5j * k * h)).reshape(sh))
+    del k3
+    return Dp, Dm
+
+
+def _curl_matrix(D):
+    Z = np.zeros(np.broadcast(D[0], D[1], D[2]).shape, dtype=complex)
+    Dx, Dy, Dz = [np.broadcast_to(v, Z.shape) for v in D]
+    return np.array([[Z, -Dz, Dy], [Dz, Z, -Dx], [-Dy, Dx, Z]])
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_field_update_equals_direct_solve_of_defining_equations(orc, order):
+    """The oracle's relaxed elliptic form equals a per-Fourier-mode direct solve
+    of the two defining equations eq:bnplus1 / eq:enplus1 (6x6 complex system),
+    which pins the derivation of eq:EllipticB, including the sign of its
+    current term (reading R3)."""
+    n, d, dt, alpha = (6, 5, 4), (0.5, 0.4, 0.3), 0.12, 0.6
+    g = orc.make_grid(n, d, dt, field_order=order, alpha=alpha, relax_tol=1e-15, relax_max_iter=500)
+    rng = np.random.default_rng(11)
+    shp = (n[2], n[1], n[0])
+    E = [rng.standard_normal(shp) for _ in range(3)]
+    J = [rng.standard_normal(shp) for _ in range(3)]
+    A = [rng.standard_normal(shp) for _ in range(3)]
+    B = [orc.diff(g, A[(a + 2) % 3], (a + 1) % 3, +1) - orc.diff(g, A[(a + 1) % 3], (a + 2) % 3, +1)
+         for a in range(3)]                         # B = curl^+ A, divergence-free
+    E0 = [e.copy() for e in E]
+    B0 = [b.copy() for b in B]
+    orc.field_update(g, E, B, J)
+
+    Dp, Dm = _symbols(g, order)
+    Cp, Cm = _curl_matrix(Dp), _curl_matrix(Dm)
+    f = lambda L: np.array([np.fft.fftn(v) for v in L])
+    Eh, Bh, Jh = f(E0), f(B0), f(J)
+    beta = 1 - alpha
+    I3 = np.eye(3)[:, :, None, None, None] * np.ones(shp)
+    # unknowns [B1; E1]:  B1 + a dt C+ E1 = B0 - b dt C+ E0 ;  -a dt C- B1 + E1 = E0 + b dt C- B0 - dt J
+    M = np.zeros((6, 6) + shp, dtype=complex)
+    M[:3, :3] = I3
+    M[:3, 3:] = alpha * dt * Cp
+    M[3:, :3] = -alpha * dt * Cm
+    M[3:, 3:] = I3
+    rhsB = Bh - beta * dt * np.einsum("ij...,j...->i...", Cp, Eh)
+    rhsE = Eh + beta * dt * np.einsum("ij...,j...->i...", Cm, Bh) - dt * Jh
+    rhs = np.concatenate([rhsB, rhsE])
+    Mt = np.moveaxis(M, (0, 1), (-2, -1))
+    sol = np.linalg.solve(Mt, np.moveaxis(rhs, 0, -1)[..., None])[..., 0]
+    sol = np.moveaxis(sol, -1, 0)
+    B1 = [np.fft.ifftn(sol[a]).real for a in range(3)]
+    E1 = [np.fft.ifftn(sol[3 + a]).real for a in range(3)]
+    scale = max(np.abs(v).max() for v in B1 + E1)
+    for a in range(3):
+        assert np.abs(B[a] - B1[a]).max() < 1e-12 * scale
+        assert np.abs(E[a] - E1[a]).max() < 1e-12 * scale
+    assert np.abs(orc.div_plus(g, B)).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+@pytest.mark.parametrize("mode", [1, 3, 6])
+def test_vacuum_mode_damping_closed_form(orc, order, mode):
+    """A vacuum plane wave loses energy per step by the closed-form factor of
+    the theta-scheme, |G|^2 = (1 + beta^2 s^2)/(1 + alpha^2 s^2), s = dt K(k)."""
+    nx, dx, dt, alpha = 16, 0.5, 0.25, 0.55
+    g = orc.make_grid((nx, 2, 2), (dx, dx, dx), dt, field_order=order, alpha=alpha, relax_tol=1e-15,
+                      relax_max_iter=500)
+    k = 2 * np.pi * mode / (nx * dx)
+    kc = orc.fd_coeffs(order)
+    K = (2 / dx) * (kc[0] * np.sin(k * dx / 2) + kc[1] * np.sin(3 * k * dx / 2) + kc[2] * np.sin(5 * k * dx / 2))
+    s = dt * K
+    ratio = (1 + (1 - alpha) ** 2 * s * s) / (1 + alpha ** 2 * s * s)
+    x = np.arange(nx) * dx
+    E = [np.zeros((2, 2, nx)) for _ in range(3)]
+    B = [np.zeros((2, 2, nx)) for _ in range(3)]
+    J = [np.zeros((2, 2, nx)) for _ in range(3)]
+    E[1][...] = np.cos(k * x)
+    B[2][...] = 0.3 * np.sin(k * (x + dx / 2))
+    W0 = sum((v ** 2).sum() for v in E + B)
+    for _ in range(3):
+        orc.field_update(g, E, B, J)
+        W1 = sum((v ** 2).sum() for v in E + B)
+        assert W1 / W0 == pytest.approx(ratio, rel=1e-12)
+        W0 = W1
+
+
+# --------------------------------------------------------------------------
+# Whole-step invariants and physics
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,forder", [(2, 6), (3, 6), (3, 4), (1, 2)])
+def test_gauss_and_divB_invariants_over_steps(orc, shape, forder):
+    import pp_synth
+    L = pp_synth.thermal(n=(8, 6, 5), ppc=2, u_th=0.3, dx=0.5, dt=0.25, seed=7)
+    sim = orc.Simulation(L.n, L.d, L.dt, field_order=forder, shape_order=shape, relax_tol=1e-14)
+    for s in L.species:
+        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    d0 = sim.diagnostics()
+    assert d0["gauss_max"] < 1e-14 and abs(d0["charge"]) < 1e-14
+    for _ in range(6):
+        sim.step(1)
+        d = sim.diagnostics()
+        assert d["gauss_max"] < 1e-12 * max(d["rho_max"], 1e-300)
+        assert d["divB_max"] < 1e-12
+        assert abs(d["charge"]) < 1e-13
+        assert d["relax_residual"] <= 1e-14
+
+
+@pytest.mark.parametrize("mode,shape", [(2, 2), (3, 3)])
+def test_quiet_two_stream_growth_matches_cold_theory(orc, mode, shape):
+    """Quiet-start cold pair two-stream: the energy in E_x grows at twice the
+    closed-form cold growth rate (relativistic longitudinal mass Gamma^3)."""
+    import pp_synth
+    L = pp_synth.quiet_two_stream(nx=32, dx=0.25, dt=0.125, mode=mode)
+    sim = orc.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=shape, relax_tol=1e-13)
+    for s in L.species:
+        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    nst = 240
+    W = []
+    for _ in range(nst):
+        sim.step(1)
+        W.append(sim.diagnostics()["energy_Ex"])
+    t = np.arange(1, nst + 1) * L.dt
+    rate, npts = theory.fit_growth(t, W)
+    expect = theory.cold_two_stream(L.params["k"], L.params["beta"])
+    assert npts >= 40
+    assert rate == pytest.approx(expect, rel=0.03)
+
+
+def test_bret_growth_formulas_reproduce_printed_values():
+    (mmi, fi, tsi), = _golden("bret_growth.txt")
+    assert theory.bret_mmi(0.1, 4.0) == pytest.approx(mmi, abs=6e-4)
+    assert theory.bret_fi(0.1, 4.0) == pytest.approx(fi, abs=6e-4)
+    assert theory.bret_tsi(0.1, 4.0) == pytest.approx(tsi, abs=6e-4)
+    # the other reading of alpha misses the printed MMI value in the third digit
+    assert abs(theory.bret_mmi(0.1 / 0.9, 4.0) - mmi) > 5e-3
+
+
+def test_cold_two_stream_closed_form_values():
+    beta = 0.2
+    ks = [2 * np.pi * m / 8.0 for m in (4, 5, 6)]
+    got = [theory.cold_two_stream(k, beta) for k in ks]
+    assert np.allclose(got, [0.452, 0.483, 0.477], atol=1.5e-3)
