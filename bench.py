@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Photon-Plasma particle step.
+
+One "step" is one full leap-frog step of the library (pp_step): per species the
+fused gather -> push -> move -> charge-conserving deposit kernel, ghost fold,
+6th-order current solve, implicit field update, and the cell sort every 20
+steps.  Workload (default): the numerical-heating plasma of the paper's
+Sec. VIII scaled to 3D, 128^3 cells, 32 macro-particles per cell per species
+(134,217,728 particles), PCS shapes, 6th-order fields, mixed precision (int32
+cell + FP32 offset).  Inputs are seeded synthetic loads (pp_synth).
+
+Prints one JSON line (rank 0).  Multi-GPU: every rank advances its own
+independent plasma (replicas, weak scaling); no collective on the data path.
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit)"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp32 momenta) read + written
+
+
+def args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["thermal", "weibel"], default="thermal")
+    ap.add_argument("--n", type=int, default=128, help="cells per axis")
+    ap.add_argument("--ppc", type=int, default=32, help="macro-particles per cell per species")
+    ap.add_argument("--deposit", choices=["auto", "global", "tiled"], default="auto")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sample-n", type=int, default=16, help="cells per axis of the oracle sample")
+    return ap.parse_args()
+
+
+def workload_load(a, seed_offset=0):
+    import pp_synth
+    n = (a.n, a.n, a.n)
+    if a.workload == "thermal":
+        return pp_synth.thermal(n=n, ppc=a.ppc, seed=1212 + seed_offset)
+    return pp_synth.weibel(n=n, ppc=a.ppc, seed=1213 + seed_offset)
+
+
+def workload_name(a, nparticles):
+    kind = "thermal pair plasma u_th=0.1c (numerical heating)" if a.workload == "thermal" else \
+        "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
+    return (f"{kind}, {a.n}^3 cells, dx=0.1, dt=0.05, {a.ppc} per cell per species ({nparticles} particles), "
+            f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset")
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(k)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(a, steps, warmup=0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    same physics and per-cell loading on a sample_n^3 periodic box."""
+    import oracle
+    import pp_synth
+    n = (a.sample_n,) * 3
+    L = (pp_synth.thermal(n=n, ppc=a.ppc, seed=1212) if a.workload == "thermal"
+         else pp_synth.weibel(n=n, ppc=a.ppc, seed=1213))
+    oracle.build()
+    sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
+                            relax_max_iter=200)
+    for s in L.species:
+        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    if warmup:
+        sim.step(warmup)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sample = (f"{a.sample_n}^3 cells x {a.ppc} per cell per species = {L.n_particles} particles, "
+              f"{steps} steps, same per-cell load and parameters as the workload, single-threaded C")
+    return L.n_particles * steps / dt, sample, dt
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = max(1, a.steps)
+    rate, sample, dt = oracle_rate(a, steps, warmup=a.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a, (a.n ** 3) * a.ppc * 2), "oracle_sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(a):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1211_4575_gb300 import build
+    build.build()
+    import paper_1211_4575_gb300 as pp
+
+    L = workload_load(a, seed_offset=rank)
+    npart = L.n_particles
+    mode = {"auto": pp.PP_DEPOSIT_AUTO, "global": pp.PP_DEPOSIT_GLOBAL, "tiled": pp.PP_DEPOSIT_TILED}[a.deposit]
+    stream = torch.cuda.current_stream()
+
+    def make():
+        return pp.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, pusher=pp.PP_VAY,
+                             precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=100, relax_tol=1e-6,
+                             deposit_mode=mode, stream=stream.cuda_stream)
+
+    sim = make()
+    for s in L.species:
+        sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+        sim.load_particles(sid, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    for _ in range(a.warmup):
+        sim.step(1)
+    sim.sync()
+
+    # ---- device-resident timed region ----
+    sim.profile_enable(True)
+    torch.cuda.synchronize()
+    barrier()
+    gpu_id = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+    clocks = Clocks(f"GPU-{gpu_id}" if gpu_id is not None else local) if rank == 0 else None
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        sim.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = sim.profile_read()
+    sim.profile_enable(False)
+    sim.sync()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_particles = npart * world
+    value = total_particles * a.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused particle kernel)
+    peak, peak_kind = measured_peak()
+    part_ms = prof["particle_ms"]
+    achieved = BYTES_PER_PARTICLE_STEP * npart * a.steps / (part_ms * 1e-3) / 1e9 if part_ms > 0 else 0.0
+    diag = sim.diagnostics()
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not a.no_e2e:
+        sim.close()
+        del sim
+        pinned = []
+        for s in L.species:
+            pinned.append({k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float64)).pin_memory()
+                           for k in ("x", "y", "z", "ux", "uy", "uz")})
+        h2d = sum(sum(t.numel() * 8 for t in p.values()) for p in pinned)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        sim2 = make()
+        for s, p in zip(L.species, pinned):
+            sid = sim2.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+            sim2.load_particles(sid, *[p[k].numpy() for k in ("x", "y", "z", "ux", "uy", "uz")])
+        sim2.step(a.steps)
+        d2 = sim2.diagnostics()
+        t1 = time.perf_counter()
+        el = t1 - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": total_particles * a.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": h2d // max(1, a.steps), "d2h_bytes_per_step": 200 // max(1, a.steps),
+               "seconds": el, "status": d2["status"]}
+        sim2.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not a.no_cpu_baseline:
+        rate, sample, _ = oracle_rate(a, steps=5)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a, npart), "grid": [a.n] * 3, "particles_per_gpu": npart,
+                   "precision": "mixed (int32 cell + fp32 offset; fp32 fields and current; fp64 reductions)",
+                   "deposit": a.deposit, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (particle state 28 B x particles, read and written every step)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "fused particle step (gather+push+move+deposit)",
+                     "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_kind": peak_kind,
+                     "kernel_ms_per_step": part_ms / a.steps},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": clk,
+        "phases_ms_per_step": {k: prof[k] / a.steps for k in ("particle_ms", "current_ms", "field_ms", "sort_ms")},
+        "diag": {"status": diag["status"], "gauss_drift_rel": diag["gauss_drift_max"] / max(diag["rho_max"], 1e-300),
+                 "relax_residual": diag["relax_residual"], "relax_iters": diag["relax_iters"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

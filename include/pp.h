@@ -1,0 +1,243 @@
+/*
+ * pp.h -- C ABI of the GB300 (sm_103a) Photon-Plasma particle step.
+ *
+ * Method: Haugboelle, Frederiksen & Nordlund, "Photon-Plasma: a modern
+ * high-order particle-in-cell code" (arXiv:1211.4575).  The library advances a
+ * 3D periodic relativistic Maxwell-Vlasov system (Sec. II, eq:vlasov ..
+ * eq:ampere) with macro-particles of B-spline shape (eq:pseudop,
+ * eq:weightfunction), leap-frog time staggering (Sec. III, step order 1-5),
+ * a Vay or Boris push, a charge-conserving high-order current (Sec. III
+ * "Charge conserving current density", eq:cc1 .. eq:penta) and the implicit
+ * de-centred field update (eq:bnplus1, eq:enplus1, eq:EllipticB).
+ *
+ * Units and normalisation: c = eps0 = mu0 = 1 (the fields c and eps0 of the
+ * grid descriptor must be 1).  Positions are physical, x in [0, nx*dx).
+ * Proper velocity u = gamma*v, staggered half a step back in time.
+ *
+ * Mesh layout seen through the ABI (pp_load_fields, pp_get_fields,
+ * pp_get_rho): FP64 arrays of nx*ny*nz values, x fastest
+ * (a[i + nx*(j + ny*k)]), Yee-staggered as in Sec. III (Fig. "Spatial
+ * staggering"): E_x, J_x at ((i+1/2)dx, j dy, k dz); B_x at
+ * (i dx, (j+1/2)dy, (k+1/2)dz); cyclic for y and z; rho at (i dx, j dy, k dz).
+ *
+ * Conventions common to every entry point:
+ *  - Return value: PP_OK (0) or one of the PP_E* codes below.  No exception or
+ *    abort crosses the ABI.  pp_last_error(ctx) describes the last failure.
+ *  - Ownership: the caller owns every host buffer it passes; the library
+ *    copies in and out and keeps no pointer to them after the call returns.
+ *    Device buffers passed with on_device = 1 are read during the call only.
+ *    The library owns all device state of a context (fields, particles,
+ *    scratch), allocated in pp_init_grid / pp_init_species and freed by
+ *    pp_destroy.
+ *  - Streams: all device work of a context is issued on the stream given in
+ *    pp_grid_desc.stream (a cudaStream_t; NULL = the legacy default stream).
+ *    pp_step, pp_deposit, pp_field_update and pp_sort only enqueue work;
+ *    calls that return data to the host synchronise that stream.
+ *  - Threading: calls on one context are not thread-safe; distinct contexts
+ *    may be used from distinct threads.
+ */
+#ifndef PP_GB300_PP_H
+#define PP_GB300_PP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PP_OK 0
+#define PP_EINVAL 1     /* invalid argument or descriptor                        */
+#define PP_ENOMEM 2     /* device or host allocation failed, or capacity exceeded */
+#define PP_EBUSY 3      /* no free slot (batched form)                           */
+#define PP_ECUDA 4      /* a CUDA runtime call failed                            */
+#define PP_ETIMEOUT 5   /* a bounded device-side wait ran out                    */
+#define PP_ENOCONV 6    /* field relaxation could not reach its tolerance       */
+#define PP_ECFL 7       /* a particle moved a cell or more in one step           */
+#define PP_ENAN 8       /* a non-finite particle value was met                   */
+#define PP_WSTAB 9      /* warning: alpha < 0.525 with 6th order + PCS (Sec. III) */
+
+/* ---- enumerations ---- */
+#define PP_VAY 0
+#define PP_BORIS 1
+#define PP_FP64 0       /* FP64 positions (cell units), momenta, fields, current   */
+#define PP_MIXED32 1    /* int32 cell + FP32 offset, FP32 momenta/fields/current;
+                           FP64 global reductions                                 */
+#define PP_DEPOSIT_AUTO 0
+#define PP_DEPOSIT_GLOBAL 1  /* one thread per particle, L2 atomics                */
+#define PP_DEPOSIT_TILED 2   /* cell tiles staged in shared memory (PP_MIXED32)     */
+
+#define PP_MAX_SPECIES 8
+
+typedef struct pp_ctx pp_ctx;
+
+/* Grid and solver parameters (Sec. III).  Validation (PP_EINVAL): n >= 1 per
+ * axis and <= 1023; d > 0; dt > 0 with c*dt/d < 1 on every axis (a particle
+ * crosses at most one cell face per step); c = eps0 = 1; field_order in
+ * {2,4,6}; 0.5 <= alpha < 1 (eq:bnplus1); shape_order in {1,2,3} (CIC, TSC,
+ * PCS of Sec. II); pusher PP_VAY or PP_BORIS; precision PP_FP64 or
+ * PP_MIXED32.  alpha < 0.525 with field_order 6 and PCS returns PP_WSTAB but
+ * still creates the context (the paper reports instability below 0.525). */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double dt;
+    double c, eps0;
+    int field_order;
+    double alpha;
+    int shape_order;
+    int pusher;
+    int precision;
+    int sort_interval;    /* cell sort every this many steps; 0 = only at load   */
+    int relax_max_iter;   /* cap on relaxation sweeps of eq:EllipticB            */
+    double relax_tol;     /* target relative residual of eq:EllipticB            */
+    int deposit_mode;     /* PP_DEPOSIT_*                                         */
+    void *stream;         /* cudaStream_t                                          */
+} pp_grid_desc;
+
+/* One particle species: charge q, mass m, and w = number density represented
+ * by one macro-particle (eq:pseudop, eq:rho2); capacity = maximum number of
+ * macro-particles the species may hold. */
+typedef struct {
+    double q, m, w;
+    int64_t capacity;
+} pp_species_desc;
+
+/* FP64 global diagnostics (Sec. III eq:gauss, eq:divb, eq:rho2; Sec. VIII
+ * field-energy series).  dV = dx*dy*dz. */
+typedef struct {
+    int64_t step;              /* steps taken since pp_init_grid                 */
+    double time;               /* step * dt                                       */
+    double energy_E;           /* sum 1/2 |E|^2 dV                                */
+    double energy_B;           /* sum 1/2 |B|^2 dV                                */
+    double energy_Ex;          /* sum 1/2 E_x^2 dV                                */
+    double kinetic[PP_MAX_SPECIES]; /* sum over particles w m (gamma - 1) dV     */
+    double kinetic_total;
+    double charge;             /* sum rho dV                                       */
+    double rho_max;            /* max |rho|                                        */
+    double gauss_max;          /* max |div^- E - rho/eps0|                         */
+    double gauss_drift_max;    /* max |G - G_0|, G_0 taken at the first load      */
+    double divB_max;           /* max |div^+ B|                                    */
+    double relax_residual;     /* max|(1 - a^2 dt^2 L)B - rhs| / max|rhs|, last solve */
+    int relax_iters;           /* relaxation sweeps of the last solve             */
+    int status;                /* PP_* code of the device status word             */
+    int64_t n_particles;       /* all species                                      */
+    int64_t n_slow;            /* particles sent to the fallback path, last step   */
+} pp_diag;
+
+/* Per-phase device time of a context, measured with CUDA events recorded on
+ * the context's own stream around every phase while profiling is enabled. */
+typedef struct {
+    double particle_ms;        /* fused gather/push/move/deposit kernels          */
+    int64_t particle_launches;
+    double current_ms;         /* ghost fold + high-order current solve           */
+    double field_ms;           /* implicit field update + ghost fill              */
+    double sort_ms;            /* cell sorts                                       */
+    int64_t steps;             /* steps (or deposit/field halves) recorded         */
+    int64_t kernel_launches;   /* every kernel this context enqueued while enabled */
+} pp_profile;
+
+/* Create a context: validates the descriptor, allocates the padded Yee mesh
+ * (fields zeroed, E = B = J = 0) and binds the stream.  *out receives the
+ * context, or NULL on failure (the error text is then available through
+ * pp_last_error(NULL)). */
+int pp_init_grid(pp_ctx **out, const pp_grid_desc *desc);
+
+/* Add a species (at most PP_MAX_SPECIES); allocates its particle storage for
+ * desc->capacity macro-particles.  *species_id receives its index 0, 1, ... */
+int pp_init_species(pp_ctx *ctx, const pp_species_desc *desc, int *species_id);
+
+/* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
+ * (physical, any real value: wrapped periodically into the box) and proper
+ * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
+ * host memory (on_device = 0) or device memory (on_device = 1).  Errors:
+ * PP_ENOMEM if the count would exceed the capacity, PP_ENAN if a value is
+ * not finite (nothing is appended then).  Loading resets the Gauss reference
+ * G_0 of pp_diagnostics and re-sorts the species by cell. */
+int pp_load_particles(pp_ctx *ctx, int sid, int64_t n, const double *x, const double *y, const double *z,
+                      const double *ux, const double *uy, const double *uz, int on_device);
+
+/* Replace E and B with caller values (initial condition), three FP64 arrays
+ * each in the mesh layout above; on_device as in pp_load_particles.  Resets
+ * the Gauss reference G_0. */
+int pp_load_fields(pp_ctx *ctx, const double *const E[3], const double *const B[3], int on_device);
+
+/* Advance nsteps full leap-frog steps (Sec. III step order 1-5): per step,
+ * [cell sort when due] -> per species gather (eq:pfields) + push (Vay/Boris)
+ * + move + charge-conserving deposit (eq:cc1, eq:jj3) -> ghost fold ->
+ * high-order current solve (eq:jj6 .. eq:penta) -> implicit field update
+ * (eq:EllipticB, eq:enplus1) -> ghost fill.  Asynchronous: the device status
+ * word is examined by the next synchronising call (pp_sync, pp_diagnostics,
+ * pp_get_*). */
+int pp_step(pp_ctx *ctx, int nsteps);
+
+/* The particle half of one step only (Sec. III steps 1-3): gather, push,
+ * move and deposit for species sid (or every species when sid = -1), then
+ * the ghost fold and the high-order current solve, leaving J^{n+1} on the
+ * mesh.  Fields are not advanced and the step counter is not incremented. */
+int pp_deposit(pp_ctx *ctx, int sid);
+
+/* The field half of one step only (Sec. III steps 4-5): eq:EllipticB with the
+ * current J on the mesh, then eq:enplus1, then the periodic ghost fill. */
+int pp_field_update(pp_ctx *ctx);
+
+/* Stable-order-free counting sort of every species by cell (Sec. III, the
+ * per-step sort "according to the cell position"). */
+int pp_sort(pp_ctx *ctx);
+
+/* Synchronise the context's stream and return the device status word as a
+ * PP_* code (PP_ECFL, PP_ENAN, PP_ENOCONV, ...; PP_OK when clean).  Clears it. */
+int pp_sync(pp_ctx *ctx);
+
+/* Global FP64 diagnostics into *out (synchronises). */
+int pp_diagnostics(pp_ctx *ctx, pp_diag *out);
+
+/* FP64 host copies of the fields in the mesh layout; any of E, B, J (each an
+ * array of three host pointers to nx*ny*nz doubles) may be NULL. */
+int pp_get_fields(pp_ctx *ctx, double *const E[3], double *const B[3], double *const J[3]);
+
+/* FP64 host copy of the charge density of eq:rho2 at the integer nodes
+ * (nx*ny*nz doubles). */
+int pp_get_rho(pp_ctx *ctx, double *rho);
+
+/* Copy of the context's grid descriptor into *desc (stream included) and
+ * the number of species into *nspecies (either pointer may be NULL). */
+int pp_get_grid(pp_ctx *ctx, pp_grid_desc *desc, int *nspecies);
+
+/* Number of macro-particles of species sid. */
+int pp_get_count(pp_ctx *ctx, int sid, int64_t *n);
+
+/* FP64 host copies of species sid (positions physical in [0, L), proper
+ * velocities), each array of pp_get_count values, in the library's current
+ * (cell-sorted) order. */
+int pp_get_particles(pp_ctx *ctx, int sid, double *x, double *y, double *z, double *ux, double *uy,
+                     double *uz);
+
+/* Start (enable = 1, totals reset) or stop (enable = 0) recording per-phase
+ * CUDA events.  Recording adds two event records per phase and no
+ * synchronisation. */
+int pp_profile_enable(pp_ctx *ctx, int enable);
+
+/* Totals since the last pp_profile_enable(ctx, 1) (synchronises). */
+int pp_profile_read(pp_ctx *ctx, pp_profile *out);
+
+/* Checkpoint: write the descriptor, species parameters, step counter, FP64
+ * fields and FP64 particle arrays to a file (Sec. IX, each attribute as one
+ * 64-bit block so that a restart does not depend on the precision form). */
+int pp_save(pp_ctx *ctx, const char *path);
+
+/* Restore a checkpoint written by pp_save into a new context on `stream`. */
+int pp_restore(pp_ctx **out, const char *path, void *stream);
+
+/* Free all device and host state of the context (NULL is accepted). */
+int pp_destroy(pp_ctx *ctx);
+
+/* Text of the last error of ctx (or of the last failed pp_init_grid /
+ * pp_restore when ctx is NULL).  Static storage owned by the library. */
+const char *pp_last_error(const pp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_GB300_PP_H */

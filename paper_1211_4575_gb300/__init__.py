@@ -1,0 +1,286 @@
+"""Python binding of the GB300 Photon-Plasma particle step (libpp_gb300.so).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels (``csrc/``), reached through the C ABI of ``include/pp.h``.  The binding
+raises ``RuntimeError`` when the library has not been built; there is no other
+code path.
+
+Arrays: fields are numpy float64 arrays of shape (nz, ny, nx) (x fastest), with
+the Yee staggering of the paper's Sec. III (E_x, J_x at (i+1/2, j, k); B_x at
+(i, j+1/2, k+1/2); cyclic).  Particle positions are physical; proper velocities
+u = gamma*v at t - dt/2.  c = eps0 = mu0 = 1.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import warnings
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpp_gb300.so")
+
+PP_OK, PP_EINVAL, PP_ENOMEM, PP_EBUSY, PP_ECUDA, PP_ETIMEOUT, PP_ENOCONV, PP_ECFL, PP_ENAN, PP_WSTAB = range(10)
+PP_VAY, PP_BORIS = 0, 1
+PP_FP64, PP_MIXED32 = 0, 1
+PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
+PP_MAX_SPECIES = 8
+_CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
+          9: "WSTAB"}
+
+
+class PPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"PP_{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double),
+                ("c", C.c_double), ("eps0", C.c_double), ("field_order", C.c_int), ("alpha", C.c_double),
+                ("shape_order", C.c_int), ("pusher", C.c_int), ("precision", C.c_int),
+                ("sort_interval", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double),
+                ("deposit_mode", C.c_int), ("stream", C.c_void_p)]
+
+
+class SpeciesDesc(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("w", C.c_double), ("capacity", C.c_int64)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("step", C.c_int64), ("time", C.c_double), ("energy_E", C.c_double), ("energy_B", C.c_double),
+                ("energy_Ex", C.c_double), ("kinetic", C.c_double * PP_MAX_SPECIES), ("kinetic_total", C.c_double),
+                ("charge", C.c_double), ("rho_max", C.c_double), ("gauss_max", C.c_double),
+                ("gauss_drift_max", C.c_double), ("divB_max", C.c_double), ("relax_residual", C.c_double),
+                ("relax_iters", C.c_int), ("status", C.c_int), ("n_particles", C.c_int64), ("n_slow", C.c_int64)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("particle_ms", C.c_double), ("particle_launches", C.c_int64), ("current_ms", C.c_double),
+                ("field_ms", C.c_double), ("sort_ms", C.c_double), ("steps", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
+# Every entry point declared in include/pp.h: name -> (restype, argtypes)
+_P = C.c_void_p
+_PP = C.POINTER(C.c_void_p)
+SIGNATURES = {
+    "pp_init_grid": (C.c_int, [_PP, C.POINTER(GridDesc)]),
+    "pp_init_species": (C.c_int, [_P, C.POINTER(SpeciesDesc), C.POINTER(C.c_int)]),
+    "pp_load_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int]),
+    "pp_load_fields": (C.c_int, [_P, _PP, _PP, C.c_int]),
+    "pp_step": (C.c_int, [_P, C.c_int]),
+    "pp_deposit": (C.c_int, [_P, C.c_int]),
+    "pp_field_update": (C.c_int, [_P]),
+    "pp_sort": (C.c_int, [_P]),
+    "pp_sync": (C.c_int, [_P]),
+    "pp_diagnostics": (C.c_int, [_P, C.POINTER(Diag)]),
+    "pp_get_fields": (C.c_int, [_P, _PP, _PP, _PP]),
+    "pp_get_rho": (C.c_int, [_P, _P]),
+    "pp_get_grid": (C.c_int, [_P, C.POINTER(GridDesc), C.POINTER(C.c_int)]),
+    "pp_get_count": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64)]),
+    "pp_get_particles": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "pp_profile_enable": (C.c_int, [_P, C.c_int]),
+    "pp_profile_read": (C.c_int, [_P, C.POINTER(Profile)]),
+    "pp_save": (C.c_int, [_P, C.c_char_p]),
+    "pp_restore": (C.c_int, [_PP, C.c_char_p, _P]),
+    "pp_destroy": (C.c_int, [_P]),
+    "pp_last_error": (C.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libpp_gb300.so (built by ``python -m paper_1211_4575_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1211_4575_gb300.build` "
+                               "(the CUDA library is the only implementation)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != PP_OK:
+        msg = lib().pp_last_error(ctx).decode(errors="replace")
+        if rc == PP_WSTAB:
+            warnings.warn(msg)
+            return
+        raise PPError(rc, msg)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # torch missing: the legacy default stream
+        pass
+    return None
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr_array(arrs):
+    return (C.c_void_p * 3)(*[a.ctypes.data if a is not None else None for a in arrs])
+
+
+class Simulation:
+    """One periodic 3D plasma on the GPU (a ``pp_ctx``)."""
+
+    def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=3, pusher=PP_VAY, precision=PP_FP64,
+                 sort_interval=20, relax_max_iter=200, relax_tol=1e-6, deposit_mode=PP_DEPOSIT_AUTO, stream=None,
+                 _handle=None):
+        self._ctx = C.c_void_p()
+        if _handle is not None:
+            self._ctx = _handle
+        else:
+            g = GridDesc(nx=n[0], ny=n[1], nz=n[2], dx=d[0], dy=d[1], dz=d[2], dt=dt, c=1.0, eps0=1.0,
+                         field_order=field_order, alpha=alpha, shape_order=shape_order, pusher=pusher,
+                         precision=precision, sort_interval=sort_interval, relax_max_iter=relax_max_iter,
+                         relax_tol=relax_tol, deposit_mode=deposit_mode,
+                         stream=stream if stream is not None else _current_stream())
+            rc = lib().pp_init_grid(C.byref(self._ctx), C.byref(g))
+            _check(rc, self._ctx if self._ctx.value else None)
+        self.n = tuple(n)
+        self.nspecies = 0
+
+    # -- lifecycle --------------------------------------------------------
+    def close(self):
+        if self._ctx is not None and self._ctx.value:
+            lib().pp_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, rc):
+        _check(rc, self._ctx)
+
+    # -- setup ------------------------------------------------------------
+    def add_species(self, q, m, w, capacity) -> int:
+        sid = C.c_int(-1)
+        self._c(lib().pp_init_species(self._ctx, C.byref(SpeciesDesc(q, m, w, int(capacity))), C.byref(sid)))
+        self.nspecies += 1
+        return sid.value
+
+    def load_particles(self, sid, x, y, z, ux, uy, uz):
+        """Append particles: numpy arrays (host) or CUDA torch tensors (device)."""
+        arrs = [x, y, z, ux, uy, uz]
+        if hasattr(x, "is_cuda") and x.is_cuda:
+            import torch
+            arrs = [a.to(torch.float64).contiguous() for a in arrs]
+            ptrs = [a.data_ptr() for a in arrs]
+            self._c(lib().pp_load_particles(self._ctx, sid, int(arrs[0].numel()), *ptrs, 1))
+            return
+        arrs = [_f64(a) for a in arrs]
+        n = arrs[0].size
+        if any(a.size != n for a in arrs):
+            raise ValueError("particle arrays differ in length")
+        self._c(lib().pp_load_particles(self._ctx, sid, n, *[a.ctypes.data for a in arrs], 0))
+
+    def load_fields(self, E, B):
+        E = [_f64(a) for a in E]
+        B = [_f64(a) for a in B]
+        self._c(lib().pp_load_fields(self._ctx, _ptr_array(E), _ptr_array(B), 0))
+
+    # -- the step -----------------------------------------------------------
+    def step(self, n: int = 1):
+        self._c(lib().pp_step(self._ctx, int(n)))
+
+    def deposit(self, sid: int = -1):
+        self._c(lib().pp_deposit(self._ctx, int(sid)))
+
+    def field_update(self):
+        self._c(lib().pp_field_update(self._ctx))
+
+    def sort(self):
+        self._c(lib().pp_sort(self._ctx))
+
+    def sync(self):
+        self._c(lib().pp_sync(self._ctx))
+
+    # -- readback -----------------------------------------------------------
+    def diagnostics(self) -> dict:
+        d = Diag()
+        self._c(lib().pp_diagnostics(self._ctx, C.byref(d)))
+        out = {k: getattr(d, k) for k, _ in Diag._fields_}
+        out["kinetic"] = list(d.kinetic)[: self.nspecies]
+        return out
+
+    def _mesh(self):
+        nx, ny, nz = self.n
+        return np.zeros((nz, ny, nx))
+
+    def fields(self):
+        E = [self._mesh() for _ in range(3)]
+        B = [self._mesh() for _ in range(3)]
+        J = [self._mesh() for _ in range(3)]
+        self._c(lib().pp_get_fields(self._ctx, _ptr_array(E), _ptr_array(B), _ptr_array(J)))
+        return E, B, J
+
+    def rho(self) -> np.ndarray:
+        r = self._mesh()
+        self._c(lib().pp_get_rho(self._ctx, r.ctypes.data))
+        return r
+
+    def count(self, sid: int) -> int:
+        n = C.c_int64(0)
+        self._c(lib().pp_get_count(self._ctx, sid, C.byref(n)))
+        return n.value
+
+    def particles(self, sid: int) -> dict:
+        n = self.count(sid)
+        out = {k: np.zeros(n) for k in ("x", "y", "z", "ux", "uy", "uz")}
+        self._c(lib().pp_get_particles(self._ctx, sid, *[out[k].ctypes.data for k in ("x", "y", "z", "ux", "uy", "uz")]))
+        return out
+
+    def profile_enable(self, enable: bool = True):
+        self._c(lib().pp_profile_enable(self._ctx, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        pr = Profile()
+        self._c(lib().pp_profile_read(self._ctx, C.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in Profile._fields_}
+
+    def save(self, path: str):
+        self._c(lib().pp_save(self._ctx, os.fsencode(path)))
+
+    @classmethod
+    def restore(cls, path: str, stream=None) -> "Simulation":
+        h = C.c_void_p()
+        rc = lib().pp_restore(C.byref(h), os.fsencode(path), stream if stream is not None else _current_stream())
+        _check(rc, None)
+        sim = cls.__new__(cls)
+        sim._ctx = h
+        g, ns = sim.grid()
+        sim.n = (g.nx, g.ny, g.nz)
+        sim.nspecies = ns
+        return sim
+
+    def grid(self):
+        """(GridDesc, number of species) of this context."""
+        g = GridDesc()
+        ns = C.c_int(0)
+        self._c(lib().pp_get_grid(self._ctx, C.byref(g), C.byref(ns)))
+        return g, ns.value

@@ -1,0 +1,768 @@
+// pp_capi.cu -- the C ABI of include/pp.h: context lifecycle, loading and
+// unloading, the step driver (Sec. III step order 1-5), diagnostics and
+// checkpointing.  All device work goes through the kernels of pp_particles.cu,
+// pp_mesh.cu and pp_sort.cu on the context's stream; no step of the particle
+// or field update runs on the host.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "pp_internal.cuh"
+
+using namespace pp;
+
+struct pp_ctx : public Ctx {};
+
+static char g_last_error[512] = "";
+
+static int fail(Ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+static int fail(Ctx *c, int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    char *dst = c ? c->err : g_last_error;
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CU(expr)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess) return fail(c, PP_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Setup of the constant operators
+// ---------------------------------------------------------------------------
+static void fd_coeffs(int order, double k[3]) {
+    // Staggered first-derivative coefficients (Sec. III).  6th order: the
+    // printed a = 25/21 violates a + 3b + 5c = 1; a = 75/64 is the value that
+    // satisfies the Taylor conditions with the printed b and c.
+    if (order == 6) { k[0] = 75.0 / 64.0; k[1] = -25.0 / 384.0; k[2] = 3.0 / 640.0; }
+    else if (order == 4) { k[0] = 9.0 / 8.0; k[1] = -1.0 / 24.0; k[2] = 0.0; }
+    else { k[0] = 1.0; k[1] = 0.0; k[2] = 0.0; }
+}
+
+// First row g of the inverse of the symmetric circulant line operator with
+// symbol p(th) = (a+b+c) + 2(b+c) cos th + 2c cos 2th (n points), via its
+// discrete Fourier representation.
+static void circulant_inverse(int n, const double k[3], std::vector<double> &g) {
+    double d0 = k[0] + k[1] + k[2], d1 = k[1] + k[2], d2 = k[2];
+    g.assign(n, 0.0);
+    for (int m = 0; m < n; ++m) {
+        double th = 2.0 * M_PI * m / n;
+        double inv = 1.0 / (d0 + 2.0 * d1 * cos(th) + 2.0 * d2 * cos(2.0 * th));
+        for (int q = 0; q < n; ++q) g[q] += cos(th * q) * inv;
+    }
+    for (int q = 0; q < n; ++q) g[q] /= n;
+}
+
+static int setup_operators(Ctx *c) {
+    fd_coeffs(c->d.field_order, c->fd);
+    // 1D stencil of d^+ d^-: autocorrelation of the half-offset kernel
+    // t(+-(m-1/2)) = +-k_m
+    double t[6] = {-c->fd[2], -c->fd[1], -c->fd[0], c->fd[0], c->fd[1], c->fd[2]};
+    for (int s = 0; s <= 5; ++s) {
+        double acc = 0.0;
+        for (int p = 0; p < 6; ++p) {
+            int q = p + s;   // offsets differ by s
+            if (q < 6) acc += t[q] * t[p];
+        }
+        c->lap[s] = -acc;    // l_s = sum_p t_p t_{s-p} = -sum_p t_{p+s} t_p by antisymmetry
+    }
+    // high-order current taps
+    std::vector<double> host(3 * kMaxTaps, 0.0);
+    double eps = c->fp64 ? 1e-18 : 1e-10;
+    for (int a = 0; a < 3; ++a) {
+        c->ntaps[a] = 0;
+        if (c->d.field_order == 2) continue;
+        int n = c->g.n[a];
+        std::vector<double> gi;
+        circulant_inverse(n, c->fd, gi);
+        if (n <= kMaxTaps) {
+            c->full_circ[a] = true;
+            c->ntaps[a] = n;
+            for (int m = 0; m < n; ++m) host[a * kMaxTaps + m] = gi[m];
+        } else {
+            int K = 1;
+            while (K < n / 2 && K < (kMaxTaps - 1) / 2 && fabs(gi[K + 1]) > eps * fabs(gi[0])) ++K;
+            c->full_circ[a] = false;
+            c->ntaps[a] = 2 * K + 1;
+            for (int m = 0; m <= 2 * K; ++m) host[a * kMaxTaps + m] = gi[abs(m - K)];
+        }
+    }
+    cudaError_t e = cudaMalloc(&c->taps, sizeof(double) * 3 * kMaxTaps);
+    if (e != cudaSuccess) return fail(c, PP_ECUDA, "taps: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(c->taps, host.data(), sizeof(double) * 3 * kMaxTaps, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(c, PP_ECUDA, "taps copy: %s", cudaGetErrorString(e));
+    // Chebyshev bounds of A = 1 - alpha^2 dt^2 L: spectrum in [1, 1 + kk sum_a max K_a^2]
+    double h[3] = {c->d.dx, c->d.dy, c->d.dz};
+    double kk = c->d.alpha * c->d.alpha * c->d.dt * c->d.dt;
+    double lmax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double best = 0.0;
+        for (int s = 0; s <= 4000; ++s) {
+            double th = M_PI * s / 4000.0;
+            double K = 2.0 * (c->fd[0] * sin(0.5 * th) + c->fd[1] * sin(1.5 * th) + c->fd[2] * sin(2.5 * th));
+            best = fmax(best, K * K);
+        }
+        lmax += kk * best * 1.0005 / (h[a] * h[a]);
+    }
+    c->cheb_theta = 0.5 * (lmax + 1.0);
+    c->cheb_delta = 0.5 * (lmax - 1.0);
+    double sk = sqrt(lmax);
+    double rho = (sk - 1.0) / (sk + 1.0);
+    double target = c->d.relax_tol / sqrt(3.0 * (double)c->g.cells()) / sk;
+    int it = 1;
+    if (c->cheb_delta > 0.0) {
+        double rk = rho;
+        while (it < 10000 && 2.0 * rk / (1.0 + rk * rk) > target) {
+            rk *= rho;
+            ++it;
+        }
+    }
+    c->cheb_iters = it < c->d.relax_max_iter ? it : c->d.relax_max_iter;
+    return PP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lifecycle
+// ---------------------------------------------------------------------------
+extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
+    Ctx *c = nullptr;
+    if (!out || !d) return fail(c, PP_EINVAL, "pp_init_grid: NULL argument");
+    *out = nullptr;
+    int n[3] = {d->nx, d->ny, d->nz};
+    double h[3] = {d->dx, d->dy, d->dz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || n[a] > 1023) return fail(c, PP_EINVAL, "grid size %d on axis %d outside [1, 1023]", n[a], a);
+        if (!(h[a] > 0.0)) return fail(c, PP_EINVAL, "cell size on axis %d must be > 0", a);
+        if (!(d->dt > 0.0) || !(d->dt / h[a] < 1.0))
+            return fail(c, PP_EINVAL, "need 0 < c dt / d < 1 on every axis (axis %d: %g)", a, d->dt / h[a]);
+    }
+    if (d->c != 1.0 || d->eps0 != 1.0) return fail(c, PP_EINVAL, "the library is normalised to c = eps0 = 1");
+    if (d->field_order != 2 && d->field_order != 4 && d->field_order != 6)
+        return fail(c, PP_EINVAL, "field_order must be 2, 4 or 6");
+    if (!(d->alpha >= 0.5 && d->alpha < 1.0)) return fail(c, PP_EINVAL, "alpha must lie in [0.5, 1)");
+    if (d->shape_order < 1 || d->shape_order > 3) return fail(c, PP_EINVAL, "shape_order must be 1, 2 or 3");
+    if (d->pusher != PP_VAY && d->pusher != PP_BORIS) return fail(c, PP_EINVAL, "unknown pusher");
+    if (d->precision != PP_FP64 && d->precision != PP_MIXED32) return fail(c, PP_EINVAL, "unknown precision");
+    if (d->relax_max_iter < 1 || !(d->relax_tol > 0.0)) return fail(c, PP_EINVAL, "relaxation cap and tolerance must be > 0");
+    if (d->sort_interval < 0) return fail(c, PP_EINVAL, "sort_interval must be >= 0");
+    if (d->deposit_mode < 0 || d->deposit_mode > 2) return fail(c, PP_EINVAL, "unknown deposit_mode");
+    if (d->deposit_mode == PP_DEPOSIT_TILED && d->precision != PP_MIXED32)
+        return fail(c, PP_EINVAL, "the tiled deposit exists for PP_MIXED32 only");
+    if (d->deposit_mode == PP_DEPOSIT_TILED && (d->nx % 8 || d->ny % 8 || d->nz % 8))
+        return fail(c, PP_EINVAL, "the tiled deposit needs every grid size to be a multiple of 8");
+
+    pp_ctx *p = new (std::nothrow) pp_ctx();
+    if (!p) return fail(c, PP_ENOMEM, "host allocation failed");
+    c = p;
+    c->d = *d;
+    c->st = (cudaStream_t)d->stream;
+    c->fp64 = d->precision == PP_FP64;
+    c->rsz = c->fp64 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) {
+        c->g.n[a] = n[a];
+        c->g.P[a] = n[a] + 2 * kGhost;
+    }
+    c->g.G = kGhost;
+    int64_t P = c->g.padded_size();
+    size_t bytes = (size_t)P * c->rsz;
+    cudaError_t e = cudaMalloc(&c->mesh, bytes * 21);
+    if (e != cudaSuccess) {
+        int r = fail(nullptr, PP_ENOMEM, "mesh allocation (%zu bytes): %s", bytes * 21, cudaGetErrorString(e));
+        delete p;
+        return r;
+    }
+    char *m = (char *)c->mesh;
+    void **groups[7] = {c->E, c->B, c->J, c->Jt, c->R, c->Xa, c->Xb};
+    for (int gidx = 0; gidx < 7; ++gidx)
+        for (int a = 0; a < 3; ++a) groups[gidx][a] = m + (size_t)(gidx * 3 + a) * bytes;
+    int rc = PP_OK;
+    auto chk = [&](cudaError_t ee, const char *what) {
+        if (ee != cudaSuccess && rc == PP_OK) rc = fail(c, PP_ECUDA, "%s: %s", what, cudaGetErrorString(ee));
+    };
+    chk(cudaMemset(c->mesh, 0, bytes * 21), "mesh clear");
+    chk(cudaMalloc(&c->rho, sizeof(double) * c->g.cells()), "rho");
+    chk(cudaMalloc(&c->G0, sizeof(double) * c->g.cells()), "G0");
+    if (rc == PP_OK) chk(cudaMemset(c->G0, 0, sizeof(double) * c->g.cells()), "G0 clear");
+    chk(cudaMalloc(&c->d_status, sizeof(int)), "status");
+    if (rc == PP_OK) chk(cudaMemset(c->d_status, 0, sizeof(int)), "status clear");
+    chk(cudaMallocHost(&c->h_status, sizeof(int)), "status mirror");
+    chk(cudaMalloc(&c->d_red, sizeof(double) * 512 * 16), "reduction partials");
+    chk(cudaMalloc(&c->d_out, sizeof(double) * (16 + PP_MAX_SPECIES)), "reduction results");
+    chk(cudaMalloc(&c->d_nslow, sizeof(unsigned long long)), "fallback counter");
+    if (rc == PP_OK) chk(cudaMemset(c->d_nslow, 0, sizeof(unsigned long long)), "fallback counter clear");
+    if (rc == PP_OK) chk(sort_setup(*c), "sort setup");
+    if (rc == PP_OK) rc = setup_operators(c);
+    if (rc != PP_OK) {
+        snprintf(g_last_error, sizeof g_last_error, "%s", c->err);
+        pp_destroy(p);
+        return rc;
+    }
+    *out = p;
+    if (d->alpha < 0.525 && d->field_order == 6 && d->shape_order == 3)
+        return fail(c, PP_WSTAB, "alpha %.4g < 0.525 with 6th-order fields and PCS is reported unstable", d->alpha);
+    return PP_OK;
+}
+
+extern "C" int pp_destroy(pp_ctx *p) {
+    if (!p) return PP_OK;
+    Ctx *c = p;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    for (int s = 0; s < c->nspecies; ++s) {
+        cudaFree(c->sp[s].buf);
+        cudaFree(c->sp[s].alt);
+        cudaFree(c->sp[s].keys);
+        cudaFree(c->sp[s].cell_start);
+    }
+    cudaFree(c->mesh);
+    cudaFree(c->rho);
+    cudaFree(c->G0);
+    cudaFree(c->taps);
+    cudaFree(c->counts);
+    cudaFree(c->scan_tmp);
+    cudaFree(c->d_status);
+    cudaFree(c->d_red);
+    cudaFree(c->d_out);
+    cudaFree(c->d_nslow);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    for (int q = 0; q < c->prof_cap; ++q) {
+        cudaEventDestroy(c->prof_ev[q].a);
+        cudaEventDestroy(c->prof_ev[q].b);
+    }
+    free(c->prof_ev);
+    delete p;
+    return PP_OK;
+}
+
+extern "C" const char *pp_last_error(const pp_ctx *p) { return p ? p->err : g_last_error; }
+
+extern "C" int pp_init_species(pp_ctx *p, const pp_species_desc *sd, int *sid) {
+    Ctx *c = p;
+    if (!c || !sd || !sid) return fail(c, PP_EINVAL, "pp_init_species: NULL argument");
+    if (c->nspecies >= PP_MAX_SPECIES) return fail(c, PP_EINVAL, "at most %d species", PP_MAX_SPECIES);
+    if (!(sd->m > 0.0) || !isfinite(sd->q) || !isfinite(sd->w) || sd->capacity < 0)
+        return fail(c, PP_EINVAL, "species needs m > 0, finite q and w, capacity >= 0");
+    if (sd->capacity > (int64_t)0x7fffffff - 64) return fail(c, PP_EINVAL, "capacity above 2^31 - 64");
+    Species &S = c->sp[c->nspecies];
+    S = Species();
+    S.q = sd->q;
+    S.m = sd->m;
+    S.w = sd->w;
+    S.limit = sd->capacity;
+    S.cap = (sd->capacity + 63) / 64 * 64;
+    if (S.cap == 0) S.cap = 64;
+    size_t per = c->fp64 ? 6 * sizeof(double) : sizeof(int32_t) + 6 * sizeof(float);
+    size_t bytes = per * (size_t)S.cap;
+    cudaError_t e1 = cudaMalloc(&S.buf, bytes), e2 = cudaMalloc(&S.alt, bytes);
+    cudaError_t e3 = cudaMalloc(&S.keys, sizeof(int32_t) * S.cap);
+    cudaError_t e4 = cudaMalloc(&S.cell_start, sizeof(int32_t) * (c->nkeys + 1));
+    if (e1 || e2 || e3 || e4) {
+        cudaFree(S.buf); cudaFree(S.alt); cudaFree(S.keys); cudaFree(S.cell_start);
+        S = Species();
+        return fail(c, PP_ENOMEM, "species storage of %zu bytes x 2", bytes);
+    }
+    if (c->fp64) {
+        double *b = (double *)S.buf;
+        S.x = b; S.y = b + S.cap; S.z = b + 2 * S.cap; S.ux = b + 3 * S.cap; S.uy = b + 4 * S.cap; S.uz = b + 5 * S.cap;
+    } else {
+        int32_t *ci = (int32_t *)S.buf;
+        float *f = (float *)(ci + S.cap);
+        S.cell = ci; S.ox = f; S.oy = f + S.cap; S.oz = f + 2 * S.cap;
+        S.fux = f + 3 * S.cap; S.fuy = f + 4 * S.cap; S.fuz = f + 5 * S.cap;
+    }
+    *sid = c->nspecies++;
+    return PP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Loading
+// ---------------------------------------------------------------------------
+static int refresh_gauss_reference(Ctx *c) {
+    double tmp[16];
+    CU(launch_rho(*c));
+    c->have_G0 = false;
+    CU(launch_mesh_diag(*c, tmp));
+    CU(cudaStreamSynchronize(c->st));
+    return PP_OK;
+}
+
+extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x, const double *y, const double *z,
+                                 const double *ux, const double *uy, const double *uz, int on_device) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    Species &S = c->sp[sid];
+    if (n < 0) return fail(c, PP_EINVAL, "negative count");
+    if (n > 0 && (!x || !y || !z || !ux || !uy || !uz)) return fail(c, PP_EINVAL, "NULL particle array");
+    if (S.n + n > S.limit) return fail(c, PP_ENOMEM, "species %d capacity %lld exceeded", sid, (long long)S.limit);
+    const int64_t chunk = (int64_t)1 << 24;
+    double *stage = nullptr;
+    if (!on_device && n > 0) CU(cudaMalloc(&stage, sizeof(double) * 6 * (size_t)(n < chunk ? n : chunk)));
+    int rc = PP_OK;
+    const double *src[6] = {x, y, z, ux, uy, uz};
+    for (int64_t off = 0; off < n && rc == PP_OK; off += chunk) {
+        int64_t m = n - off < chunk ? n - off : chunk;
+        const double *a[6];
+        for (int k = 0; k < 6; ++k) {
+            if (on_device) {
+                a[k] = src[k] + off;
+            } else {
+                double *dst = stage + (size_t)k * (size_t)(n < chunk ? n : chunk);
+                cudaError_t e = cudaMemcpyAsync(dst, src[k] + off, sizeof(double) * m, cudaMemcpyHostToDevice, c->st);
+                if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "particle upload: %s", cudaGetErrorString(e)); break; }
+                a[k] = dst;
+            }
+        }
+        if (rc != PP_OK) break;
+        cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
+        if (e == cudaSuccess) e = launch_check_finite(*c, m, a, 6, c->d_status);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "particle check: %s", cudaGetErrorString(e)); break; }
+        if (*c->h_status) { rc = fail(c, PP_ENAN, "non-finite particle value in rows %lld..%lld", (long long)off, (long long)(off + m)); break; }
+        e = launch_convert_in(*c, sid, S.n + off, m, a[0], a[1], a[2], a[3], a[4], a[5]);
+        if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "particle convert: %s", cudaGetErrorString(e)); break; }
+    }
+    if (stage) {
+        cudaStreamSynchronize(c->st);
+        cudaFree(stage);
+    }
+    if (rc != PP_OK) return rc;
+    S.n += n;
+    CU(launch_sort(*c, sid));
+    return refresh_gauss_reference(c);
+}
+
+template <typename R>
+__global__ void k_compact_to_padded(Geom g, const double *src, R *dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    int i = (int)(t % g.n[0]);
+    int64_t r = t / g.n[0];
+    int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+    dst[g.at(i, j, k)] = (R)src[t];
+}
+
+template <typename R>
+__global__ void k_padded_to_compact(Geom g, const R *src, double *dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    int i = (int)(t % g.n[0]);
+    int64_t r = t / g.n[0];
+    int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+    dst[t] = (double)src[g.at(i, j, k)];
+}
+
+static cudaError_t to_padded(Ctx *c, const double *src, void *dst) {
+    unsigned b = (unsigned)((c->g.cells() + 255) / 256);
+    if (c->fp64) k_compact_to_padded<double><<<b, 256, 0, c->st>>>(c->g, src, (double *)dst);
+    else k_compact_to_padded<float><<<b, 256, 0, c->st>>>(c->g, src, (float *)dst);
+    ++c->nlaunch;
+    return cudaGetLastError();
+}
+
+static cudaError_t to_compact(Ctx *c, const void *src, double *dst) {
+    unsigned b = (unsigned)((c->g.cells() + 255) / 256);
+    if (c->fp64) k_padded_to_compact<double><<<b, 256, 0, c->st>>>(c->g, (const double *)src, dst);
+    else k_padded_to_compact<float><<<b, 256, 0, c->st>>>(c->g, (const float *)src, dst);
+    ++c->nlaunch;
+    return cudaGetLastError();
+}
+
+extern "C" int pp_load_fields(pp_ctx *p, const double *const E[3], const double *const B[3], int on_device) {
+    Ctx *c = p;
+    if (!c || !E || !B) return fail(c, PP_EINVAL, "pp_load_fields: NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (!E[a] || !B[a]) return fail(c, PP_EINVAL, "pp_load_fields: NULL component");
+    size_t nb = sizeof(double) * (size_t)c->g.cells();
+    double *stage = nullptr;
+    if (!on_device) CU(cudaMalloc(&stage, nb));
+    const double *const *srcs[2] = {E, B};
+    void **dsts[2] = {c->E, c->B};
+    for (int f = 0; f < 2; ++f)
+        for (int a = 0; a < 3; ++a) {
+            const double *s = srcs[f][a];
+            if (!on_device) {
+                CU(cudaMemcpyAsync(stage, s, nb, cudaMemcpyHostToDevice, c->st));
+                s = stage;
+            }
+            CU(to_padded(c, s, dsts[f][a]));
+        }
+    CU(launch_ghost_fill(*c, c->E, c->B));
+    CU(cudaStreamSynchronize(c->st));
+    if (stage) cudaFree(stage);
+    return refresh_gauss_reference(c);
+}
+
+// ---------------------------------------------------------------------------
+// Profiling: a pair of events around each phase while enabled.
+// ---------------------------------------------------------------------------
+static cudaError_t prof_mark(Ctx *c, int phase, bool begin) {
+    if (!c->prof) return cudaSuccess;
+    if (begin) {
+        if (c->prof_n == c->prof_cap) {
+            int cap = c->prof_cap ? 2 * c->prof_cap : 256;
+            EventPair *nv = (EventPair *)realloc(c->prof_ev, sizeof(EventPair) * cap);
+            if (!nv) return cudaErrorMemoryAllocation;
+            for (int q = c->prof_cap; q < cap; ++q) {
+                nv[q].phase = -1;
+                cudaError_t e = cudaEventCreate(&nv[q].a);
+                if (e == cudaSuccess) e = cudaEventCreate(&nv[q].b);
+                if (e != cudaSuccess) { c->prof_ev = nv; c->prof_cap = q; return e; }
+            }
+            c->prof_ev = nv;
+            c->prof_cap = cap;
+        }
+        c->prof_ev[c->prof_n].phase = phase;
+        return cudaEventRecord(c->prof_ev[c->prof_n].a, c->st);
+    }
+    cudaError_t e = cudaEventRecord(c->prof_ev[c->prof_n].b, c->st);
+    ++c->prof_n;
+    return e;
+}
+
+// Fold the recorded pairs into the totals (after a synchronisation).
+static cudaError_t prof_collect(Ctx *c) {
+    for (int q = 0; q < c->prof_n; ++q) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventElapsedTime(&ms, c->prof_ev[q].a, c->prof_ev[q].b);
+        if (e != cudaSuccess) return e;
+        c->prof_ms[c->prof_ev[q].phase] += ms;
+    }
+    c->prof_n = 0;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// The step
+// ---------------------------------------------------------------------------
+static int particle_phase(Ctx *c, int only) {
+    CU(launch_zero_J(*c));
+    CU(cudaMemsetAsync(c->d_nslow, 0, sizeof(unsigned long long), c->st));
+    CU(prof_mark(c, PH_PARTICLE, true));
+    for (int s = 0; s < c->nspecies; ++s) {
+        if (only >= 0 && s != only) continue;
+        if (c->sp[s].n == 0) continue;
+        if (c->fp64) CU(launch_particles_fp64(*c, s));
+        else if (c->d.deposit_mode == PP_DEPOSIT_TILED ||
+                 (c->d.deposit_mode == PP_DEPOSIT_AUTO && tiled_supported(*c) && c->sp[s].sorted))
+            CU(launch_particles_mixed_tiled(*c, s));
+        else CU(launch_particles_mixed_global(*c, s));
+        if (c->prof) ++c->prof_particle_launches;
+    }
+    CU(prof_mark(c, PH_PARTICLE, false));
+    CU(prof_mark(c, PH_CURRENT, true));
+    CU(launch_fold_J(*c));
+    CU(launch_current_solve(*c));
+    CU(prof_mark(c, PH_CURRENT, false));
+    if (c->prof) ++c->prof_steps;
+    if (c->prof && c->prof_n > 4096) {
+        CU(cudaStreamSynchronize(c->st));
+        CU(prof_collect(c));
+    }
+    return PP_OK;
+}
+
+static int field_phase(Ctx *c) {
+    CU(prof_mark(c, PH_FIELD, true));
+    CU(launch_field_update(*c));
+    CU(prof_mark(c, PH_FIELD, false));
+    return PP_OK;
+}
+
+extern "C" int pp_profile_enable(pp_ctx *p, int enable) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (enable) {
+        CU(cudaStreamSynchronize(c->st));
+        c->prof_n = 0;
+        for (int q = 0; q < PH_N; ++q) c->prof_ms[q] = 0.0;
+        c->prof_particle_launches = c->prof_steps = 0;
+        c->nlaunch = 0;
+    }
+    c->prof = enable != 0;
+    return PP_OK;
+}
+
+extern "C" int pp_profile_read(pp_ctx *p, pp_profile *out) {
+    Ctx *c = p;
+    if (!c || !out) return fail(c, PP_EINVAL, "pp_profile_read: NULL argument");
+    CU(cudaStreamSynchronize(c->st));
+    CU(prof_collect(c));
+    out->particle_ms = c->prof_ms[PH_PARTICLE];
+    out->particle_launches = c->prof_particle_launches;
+    out->current_ms = c->prof_ms[PH_CURRENT];
+    out->field_ms = c->prof_ms[PH_FIELD];
+    out->sort_ms = c->prof_ms[PH_SORT];
+    out->steps = c->prof_steps;
+    out->kernel_launches = c->nlaunch;
+    return PP_OK;
+}
+
+extern "C" int pp_sort(pp_ctx *p) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    CU(prof_mark(c, PH_SORT, true));
+    for (int s = 0; s < c->nspecies; ++s) CU(launch_sort(*c, s));
+    CU(prof_mark(c, PH_SORT, false));
+    c->since_sort = 0;
+    return PP_OK;
+}
+
+extern "C" int pp_step(pp_ctx *p, int nsteps) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (nsteps < 0) return fail(c, PP_EINVAL, "negative step count");
+    for (int it = 0; it < nsteps; ++it) {
+        if (c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval) {
+            int r = pp_sort(p);
+            if (r) return r;
+        }
+        int r = particle_phase(c, -1);
+        if (r) return r;
+        r = field_phase(c);
+        if (r) return r;
+        ++c->step;
+        ++c->since_sort;
+    }
+    return PP_OK;
+}
+
+extern "C" int pp_deposit(pp_ctx *p, int sid) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (sid < -1 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    int r = particle_phase(c, sid);
+    if (r == PP_OK) ++c->since_sort;
+    return r;
+}
+
+extern "C" int pp_field_update(pp_ctx *p) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    return field_phase(c);
+}
+
+static int status_code(int bits) {
+    if (bits & ST_NAN) return PP_ENAN;
+    if (bits & ST_CFL) return PP_ECFL;
+    if (bits & ST_NOCONV) return PP_ENOCONV;
+    if (bits & ST_RANGE) return PP_EINVAL;
+    return PP_OK;
+}
+
+extern "C" int pp_sync(pp_ctx *p) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    CU(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
+    CU(cudaStreamSynchronize(c->st));
+    int code = status_code(*c->h_status);
+    if (code) return fail(c, code, "device status 0x%x (NaN=1, CFL=2, relaxation=4, range=8)", *c->h_status);
+    return PP_OK;
+}
+
+extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
+    Ctx *c = p;
+    if (!c || !out) return fail(c, PP_EINVAL, "pp_diagnostics: NULL argument");
+    int st = pp_sync(p);
+    memset(out, 0, sizeof(*out));
+    out->status = st;
+    double mesh[16], kin[PP_MAX_SPECIES];
+    unsigned long long nslow = 0;
+    CU(cudaMemcpyAsync(&nslow, c->d_nslow, sizeof nslow, cudaMemcpyDeviceToHost, c->st));
+    CU(launch_rho(*c));
+    CU(launch_kinetic(*c, c->d_out + 16));
+    CU(launch_mesh_diag(*c, mesh));
+    CU(cudaMemcpyAsync(kin, c->d_out + 16, sizeof(double) * PP_MAX_SPECIES, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    double dV = c->d.dx * c->d.dy * c->d.dz;
+    out->step = c->step;
+    out->time = c->step * c->d.dt;
+    out->energy_E = mesh[0] * dV;
+    out->energy_B = mesh[1] * dV;
+    out->energy_Ex = mesh[2] * dV;
+    out->charge = mesh[3] * dV;
+    out->rho_max = mesh[4];
+    out->gauss_max = mesh[5];
+    out->gauss_drift_max = mesh[6];
+    out->divB_max = mesh[7];
+    out->relax_residual = (c->last_iters > 0 && mesh[9] > 0.0) ? mesh[8] / mesh[9] : 0.0;
+    out->relax_iters = c->last_iters;
+    for (int s = 0; s < c->nspecies; ++s) {
+        out->kinetic[s] = kin[s];
+        out->kinetic_total += kin[s];
+        out->n_particles += c->sp[s].n;
+    }
+    out->n_slow = (int64_t)nslow;
+    if (c->last_iters > 0 && out->relax_residual > 10.0 * c->d.relax_tol && out->status == PP_OK)
+        out->status = PP_ENOCONV;
+    return PP_OK;
+}
+
+extern "C" int pp_get_fields(pp_ctx *p, double *const E[3], double *const B[3], double *const J[3]) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    size_t nb = sizeof(double) * (size_t)c->g.cells();
+    double *stage = nullptr;
+    CU(cudaMalloc(&stage, nb));
+    double *const *dsts[3] = {E, B, J};
+    void **srcs[3] = {c->E, c->B, c->J};
+    int rc = PP_OK;
+    for (int f = 0; f < 3 && rc == PP_OK; ++f) {
+        if (!dsts[f]) continue;
+        for (int a = 0; a < 3; ++a) {
+            if (!dsts[f][a]) continue;
+            cudaError_t e = to_compact(c, srcs[f][a], stage);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dsts[f][a], stage, nb, cudaMemcpyDeviceToHost, c->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+            if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "field readback: %s", cudaGetErrorString(e)); break; }
+        }
+    }
+    cudaFree(stage);
+    return rc;
+}
+
+extern "C" int pp_get_rho(pp_ctx *p, double *rho) {
+    Ctx *c = p;
+    if (!c || !rho) return fail(c, PP_EINVAL, "pp_get_rho: NULL argument");
+    CU(launch_rho(*c));
+    CU(cudaMemcpyAsync(rho, c->rho, sizeof(double) * c->g.cells(), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return PP_OK;
+}
+
+extern "C" int pp_get_grid(pp_ctx *p, pp_grid_desc *desc, int *nspecies) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (desc) *desc = c->d;
+    if (nspecies) *nspecies = c->nspecies;
+    return PP_OK;
+}
+
+extern "C" int pp_get_count(pp_ctx *p, int sid, int64_t *n) {
+    Ctx *c = p;
+    if (!c || !n) return fail(c, PP_EINVAL, "pp_get_count: NULL argument");
+    if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    *n = c->sp[sid].n;
+    return PP_OK;
+}
+
+extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double *z, double *ux, double *uy,
+                                double *uz) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    Species &S = c->sp[sid];
+    if (S.n == 0) return PP_OK;
+    if (!x || !y || !z || !ux || !uy || !uz) return fail(c, PP_EINVAL, "NULL particle array");
+    double *stage = nullptr;
+    size_t nb = sizeof(double) * (size_t)S.n;
+    CU(cudaMalloc(&stage, nb * 6));
+    double *d[6];
+    for (int k = 0; k < 6; ++k) d[k] = stage + (size_t)k * S.n;
+    double *h[6] = {x, y, z, ux, uy, uz};
+    int rc = PP_OK;
+    cudaError_t e = launch_convert_out(*c, sid, d[0], d[1], d[2], d[3], d[4], d[5]);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaMemcpyAsync(h[k], d[k], nb, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle readback: %s", cudaGetErrorString(e));
+    cudaFree(stage);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / restart (FP64 blocks, independent of the precision form)
+// ---------------------------------------------------------------------------
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '1'};
+
+extern "C" int pp_save(pp_ctx *p, const char *path) {
+    Ctx *c = p;
+    if (!c || !path) return fail(c, PP_EINVAL, "pp_save: NULL argument");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(c, PP_EINVAL, "cannot open %s for writing", path);
+    int64_t N = c->g.cells();
+    std::vector<double> buf((size_t)N * 6);
+    double *E[3] = {buf.data(), buf.data() + N, buf.data() + 2 * N};
+    double *B[3] = {buf.data() + 3 * N, buf.data() + 4 * N, buf.data() + 5 * N};
+    int rc = pp_get_fields(p, E, B, nullptr);
+    pp_grid_desc d = c->d;
+    d.stream = nullptr;
+    bool ok = rc == PP_OK;
+    ok = ok && fwrite(kMagic, 1, 8, f) == 8 && fwrite(&d, sizeof d, 1, f) == 1;
+    ok = ok && fwrite(&c->step, sizeof c->step, 1, f) == 1 && fwrite(&c->nspecies, sizeof(int), 1, f) == 1;
+    ok = ok && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    for (int s = 0; s < c->nspecies && ok; ++s) {
+        Species &S = c->sp[s];
+        pp_species_desc sd{S.q, S.m, S.w, S.limit};
+        ok = fwrite(&sd, sizeof sd, 1, f) == 1 && fwrite(&S.n, sizeof S.n, 1, f) == 1;
+        std::vector<double> pb((size_t)S.n * 6);
+        if (ok && S.n) {
+            rc = pp_get_particles(p, s, pb.data(), pb.data() + S.n, pb.data() + 2 * S.n, pb.data() + 3 * S.n,
+                                  pb.data() + 4 * S.n, pb.data() + 5 * S.n);
+            ok = rc == PP_OK && fwrite(pb.data(), sizeof(double), pb.size(), f) == pb.size();
+        }
+    }
+    if (fclose(f) != 0) ok = false;
+    if (!ok) return rc != PP_OK ? rc : fail(c, PP_EINVAL, "write to %s failed", path);
+    return PP_OK;
+}
+
+extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
+    Ctx *c = nullptr;
+    if (!out || !path) return fail(c, PP_EINVAL, "pp_restore: NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(c, PP_EINVAL, "cannot open %s", path);
+    char magic[8];
+    pp_grid_desc d;
+    int64_t step = 0;
+    int ns = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(&d, sizeof d, 1, f) == 1 &&
+              fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
+              ns <= PP_MAX_SPECIES;
+    if (!ok) { fclose(f); return fail(c, PP_EINVAL, "%s is not a checkpoint of this library", path); }
+    d.stream = stream;
+    pp_ctx *p = nullptr;
+    int rc = pp_init_grid(&p, &d);
+    if (rc != PP_OK && rc != PP_WSTAB) { fclose(f); return rc; }
+    c = p;
+    int64_t N = c->g.cells();
+    std::vector<double> buf((size_t)N * 6);
+    ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    const double *E[3] = {buf.data(), buf.data() + N, buf.data() + 2 * N};
+    const double *B[3] = {buf.data() + 3 * N, buf.data() + 4 * N, buf.data() + 5 * N};
+    if (ok) rc = pp_load_fields(p, E, B, 0);
+    for (int s = 0; s < ns && ok && rc == PP_OK; ++s) {
+        pp_species_desc sd;
+        int64_t n = 0;
+        int sid = -1;
+        ok = fread(&sd, sizeof sd, 1, f) == 1 && fread(&n, sizeof n, 1, f) == 1 && n >= 0 && n <= sd.capacity;
+        if (!ok) break;
+        rc = pp_init_species(p, &sd, &sid);
+        std::vector<double> pb((size_t)n * 6);
+        if (rc == PP_OK) ok = fread(pb.data(), sizeof(double), pb.size(), f) == pb.size();
+        if (rc == PP_OK && ok && n)
+            rc = pp_load_particles(p, sid, n, pb.data(), pb.data() + n, pb.data() + 2 * n, pb.data() + 3 * n,
+                                   pb.data() + 4 * n, pb.data() + 5 * n, 0);
+    }
+    fclose(f);
+    if (!ok || rc != PP_OK) {
+        int code = rc != PP_OK ? rc : PP_EINVAL;
+        snprintf(g_last_error, sizeof g_last_error, "restore of %.200s failed: %.280s", path, c->err[0] ? c->err : "truncated file");
+        pp_destroy(p);
+        return code;
+    }
+    c->step = step;
+    *out = p;
+    return PP_OK;
+}

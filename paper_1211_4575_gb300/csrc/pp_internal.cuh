@@ -1,0 +1,347 @@
+// pp_internal.cuh -- shared declarations of the GB300 Photon-Plasma library.
+//
+// Device-side building blocks of the particle step (Sec. II weight functions,
+// Sec. III pushers and charge-conserving deposit) and the context structure
+// behind the C ABI of include/pp.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pp.h"
+
+namespace pp {
+
+// ---------------------------------------------------------------------------
+// Mesh geometry: every mesh array is padded by G ghost layers per side,
+// x fastest.  Interior index (i,j,k) in [0,n) maps to the padded offset below.
+// ---------------------------------------------------------------------------
+constexpr int kGhost = 5;   // covers the deposit reach of a particle sorted up to
+                            // two cells outside its tile plus the PCS support
+
+struct Geom {
+    int n[3];     // interior cells
+    int P[3];     // padded extents n + 2G
+    int G;
+    __host__ __device__ __forceinline__ int64_t at(int i, int j, int k) const {
+        return ((int64_t)(k + G) * P[1] + (j + G)) * P[0] + (i + G);
+    }
+    __host__ __device__ __forceinline__ int64_t padded_size() const { return (int64_t)P[0] * P[1] * P[2]; }
+    __host__ __device__ __forceinline__ int64_t cells() const { return (int64_t)n[0] * n[1] * n[2]; }
+};
+
+// Wrap an index that lies within a few periods of [0, n).
+__host__ __device__ __forceinline__ int wrap(int i, int n) {
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
+}
+
+// Device status bits (collected into one word, mapped to PP_* on the host).
+enum : int { ST_NAN = 1, ST_CFL = 2, ST_NOCONV = 4, ST_RANGE = 8 };
+
+// ---------------------------------------------------------------------------
+// B-spline weights of order O (Sec. II, W^1..W^3) written in the fractional
+// coordinate f in [0,1) of the first support node: node i0+m has weight w[m].
+// ---------------------------------------------------------------------------
+template <int O, typename R>
+__device__ __forceinline__ void bspline(R f, R (&w)[O + 1]) {
+    if constexpr (O == 1) {
+        w[0] = R(1) - f;
+        w[1] = f;
+    } else if constexpr (O == 2) {
+        R g = R(1) - f;
+        R h = f - R(0.5);
+        w[0] = R(0.5) * g * g;
+        w[1] = R(0.75) - h * h;
+        w[2] = R(0.5) * f * f;
+    } else {
+        R g = R(1) - f;
+        R f2 = f * f, f3 = f2 * f;
+        w[0] = g * g * g * R(1.0 / 6.0);
+        w[1] = (R(3) * f3 - R(6) * f2 + R(4)) * R(1.0 / 6.0);
+        w[2] = (R(-3) * f3 + R(3) * f2 + R(3) * f + R(1)) * R(1.0 / 6.0);
+        w[3] = f3 * R(1.0 / 6.0);
+    }
+}
+
+// Support start and weights for a position xi (cell units, in some integer
+// frame) on integer nodes (half = false) or on half-integer nodes i+1/2
+// stored at index i (half = true).
+template <int O, typename R>
+__device__ __forceinline__ int support(R xi, bool half, R (&w)[O + 1]) {
+    R y = xi - (half ? R(0.5 * O) : R(0.5 * (O - 1)));
+    R fl = floor(y);
+    bspline<O, R>(y - fl, w);
+    return (int)fl;
+}
+
+// ---------------------------------------------------------------------------
+// Relativistic pushers (Sec. III "Particle motion"), c = 1.
+// qmdt = q dt / m.  u: proper velocity at t - dt/2 in, t + dt/2 out.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void push_vay(R qmdt, const R (&E)[3], const R (&B)[3], R (&u)[3]) {
+    R ginv = R(1) / sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    R h = R(0.5) * qmdt;
+    R tx = h * B[0], ty = h * B[1], tz = h * B[2];
+    // u' = u + qdt/m E + v x tau
+    R vx = u[0] * ginv, vy = u[1] * ginv, vz = u[2] * ginv;
+    R px = u[0] + qmdt * E[0] + (vy * tz - vz * ty);
+    R py = u[1] + qmdt * E[1] + (vz * tx - vx * tz);
+    R pz = u[2] + qmdt * E[2] + (vx * ty - vy * tx);
+    R tau2 = tx * tx + ty * ty + tz * tz;
+    R us = px * tx + py * ty + pz * tz;
+    R sigma = R(1) + px * px + py * py + pz * pz - tau2;
+    R gnew = sqrt(R(0.5) * (sigma + sqrt(sigma * sigma + R(4) * (tau2 + us * us))));
+    R gi = R(1) / gnew;
+    tx *= gi; ty *= gi; tz *= gi;
+    R s = R(1) / (R(1) + tx * tx + ty * ty + tz * tz);
+    R pt = px * tx + py * ty + pz * tz;
+    u[0] = s * (px + pt * tx + (py * tz - pz * ty));
+    u[1] = s * (py + pt * ty + (pz * tx - px * tz));
+    u[2] = s * (pz + pt * tz + (px * ty - py * tx));
+}
+
+template <typename R>
+__device__ __forceinline__ void push_boris(R qmdt, const R (&E)[3], const R (&B)[3], R (&u)[3]) {
+    R h = R(0.5) * qmdt;
+    R mx = u[0] + h * E[0], my = u[1] + h * E[1], mz = u[2] + h * E[2];
+    R gi = R(1) / sqrt(R(1) + mx * mx + my * my + mz * mz);
+    R tx = h * B[0] * gi, ty = h * B[1] * gi, tz = h * B[2] * gi;
+    R ax = mx + (my * tz - mz * ty);
+    R ay = my + (mz * tx - mx * tz);
+    R az = mz + (mx * ty - my * tx);
+    R f = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
+    R sx = f * tx, sy = f * ty, sz = f * tz;
+    u[0] = mx + (ay * sz - az * sy) + h * E[0];
+    u[1] = my + (az * sx - ax * sz) + h * E[1];
+    u[2] = mz + (ax * sy - ay * sx) + h * E[2];
+}
+
+// ---------------------------------------------------------------------------
+// Gather of one staggered component (eq:pfields): separable triple sum over
+// the (O+1)^3 support, x innermost.  Acc::F(kind, comp, i, j, k) reads the
+// field at frame indices; kind 0 = E, 1 = B.
+// ---------------------------------------------------------------------------
+template <int O, typename R, class Acc>
+__device__ __forceinline__ R gather_one(const Acc &acc, int kind, int comp, int i0, int j0, int k0,
+                                        const R (&wx)[O + 1], const R (&wy)[O + 1], const R (&wz)[O + 1]) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k <= O; ++k) {
+        R sy = R(0);
+#pragma unroll
+        for (int j = 0; j <= O; ++j) {
+            R sx = R(0);
+#pragma unroll
+            for (int i = 0; i <= O; ++i) sx += wx[i] * acc.F(kind, comp, i0 + i, j0 + j, k0 + k);
+            sy += wy[j] * sx;
+        }
+        s += wz[k] * sy;
+    }
+    return s;
+}
+
+template <int O, typename R, class Acc>
+__device__ __forceinline__ void gather_EB(const Acc &acc, const R (&xi)[3], R (&E)[3], R (&B)[3]) {
+    R wI[3][O + 1], wH[3][O + 1];
+    int iI[3], iH[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        iI[a] = support<O, R>(xi[a], false, wI[a]);
+        iH[a] = support<O, R>(xi[a], true, wH[a]);
+    }
+    // E_a: half-integer along a; B_a: integer along a, half-integer across.
+    E[0] = gather_one<O, R>(acc, 0, 0, iH[0], iI[1], iI[2], wH[0], wI[1], wI[2]);
+    E[1] = gather_one<O, R>(acc, 0, 1, iI[0], iH[1], iI[2], wI[0], wH[1], wI[2]);
+    E[2] = gather_one<O, R>(acc, 0, 2, iI[0], iI[1], iH[2], wI[0], wI[1], wH[2]);
+    B[0] = gather_one<O, R>(acc, 1, 0, iI[0], iH[1], iH[2], wI[0], wH[1], wH[2]);
+    B[1] = gather_one<O, R>(acc, 1, 1, iH[0], iI[1], iH[2], wH[0], wI[1], wH[2]);
+    B[2] = gather_one<O, R>(acc, 1, 2, iH[0], iH[1], iI[2], wH[0], wH[1], wI[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Charge-conserving deposit of one particle (Sec. III, eq:cc1 / eq:jj3 with
+// Esirkepov's decomposition) written directly as the 2nd-order current:
+// J_a(face lo_a+m+1/2, lo_b+mb, lo_c+mc) = jscale_a * C_a[m] * Y_a[mb][mc],
+// C_a[m] = sum_{m' <= m} dS_a[m'] (the per-particle prefix sum along a),
+// Y_a = S0_b S0_c + dS_b S0_c / 2 + S0_b dS_c / 2 + dS_b dS_c / 3,
+// jscale_a = -q w dx_a / dt.  xi0/xi1: old/new position in the frame of Acc.
+// Acc::addJ(comp, i, j, k, v) accumulates into the current of the frame.
+// ---------------------------------------------------------------------------
+template <int O, typename R, class Acc>
+__device__ __forceinline__ void deposit_esirkepov(Acc &acc, const R (&xi0)[3], const R (&xi1)[3],
+                                                  const R (&jscale)[3]) {
+    constexpr int S = O + 2;
+    R S0[3][S], DS[3][S];
+    int lo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R wo[O + 1], wn[O + 1];
+        int io = support<O, R>(xi0[a], false, wo);
+        int in = support<O, R>(xi1[a], false, wn);
+        int l = io < in ? io : in;
+        bool so = io != l, sn = in != l;
+#pragma unroll
+        for (int m = 0; m < S; ++m) {
+            R a0 = so ? (m >= 1 ? wo[m - 1] : R(0)) : (m <= O ? wo[m] : R(0));
+            R a1 = sn ? (m >= 1 ? wn[m - 1] : R(0)) : (m <= O ? wn[m] : R(0));
+            S0[a][m] = a0;
+            DS[a][m] = a1 - a0;
+        }
+        lo[a] = l;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        R C[O + 1];
+        R run = R(0);
+#pragma unroll
+        for (int m = 0; m <= O; ++m) {
+            run += DS[a][m];
+            C[m] = run * jscale[a];
+        }
+#pragma unroll
+        for (int mc = 0; mc < S; ++mc) {
+            R p = S0[c][mc] + R(0.5) * DS[c][mc];
+            R q = R(0.5) * S0[c][mc] + R(1.0 / 3.0) * DS[c][mc];
+#pragma unroll
+            for (int mb = 0; mb < S; ++mb) {
+                R Y = S0[b][mb] * p + DS[b][mb] * q;
+                if (Y == R(0)) continue;
+#pragma unroll
+                for (int m = 0; m <= O; ++m) {
+                    R v = C[m] * Y;
+                    if (v == R(0)) continue;
+                    int idx[3];
+                    idx[a] = lo[a] + m;
+                    idx[b] = lo[b] + mb;
+                    idx[c] = lo[c] + mc;
+                    acc.addJ(a, idx[0], idx[1], idx[2], v);
+                }
+            }
+        }
+    }
+}
+
+// Charge weights of one particle on the integer nodes (eq:rho2).
+template <int O, typename R, class Acc>
+__device__ __forceinline__ void deposit_rho(Acc &acc, const R (&xi)[3], R qw) {
+    R w[3][O + 1];
+    int i0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) i0[a] = support<O, R>(xi[a], false, w[a]);
+#pragma unroll
+    for (int k = 0; k <= O; ++k)
+#pragma unroll
+        for (int j = 0; j <= O; ++j)
+#pragma unroll
+            for (int i = 0; i <= O; ++i) acc.addRho(i0[0] + i, i0[1] + j, i0[2] + k, qw * w[0][i] * w[1][j] * w[2][k]);
+}
+
+// ---------------------------------------------------------------------------
+// Context (host side)
+// ---------------------------------------------------------------------------
+struct Species {
+    double q, m, w;
+    int64_t cap = 0, n = 0;   // allocated slots (rounded up to 64) and particles held
+    int64_t limit = 0;        // capacity requested by the caller
+    // PP_FP64: positions in cell units xi = x/dx in [0, n); momenta
+    double *x = nullptr, *y = nullptr, *z = nullptr, *ux = nullptr, *uy = nullptr, *uz = nullptr;
+    // PP_MIXED32: packed cell (x | y << 10 | z << 20) + FP32 offsets and momenta
+    int32_t *cell = nullptr;
+    float *ox = nullptr, *oy = nullptr, *oz = nullptr, *fux = nullptr, *fuy = nullptr, *fuz = nullptr;
+    void *buf = nullptr;      // primary particle storage
+    void *alt = nullptr;      // sort target of the same layout
+    int32_t *keys = nullptr;  // sort keys
+    int32_t *cell_start = nullptr; // offsets per sort key (nkeys + 1), valid after a sort
+    bool sorted = false;
+};
+
+enum Phase { PH_PARTICLE = 0, PH_CURRENT = 1, PH_FIELD = 2, PH_SORT = 3, PH_N = 4 };
+
+struct EventPair {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+struct Ctx {
+    pp_grid_desc d;
+    cudaStream_t st = nullptr;
+    Geom g;
+    bool fp64 = true;
+    size_t rsz = 8;
+    void *mesh = nullptr;
+    void *E[3], *B[3], *J[3], *Jt[3], *R[3], *Xa[3], *Xb[3];
+    double *rho = nullptr;   // compact FP64 charge density (diagnostics)
+    double *G0 = nullptr;    // compact FP64 Gauss reference
+    bool have_G0 = false;
+    // high-order current: symmetric circulant taps of the inverse of the
+    // (c, b+c, a+b+c, b+c, c) line operator, per axis
+    double *taps = nullptr;  // device, 3 x kMaxTaps
+    int ntaps[3] = {0, 0, 0};
+    bool full_circ[3] = {false, false, false};
+    // field solve
+    double fd[3];            // a, b, c
+    double lap[6];           // 1D stencil of d^+ d^- at offsets 0..5
+    int cheb_iters = 0;
+    double cheb_theta = 1, cheb_delta = 0;
+    int last_iters = 0;
+    // sort
+    int tile[3] = {8, 8, 8};
+    int ntile[3] = {1, 1, 1};
+    int64_t nkeys = 0;
+    int32_t *counts = nullptr;   // nkeys + 1
+    void *scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
+    int since_sort = 0;
+    // status
+    int *d_status = nullptr;
+    int *h_status = nullptr;     // pinned mirror
+    unsigned long long *d_nslow = nullptr;
+    // reductions
+    double *d_red = nullptr;     // partials
+    double *d_out = nullptr;     // final values
+    int64_t step = 0;
+    // profiling (pp_profile_enable / pp_profile_read)
+    bool prof = false;
+    EventPair *prof_ev = nullptr;
+    int prof_n = 0, prof_cap = 0;
+    double prof_ms[PH_N] = {0, 0, 0, 0};
+    int64_t prof_particle_launches = 0, prof_steps = 0;
+    int64_t nlaunch = 0;          // kernels enqueued (counted by the launchers)
+    int nspecies = 0;
+    Species sp[PP_MAX_SPECIES];
+    char err[512] = {0};
+};
+
+constexpr int kMaxTaps = 64;
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files); all enqueue on c.st.
+// ---------------------------------------------------------------------------
+cudaError_t launch_particles_fp64(Ctx &c, int s);
+cudaError_t launch_particles_mixed_global(Ctx &c, int s);
+cudaError_t launch_particles_mixed_tiled(Ctx &c, int s);
+bool tiled_supported(const Ctx &c);
+cudaError_t launch_rho(Ctx &c);
+cudaError_t launch_kinetic(Ctx &c, double *out_per_species);
+
+cudaError_t launch_zero_J(Ctx &c);
+cudaError_t launch_fold_J(Ctx &c);
+cudaError_t launch_current_solve(Ctx &c);
+cudaError_t launch_field_update(Ctx &c);
+cudaError_t launch_ghost_fill(Ctx &c, void *const src_E[3], void *const src_B[3]);
+cudaError_t launch_mesh_diag(Ctx &c, double *host_out /* 9 values */);
+
+cudaError_t launch_sort(Ctx &c, int s);
+cudaError_t sort_setup(Ctx &c);
+
+cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const double *x, const double *y,
+                              const double *z, const double *ux, const double *uy, const double *uz);
+cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, double *ux, double *uy,
+                               double *uz);
+cudaError_t launch_check_finite(Ctx &c, int64_t n, const double *const *arrs, int narr, int *flag);
+
+}  // namespace pp

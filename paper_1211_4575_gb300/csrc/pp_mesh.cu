@@ -1,0 +1,465 @@
+// pp_mesh.cu -- mesh kernels of the step: periodic ghost fold of the deposited
+// current, the high-order current solve (Sec. III eq:jj6 .. eq:penta), the
+// implicit de-centred field update (eq:bnplus1, eq:enplus1, eq:EllipticB),
+// the periodic ghost fill of E and B, and the FP64 mesh diagnostics.
+//
+// Mesh arrays are padded (Geom::at); stencils read interior values through
+// periodic wrapping, so only E and B (read by the particle gather) need their
+// ghost layers filled.
+#include "pp_internal.cuh"
+
+namespace pp {
+
+__device__ __forceinline__ void unflatten(int64_t t, const Geom &g, int &i, int &j, int &k) {
+    i = (int)(t % g.n[0]);
+    int64_t r = t / g.n[0];
+    j = (int)(r % g.n[1]);
+    k = (int)(r / g.n[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Ghost fold: every interior node collects the ghost images of itself along
+// one axis (coordinate + m*n, m != 0, inside the padding) and the ghosts are
+// cleared.  Passes x, y, z in turn; each ghost is read by exactly one thread.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_fold_axis(Geom g, R *J0, R *J1, R *J2, int axis, int lo0, int lo1, int lo2, int e0, int e1,
+                            int e2) {
+    int64_t total = (int64_t)e0 * e1 * e2;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int c[3];
+    c[0] = lo0 + (int)(t % e0);
+    int64_t r = t / e0;
+    c[1] = lo1 + (int)(r % e1);
+    c[2] = lo2 + (int)(r / e1);
+    R *Js[3] = {J0, J1, J2};
+    int n = g.n[axis];
+    int64_t base = g.at(c[0], c[1], c[2]);
+    int64_t stride = axis == 0 ? 1 : (axis == 1 ? (int64_t)g.P[0] : (int64_t)g.P[0] * g.P[1]);
+    int x = c[axis];
+    for (int comp = 0; comp < 3; ++comp) {
+        R *J = Js[comp];
+        R acc = J[base];
+        for (int m = -((g.G + n - 1) / n); m <= (g.G + n - 1) / n; ++m) {
+            if (m == 0) continue;
+            int y = x + m * n;
+            if (y < -g.G || y >= n + g.G) continue;
+            int64_t q = base + (int64_t)(y - x) * stride;
+            acc += J[q];
+            J[q] = R(0);
+        }
+        J[base] = acc;
+    }
+}
+
+template <typename R>
+static cudaError_t fold_impl(Ctx &c) {
+    const Geom &g = c.g;
+    int G = g.G;
+    R *J0 = (R *)c.J[0], *J1 = (R *)c.J[1], *J2 = (R *)c.J[2];
+    // x pass over padded y, z; y pass over interior x, padded z; z pass over interior x, y
+    int lo[3][3] = {{0, -G, -G}, {0, 0, -G}, {0, 0, 0}};
+    int ex[3][3] = {{g.n[0], g.n[1] + 2 * G, g.n[2] + 2 * G}, {g.n[0], g.n[1], g.n[2] + 2 * G}, {g.n[0], g.n[1], g.n[2]}};
+    for (int a = 0; a < 3; ++a) {
+        int64_t total = (int64_t)ex[a][0] * ex[a][1] * ex[a][2];
+        k_fold_axis<R><<<(unsigned)((total + 255) / 256), 256, 0, c.st>>>(g, J0, J1, J2, a, lo[a][0], lo[a][1], lo[a][2],
+                                                                          ex[a][0], ex[a][1], ex[a][2]);
+        ++c.nlaunch;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_fold_J(Ctx &c) { return c.fp64 ? fold_impl<double>(c) : fold_impl<float>(c); }
+
+cudaError_t launch_zero_J(Ctx &c) {
+    size_t bytes = (size_t)c.g.padded_size() * c.rsz;
+    for (int a = 0; a < 3; ++a) {
+        cudaError_t e = cudaMemsetAsync(c.J[a], 0, bytes, c.st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// High-order current: along the axis of each component, J_out = P^{-1} J_in
+// with P the symmetric cyclic line operator (c, b+c, a+b+c, b+c, c) that
+// turns the 2nd-order difference into the high-order one; applied as the
+// exact (or exponentially truncated) circulant inverse, taps precomputed in
+// FP64 on the host.  out(i) = sum_m T[m] * in(i + off + m).
+// ---------------------------------------------------------------------------
+struct TapSet {
+    const double *T[3];
+    int L[3];
+    int off[3];
+};
+
+template <typename R>
+__global__ void k_current_solve(Geom g, TapSet ts, const R *I0, const R *I1, const R *I2, R *O0, R *O1, R *O2) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int comp = blockIdx.y;
+    if (t >= g.cells()) return;
+    int c[3];
+    unflatten(t, g, c[0], c[1], c[2]);
+    const R *in = comp == 0 ? I0 : (comp == 1 ? I1 : I2);
+    R *out = comp == 0 ? O0 : (comp == 1 ? O1 : O2);
+    const double *T = ts.T[comp];
+    int L = ts.L[comp], off = ts.off[comp], n = g.n[comp];
+    int x = c[comp];
+    R acc = R(0);
+    int q[3] = {c[0], c[1], c[2]};
+    for (int m = 0; m < L; ++m) {
+        q[comp] = wrap(x + off + m, n);
+        acc += (R)__ldg(T + m) * in[g.at(q[0], q[1], q[2])];
+    }
+    out[g.at(c[0], c[1], c[2])] = acc;
+}
+
+cudaError_t launch_current_solve(Ctx &c) {
+    if (c.d.field_order == 2) return cudaSuccess;
+    TapSet ts;
+    for (int a = 0; a < 3; ++a) {
+        ts.T[a] = c.taps + a * kMaxTaps;
+        ts.L[a] = c.ntaps[a];
+        ts.off[a] = c.full_circ[a] ? 0 : -(c.ntaps[a] / 2);
+    }
+    dim3 grid((unsigned)((c.g.cells() + 255) / 256), 3);
+    if (c.fp64)
+        k_current_solve<double><<<grid, 256, 0, c.st>>>(c.g, ts, (double *)c.J[0], (double *)c.J[1], (double *)c.J[2],
+                                                        (double *)c.Jt[0], (double *)c.Jt[1], (double *)c.Jt[2]);
+    else
+        k_current_solve<float><<<grid, 256, 0, c.st>>>(c.g, ts, (float *)c.J[0], (float *)c.J[1], (float *)c.J[2],
+                                                       (float *)c.Jt[0], (float *)c.Jt[1], (float *)c.Jt[2]);
+    ++c.nlaunch;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int a = 0; a < 3; ++a) {
+        void *t = c.J[a];
+        c.J[a] = c.Jt[a];
+        c.Jt[a] = t;
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Field update.  Staggered first differences (Sec. III):
+//   d^+ f (i+1/2) = sum_m k_m (f[i+m] - f[i+1-m]) / h
+//   d^- f (i)     = sum_m k_m (f[i+m-1] - f[i-m]) / h
+// and the Laplacian sum_a d^+_a d^-_a as the symmetric 11-point stencil lap[].
+// ---------------------------------------------------------------------------
+struct FieldCoef {
+    double k[3];      // a, b, c
+    double lap[6];    // offsets 0..5 of the 1D d^+ d^- stencil (times 1)
+    double ih[3];     // 1/h per axis
+    double ih2[3];    // 1/h^2 per axis
+};
+
+template <typename R>
+struct Nb {
+    const Geom &g;
+    int c[3];
+    __device__ __forceinline__ R at(const R *f, int axis, int s) const {
+        int q[3] = {c[0], c[1], c[2]};
+        q[axis] = wrap(c[axis] + s, g.n[axis]);
+        return f[g.at(q[0], q[1], q[2])];
+    }
+    __device__ __forceinline__ R dplus(const R *f, int axis, const FieldCoef &k) const {
+        R s = R(0);
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) s += (R)k.k[m - 1] * (at(f, axis, m) - at(f, axis, 1 - m));
+        return s * (R)k.ih[axis];
+    }
+    __device__ __forceinline__ R dminus(const R *f, int axis, const FieldCoef &k) const {
+        R s = R(0);
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) s += (R)k.k[m - 1] * (at(f, axis, m - 1) - at(f, axis, -m));
+        return s * (R)k.ih[axis];
+    }
+    __device__ __forceinline__ R lap(const R *f, const FieldCoef &k) const {
+        R center = f[g.at(c[0], c[1], c[2])];
+        R s = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R sa = (R)k.lap[0] * center;
+#pragma unroll
+            for (int o = 1; o <= 5; ++o) sa += (R)k.lap[o] * (at(f, a, o) + at(f, a, -o));
+            s += sa * (R)k.ih2[a];
+        }
+        return s;
+    }
+};
+
+template <typename R>
+struct Vec3 {
+    const R *p[3];
+};
+
+// rhs_a = B_a + alpha beta dt^2 (L B)_a - dt (curl^+ E)_a + alpha dt^2 (curl^+ J)_a
+// (eq:EllipticB; the current term's sign follows from eq:bnplus1 + eq:enplus1)
+template <typename R>
+__global__ void k_rhs(Geom g, FieldCoef k, Vec3<R> E, Vec3<R> B, Vec3<R> J, R *O0, R *O1, R *O2, R ab_dt2,
+                      R dt, R a_dt2) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    Nb<R> nb{g, {0, 0, 0}};
+    unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
+    int64_t q = g.at(nb.c[0], nb.c[1], nb.c[2]);
+    R *out[3] = {O0, O1, O2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        R curlE = nb.dplus(E.p[c], b, k) - nb.dplus(E.p[b], c, k);
+        R curlJ = nb.dplus(J.p[c], b, k) - nb.dplus(J.p[b], c, k);
+        out[a][q] = B.p[a][q] + ab_dt2 * nb.lap(B.p[a], k) - dt * curlE + a_dt2 * curlJ;
+    }
+}
+
+// One Chebyshev semi-iteration step for (1 - kk L) x = rhs:
+// x_new = x + c1 (x - x_prev) + c2 (rhs - x + kk L x); x_new may alias x_prev.
+template <typename R>
+__global__ void k_cheb(Geom g, FieldCoef k, Vec3<R> X, Vec3<R> Xp, Vec3<R> Rh, R *O0, R *O1, R *O2, R kk, R c1,
+                       R c2) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    Nb<R> nb{g, {0, 0, 0}};
+    unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
+    int64_t q = g.at(nb.c[0], nb.c[1], nb.c[2]);
+    R *out[3] = {O0, O1, O2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R x = X.p[a][q];
+        R r = Rh.p[a][q] - x + kk * nb.lap(X.p[a], k);
+        R xp = Xp.p[a][q];
+        out[a][q] = x + c1 * (x - xp) + c2 * r;
+    }
+}
+
+// E_new = E + dt (curl^- (alpha B_new + beta B_old) - J)   (eq:enplus1, c^2 mu0 = 1)
+template <typename R>
+struct MixB {
+    const R *Bn, *Bo;
+    R al, be;
+};
+
+template <typename R>
+__global__ void k_e_update(Geom g, FieldCoef k, R *E0, R *E1, R *E2, Vec3<R> Bn, Vec3<R> Bo, Vec3<R> J, R alpha,
+                           R beta, R dt) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    Nb<R> nb{g, {0, 0, 0}};
+    unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
+    int64_t q = g.at(nb.c[0], nb.c[1], nb.c[2]);
+    R *E[3] = {E0, E1, E2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        R cur = alpha * (nb.dminus(Bn.p[c], b, k) - nb.dminus(Bn.p[b], c, k)) +
+                beta * (nb.dminus(Bo.p[c], b, k) - nb.dminus(Bo.p[b], c, k));
+        E[a][q] = E[a][q] + dt * (cur - J.p[a][q]);
+    }
+}
+
+// Periodic ghost fill of E (from its own interior) and B (from src, which may
+// be a different array than B: the converged relaxation iterate).
+template <typename R>
+__global__ void k_ghost_fill(Geom g, R *E0, R *E1, R *E2, const R *S0, const R *S1, const R *S2, R *B0, R *B1, R *B2,
+                             int e_ghost_only) {
+    int64_t total = g.padded_size();
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i = (int)(t % g.P[0]);
+    int64_t r = t / g.P[0];
+    int j = (int)(r % g.P[1]);
+    int k = (int)(r / g.P[1]);
+    int ci = i - g.G, cj = j - g.G, ck = k - g.G;
+    bool ghost = ci < 0 || cj < 0 || ck < 0 || ci >= g.n[0] || cj >= g.n[1] || ck >= g.n[2];
+    int64_t src = g.at(wrap(ci, g.n[0]), wrap(cj, g.n[1]), wrap(ck, g.n[2]));
+    if (ghost || !e_ghost_only) {
+        E0[t] = E0[src]; E1[t] = E1[src]; E2[t] = E2[src];
+    }
+    B0[t] = S0[src]; B1[t] = S1[src]; B2[t] = S2[src];
+}
+
+template <typename R>
+static Vec3<R> v3(void *const p[3]) {
+    return Vec3<R>{{(const R *)p[0], (const R *)p[1], (const R *)p[2]}};
+}
+
+static FieldCoef field_coef(const Ctx &c) {
+    FieldCoef k;
+    double h[3] = {c.d.dx, c.d.dy, c.d.dz};
+    for (int m = 0; m < 3; ++m) k.k[m] = c.fd[m];
+    for (int m = 0; m < 6; ++m) k.lap[m] = c.lap[m];
+    for (int a = 0; a < 3; ++a) {
+        k.ih[a] = 1.0 / h[a];
+        k.ih2[a] = 1.0 / (h[a] * h[a]);
+    }
+    return k;
+}
+
+template <typename R>
+static cudaError_t field_update_impl(Ctx &c) {
+    const Geom &g = c.g;
+    FieldCoef k = field_coef(c);
+    unsigned blocks = (unsigned)((g.cells() + 255) / 256);
+    double al = c.d.alpha, be = 1.0 - c.d.alpha, dt = c.d.dt;
+    double kk = al * al * dt * dt;
+    cudaError_t e;
+    k_rhs<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.J), (R *)c.R[0], (R *)c.R[1], (R *)c.R[2],
+                                       (R)(al * be * dt * dt), (R)dt, (R)(al * dt * dt));
+    ++c.nlaunch;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Chebyshev semi-iteration on the spectrum [1, lmax] of the SPD operator,
+    // starting from B^n (Saad, Iterative Methods, Alg. 12.1 in 3-term form).
+    double theta = c.cheb_theta, delta = c.cheb_delta;
+    void **cur = c.B, **prev = c.B;
+    void **bufs[2] = {c.Xa, c.Xb};
+    int nb = 0;
+    double rho_prev = delta > 0 ? delta / theta : 0.0;
+    for (int it = 0; it < c.cheb_iters; ++it) {
+        double c1, c2;
+        if (it == 0) {
+            c1 = 0.0;
+            c2 = 1.0 / theta;
+        } else {
+            double sigma = theta / delta;
+            double rho = 1.0 / (2.0 * sigma - rho_prev);
+            c1 = rho * rho_prev;
+            c2 = 2.0 * rho / delta;
+            rho_prev = rho;
+        }
+        // output: a scratch buffer that is neither cur nor (when prev is B) B
+        void **out = (prev == c.B || prev == cur) ? bufs[nb] : prev;
+        if (out == cur) out = bufs[1 - nb];
+        k_cheb<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(cur), v3<R>(prev), v3<R>(c.R), (R *)out[0], (R *)out[1],
+                                            (R *)out[2], (R)kk, (R)c1, (R)c2);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        prev = cur;
+        cur = out;
+        nb = (out == bufs[0]) ? 1 : 0;
+    }
+    c.last_iters = c.cheb_iters;
+    // eq:enplus1 with B^{n+1} = cur, B^n = B
+    k_e_update<R><<<blocks, 256, 0, c.st>>>(g, k, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], v3<R>(cur), v3<R>(c.B),
+                                            v3<R>(c.J), (R)al, (R)be, (R)dt);
+    ++c.nlaunch;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned pblocks = (unsigned)((g.padded_size() + 255) / 256);
+    k_ghost_fill<R><<<pblocks, 256, 0, c.st>>>(g, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], (const R *)cur[0],
+                                               (const R *)cur[1], (const R *)cur[2], (R *)c.B[0], (R *)c.B[1],
+                                               (R *)c.B[2], 1);
+    ++c.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_update(Ctx &c) { return c.fp64 ? field_update_impl<double>(c) : field_update_impl<float>(c); }
+
+template <typename R>
+static cudaError_t ghost_fill_impl(Ctx &c, void *const sE[3], void *const sB[3]) {
+    (void)sE;
+    unsigned pblocks = (unsigned)((c.g.padded_size() + 255) / 256);
+    k_ghost_fill<R><<<pblocks, 256, 0, c.st>>>(c.g, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], (const R *)sB[0],
+                                               (const R *)sB[1], (const R *)sB[2], (R *)c.B[0], (R *)c.B[1],
+                                               (R *)c.B[2], 1);
+    ++c.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_fill(Ctx &c, void *const sE[3], void *const sB[3]) {
+    return c.fp64 ? ghost_fill_impl<double>(c, sE, sB) : ghost_fill_impl<float>(c, sE, sB);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 mesh diagnostics: sums (energies, charge) and maxima (|rho|, Gauss
+// residual, its drift from G_0, div B, relaxation residual, |rhs|).
+// ---------------------------------------------------------------------------
+constexpr int kDiagSums = 4, kDiagMax = 6, kDiagN = kDiagSums + kDiagMax;
+
+template <typename R>
+__global__ void k_mesh_diag(Geom g, FieldCoef k, Vec3<R> E, Vec3<R> B, Vec3<R> Rh, const double *rho, double *G0,
+                            int capture, double kk, double *partial) {
+    double v[kDiagN];
+    for (int m = 0; m < kDiagN; ++m) v[m] = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.cells(); t += (int64_t)gridDim.x * blockDim.x) {
+        Nb<R> nb{g, {0, 0, 0}};
+        unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
+        int64_t q = g.at(nb.c[0], nb.c[1], nb.c[2]);
+        double e0 = E.p[0][q], e1 = E.p[1][q], e2 = E.p[2][q];
+        double b0 = B.p[0][q], b1 = B.p[1][q], b2 = B.p[2][q];
+        v[0] += 0.5 * (e0 * e0 + e1 * e1 + e2 * e2);
+        v[1] += 0.5 * (b0 * b0 + b1 * b1 + b2 * b2);
+        v[2] += 0.5 * e0 * e0;
+        double r = rho[t];
+        v[3] += r;
+        double divE = 0.0, divB = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            divE += (double)nb.dminus(E.p[a], a, k);
+            divB += (double)nb.dplus(B.p[a], a, k);
+        }
+        double G = divE - r;
+        if (capture) G0[t] = G;
+        v[4] = fmax(v[4], fabs(r));
+        v[5] = fmax(v[5], fabs(G));
+        v[6] = fmax(v[6], fabs(G - G0[t]));
+        v[7] = fmax(v[7], fabs(divB));
+        for (int a = 0; a < 3; ++a) {
+            double res = (double)Rh.p[a][q] - ((double)B.p[a][q] - kk * (double)nb.lap(B.p[a], k));
+            v[8] = fmax(v[8], fabs(res));
+            v[9] = fmax(v[9], fabs((double)Rh.p[a][q]));
+        }
+    }
+    __shared__ double sh[kDiagN][256];
+    for (int m = 0; m < kDiagN; ++m) sh[m][threadIdx.x] = v[m];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int m = 0; m < kDiagN; ++m) {
+                double a = sh[m][threadIdx.x], b = sh[m][threadIdx.x + s];
+                sh[m][threadIdx.x] = m < kDiagSums ? a + b : fmax(a, b);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int m = 0; m < kDiagN; ++m) partial[(int64_t)blockIdx.x * kDiagN + m] = sh[m][0];
+}
+
+__global__ void k_diag_final(const double *partial, int nblk, double *out) {
+    int m = threadIdx.x;
+    if (m >= kDiagN) return;
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        double v = partial[(int64_t)b * kDiagN + m];
+        acc = m < kDiagSums ? acc + v : fmax(acc, v);
+    }
+    out[m] = acc;
+}
+
+constexpr int kDiagBlocks = 512;
+
+template <typename R>
+static cudaError_t mesh_diag_impl(Ctx &c, double *host_out) {
+    FieldCoef k = field_coef(c);
+    int capture = c.have_G0 ? 0 : 1;
+    double kk = c.d.alpha * c.d.alpha * c.d.dt * c.d.dt;
+    int64_t want = (c.g.cells() + 255) / 256;
+    int nblk = (int)(want < kDiagBlocks ? want : kDiagBlocks);
+    k_mesh_diag<R><<<nblk, 256, 0, c.st>>>(c.g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.R), c.rho, c.G0, capture, kk, c.d_red);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_diag_final<<<1, 32, 0, c.st>>>(c.d_red, nblk, c.d_out);
+    c.nlaunch += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(host_out, c.d_out, sizeof(double) * kDiagN, cudaMemcpyDeviceToHost, c.st);
+    if (e != cudaSuccess) return e;
+    c.have_G0 = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mesh_diag(Ctx &c, double *host_out) {
+    return c.fp64 ? mesh_diag_impl<double>(c, host_out) : mesh_diag_impl<float>(c, host_out);
+}
+
+}  // namespace pp

@@ -1,0 +1,233 @@
+// pp_sort.cu -- counting sort of a species' particle arrays by cell (Sec. III:
+// between the current deposit and the field update the particles are "sorted
+// sequentially according to the cell position" for cache locality).
+//
+// The key of a particle is its cell, numbered tile by tile (tiles of up to
+// 8x8x8 cells, x fastest inside a tile and across tiles), so that the sorted
+// arrays hold every tile as one contiguous range.  Pipeline: key + histogram
+// (warp-aggregated atomics) -> exclusive scan -> scatter through per-key
+// cursors.  The order inside a cell is not deterministic.
+#include "pp_internal.cuh"
+
+namespace pp {
+
+struct KeyGeom {
+    int n[3];
+    int T[3];
+    int nt[3];
+    int64_t tile_vol;
+};
+
+__device__ __forceinline__ int32_t cell_key(const KeyGeom &k, int x, int y, int z) {
+    int tx = x / k.T[0], ty = y / k.T[1], tz = z / k.T[2];
+    int lx = x - tx * k.T[0], ly = y - ty * k.T[1], lz = z - tz * k.T[2];
+    int64_t tile = ((int64_t)tz * k.nt[1] + ty) * k.nt[0] + tx;
+    return (int32_t)(tile * k.tile_vol + ((int64_t)lz * k.T[1] + ly) * k.T[0] + lx);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Returns, for every calling lane, a slot from *counter reserved jointly by all
+// active lanes with the same key (one atomic per distinct key per warp).
+__device__ __forceinline__ int32_t aggregated_add(int32_t *base, int32_t key) {
+    unsigned active = __activemask();
+    unsigned peers = __match_any_sync(active, key);
+    int leader = __ffs(peers) - 1;
+    int rank = __popc(peers & lanemask_lt());
+    int32_t b = 0;
+    if ((int)(threadIdx.x & 31) == leader) b = atomicAdd(base + key, __popc(peers));
+    b = __shfl_sync(peers, b, leader);
+    return b + rank;
+}
+
+__global__ void k_keys_fp64(KeyGeom kg, int64_t n, const double *x, const double *y, const double *z, int32_t *keys,
+                            int32_t *counts) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int cx = (int)floor(x[t]), cy = (int)floor(y[t]), cz = (int)floor(z[t]);
+    cx = min(max(cx, 0), kg.n[0] - 1);
+    cy = min(max(cy, 0), kg.n[1] - 1);
+    cz = min(max(cz, 0), kg.n[2] - 1);
+    int32_t key = cell_key(kg, cx, cy, cz);
+    keys[t] = key;
+    aggregated_add(counts, key);
+}
+
+__global__ void k_keys_mixed(KeyGeom kg, int64_t n, const int32_t *cell, int32_t *keys, int32_t *counts) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int32_t c = cell[t];
+    int32_t key = cell_key(kg, c & 1023, (c >> 10) & 1023, (c >> 20) & 1023);
+    keys[t] = key;
+    aggregated_add(counts, key);
+}
+
+// ---- exclusive scan of int32 counts (multi-level, 2048 values per block) ----
+constexpr int kScanThreads = 256, kScanPer = 8, kScanChunk = kScanThreads * kScanPer;
+
+__global__ void k_scan_block(const int32_t *in, int32_t *out, int64_t n, int32_t *sums) {
+    __shared__ int32_t sh[kScanThreads];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+    int32_t v[kScanPer];
+    int32_t local = 0;
+#pragma unroll
+    for (int m = 0; m < kScanPer; ++m) {
+        int64_t q = base + m;
+        v[m] = q < n ? in[q] : 0;
+        local += v[m];
+    }
+    sh[threadIdx.x] = local;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        int32_t a = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += a;
+        __syncthreads();
+    }
+    int32_t run = sh[threadIdx.x] - local;   // exclusive prefix of this thread
+#pragma unroll
+    for (int m = 0; m < kScanPer; ++m) {
+        int64_t q = base + m;
+        if (q < n) out[q] = run;
+        run += v[m];
+    }
+    if (threadIdx.x == kScanThreads - 1 && sums) sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+__global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *sums) {
+    int64_t q = (int64_t)blockIdx.x * kScanChunk + threadIdx.x;
+    int32_t add = sums[blockIdx.x];
+    for (int m = 0; m < kScanPer; ++m, q += kScanThreads)
+        if (q < n) out[q] += add;
+}
+
+// tmp must hold the block sums of every level (sum of ceil(n / 2048^l)).
+static cudaError_t scan(cudaStream_t st, const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, int64_t &nl) {
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb <= 1) {
+        k_scan_block<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        ++nl;
+        return cudaGetLastError();
+    }
+    k_scan_block<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, tmp);
+    ++nl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan(st, tmp, tmp, nb, tmp + nb, nl);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, tmp);
+    ++nl;
+    return cudaGetLastError();
+}
+
+static size_t scan_tmp_count(int64_t n) {
+    size_t total = 0;
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    while (nb > 1) {
+        total += (size_t)nb;
+        nb = (nb + kScanChunk - 1) / kScanChunk;
+    }
+    return total + 1;
+}
+
+template <typename T>
+__device__ __forceinline__ void mv(const T *src, T *dst, int64_t from, int64_t to) {
+    dst[to] = src[from];
+}
+
+__global__ void k_scatter_fp64(int64_t n, const int32_t *keys, int32_t *cursor, const double *x, const double *y,
+                               const double *z, const double *ux, const double *uy, const double *uz, double *x2,
+                               double *y2, double *z2, double *ux2, double *uy2, double *uz2) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int64_t p = aggregated_add(cursor, keys[t]);
+    mv(x, x2, t, p); mv(y, y2, t, p); mv(z, z2, t, p);
+    mv(ux, ux2, t, p); mv(uy, uy2, t, p); mv(uz, uz2, t, p);
+}
+
+__global__ void k_scatter_mixed(int64_t n, const int32_t *keys, int32_t *cursor, const int32_t *cell, const float *ox,
+                                const float *oy, const float *oz, const float *ux, const float *uy, const float *uz,
+                                int32_t *cell2, float *ox2, float *oy2, float *oz2, float *ux2, float *uy2,
+                                float *uz2) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int64_t p = aggregated_add(cursor, keys[t]);
+    mv(cell, cell2, t, p);
+    mv(ox, ox2, t, p); mv(oy, oy2, t, p); mv(oz, oz2, t, p);
+    mv(ux, ux2, t, p); mv(uy, uy2, t, p); mv(uz, uz2, t, p);
+}
+
+static KeyGeom key_geom(const Ctx &c) {
+    KeyGeom k;
+    for (int a = 0; a < 3; ++a) {
+        k.n[a] = c.g.n[a];
+        k.T[a] = c.tile[a];
+        k.nt[a] = c.ntile[a];
+    }
+    k.tile_vol = (int64_t)c.tile[0] * c.tile[1] * c.tile[2];
+    return k;
+}
+
+cudaError_t sort_setup(Ctx &c) {
+    for (int a = 0; a < 3; ++a) {
+        c.tile[a] = c.g.n[a] < 8 ? c.g.n[a] : 8;
+        c.ntile[a] = (c.g.n[a] + c.tile[a] - 1) / c.tile[a];
+    }
+    c.nkeys = (int64_t)c.ntile[0] * c.ntile[1] * c.ntile[2] * c.tile[0] * c.tile[1] * c.tile[2];
+    cudaError_t e = cudaMalloc(&c.counts, sizeof(int32_t) * (c.nkeys + 1));
+    if (e != cudaSuccess) return e;
+    c.scan_tmp_bytes = sizeof(int32_t) * scan_tmp_count(c.nkeys + 1);
+    return cudaMalloc(&c.scan_tmp, c.scan_tmp_bytes);
+}
+
+cudaError_t launch_sort(Ctx &c, int s) {
+    Species &S = c.sp[s];
+    S.sorted = true;
+    cudaError_t e = cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
+    if (e != cudaSuccess) return e;
+    if (S.n == 0) return cudaMemsetAsync(S.cell_start, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
+    KeyGeom kg = key_geom(c);
+    unsigned blocks = (unsigned)((S.n + 255) / 256);
+    if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
+    else k_keys_mixed<<<blocks, 256, 0, c.st>>>(kg, S.n, S.cell, S.keys, c.counts);
+    ++c.nlaunch;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // cell_start = exclusive scan of counts; counts then becomes the cursor
+    if ((e = scan(c.st, c.counts, S.cell_start, c.nkeys + 1, (int32_t *)c.scan_tmp, c.nlaunch)) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(c.counts, S.cell_start, sizeof(int32_t) * (c.nkeys + 1), cudaMemcpyDeviceToDevice, c.st);
+    if (e != cudaSuccess) return e;
+    if (c.fp64) {
+        double *b = (double *)S.alt;
+        int64_t cp = S.cap;
+        k_scatter_fp64<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts, S.x, S.y, S.z, S.ux, S.uy, S.uz, b, b + cp,
+                                                 b + 2 * cp, b + 3 * cp, b + 4 * cp, b + 5 * cp);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        void *old = S.buf;
+        S.buf = S.alt;
+        S.alt = old;
+        double *p = (double *)S.buf;
+        S.x = p; S.y = p + cp; S.z = p + 2 * cp; S.ux = p + 3 * cp; S.uy = p + 4 * cp; S.uz = p + 5 * cp;
+    } else {
+        int64_t cp = S.cap;
+        int32_t *c2 = (int32_t *)S.alt;
+        float *f2 = (float *)(c2 + cp);
+        k_scatter_mixed<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts, S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz,
+                                                  c2, f2, f2 + cp, f2 + 2 * cp, f2 + 3 * cp, f2 + 4 * cp, f2 + 5 * cp);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        void *old = S.buf;
+        S.buf = S.alt;
+        S.alt = old;
+        int32_t *ci = (int32_t *)S.buf;
+        float *f = (float *)(ci + cp);
+        S.cell = ci; S.ox = f; S.oy = f + cp; S.oz = f + 2 * cp; S.fux = f + 3 * cp; S.fuy = f + 4 * cp; S.fuz = f + 5 * cp;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace pp

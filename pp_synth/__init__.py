@@ -88,7 +88,7 @@ def pair_plasma(n, d, dt, populations, seed, masses=(1.0, 1.0), cells=None) -> L
             ri = rng.random((3, c.size))
             u0 = _draw_u(rng, c.size, pop)
             u1 = _draw_u(rng, c.size, pop)
-            keep = np.isin(c, sel)
+            keep = np.isin(c, sel) if sel.size < nb else np.ones(c.size, dtype=bool)
             c = c[keep]
             ix = c % nx
             iy = (c // nx) % ny

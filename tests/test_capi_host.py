@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every entry point include/pp.h declares, the ctypes
+structures match the C layout, and descriptor validation rejects bad input
+before touching the device."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pp.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1211_4575_gb300 import build
+    build.build()
+    import paper_1211_4575_gb300 as pp
+    return pp
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(pp_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("pp_init_grid", "pp_init_species", "pp_load_particles", "pp_step", "pp_deposit",
+                 "pp_field_update", "pp_diagnostics"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = built.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in built.SIGNATURES, name
+
+
+def test_ctypes_layout_matches_c(built, tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "pp.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(pp_grid_desc), offsetof(pp_grid_desc, stream),
+         sizeof(pp_species_desc), sizeof(pp_diag), offsetof(pp_diag, n_slow), offsetof(pp_diag, relax_iters));
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    import ctypes as C
+    pp = built
+    assert vals == [C.sizeof(pp.GridDesc), pp.GridDesc.stream.offset, C.sizeof(pp.SpeciesDesc),
+                    C.sizeof(pp.Diag), pp.Diag.n_slow.offset, pp.Diag.relax_iters.offset]
+
+
+@pytest.mark.parametrize("bad", [dict(dt=0.6), dict(field_order=5), dict(alpha=0.4), dict(shape_order=0),
+                                 dict(n=(0, 8, 8)), dict(precision=3)])
+def test_descriptor_validation_without_gpu(built, bad):
+    kw = dict(n=(8, 8, 8), d=(0.5, 0.5, 0.5), dt=0.25)
+    n = bad.pop("n", kw.pop("n"))
+    dt = bad.pop("dt", kw.pop("dt"))
+    with pytest.raises(built.PPError) as ei:
+        built.Simulation(n, kw["d"], dt, stream=0, **bad)
+    assert ei.value.code == built.PP_EINVAL
