@@ -198,6 +198,7 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     chk(cudaMalloc(&c->d_red, sizeof(double) * 512 * 16), "reduction partials");
     chk(cudaMalloc(&c->d_out, sizeof(double) * (16 + PP_MAX_SPECIES)), "reduction results");
     chk(cudaMalloc(&c->d_nslow, sizeof(unsigned long long)), "fallback counter");
+    chk(cudaMalloc(&c->d_slow_count, sizeof(unsigned) * PP_MAX_SPECIES), "fallback lists");
     if (rc == PP_OK) chk(cudaMemset(c->d_nslow, 0, sizeof(unsigned long long)), "fallback counter clear");
     if (rc == PP_OK) chk(sort_setup(*c), "sort setup");
     if (rc == PP_OK) rc = setup_operators(c);
@@ -233,6 +234,7 @@ extern "C" int pp_destroy(pp_ctx *p) {
     cudaFree(c->d_red);
     cudaFree(c->d_out);
     cudaFree(c->d_nslow);
+    cudaFree(c->d_slow_count);
     if (c->h_status) cudaFreeHost(c->h_status);
     for (int q = 0; q < c->prof_cap; ++q) {
         cudaEventDestroy(c->prof_ev[q].a);
@@ -449,15 +451,21 @@ static int particle_phase(Ctx *c, int only) {
     CU(launch_zero_J(*c));
     CU(cudaMemsetAsync(c->d_nslow, 0, sizeof(unsigned long long), c->st));
     CU(prof_mark(c, PH_PARTICLE, true));
-    for (int s = 0; s < c->nspecies; ++s) {
-        if (only >= 0 && s != only) continue;
-        if (c->sp[s].n == 0) continue;
-        if (c->fp64) CU(launch_particles_fp64(*c, s));
-        else if (c->d.deposit_mode == PP_DEPOSIT_TILED ||
-                 (c->d.deposit_mode == PP_DEPOSIT_AUTO && tiled_supported(*c) && c->sp[s].sorted))
-            CU(launch_particles_mixed_tiled(*c, s));
-        else CU(launch_particles_mixed_global(*c, s));
+    bool all_sorted = true;
+    for (int s = 0; s < c->nspecies; ++s) all_sorted = all_sorted && (c->sp[s].sorted || c->sp[s].n == 0);
+    bool tiled = !c->fp64 && (c->d.deposit_mode == PP_DEPOSIT_TILED ||
+                              (c->d.deposit_mode == PP_DEPOSIT_AUTO && tiled_supported(*c) && all_sorted));
+    if (tiled && only < 0) {
+        CU(launch_particles_tiled_all(*c));
         if (c->prof) ++c->prof_particle_launches;
+    } else {
+        for (int s = 0; s < c->nspecies; ++s) {
+            if (only >= 0 && s != only) continue;
+            if (c->sp[s].n == 0) continue;
+            if (c->fp64) CU(launch_particles_fp64(*c, s));
+            else CU(launch_particles_mixed_global(*c, s));
+            if (c->prof) ++c->prof_particle_launches;
+        }
     }
     CU(prof_mark(c, PH_PARTICLE, false));
     CU(prof_mark(c, PH_CURRENT, true));

@@ -195,12 +195,25 @@ __device__ __forceinline__ void deposit_esirkepov(Acc &acc, const R (&xi0)[3], c
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
+        // C[m] = sum_{m' <= m} dS[m'] = -sum_{m' > m} dS[m'] (the support sums
+        // to zero): the upper faces use the suffix form, so a particle that
+        // stays inside its cell gets exact zeros there.
         R C[O + 1];
         R run = R(0);
 #pragma unroll
         for (int m = 0; m <= O; ++m) {
-            run += DS[a][m];
-            C[m] = run * jscale[a];
+            if (2 * m < O + 1) {
+                run += DS[a][m];
+                C[m] = run * jscale[a];
+            }
+        }
+        run = R(0);
+#pragma unroll
+        for (int m = O; m >= 0; --m) {
+            if (2 * m >= O + 1) {
+                run -= DS[a][m + 1];
+                C[m] = run * jscale[a];
+            }
         }
 #pragma unroll
         for (int mc = 0; mc < S; ++mc) {
@@ -209,7 +222,6 @@ __device__ __forceinline__ void deposit_esirkepov(Acc &acc, const R (&xi0)[3], c
 #pragma unroll
             for (int mb = 0; mb < S; ++mb) {
                 R Y = S0[b][mb] * p + DS[b][mb] * q;
-                if (Y == R(0)) continue;
 #pragma unroll
                 for (int m = 0; m <= O; ++m) {
                     R v = C[m] * Y;
@@ -300,6 +312,7 @@ struct Ctx {
     int *d_status = nullptr;
     int *h_status = nullptr;     // pinned mirror
     unsigned long long *d_nslow = nullptr;
+    unsigned *d_slow_count = nullptr;   // per species, particles left to the global-mesh kernel
     // reductions
     double *d_red = nullptr;     // partials
     double *d_out = nullptr;     // final values
@@ -323,7 +336,7 @@ constexpr int kMaxTaps = 64;
 // ---------------------------------------------------------------------------
 cudaError_t launch_particles_fp64(Ctx &c, int s);
 cudaError_t launch_particles_mixed_global(Ctx &c, int s);
-cudaError_t launch_particles_mixed_tiled(Ctx &c, int s);
+cudaError_t launch_particles_tiled_all(Ctx &c);
 bool tiled_supported(const Ctx &c);
 cudaError_t launch_rho(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c, double *out_per_species);

@@ -204,31 +204,48 @@ cudaError_t launch_particles_mixed_global(Ctx &c, int s) {
 
 // ---------------------------------------------------------------------------
 // Tiled form (mixed precision).  One CTA per 8x8x8 cell tile of the last cell
-// sort; the E/B nodes the tile's particles can touch are staged in shared
-// memory, the current is accumulated in a shared tile and flushed to the
-// global mesh once.  Thread t owns cell t of the tile and walks that cell's
-// sorted particle range, so the 32 lanes of a warp sit in 32 distinct cells
-// and their shared-memory atomics hit distinct addresses.
+// sort, all species in one launch.  The E/B nodes the tile's particles can
+// touch are staged in shared memory, the current is accumulated in a shared
+// window and flushed to the global mesh once per tile.
+//
+// Particles are streamed in chunks of kChunk: a coalesced copy into a padded
+// shared staging buffer, then thread (warp w, lane l) takes chunk slots
+// 32 l + w + W r (W warps, r < 1024 / (32 W)) -- consecutive lanes 32 sorted
+// particles apart,
+// i.e. in distinct cells, so their shared-memory atomics rarely collide --
+// and the results leave through the same buffer with coalesced stores.
 //
 // A particle may have drifted since the sort: it is handled from shared
 // memory while its cell lies within kMargin cells of the tile (minimal
-// periodic image), otherwise through the global mesh (counted in n_slow).
+// periodic image); otherwise its index is appended to a per-species list and
+// k_particles_listed advances it through the global mesh afterwards (counted
+// in n_slow).
 // ---------------------------------------------------------------------------
 constexpr int kTile = 8;                       // tile edge (cells)
+constexpr int kTileCells = kTile * kTile * kTile;
+#ifndef PP_TILED_THREADS
+#define PP_TILED_THREADS 512
+#endif
+constexpr int kThreads = PP_TILED_THREADS;     // threads per tile CTA
+constexpr int kWarps = kThreads / 32;
 constexpr int kMargin = 2;                     // drift allowed before the fallback
 constexpr int kReachLo = 2, kReachHi = 3;      // deposit/gather reach around a cell
 constexpr int kWin = kTile + 2 * kMargin + kReachLo + kReachHi;   // 17 nodes per axis
 constexpr int kWin3 = kWin * kWin * kWin;
 constexpr int kWinLo = kMargin + kReachLo;     // window node 0 = tile origin - kWinLo
-constexpr size_t kTiledSmem = sizeof(float) * 9 * kWin3;
+constexpr int kChunk = 1024;                   // particles staged per round
+constexpr int kPerThread = kChunk / kThreads;  // particles per thread per round
+constexpr int kLaneStride = kChunk / 32;       // sorted-order distance between lanes
+static_assert(kChunk % kThreads == 0 && kLaneStride == kWarps * kPerThread, "chunk must split evenly over the CTA");
+constexpr int kStage = kChunk + kChunk / 32;   // one pad word per 32 (bank spread)
+constexpr size_t kTiledSmem = sizeof(float) * (9 * kWin3 + 7 * kStage);
+constexpr int kMaxTiledSpecies = PP_MAX_SPECIES;
 
 struct SmemAcc {
     const float *Fw;  // 6 windows: E0 E1 E2 B0 B1 B2
     float *J;         // 3 windows
-    int fx, fy, fz;   // window index of the particle's cell
-    __device__ __forceinline__ int at(int i, int j, int k) const {
-        return ((k + fz) * kWin + (j + fy)) * kWin + (i + fx);
-    }
+    int base;         // window offset of the particle's cell
+    __device__ __forceinline__ int at(int i, int j, int k) const { return base + (k * kWin + j) * kWin + i; }
     __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
         return Fw[(kind * 3 + comp) * kWin3 + at(i, j, k)];
     }
@@ -237,12 +254,25 @@ struct SmemAcc {
     }
 };
 
-struct TiledArgs {
-    StepArgs<float> a;
+struct TiledSpecies {
     MixedParticles p;
     const int32_t *cell_start;   // per sort key, tile-major
+    int32_t *slow_list;          // indices of particles left to the global-mesh kernel
+    unsigned *slow_count;
+    float qmdt;
+    float jscale[3];
+};
+
+struct TiledArgs {
+    Geom g;
+    const float *E[3];
+    const float *B[3];
+    float *J[3];
+    float dtdx[3];
     int nt[3];                   // tiles per axis
-    unsigned long long *nslow;
+    int ns;
+    TiledSpecies sp[kMaxTiledSpecies];
+    int *status;
 };
 
 __device__ __forceinline__ int min_image(int d, int n) {
@@ -252,43 +282,121 @@ __device__ __forceinline__ int min_image(int d, int n) {
 }
 
 template <int O, int PUSH>
-__global__ void __launch_bounds__(kTile * kTile * kTile, 1) k_particles_tiled(TiledArgs T) {
+__global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_constant__ TiledArgs T) {
     extern __shared__ float smem[];
     float *F = smem;
     float *Jw = smem + 6 * kWin3;
-    const StepArgs<float> &a = T.a;
-    const Geom &g = a.g;
-    int tile = blockIdx.x;
-    int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
-    int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
-    int wx = ox - kWinLo, wy = oy - kWinLo, wz = oz - kWinLo;
+    float *stg = smem + 9 * kWin3;
+    int32_t *s_cell = (int32_t *)stg;
+    float *s_o[3] = {stg + kStage, stg + 2 * kStage, stg + 3 * kStage};
+    float *s_u[3] = {stg + 4 * kStage, stg + 5 * kStage, stg + 6 * kStage};
+    const Geom &g = T.g;
+    const int tile = blockIdx.x;
+    const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
+    const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
+    const int wx = ox - kWinLo, wy = oy - kWinLo, wz = oz - kWinLo;
     // stage E and B (ghost layers hold the periodic images), clear the current window
-    for (int idx = threadIdx.x; idx < 6 * kWin3; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < 6 * kWin3; idx += kThreads) {
         int comp = idx / kWin3, r = idx - comp * kWin3;
         int i = r % kWin, j = (r / kWin) % kWin, k = r / (kWin * kWin);
-        const float *src = comp < 3 ? a.E[comp] : a.B[comp - 3];
+        const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
         F[idx] = __ldg(src + g.at(wx + i, wy + j, wz + k));
     }
-    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += blockDim.x) Jw[idx] = 0.0f;
+    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += kThreads) Jw[idx] = 0.0f;
     __syncthreads();
 
-    int lc = threadIdx.x;
-    int key = tile * (kTile * kTile * kTile) + lc;
-    int begin = T.cell_start[key], end = T.cell_start[key + 1];
-    GlobalAcc<float> gacc{g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, 0, 0, 0};
-    for (int t = begin; t < end; ++t) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = 0; s < T.ns; ++s) {
+        const TiledSpecies &S = T.sp[s];
+        const int tb = S.cell_start[tile * kTileCells], te = S.cell_start[(tile + 1) * kTileCells];
+        for (int cb = tb; cb < te; cb += kChunk) {
+            const int cn = min(kChunk, te - cb);
+            for (int q = threadIdx.x; q < cn; q += kThreads) {
+                int sq = q + (q >> 5);
+                s_cell[sq] = S.p.cell[cb + q];
+                s_o[0][sq] = S.p.ox[cb + q]; s_o[1][sq] = S.p.oy[cb + q]; s_o[2][sq] = S.p.oz[cb + q];
+                s_u[0][sq] = S.p.ux[cb + q]; s_u[1][sq] = S.p.uy[cb + q]; s_u[2][sq] = S.p.uz[cb + q];
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int r = 0; r < kPerThread; ++r) {
+                const int q = lane * kLaneStride + warp + kWarps * r;
+                if (q >= cn) continue;
+                const int sq = q + (q >> 5);
+                int cx, cy, cz;
+                unpack_cell(s_cell[sq], cx, cy, cz);
+                float xi0[3] = {s_o[0][sq], s_o[1][sq], s_o[2][sq]};
+                float u[3] = {s_u[0][sq], s_u[1][sq], s_u[2][sq]};
+                int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
+                bool inside = rx >= -kMargin && rx < kTile + kMargin && ry >= -kMargin && ry < kTile + kMargin &&
+                              rz >= -kMargin && rz < kTile + kMargin;
+                if (!inside) {   // drifted too far from the tile: leave it to the global-mesh kernel
+                    unsigned slot = atomicAdd(S.slow_count, 1u);
+                    S.slow_list[slot] = cb + q;
+                    continue;
+                }
+                float E[3], B[3];
+                SmemAcc sacc{F, Jw, ((rz + kWinLo) * kWin + (ry + kWinLo)) * kWin + (rx + kWinLo)};
+                gather_EB<O, float>(sacc, xi0, E, B);
+                if (PUSH == PP_BORIS) push_boris<float>(S.qmdt, E, B, u);
+                else push_vay<float>(S.qmdt, E, B, u);
+                float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                float xi1[3];
+                bool ok = true;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    float dx = T.dtdx[d] * u[d] * gi;
+                    xi1[d] = xi0[d] + dx;
+                    ok = ok && (fabsf(dx) < 1.0f);
+                }
+                if (!ok) {   // leave the particle unchanged and flag the step
+                    atomicOr(T.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
+                    continue;
+                }
+                deposit_esirkepov<O, float>(sacc, xi0, xi1, S.jscale);
+                rebin(xi1[0], cx, g.n[0]);
+                rebin(xi1[1], cy, g.n[1]);
+                rebin(xi1[2], cz, g.n[2]);
+                s_cell[sq] = pack_cell(cx, cy, cz);
+                s_o[0][sq] = xi1[0]; s_o[1][sq] = xi1[1]; s_o[2][sq] = xi1[2];
+                s_u[0][sq] = u[0]; s_u[1][sq] = u[1]; s_u[2][sq] = u[2];
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < cn; q += kThreads) {
+                int sq = q + (q >> 5);
+                S.p.cell[cb + q] = s_cell[sq];
+                S.p.ox[cb + q] = s_o[0][sq]; S.p.oy[cb + q] = s_o[1][sq]; S.p.oz[cb + q] = s_o[2][sq];
+                S.p.ux[cb + q] = s_u[0][sq]; S.p.uy[cb + q] = s_u[1][sq]; S.p.uz[cb + q] = s_u[2][sq];
+            }
+            __syncthreads();
+        }
+    }
+    // one flush of the current window into the global mesh (ghosts folded later)
+    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += kThreads) {
+        float v = Jw[idx];
+        if (v == 0.0f) continue;
+        int comp = idx / kWin3, r = idx - comp * kWin3;
+        int i = r % kWin, j = (r / kWin) % kWin, k = r / (kWin * kWin);
+        atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), v);
+    }
+}
+
+// Particles the tile kernel left out (drifted more than kMargin cells from
+// their tile since the last sort), advanced through the global mesh.
+template <int O, int PUSH>
+__global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, MixedParticles p, const int32_t *list,
+                                                          const unsigned *count, unsigned long long *nslow) {
+    unsigned n = *count;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(nslow, (unsigned long long)n);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int t = list[k];
         int cx, cy, cz;
-        unpack_cell(T.p.cell[t], cx, cy, cz);
-        float xi0[3] = {T.p.ox[t], T.p.oy[t], T.p.oz[t]};
-        float u[3] = {T.p.ux[t], T.p.uy[t], T.p.uz[t]};
-        int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
-        bool inside = rx >= -kMargin && rx < kTile + kMargin && ry >= -kMargin && ry < kTile + kMargin &&
-                      rz >= -kMargin && rz < kTile + kMargin;
+        unpack_cell(p.cell[t], cx, cy, cz);
+        float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
+        float u[3] = {p.ux[t], p.uy[t], p.uz[t]};
+        GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
         float E[3], B[3];
-        SmemAcc sacc{F, Jw, rx + kWinLo, ry + kWinLo, rz + kWinLo};
-        gacc.ox = cx; gacc.oy = cy; gacc.oz = cz;
-        if (inside) gather_EB<O, float>(sacc, xi0, E, B);
-        else gather_EB<O, float>(gacc, xi0, E, B);
+        gather_EB<O, float>(acc, xi0, E, B);
         if (PUSH == PP_BORIS) push_boris<float>(a.qmdt, E, B, u);
         else push_vay<float>(a.qmdt, E, B, u);
         float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -304,47 +412,56 @@ __global__ void __launch_bounds__(kTile * kTile * kTile, 1) k_particles_tiled(Ti
             atomicOr(a.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
             continue;
         }
-        if (inside) {
-            deposit_esirkepov<O, float>(sacc, xi0, xi1, a.jscale);
-        } else {
-            deposit_esirkepov<O, float>(gacc, xi0, xi1, a.jscale);
-            atomicAdd(T.nslow, 1ull);
-        }
-        rebin(xi1[0], cx, g.n[0]);
-        rebin(xi1[1], cy, g.n[1]);
-        rebin(xi1[2], cz, g.n[2]);
-        T.p.cell[t] = pack_cell(cx, cy, cz);
-        T.p.ox[t] = xi1[0]; T.p.oy[t] = xi1[1]; T.p.oz[t] = xi1[2];
-        T.p.ux[t] = u[0]; T.p.uy[t] = u[1]; T.p.uz[t] = u[2];
-    }
-    __syncthreads();
-    // one flush of the current window into the global mesh (ghosts folded later)
-    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += blockDim.x) {
-        float v = Jw[idx];
-        if (v == 0.0f) continue;
-        int comp = idx / kWin3, r = idx - comp * kWin3;
-        int i = r % kWin, j = (r / kWin) % kWin, k = r / (kWin * kWin);
-        atomicAdd(a.J[comp] + g.at(wx + i, wy + j, wz + k), v);
+        deposit_esirkepov<O, float>(acc, xi0, xi1, a.jscale);
+        rebin(xi1[0], cx, a.g.n[0]);
+        rebin(xi1[1], cy, a.g.n[1]);
+        rebin(xi1[2], cz, a.g.n[2]);
+        p.cell[t] = pack_cell(cx, cy, cz);
+        p.ox[t] = xi1[0]; p.oy[t] = xi1[1]; p.oz[t] = xi1[2];
+        p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
     }
 }
 
 bool tiled_supported(const Ctx &c) {
+    if (c.fp64 || c.g.G < kWinLo || c.g.G < kWin - kWinLo - kTile) return false;
     for (int a = 0; a < 3; ++a)
-        if (c.g.n[a] % kTile != 0 || c.tile[a] != kTile || c.g.G < kWinLo || c.g.G + 1 < kWin - kWinLo - kTile + 1)
-            return false;
-    return !c.fp64;
+        if (c.g.n[a] % kTile != 0 || c.tile[a] != kTile) return false;
+    return true;
 }
 
-cudaError_t launch_particles_mixed_tiled(Ctx &c, int s) {
-    Species &S = c.sp[s];
-    if (S.n == 0) return cudaSuccess;
-    if (!tiled_supported(c) || !S.sorted) return cudaErrorInvalidConfiguration;
+// All species of the context in one launch (species with no particles skip
+// their loop); fails if a species has not been sorted yet.
+cudaError_t launch_particles_tiled_all(Ctx &c) {
+    if (!tiled_supported(c)) return cudaErrorInvalidConfiguration;
     TiledArgs T;
-    T.a = step_args<float>(c, s);
-    T.p = MixedParticles{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
-    T.cell_start = S.cell_start;
-    for (int a = 0; a < 3; ++a) T.nt[a] = c.ntile[a];
-    T.nslow = c.d_nslow;
+    T.g = c.g;
+    double h[3] = {c.d.dx, c.d.dy, c.d.dz};
+    for (int d = 0; d < 3; ++d) {
+        T.E[d] = (const float *)c.E[d];
+        T.B[d] = (const float *)c.B[d];
+        T.J[d] = (float *)c.J[d];
+        T.dtdx[d] = (float)(c.d.dt / h[d]);
+        T.nt[d] = c.ntile[d];
+    }
+    T.ns = 0;
+    int sid[kMaxTiledSpecies];
+    cudaError_t e0 = cudaMemsetAsync(c.d_slow_count, 0, sizeof(unsigned) * PP_MAX_SPECIES, c.st);
+    if (e0 != cudaSuccess) return e0;
+    for (int s = 0; s < c.nspecies; ++s) {
+        const Species &S = c.sp[s];
+        if (S.n == 0) continue;
+        if (!S.sorted) return cudaErrorInvalidConfiguration;
+        sid[T.ns] = s;
+        TiledSpecies &t = T.sp[T.ns++];
+        t.p = MixedParticles{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+        t.cell_start = S.cell_start;
+        t.slow_list = S.keys;              // the sort keys are dead between sorts
+        t.slow_count = c.d_slow_count + s;
+        t.qmdt = (float)(S.q * c.d.dt / S.m);
+        for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.d.dt);
+    }
+    if (T.ns == 0) return cudaSuccess;
+    T.status = c.d_status;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
     static bool attr_done[2][4] = {{false}};
@@ -356,7 +473,7 @@ cudaError_t launch_particles_mixed_tiled(Ctx &c, int s) {
             if (e_ != cudaSuccess) return e_;                                                               \
             attr_done[PU][O] = true;                                                                        \
         }                                                                                                   \
-        k_particles_tiled<O, PU><<<blocks, kTile * kTile * kTile, kTiledSmem, c.st>>>(T);                   \
+        k_particles_tiled<O, PU><<<blocks, kThreads, kTiledSmem, c.st>>>(T);                                \
     } while (0)
     if (pu == PP_BORIS) {
         if (o == 1) PP_T(1, PP_BORIS); else if (o == 2) PP_T(2, PP_BORIS); else PP_T(3, PP_BORIS);
@@ -365,7 +482,25 @@ cudaError_t launch_particles_mixed_tiled(Ctx &c, int s) {
     }
 #undef PP_T
     ++c.nlaunch;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the left-out particles of every species, on a fixed grid (count read on the device)
+    for (int k = 0; k < T.ns; ++k) {
+        const Species &S = c.sp[sid[k]];
+        StepArgs<float> a = step_args<float>(c, sid[k]);
+        MixedParticles p{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+        const unsigned *cnt = c.d_slow_count + sid[k];
+#define PP_S(O, PU) k_particles_listed<O, PU><<<304, 256, 0, c.st>>>(a, p, S.keys, cnt, c.d_nslow)
+        if (pu == PP_BORIS) {
+            if (o == 1) PP_S(1, PP_BORIS); else if (o == 2) PP_S(2, PP_BORIS); else PP_S(3, PP_BORIS);
+        } else {
+            if (o == 1) PP_S(1, PP_VAY); else if (o == 2) PP_S(2, PP_VAY); else PP_S(3, PP_VAY);
+        }
+#undef PP_S
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

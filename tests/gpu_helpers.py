@@ -46,27 +46,26 @@ def field_errors(gpu, orc_sim):
     return out
 
 
-def _order(p, L):
-    # lexicographic order by cell then position: unique for random loads
-    keys = [np.round(p[k], 9) for k in ("z", "y", "x")]
-    return np.lexsort(keys)
-
-
 def particle_errors(gpu_p, orc_p, box):
-    """Match the two particle sets by sorting on position and compare.
+    """Match the two particle sets one to one by periodic nearest neighbour in
+    position (the library keeps particles in cell-sorted order) and compare.
     Returns (max periodic position difference, relative momentum error)."""
+    from scipy.spatial import cKDTree
     n = len(orc_p["x"])
     assert len(gpu_p["x"]) == n
     if n == 0:
         return 0.0, 0.0
-    ig = np.lexsort([gpu_p["x"], gpu_p["y"], gpu_p["z"]][::-1])
-    io = np.lexsort([orc_p["x"], orc_p["y"], orc_p["z"]][::-1])
-    dpos = 0.0
-    for k, Lk in zip(("x", "y", "z"), box):
-        d = gpu_p[k][ig] - orc_p[k][io]
-        d = (d + 0.5 * Lk) % Lk - 0.5 * Lk
-        dpos = max(dpos, np.abs(d).max())
-    du = max(np.abs(gpu_p[k][ig] - orc_p[k][io]).max() for k in ("ux", "uy", "uz"))
+    Lb = np.asarray(box, dtype=float)
+    P = np.stack([np.mod(gpu_p[k], Lb[a]) for a, k in enumerate("xyz")], 1)
+    O = np.stack([np.mod(orc_p[k], Lb[a]) for a, k in enumerate("xyz")], 1)
+    P = np.minimum(P, np.nextafter(Lb, 0))
+    O = np.minimum(O, np.nextafter(Lb, 0))
+    _, j = cKDTree(O, boxsize=Lb).query(P, k=1)
+    assert len(np.unique(j)) == n, "particle sets do not match one to one"
+    d = P - O[j]
+    d = (d + 0.5 * Lb) % Lb - 0.5 * Lb
+    dpos = np.abs(d).max()
+    du = max(np.abs(gpu_p[k] - orc_p[k][j]).max() for k in ("ux", "uy", "uz"))
     us = max(np.abs(orc_p[k]).max() for k in ("ux", "uy", "uz"))
     return dpos, (du / us if us > 0 else du)
 

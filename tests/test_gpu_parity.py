@@ -243,3 +243,28 @@ def test_invalid_inputs_fail_loudly(pp):
     with pytest.raises(pp.PPError):
         sim.load_particles(sid, *[np.zeros(5)] * 6)          # above the requested capacity of 4
     assert sim.count(sid) == 0
+
+
+def test_mixed_tiled_drift_fallback(pp, orc):
+    """No re-sort after the load and fast particles: many drift more than the
+    tiled kernel's margin from their tile and go through the global-mesh
+    fallback; the result still matches the oracle and the global form."""
+    L = pp_synth.random_particles((16, 16, 16), (0.5, 0.5, 0.5), 0.25, 4000, seed=77, u_scale=3.0)
+    tiled = H.gpu_sim(pp, L, pp.PP_MIXED32, 3, deposit_mode=2, sort_interval=0)
+    glob = H.gpu_sim(pp, L, pp.PP_MIXED32, 3, deposit_mode=1, sort_interval=0)
+    osim = H.oracle_sim(orc, L, 3)
+    for sim in (tiled, glob):
+        E, B = pp_synth.random_fields(L.n, 3, 0.02)
+        sim.load_fields(E, B)
+    osim.load_fields(*pp_synth.random_fields(L.n, 3, 0.02))
+    for _ in range(12):
+        tiled.step(1)
+        glob.step(1)
+        osim.step(1)
+    d = tiled.diagnostics()
+    assert d["status"] == 0 and d["n_slow"] > 100
+    _compare(tiled, osim, L, 2e-4, 2e-5, 2e-5)
+    Et, Bt, Jt = tiled.fields()
+    Eg, Bg, Jg = glob.fields()
+    assert max(H.rel_err(Et[a], Eg[a]) for a in range(3)) <= 1e-4
+    assert max(H.rel_err(Jt[a], Jg[a]) for a in range(3)) <= 1e-4
