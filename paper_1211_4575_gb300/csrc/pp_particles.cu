@@ -205,15 +205,22 @@ cudaError_t launch_particles_mixed_global(Ctx &c, int s) {
 // ---------------------------------------------------------------------------
 // Tiled form (mixed precision).  One CTA per 8x8x8 cell tile of the last cell
 // sort, all species in one launch.  The E/B nodes the tile's particles can
-// touch are staged in shared memory, the current is accumulated in a shared
-// window and flushed to the global mesh once per tile.
+// touch are staged in shared memory, and the current is accumulated in a shared
+// int32 fixed-point window (native shared integer atomics; FP32 shared
+// atomics are several times slower on this part) that each chunk of
+// particles flushes, over the box it touched, into the FP32 global mesh.
 //
-// Particles are streamed in chunks of kChunk: a coalesced copy into a padded
-// shared staging buffer, then thread (warp w, lane l) takes chunk slots
-// 32 l + w + W r (W warps, r < 1024 / (32 W)) -- consecutive lanes 32 sorted
-// particles apart,
-// i.e. in distinct cells, so their shared-memory atomics rarely collide --
-// and the results leave through the same buffer with coalesced stores.
+// Fixed point, chosen per chunk and per current component a: the chunk is
+// first gathered, pushed and moved; then, with |C| <= |dxi_a| (the prefix of
+// dS is a difference of B-spline cumulative sums, whose slope is at most 1)
+// and |Y| <= 3/2, no node can receive more than
+//     bound_a = 3/2 |jscale_a| sum_p (|dxi_{p,a}| + 1e-6)
+// (the 1e-6 per particle covers the FP32 rounding of the weights in C)
+// from the chunk, and the unit 2^30 / bound_a keeps every int32 sum below
+// 2^30 (plus at most 1024 rounding halves).  The rounding of a contribution
+// is half a unit, i.e. relative to the chunk's total motion rather than to
+// the largest possible current; the sum inside a chunk is exact and does not
+// depend on the order of the atomics.
 //
 // A particle may have drifted since the sort: it is handled from shared
 // memory while its cell lies within kMargin cells of the tile (minimal
@@ -238,19 +245,23 @@ constexpr int kPerThread = kChunk / kThreads;  // particles per thread per round
 constexpr int kLaneStride = kChunk / 32;       // sorted-order distance between lanes
 static_assert(kChunk % kThreads == 0 && kLaneStride == kWarps * kPerThread, "chunk must split evenly over the CTA");
 constexpr int kStage = kChunk + kChunk / 32;   // one pad word per 32 (bank spread)
-constexpr size_t kTiledSmem = sizeof(float) * (9 * kWin3 + 7 * kStage);
+constexpr int kStageArrays = 10;               // cell, 3 offsets, 3 momenta, 3 displacements
+constexpr size_t kTiledSmem = sizeof(float) * (9 * kWin3 + kStageArrays * kStage) + sizeof(int) * 16;
+constexpr float kFixedRange = 1073741824.0f;   // 2^30
+static_assert(kChunk <= 1024, "the fixed-point bound allows at most 1024 rounding halves per flush");
 constexpr int kMaxTiledSpecies = PP_MAX_SPECIES;
 
 struct SmemAcc {
     const float *Fw;  // 6 windows: E0 E1 E2 B0 B1 B2
-    float *J;         // 3 windows
+    int *J;           // 3 fixed-point windows
     int base;         // window offset of the particle's cell
     __device__ __forceinline__ int at(int i, int j, int k) const { return base + (k * kWin + j) * kWin + i; }
     __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
         return Fw[(kind * 3 + comp) * kWin3 + at(i, j, k)];
     }
     __device__ __forceinline__ void addJ(int comp, int i, int j, int k, float v) const {
-        atomicAdd(J + comp * kWin3 + at(i, j, k), v);
+        int iv = __float2int_rn(v);   // v is pre-scaled by the fixed-point unit
+        if (iv != 0) atomicAdd(J + comp * kWin3 + at(i, j, k), iv);
     }
 };
 
@@ -260,7 +271,7 @@ struct TiledSpecies {
     int32_t *slow_list;          // indices of particles left to the global-mesh kernel
     unsigned *slow_count;
     float qmdt;
-    float jscale[3];
+    float jscale[3];             // -q w dx_a / dt
 };
 
 struct TiledArgs {
@@ -285,11 +296,14 @@ template <int O, int PUSH>
 __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_constant__ TiledArgs T) {
     extern __shared__ float smem[];
     float *F = smem;
-    float *Jw = smem + 6 * kWin3;
+    int *Jw = (int *)(smem + 6 * kWin3);
     float *stg = smem + 9 * kWin3;
     int32_t *s_cell = (int32_t *)stg;
-    float *s_o[3] = {stg + kStage, stg + 2 * kStage, stg + 3 * kStage};
-    float *s_u[3] = {stg + 4 * kStage, stg + 5 * kStage, stg + 6 * kStage};
+    float *s_o = stg + kStage;           // 3 arrays: offsets at t
+    float *s_u = stg + 4 * kStage;       // 3 arrays: momenta
+    float *s_d = stg + 7 * kStage;       // 3 arrays: displacement of the step (NaN: not deposited here)
+    int *bbox = (int *)(stg + kStageArrays * kStage);   // min x,y,z, max x,y,z of the deposited cells
+    float *tot = (float *)(bbox + 8);                     // sum |dxi| per axis
     const Geom &g = T.g;
     const int tile = blockIdx.x;
     const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
@@ -302,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
         const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
         F[idx] = __ldg(src + g.at(wx + i, wy + j, wz + k));
     }
-    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += kThreads) Jw[idx] = 0.0f;
+    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += kThreads) Jw[idx] = 0;
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -311,13 +325,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
         const int tb = S.cell_start[tile * kTileCells], te = S.cell_start[(tile + 1) * kTileCells];
         for (int cb = tb; cb < te; cb += kChunk) {
             const int cn = min(kChunk, te - cb);
+            if (threadIdx.x < 3) { bbox[threadIdx.x] = 1 << 20; tot[threadIdx.x] = 0.0f; }
+            else if (threadIdx.x < 6) bbox[threadIdx.x] = -(1 << 20);
             for (int q = threadIdx.x; q < cn; q += kThreads) {
                 int sq = q + (q >> 5);
                 s_cell[sq] = S.p.cell[cb + q];
-                s_o[0][sq] = S.p.ox[cb + q]; s_o[1][sq] = S.p.oy[cb + q]; s_o[2][sq] = S.p.oz[cb + q];
-                s_u[0][sq] = S.p.ux[cb + q]; s_u[1][sq] = S.p.uy[cb + q]; s_u[2][sq] = S.p.uz[cb + q];
+                s_o[sq] = S.p.ox[cb + q]; s_o[kStage + sq] = S.p.oy[cb + q]; s_o[2 * kStage + sq] = S.p.oz[cb + q];
+                s_u[sq] = S.p.ux[cb + q]; s_u[kStage + sq] = S.p.uy[cb + q]; s_u[2 * kStage + sq] = S.p.uz[cb + q];
             }
             __syncthreads();
+            // ---- phase 1: gather, push, move (displacements kept in the frame of the old cell)
+            float sum[3] = {0.0f, 0.0f, 0.0f};
+            int lo[3] = {1 << 20, 1 << 20, 1 << 20}, hi[3] = {-(1 << 20), -(1 << 20), -(1 << 20)};
 #pragma unroll 1
             for (int r = 0; r < kPerThread; ++r) {
                 const int q = lane * kLaneStride + warp + kWarps * r;
@@ -325,11 +344,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 const int sq = q + (q >> 5);
                 int cx, cy, cz;
                 unpack_cell(s_cell[sq], cx, cy, cz);
-                float xi0[3] = {s_o[0][sq], s_o[1][sq], s_o[2][sq]};
-                float u[3] = {s_u[0][sq], s_u[1][sq], s_u[2][sq]};
+                float xi0[3] = {s_o[sq], s_o[kStage + sq], s_o[2 * kStage + sq]};
+                float u[3] = {s_u[sq], s_u[kStage + sq], s_u[2 * kStage + sq]};
                 int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
                 bool inside = rx >= -kMargin && rx < kTile + kMargin && ry >= -kMargin && ry < kTile + kMargin &&
                               rz >= -kMargin && rz < kTile + kMargin;
+                s_d[sq] = __int_as_float(0x7fc00000);   // not deposited here unless set below
                 if (!inside) {   // drifted too far from the tile: leave it to the global-mesh kernel
                     unsigned slot = atomicAdd(S.slow_count, 1u);
                     S.slow_list[slot] = cb + q;
@@ -341,43 +361,95 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 if (PUSH == PP_BORIS) push_boris<float>(S.qmdt, E, B, u);
                 else push_vay<float>(S.qmdt, E, B, u);
                 float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                float xi1[3];
+                float dx[3];
                 bool ok = true;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    float dx = T.dtdx[d] * u[d] * gi;
-                    xi1[d] = xi0[d] + dx;
-                    ok = ok && (fabsf(dx) < 1.0f);
+                    dx[d] = T.dtdx[d] * u[d] * gi;
+                    ok = ok && (fabsf(dx[d]) < 1.0f);
                 }
                 if (!ok) {   // leave the particle unchanged and flag the step
                     atomicOr(T.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
                     continue;
                 }
-                deposit_esirkepov<O, float>(sacc, xi0, xi1, S.jscale);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    s_d[d * kStage + sq] = dx[d];
+                    sum[d] += fabsf(dx[d]);
+                }
+                s_u[sq] = u[0]; s_u[kStage + sq] = u[1]; s_u[2 * kStage + sq] = u[2];
+                lo[0] = min(lo[0], rx); lo[1] = min(lo[1], ry); lo[2] = min(lo[2], rz);
+                hi[0] = max(hi[0], rx); hi[1] = max(hi[1], ry); hi[2] = max(hi[2], rz);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float sd = sum[d];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                int l = __reduce_min_sync(0xffffffffu, lo[d]), h = __reduce_max_sync(0xffffffffu, hi[d]);
+                if (lane == 0) {
+                    atomicAdd(tot + d, sd);
+                    atomicMin(bbox + d, l);
+                    atomicMax(bbox + 3 + d, h);
+                }
+            }
+            __syncthreads();
+            // ---- phase 2: fixed-point unit per component, deposit, re-bin
+            float unit[3], jsc[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float bound = 1.5f * fabsf(S.jscale[d]) * (tot[d] + 1e-6f * (float)cn) * 1.0001f;
+                unit[d] = bound > 0.0f ? kFixedRange / bound : 0.0f;
+                jsc[d] = S.jscale[d] * unit[d];
+            }
+#pragma unroll 1
+            for (int r = 0; r < kPerThread; ++r) {
+                const int q = lane * kLaneStride + warp + kWarps * r;
+                if (q >= cn) continue;
+                const int sq = q + (q >> 5);
+                float dx0 = s_d[sq];
+                if (isnan(dx0)) continue;
+                int cx, cy, cz;
+                unpack_cell(s_cell[sq], cx, cy, cz);
+                float xi0[3] = {s_o[sq], s_o[kStage + sq], s_o[2 * kStage + sq]};
+                float xi1[3] = {xi0[0] + dx0, xi0[1] + s_d[kStage + sq], xi0[2] + s_d[2 * kStage + sq]};
+                int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
+                SmemAcc sacc{F, Jw, ((rz + kWinLo) * kWin + (ry + kWinLo)) * kWin + (rx + kWinLo)};
+                deposit_esirkepov<O, float>(sacc, xi0, xi1, jsc);
                 rebin(xi1[0], cx, g.n[0]);
                 rebin(xi1[1], cy, g.n[1]);
                 rebin(xi1[2], cz, g.n[2]);
                 s_cell[sq] = pack_cell(cx, cy, cz);
-                s_o[0][sq] = xi1[0]; s_o[1][sq] = xi1[1]; s_o[2][sq] = xi1[2];
-                s_u[0][sq] = u[0]; s_u[1][sq] = u[1]; s_u[2][sq] = u[2];
+                s_o[sq] = xi1[0]; s_o[kStage + sq] = xi1[1]; s_o[2 * kStage + sq] = xi1[2];
             }
             __syncthreads();
             for (int q = threadIdx.x; q < cn; q += kThreads) {
                 int sq = q + (q >> 5);
                 S.p.cell[cb + q] = s_cell[sq];
-                S.p.ox[cb + q] = s_o[0][sq]; S.p.oy[cb + q] = s_o[1][sq]; S.p.oz[cb + q] = s_o[2][sq];
-                S.p.ux[cb + q] = s_u[0][sq]; S.p.uy[cb + q] = s_u[1][sq]; S.p.uz[cb + q] = s_u[2][sq];
+                S.p.ox[cb + q] = s_o[sq]; S.p.oy[cb + q] = s_o[kStage + sq]; S.p.oz[cb + q] = s_o[2 * kStage + sq];
+                S.p.ux[cb + q] = s_u[sq]; S.p.uy[cb + q] = s_u[kStage + sq]; S.p.uz[cb + q] = s_u[2 * kStage + sq];
+            }
+            // flush the window nodes this chunk could touch (cells +- support) into the FP32 mesh
+            if (bbox[0] <= bbox[3]) {
+                const int x0 = bbox[0] + kWinLo - kReachLo, y0 = bbox[1] + kWinLo - kReachLo,
+                          z0 = bbox[2] + kWinLo - kReachLo;
+                const int ex = bbox[3] - bbox[0] + kReachLo + kReachHi + 1;
+                const int ey = bbox[4] - bbox[1] + kReachLo + kReachHi + 1;
+                const int ez = bbox[5] - bbox[2] + kReachLo + kReachHi + 1;
+                const int vol = ex * ey * ez;
+                for (int idx = threadIdx.x; idx < 3 * vol; idx += kThreads) {
+                    int comp = idx / vol, r = idx - comp * vol;
+                    int i = x0 + r % ex, j = y0 + (r / ex) % ey, k = z0 + r / (ex * ey);
+                    int w = (k * kWin + j) * kWin + i;
+                    int iv = Jw[comp * kWin3 + w];
+                    if (iv == 0) continue;
+                    Jw[comp * kWin3 + w] = 0;
+                    float uc = comp == 0 ? unit[0] : (comp == 1 ? unit[1] : unit[2]);
+                    atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), (float)iv / uc);
+                }
             }
             __syncthreads();
         }
-    }
-    // one flush of the current window into the global mesh (ghosts folded later)
-    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += kThreads) {
-        float v = Jw[idx];
-        if (v == 0.0f) continue;
-        int comp = idx / kWin3, r = idx - comp * kWin3;
-        int i = r % kWin, j = (r / kWin) % kWin, k = r / (kWin * kWin);
-        atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), v);
     }
 }
 
