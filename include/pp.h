@@ -229,6 +229,26 @@ int pp_save(pp_ctx *ctx, const char *path);
 /* Restore a checkpoint written by pp_save into a new context on `stream`. */
 int pp_restore(pp_ctx **out, const char *path, void *stream);
 
+/* Allocation-free FP64 field energies: out[0] = sum 1/2 |E|^2 dV,
+ * out[1] = sum 1/2 |B|^2 dV, out[2] = sum 1/2 E_x^2 dV over an nx*ny*nz mesh,
+ * the same sums pp_diagnostics reports.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need the energies (allocation forbidden after start-up, a CUDA graph being
+ * captured, a host that hands over pre-allocated buffers only).
+ * E, B: arrays of three DEVICE pointers to nx*ny*nz FP64 values each (the
+ * mesh layout above; the caller owns them).  out: DEVICE pointer to three
+ * FP64 values, written on `stream` (cudaStream_t, NULL = legacy default).
+ * The call allocates nothing: its scratch (1024 x 3 FP64 partial sums, 24 KiB)
+ * is a fixed array inside the library, one per device, held until the process
+ * exits.  The first call on a device looks that array up (with the device
+ * current); make it before any stream capture.  Calls whose kernels overlap
+ * on the GPU share the array and race.  Errors: PP_EINVAL for NULL pointers or
+ * a mesh of more than 1023^3 cells, PP_ECUDA for a failed lookup or launch;
+ * pp_field_energy_noalloc_error() then returns the message (per host thread). */
+int pp_field_energy_noalloc(const double *const E[3], const double *const B[3], int nx, int ny, int nz, double dV,
+                            double *out, void *stream);
+const char *pp_field_energy_noalloc_error(void);
+
 /* Free all device and host state of the context (NULL is accepted). */
 int pp_destroy(pp_ctx *ctx);
 

@@ -86,6 +86,8 @@ SIGNATURES = {
     "pp_profile_read": (C.c_int, [_P, C.POINTER(Profile)]),
     "pp_save": (C.c_int, [_P, C.c_char_p]),
     "pp_restore": (C.c_int, [_PP, C.c_char_p, _P]),
+    "pp_field_energy_noalloc": (C.c_int, [_PP, _PP, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
+    "pp_field_energy_noalloc_error": (C.c_char_p, []),
     "pp_destroy": (C.c_int, [_P]),
     "pp_last_error": (C.c_char_p, [_P]),
 }
@@ -134,6 +136,23 @@ def _f64(a) -> np.ndarray:
 
 def _ptr_array(arrs):
     return (C.c_void_p * 3)(*[a.ctypes.data if a is not None else None for a in arrs])
+
+
+def field_energy_noalloc(E, B, dV, out, stream=None):
+    """Field energies of caller-owned CUDA FP64 tensors E[3], B[3] (each shaped
+    (nz, ny, nx), contiguous) written into the CUDA FP64 tensor ``out`` of 3
+    values, through the allocation-free entry point (no device memory is
+    allocated by the call)."""
+    for t in list(E) + list(B):
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+            raise ValueError("E and B must be contiguous CUDA float64 tensors")
+    nz, ny, nx = E[0].shape
+    pe = (C.c_void_p * 3)(*[t.data_ptr() for t in E])
+    pb = (C.c_void_p * 3)(*[t.data_ptr() for t in B])
+    rc = lib().pp_field_energy_noalloc(pe, pb, nx, ny, nz, float(dV), out.data_ptr(),
+                                       stream if stream is not None else _current_stream())
+    if rc != PP_OK:
+        raise PPError(rc, lib().pp_field_energy_noalloc_error().decode(errors="replace"))
 
 
 class Simulation:
