@@ -325,8 +325,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
         const int tb = S.cell_start[tile * kTileCells], te = S.cell_start[(tile + 1) * kTileCells];
         for (int cb = tb; cb < te; cb += kChunk) {
             const int cn = min(kChunk, te - cb);
-            if (threadIdx.x < 3) { bbox[threadIdx.x] = 1 << 20; tot[threadIdx.x] = 0.0f; }
-            else if (threadIdx.x < 6) bbox[threadIdx.x] = -(1 << 20);
+            if (threadIdx.x < 3) {
+                bbox[threadIdx.x] = 1 << 20;          // running minimum
+                bbox[3 + threadIdx.x] = -(1 << 20);   // running maximum
+                tot[threadIdx.x] = 0.0f;
+            }
             for (int q = threadIdx.x; q < cn; q += kThreads) {
                 int sq = q + (q >> 5);
                 s_cell[sq] = S.p.cell[cb + q];
@@ -431,11 +434,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
             }
             // flush the window nodes this chunk could touch (cells +- support) into the FP32 mesh
             if (bbox[0] <= bbox[3]) {
-                const int x0 = bbox[0] + kWinLo - kReachLo, y0 = bbox[1] + kWinLo - kReachLo,
-                          z0 = bbox[2] + kWinLo - kReachLo;
-                const int ex = bbox[3] - bbox[0] + kReachLo + kReachHi + 1;
-                const int ey = bbox[4] - bbox[1] + kReachLo + kReachHi + 1;
-                const int ez = bbox[5] - bbox[2] + kReachLo + kReachHi + 1;
+                // box of window nodes, clamped to the window (deposited cells lie in
+                // [-kMargin, kTile + kMargin) so the clamp never cuts real deposits)
+                const int x0 = max(bbox[0] + kWinLo - kReachLo, 0), y0 = max(bbox[1] + kWinLo - kReachLo, 0),
+                          z0 = max(bbox[2] + kWinLo - kReachLo, 0);
+                const int ex = min(bbox[3] + kWinLo + kReachHi, kWin - 1) - x0 + 1;
+                const int ey = min(bbox[4] + kWinLo + kReachHi, kWin - 1) - y0 + 1;
+                const int ez = min(bbox[5] + kWinLo + kReachHi, kWin - 1) - z0 + 1;
                 const int vol = ex * ey * ez;
                 for (int idx = threadIdx.x; idx < 3 * vol; idx += kThreads) {
                     int comp = idx / vol, r = idx - comp * vol;
@@ -588,9 +593,15 @@ struct RhoAcc {
     }
 };
 
+// Lane l of every warp takes particles from the l-th thirty-second of the
+// (cell-sorted) array, so the lanes of a warp sit in distinct cells and their
+// FP64 atomics do not pile onto the same nodes.
 template <int O>
 __global__ void k_rho(Geom g, double qw, int64_t n, Fp64Particles p64, MixedParticles pm, int mixed, double *rho) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n32 = (n + 31) / 32;
+    if (tt >= n32 * 32) return;
+    int64_t t = (tt & 31) * n32 + (tt >> 5);
     if (t >= n) return;
     RhoAcc acc{g, rho, 0, 0, 0};
     double xi[3];
@@ -611,7 +622,7 @@ cudaError_t launch_rho(Ctx &c) {
         if (S.n == 0) continue;
         Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
         MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
-        unsigned blocks = (unsigned)((S.n + 255) / 256);
+        unsigned blocks = (unsigned)(((S.n + 31) / 32 * 32 + 255) / 256);
         double qw = S.q * S.w;
         int mixed = c.fp64 ? 0 : 1;
         if (c.d.shape_order == 1) k_rho<1><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);
