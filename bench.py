@@ -32,6 +32,25 @@ METRIC = "particle-steps/s (gather+push+deposit)"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp32 momenta) read + written
 
+# DRAM traffic of the fused particle kernel per particle, from the committed ncu
+# capture profiles/k_particles_tiled_thermal64.md (64^3 x 32 ppc; traffic grows
+# with the particle count).  Valid only for the kernel sources it was taken on.
+PROFILED_BYTES_PER_PARTICLE = 902.620160e6 / 16777216
+PROFILED_SOURCES = {
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "dc1a870ca812fd94c679263148181883e382bf3987a9435419bd450134926c53",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "8daecefd83d3900ac9d04ed13b1c9b100583e3bc677e2a6ee4388832d3fd060e",
+}
+
+
+def profiled_traffic(particles_per_launch):
+    """ncu DRAM bytes per launch scaled to this launch, or None once the kernel changed."""
+    import hashlib
+    for rel, digest in PROFILED_SOURCES.items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return PROFILED_BYTES_PER_PARTICLE * particles_per_launch
+
 
 def args():
     ap = argparse.ArgumentParser()
@@ -46,6 +65,10 @@ def args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-n", type=int, default=16, help="cells per axis of the oracle sample")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving form: p50/p99 time-to-result of a Poisson request trace, batched vs one at a time")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--rate", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -272,7 +295,8 @@ def run_gpu(a):
                    "deposit": a.deposit, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state 28 B x particles, read and written every step)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": profiled_traffic(npart * a.steps / max(1, prof["particle_launches"])),
                      "kernel": "fused particle step (gather+push+move+deposit)",
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_kind": peak_kind,
                      "kernel_ms_per_step": part_ms / a.steps},
@@ -289,9 +313,35 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def run_serve(a):
+    """Serving form on a reduced Poisson trace (same distributions as the
+    serving config, edges 16..48 and 20..100 steps so that it ends in minutes):
+    continuous batching through pp_batch_* against the same requests run one
+    at a time."""
+    import torch
+    import pp_synth
+    from paper_1211_4575_gb300 import build
+    build.build()
+    from paper_1211_4575_gb300 import serving
+    trace = pp_synth.serving_trace(n_requests=a.requests, rate=a.rate, edges=(16, 24, 32, 40, 48), steps=(20, 100))
+    warm = [dict(r, arrival=0.0, steps=2) for r in trace[:2]]
+    serving.sequential(warm)
+    seq, _ = serving.sequential(trace)
+    bat, _ = serving.serve(trace, budget_bytes=64 << 30, max_slots=32, chunk=4)
+    line = {"metric": "serving p50/p99 time-to-result", "value": bat["p99_s"], "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{a.requests} Poisson arrivals at {a.rate}/s of two-stream/Weibel runs, "
+                                   "edges 16..48, 8..32 ppc per species, pair or m_i/m_e=25, 20..100 steps, "
+                                   "mixed precision, PCS; budget 64 GiB, 32 slots"},
+               "batched": bat, "sequential": seq}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serve:
+        run_serve(a)
     else:
         run_gpu(a)

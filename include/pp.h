@@ -249,6 +249,49 @@ int pp_field_energy_noalloc(const double *const E[3], const double *const B[3], 
                             double *out, void *stream);
 const char *pp_field_energy_noalloc_error(void);
 
+/* ---- batched / served form ---------------------------------------------
+ * Independent periodic runs (one context each, loaded by the caller) admitted
+ * into the slots of a batch by device-memory budget and advanced together:
+ * each slot's steps go to its context's own stream, so runs of different
+ * sizes overlap on the GPU.  The paper runs one simulation per job; the
+ * method inside a slot is exactly pp_step.  The batch does not own the
+ * contexts: a slot refers to one until the slot is reported done or failed. */
+typedef struct pp_batch pp_batch;
+
+#define PP_BATCH_FREE 0     /* slot unused                                     */
+#define PP_BATCH_RUNNING 1  /* steps left to enqueue, or enqueued and running  */
+#define PP_BATCH_DONE 2     /* all steps finished on the device (reported once) */
+#define PP_BATCH_FAILED 3   /* a step returned an error (reported once)         */
+
+/* Device bytes a context holds (mesh, scratch and particle storage). */
+int64_t pp_device_bytes(pp_ctx *ctx);
+
+/* New batch admitting contexts while their device bytes sum to at most
+ * budget_bytes, in at most max_slots (1..4096) slots.  PP_EINVAL, PP_ENOMEM. */
+int pp_batch_create(pp_batch **out, int64_t budget_bytes, int max_slots);
+
+/* Admit ctx for `steps` steps into a free slot (*slot receives it).
+ * PP_EBUSY when no slot is free or the budget would be exceeded (nothing
+ * changes then).  Give every admitted context its own stream for overlap. */
+int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot);
+
+/* Enqueue up to max_steps steps of every running slot, one step per slot in
+ * turn, then record each slot's completion event.  Does not synchronise. */
+int pp_batch_advance(pp_batch *b, int max_steps);
+
+/* Non-blocking state of a slot (PP_BATCH_*), and the steps enqueued so far.
+ * A slot reported DONE or FAILED is released (its bytes return to the
+ * budget); its return value is then the failing step's code. */
+int pp_batch_poll(pp_batch *b, int slot, int64_t *steps_done, int *state);
+
+/* Bytes admitted and slots in use. */
+int pp_batch_used(pp_batch *b, int64_t *bytes, int *active);
+
+const char *pp_batch_last_error(const pp_batch *b);
+
+/* Free the batch (not the contexts). */
+int pp_batch_destroy(pp_batch *b);
+
 /* Free all device and host state of the context (NULL is accepted). */
 int pp_destroy(pp_ctx *ctx);
 

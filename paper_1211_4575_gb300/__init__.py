@@ -26,6 +26,7 @@ PP_VAY, PP_BORIS = 0, 1
 PP_FP64, PP_MIXED32 = 0, 1
 PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
 PP_MAX_SPECIES = 8
+PP_BATCH_FREE, PP_BATCH_RUNNING, PP_BATCH_DONE, PP_BATCH_FAILED = 0, 1, 2, 3
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
           9: "WSTAB"}
 
@@ -88,6 +89,14 @@ SIGNATURES = {
     "pp_restore": (C.c_int, [_PP, C.c_char_p, _P]),
     "pp_field_energy_noalloc": (C.c_int, [_PP, _PP, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
     "pp_field_energy_noalloc_error": (C.c_char_p, []),
+    "pp_device_bytes": (C.c_int64, [_P]),
+    "pp_batch_create": (C.c_int, [_PP, C.c_int64, C.c_int]),
+    "pp_batch_admit": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int)]),
+    "pp_batch_advance": (C.c_int, [_P, C.c_int]),
+    "pp_batch_poll": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "pp_batch_used": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "pp_batch_last_error": (C.c_char_p, [_P]),
+    "pp_batch_destroy": (C.c_int, [_P]),
     "pp_destroy": (C.c_int, [_P]),
     "pp_last_error": (C.c_char_p, [_P]),
 }
@@ -274,6 +283,9 @@ class Simulation:
         self._c(lib().pp_get_particles(self._ctx, sid, *[out[k].ctypes.data for k in ("x", "y", "z", "ux", "uy", "uz")]))
         return out
 
+    def device_bytes(self) -> int:
+        return int(lib().pp_device_bytes(self._ctx))
+
     def profile_enable(self, enable: bool = True):
         self._c(lib().pp_profile_enable(self._ctx, 1 if enable else 0))
 
@@ -303,3 +315,55 @@ class Simulation:
         ns = C.c_int(0)
         self._c(lib().pp_get_grid(self._ctx, C.byref(g), C.byref(ns)))
         return g, ns.value
+
+
+class Batch:
+    """Slots of independent runs advanced together (pp_batch_*)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64):
+        self._b = C.c_void_p()
+        rc = lib().pp_batch_create(C.byref(self._b), int(budget_bytes), int(max_slots))
+        if rc != PP_OK:
+            raise PPError(rc, "pp_batch_create failed")
+        self.max_slots = max_slots
+
+    def admit(self, sim: "Simulation", steps: int):
+        """Slot index, or None when the batch is full (PP_EBUSY)."""
+        slot = C.c_int(-1)
+        rc = lib().pp_batch_admit(self._b, sim._ctx, int(steps), C.byref(slot))
+        if rc == PP_EBUSY:
+            return None
+        if rc != PP_OK:
+            raise PPError(rc, lib().pp_batch_last_error(self._b).decode(errors="replace"))
+        return slot.value
+
+    def advance(self, max_steps: int):
+        rc = lib().pp_batch_advance(self._b, int(max_steps))
+        if rc != PP_OK:
+            raise PPError(rc, lib().pp_batch_last_error(self._b).decode(errors="replace"))
+
+    def poll(self, slot: int):
+        """(state, steps enqueued) of a slot; DONE/FAILED are reported once."""
+        done = C.c_int64(0)
+        state = C.c_int(0)
+        rc = lib().pp_batch_poll(self._b, int(slot), C.byref(done), C.byref(state))
+        if rc != PP_OK and state.value != PP_BATCH_FAILED:
+            raise PPError(rc, lib().pp_batch_last_error(self._b).decode(errors="replace"))
+        return state.value, done.value
+
+    def used(self):
+        b = C.c_int64(0)
+        a = C.c_int(0)
+        lib().pp_batch_used(self._b, C.byref(b), C.byref(a))
+        return b.value, a.value
+
+    def close(self):
+        if self._b is not None and self._b.value:
+            lib().pp_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,173 @@
+// pp_batch.cu -- batched and served form: independent periodic plasmas admitted
+// into slots by device-memory budget and advanced together.
+//
+// Each admitted context keeps its own particles, fields and stream on the
+// device; pp_batch_advance enqueues up to max_steps steps of every active slot
+// on that slot's stream, so the runs of different sizes overlap on the GPU,
+// and records an event per slot.  pp_batch_poll reads the event without
+// blocking; a slot whose steps are all enqueued and whose event has completed
+// reports PP_BATCH_DONE once and is released (its memory returns to the budget;
+// the context itself stays with the caller).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "pp_internal.cuh"
+
+using namespace pp;
+
+struct pp_batch {
+    size_t budget = 0, used = 0;
+    int nslots = 0;
+    struct Slot {
+        pp_ctx *ctx = nullptr;
+        int64_t left = 0;       // steps not yet enqueued
+        int64_t done = 0;       // steps enqueued
+        size_t bytes = 0;
+        cudaEvent_t ev = nullptr;
+        bool busy = false;
+        int status = PP_OK;
+    } *slot = nullptr;
+    char err[256] = {0};
+};
+
+static int bfail(pp_batch *b, int code, const char *msg) {
+    if (b) snprintf(b->err, sizeof b->err, "%s", msg);
+    return code;
+}
+
+// Device bytes held by a context (mesh, diagnostics and particle storage).
+extern "C" int64_t pp_device_bytes(pp_ctx *p) {
+    if (!p) return 0;
+    Ctx *c = p;
+    int64_t bytes = (int64_t)c->g.padded_size() * (int64_t)c->rsz * 21 + 2 * 8 * c->g.cells();
+    for (int s = 0; s < c->nspecies; ++s) {
+        int64_t per = c->fp64 ? 48 : 28;
+        bytes += 2 * per * c->sp[s].cap + 4 * c->sp[s].cap + 4 * (c->nkeys + 1);
+    }
+    bytes += 4 * (c->nkeys + 1);
+    return bytes;
+}
+
+extern "C" int pp_batch_create(pp_batch **out, int64_t budget_bytes, int max_slots) {
+    if (!out || budget_bytes <= 0 || max_slots < 1 || max_slots > 4096) return PP_EINVAL;
+    pp_batch *b = new (std::nothrow) pp_batch();
+    if (!b) return PP_ENOMEM;
+    b->budget = (size_t)budget_bytes;
+    b->nslots = max_slots;
+    b->slot = new (std::nothrow) pp_batch::Slot[max_slots];
+    if (!b->slot) {
+        delete b;
+        return PP_ENOMEM;
+    }
+    *out = b;
+    return PP_OK;
+}
+
+extern "C" int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot_out) {
+    if (!b || !ctx || steps < 0 || !slot_out) return bfail(b, PP_EINVAL, "pp_batch_admit: bad argument");
+    size_t bytes = (size_t)pp_device_bytes(ctx);
+    if (b->used + bytes > b->budget) return bfail(b, PP_EBUSY, "device-memory budget exhausted");
+    int k = -1;
+    for (int q = 0; q < b->nslots; ++q)
+        if (!b->slot[q].busy) { k = q; break; }
+    if (k < 0) return bfail(b, PP_EBUSY, "no free slot");
+    pp_batch::Slot &S = b->slot[k];
+    if (!S.ev && cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming) != cudaSuccess)
+        return bfail(b, PP_ECUDA, "event creation failed");
+    S.ctx = ctx;
+    S.left = steps;
+    S.done = 0;
+    S.bytes = bytes;
+    S.busy = true;
+    S.status = PP_OK;
+    b->used += bytes;
+    *slot_out = k;
+    return PP_OK;
+}
+
+extern "C" int pp_batch_advance(pp_batch *b, int max_steps) {
+    if (!b || max_steps < 0) return bfail(b, PP_EINVAL, "pp_batch_advance: bad argument");
+    // one step per slot per round, so that slots interleave on the device
+    for (int r = 0; r < max_steps; ++r) {
+        bool any = false;
+        for (int q = 0; q < b->nslots; ++q) {
+            pp_batch::Slot &S = b->slot[q];
+            if (!S.busy || S.left <= 0 || S.status != PP_OK) continue;
+            int rc = pp_step(S.ctx, 1);
+            if (rc != PP_OK) {
+                S.status = rc;
+                continue;
+            }
+            --S.left;
+            ++S.done;
+            any = true;
+        }
+        if (!any) break;
+    }
+    for (int q = 0; q < b->nslots; ++q) {
+        pp_batch::Slot &S = b->slot[q];
+        if (!S.busy) continue;
+        Ctx *c = S.ctx;
+        if (cudaEventRecord(S.ev, c->st) != cudaSuccess) S.status = PP_ECUDA;
+    }
+    return PP_OK;
+}
+
+extern "C" int pp_batch_poll(pp_batch *b, int slot, int64_t *steps_done, int *state) {
+    if (!b || slot < 0 || slot >= b->nslots || !state) return bfail(b, PP_EINVAL, "pp_batch_poll: bad argument");
+    pp_batch::Slot &S = b->slot[slot];
+    if (!S.busy) {
+        *state = PP_BATCH_FREE;
+        return PP_OK;
+    }
+    if (steps_done) *steps_done = S.done;
+    if (S.status != PP_OK) {
+        *state = PP_BATCH_FAILED;
+        int st = S.status;
+        S.busy = false;
+        b->used -= S.bytes;
+        return st;
+    }
+    if (S.left > 0) {
+        *state = PP_BATCH_RUNNING;
+        return PP_OK;
+    }
+    cudaError_t e = cudaEventQuery(S.ev);
+    if (e == cudaErrorNotReady) {
+        *state = PP_BATCH_RUNNING;
+        return PP_OK;
+    }
+    S.busy = false;
+    b->used -= S.bytes;
+    if (e != cudaSuccess) {
+        *state = PP_BATCH_FAILED;
+        return PP_ECUDA;
+    }
+    *state = PP_BATCH_DONE;
+    return PP_OK;
+}
+
+extern "C" int pp_batch_used(pp_batch *b, int64_t *used, int *active) {
+    if (!b) return PP_EINVAL;
+    if (used) *used = (int64_t)b->used;
+    if (active) {
+        int n = 0;
+        for (int q = 0; q < b->nslots; ++q) n += b->slot[q].busy ? 1 : 0;
+        *active = n;
+    }
+    return PP_OK;
+}
+
+extern "C" const char *pp_batch_last_error(const pp_batch *b) { return b ? b->err : ""; }
+
+extern "C" int pp_batch_destroy(pp_batch *b) {
+    if (!b) return PP_OK;
+    for (int q = 0; q < b->nslots; ++q)
+        if (b->slot[q].ev) cudaEventDestroy(b->slot[q].ev);
+    delete[] b->slot;
+    delete b;
+    return PP_OK;
+}

@@ -16,8 +16,6 @@
 
 using namespace pp;
 
-struct pp_ctx : public Ctx {};
-
 static char g_last_error[512] = "";
 
 static int fail(Ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));

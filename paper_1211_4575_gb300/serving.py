@@ -1,0 +1,101 @@
+"""Serving loop over the batched C ABI (pp_batch_*): requests for independent
+plasma runs arrive over time, are admitted into slots as device memory and
+slots allow, advance together on the GPU (each on its own stream), and report
+their time to result.  `sequential` runs the same requests one at a time.
+
+Host-side work here is orchestration only (building each run's seeded load,
+admission, polling); every step of every run executes in the library's kernels.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import PP_BATCH_DONE, PP_BATCH_FAILED, PP_MIXED32, Batch, PPError, Simulation
+
+
+def _build(req, precision, stream):
+    import pp_synth
+    L = pp_synth.run_load(req)
+    sim = Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=req.get("shape", 3),
+                     precision=precision, sort_interval=20, relax_max_iter=100,
+                     relax_tol=1e-6 if precision == PP_MIXED32 else 1e-12, stream=stream)
+    for s in L.species:
+        sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+        sim.load_particles(sid, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    return sim, L.n_particles
+
+
+def _summary(lat, work, makespan):
+    lat = np.asarray(lat, dtype=float)
+    return {"requests": int(lat.size), "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_s": float(np.percentile(lat, 99)) if lat.size else None, "makespan_s": makespan,
+            "particle_steps_per_s": work / makespan if makespan > 0 else None}
+
+
+def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, keep=False):
+    """Continuous batching.  Returns (summary, per-request results); with keep
+    the finished Simulations are returned too (for comparisons)."""
+    import torch
+    pending = sorted(requests, key=lambda r: r.get("arrival", 0.0))
+    batch = Batch(budget_bytes, max_slots)
+    active = {}
+    lat, work, results = [], 0, []
+    t0 = time.perf_counter()
+    while pending or active:
+        now = time.perf_counter() - t0
+        while pending and pending[0].get("arrival", 0.0) <= now:
+            req = pending[0]
+            stream = torch.cuda.Stream()
+            sim, npart = _build(req, precision, stream.cuda_stream)
+            slot = batch.admit(sim, req["steps"])
+            if slot is None:          # full: retry once capacity frees up
+                sim.close()
+                break
+            pending.pop(0)
+            active[slot] = (req, sim, npart, stream)
+        if not active:
+            if pending:
+                time.sleep(max(0.0, min(0.01, pending[0].get("arrival", 0.0) - now)))
+            continue
+        batch.advance(chunk)
+        for slot in list(active):
+            state, _ = batch.poll(slot)
+            if state in (PP_BATCH_DONE, PP_BATCH_FAILED):
+                req, sim, npart, stream = active.pop(slot)
+                t = time.perf_counter() - t0
+                if state == PP_BATCH_FAILED:
+                    raise PPError(state, f"request {req.get('seed')} failed")
+                lat.append(t - req.get("arrival", 0.0))
+                work += npart * req["steps"]
+                results.append((req, sim if keep else None))
+                if not keep:
+                    sim.close()
+    makespan = time.perf_counter() - t0
+    batch.close()
+    return _summary(lat, work, makespan), results
+
+
+def sequential(requests, precision=PP_MIXED32, keep=False):
+    """The same requests one at a time, in arrival order, on one stream."""
+    import torch
+    pending = sorted(requests, key=lambda r: r.get("arrival", 0.0))
+    lat, work, results = [], 0, []
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    for req in pending:
+        now = time.perf_counter() - t0
+        if req.get("arrival", 0.0) > now:
+            time.sleep(req["arrival"] - now)
+        sim, npart = _build(req, precision, stream)
+        sim.step(req["steps"])
+        sim.sync()
+        t = time.perf_counter() - t0
+        lat.append(t - req.get("arrival", 0.0))
+        work += npart * req["steps"]
+        results.append((req, sim if keep else None))
+        if not keep:
+            sim.close()
+    makespan = time.perf_counter() - t0
+    return _summary(lat, work, makespan), results

@@ -236,3 +236,53 @@ def quiet_two_stream(nx=32, ntr=2, dx=0.25, dt=0.125, ppc=8, beta=0.2, mode=2, e
     L = Load(n=(nx, ntr, ntr), d=(dx, dx, dx), dt=dt, species=species)
     L.params = dict(workload="quiet-two-stream", beta=beta, mode=mode, k=kx)
     return L
+
+
+# --------------------------------------------------------------------------
+# Independent-run workloads of the batched and served forms.
+# --------------------------------------------------------------------------
+
+def run_load(req) -> Load:
+    """The seeded load of one independent run described by a request dict
+    (kind, n, ppc, plasma, seed; see batched_runs / serving_trace)."""
+    n = (req["n"],) * 3
+    masses = (1.0, 25.0) if req.get("plasma") == "ion" else (1.0, 1.0)
+    ppc = max(2, int(req["ppc"]) // 2 * 2)
+    # two-stream and Weibel loads are both counter-streaming neutral beams along x;
+    # they differ in drift and temperature (set by the request)
+    pops = [Population(ppc // 2, 0.5, +req["beta"], req["u_th"]), Population(ppc // 2, 0.5, -req["beta"], req["u_th"])]
+    dx = req.get("dx", 0.5)
+    L = pair_plasma(n, (dx, dx, dx), 0.5 * dx, pops, req["seed"], masses=masses)
+    L.params = dict(workload=req["kind"], shape_order=req.get("shape", 3), field_order=6, alpha=0.55)
+    return L
+
+
+def batched_runs(n_runs=64, seed=1215, edges=tuple(range(16, 97, 8)), ppc=(8, 64), steps=300):
+    """64 independent runs of uneven size: cubic edge uniform in {16, 24, .., 96},
+    ppc per species uniform in [8, 64], drift 0.05..0.5 c, u_th 0.01..0.1 c,
+    TSC or PCS by coin flip (two-stream pair plasmas)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n_runs):
+        out.append(dict(kind="two-stream", n=int(rng.choice(edges)), ppc=int(rng.integers(ppc[0], ppc[1] + 1)),
+                        beta=float(rng.uniform(0.05, 0.5)), u_th=float(rng.uniform(0.01, 0.1)),
+                        shape=int(rng.choice([2, 3])), plasma="pair", steps=int(steps), seed=seed * 1000 + k))
+    return out
+
+
+def serving_trace(n_requests=256, rate=20.0, seed=1216, edges=tuple(range(32, 193, 16)), ppc=(8, 32),
+                  steps=(200, 1000)):
+    """Poisson arrivals (mean `rate` per second) of two-stream and Weibel runs:
+    cubic edge from `edges`, ppc per species in [ppc], pair or mass-ratio-25
+    plasma, steps uniform in [steps]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for k in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        kind = "two-stream" if rng.random() < 0.5 else "weibel"
+        out.append(dict(arrival=t, kind=kind, n=int(rng.choice(edges)), ppc=int(rng.integers(ppc[0], ppc[1] + 1)),
+                        beta=0.2 if kind == "two-stream" else 0.5, u_th=0.05 if kind == "two-stream" else 0.1,
+                        plasma="pair" if rng.random() < 0.5 else "ion", shape=3,
+                        steps=int(rng.integers(steps[0], steps[1] + 1)), seed=seed * 1000 + k))
+    return out

@@ -69,3 +69,20 @@ def test_descriptor_validation_without_gpu(built, bad):
     with pytest.raises(built.PPError) as ei:
         built.Simulation(n, kw["d"], dt, stream=0, **bad)
     assert ei.value.code == built.PP_EINVAL
+
+
+def test_batch_create_validation_without_gpu(built):
+    import ctypes as C
+    lib = built.lib()
+    b = C.c_void_p()
+    assert lib.pp_batch_create(C.byref(b), 0, 4) == built.PP_EINVAL
+    assert lib.pp_batch_create(C.byref(b), 1 << 30, 0) == built.PP_EINVAL
+    assert lib.pp_batch_create(C.byref(b), 1 << 30, 4) == built.PP_OK
+    used = C.c_int64(-1)
+    active = C.c_int(-1)
+    assert lib.pp_batch_used(b, C.byref(used), C.byref(active)) == built.PP_OK
+    assert (used.value, active.value) == (0, 0)
+    state = C.c_int(-1)
+    assert lib.pp_batch_poll(b, 0, None, C.byref(state)) == built.PP_OK and state.value == built.PP_BATCH_FREE
+    assert lib.pp_batch_poll(b, 9, None, C.byref(state)) == built.PP_EINVAL
+    assert lib.pp_batch_destroy(b) == built.PP_OK
