@@ -14,7 +14,7 @@
 
 #include <new>
 
-#include "pp_internal.cuh"
+#include "pp_ctx.cuh"
 
 using namespace pp;
 

@@ -12,7 +12,7 @@
 #include <new>
 #include <vector>
 
-#include "pp_internal.cuh"
+#include "pp_ctx.cuh"
 
 using namespace pp;
 

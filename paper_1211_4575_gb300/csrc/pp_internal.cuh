@@ -358,6 +358,3 @@ cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, d
 cudaError_t launch_check_finite(Ctx &c, int64_t n, const double *const *arrs, int narr, int *flag);
 
 }  // namespace pp
-
-// The opaque handle of include/pp.h is the context itself.
-struct pp_ctx : public pp::Ctx {};
