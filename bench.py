@@ -140,6 +140,22 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x, dist, device):
+    """Max of a float over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(particles_per_rank, world, steps, max_ms):
+    """Whole-job throughput of independent replicas: every rank's particle-steps
+    over the slowest rank's time."""
+    return particles_per_rank * world * steps / (max_ms * 1e-3)
+
+
 def oracle_rate(a, steps, warmup=0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
     same physics and per-cell loading on a sample_n^3 periodic box."""
@@ -235,12 +251,9 @@ def run_gpu(a):
     prof = sim.profile_read()
     sim.profile_enable(False)
     sim.sync()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, "cuda")
     total_particles = npart * world
-    value = total_particles * a.steps / (ms * 1e-3)
+    value = replica_value(npart, world, a.steps, ms)
 
     # roofline of the dominant kernel (the fused particle kernel)
     peak, peak_kind = measured_peak()
@@ -268,11 +281,7 @@ def run_gpu(a):
         sim2.step(a.steps)
         d2 = sim2.diagnostics()
         t1 = time.perf_counter()
-        el = t1 - t0
-        if dist is not None:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = reduce_max(t1 - t0, dist, "cuda")
         e2e = {"value": total_particles * a.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": h2d // max(1, a.steps), "d2h_bytes_per_step": 200 // max(1, a.steps),
                "seconds": el, "status": d2["status"]}

@@ -185,6 +185,13 @@ int pp_field_update(pp_ctx *ctx);
  * per-step sort "according to the cell position"). */
 int pp_sort(pp_ctx *ctx);
 
+/* Change the cell-sort interval (>= 0) and the deposit mode (PP_DEPOSIT_*) of
+ * a live context; both take effect from the next step and change only how
+ * fast a step runs, not what it computes (the tuning knobs of the
+ * autotuner).  PP_EINVAL for values the context cannot use (the tiled
+ * deposit needs PP_MIXED32 and grid sizes that are multiples of 8). */
+int pp_set_tuning(pp_ctx *ctx, int sort_interval, int deposit_mode);
+
 /* Synchronise the context's stream and return the device status word as a
  * PP_* code (PP_ECFL, PP_ENAN, PP_ENOCONV, ...; PP_OK when clean).  Clears it. */
 int pp_sync(pp_ctx *ctx);

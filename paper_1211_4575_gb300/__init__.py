@@ -77,6 +77,7 @@ SIGNATURES = {
     "pp_field_update": (C.c_int, [_P]),
     "pp_sort": (C.c_int, [_P]),
     "pp_sync": (C.c_int, [_P]),
+    "pp_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "pp_diagnostics": (C.c_int, [_P, C.POINTER(Diag)]),
     "pp_get_fields": (C.c_int, [_P, _PP, _PP, _PP]),
     "pp_get_rho": (C.c_int, [_P, _P]),
@@ -247,6 +248,9 @@ class Simulation:
 
     def sync(self):
         self._c(lib().pp_sync(self._ctx))
+
+    def set_tuning(self, sort_interval: int, deposit_mode: int):
+        self._c(lib().pp_set_tuning(self._ctx, int(sort_interval), int(deposit_mode)))
 
     # -- readback -----------------------------------------------------------
     def diagnostics(self) -> dict:

@@ -558,6 +558,18 @@ extern "C" int pp_field_update(pp_ctx *p) {
     return field_phase(c);
 }
 
+extern "C" int pp_set_tuning(pp_ctx *p, int sort_interval, int deposit_mode) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (sort_interval < 0) return fail(c, PP_EINVAL, "sort_interval must be >= 0");
+    if (deposit_mode < 0 || deposit_mode > 2) return fail(c, PP_EINVAL, "unknown deposit_mode");
+    if (deposit_mode == PP_DEPOSIT_TILED && !tiled_supported(*c))
+        return fail(c, PP_EINVAL, "the tiled deposit needs PP_MIXED32 and grid sizes that are multiples of 8");
+    c->d.sort_interval = sort_interval;
+    c->d.deposit_mode = deposit_mode;
+    return PP_OK;
+}
+
 static int status_code(int bits) {
     if (bits & ST_NAN) return PP_ENAN;
     if (bits & ST_CFL) return PP_ECFL;

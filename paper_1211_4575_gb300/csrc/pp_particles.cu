@@ -259,9 +259,10 @@ struct SmemAcc {
     __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
         return Fw[(kind * 3 + comp) * kWin3 + at(i, j, k)];
     }
+    // v is pre-scaled by the fixed-point unit.  Zero contributions are added
+    // too: a per-site test costs more than the extra shared-memory traffic.
     __device__ __forceinline__ void addJ(int comp, int i, int j, int k, float v) const {
-        int iv = __float2int_rn(v);   // v is pre-scaled by the fixed-point unit
-        if (iv != 0) atomicAdd(J + comp * kWin3 + at(i, j, k), iv);
+        atomicAdd(J + comp * kWin3 + at(i, j, k), __float2int_rn(v));
     }
 };
 

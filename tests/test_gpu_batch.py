@@ -87,3 +87,20 @@ def test_admission_by_budget_and_slots(pp):
     assert batch.used() == (0, 0)
     assert batch.admit(c, 2) is not None             # capacity came back
     batch.close()
+
+
+def test_autotuner_picks_a_candidate_and_keeps_physics(pp):
+    import pp_synth
+    from paper_1211_4575_gb300 import autotune
+    L = pp_synth.thermal(n=(16, 16, 16), ppc=8, dx=0.1, dt=0.05, seed=3)
+    sim = H.gpu_sim(pp, L, pp.PP_MIXED32, 3)
+    best, timings = autotune.autotune(sim, sort_intervals=(2, 4), steps=4, use_cache=False)
+    assert best in timings and len(timings) == 4
+    g, _ = sim.grid()
+    assert (g.sort_interval, g.deposit_mode) == best
+    d = sim.diagnostics()
+    assert d["status"] == 0 and d["step"] == 16
+    assert d["gauss_drift_max"] <= 2e-5 * d["rho_max"]
+    with pytest.raises(pp.PPError):
+        H.gpu_sim(pp, pp_synth.thermal(n=(12, 12, 12), ppc=2, dx=0.1, dt=0.05), pp.PP_MIXED32, 3).set_tuning(
+            20, pp.PP_DEPOSIT_TILED)
