@@ -35,9 +35,9 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # DRAM traffic of the fused particle kernel per particle, from the committed ncu
 # capture profiles/k_particles_tiled_thermal64.md (64^3 x 32 ppc; traffic grows
 # with the particle count).  Valid only for the kernel sources it was taken on.
-PROFILED_BYTES_PER_PARTICLE = 902.620160e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 906.302720e6 / 16777216
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "dc1a870ca812fd94c679263148181883e382bf3987a9435419bd450134926c53",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "6bf89df4b7a27e63f2f445318a437eed212d8a62f6b4adb088d509a6970a6b39",
     "paper_1211_4575_gb300/csrc/pp_internal.cuh": "8daecefd83d3900ac9d04ed13b1c9b100583e3bc677e2a6ee4388832d3fd060e",
 }
 
