@@ -33,12 +33,17 @@ UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp32 momenta) read + written
 
 # DRAM traffic of the fused particle kernel per particle, from the committed ncu
-# capture profiles/k_particles_tiled_thermal64.md (64^3 x 32 ppc; traffic grows
-# with the particle count).  Valid only for the kernel sources it was taken on.
-PROFILED_BYTES_PER_PARTICLE = 906.302720e6 / 16777216
+# capture of the 64^3 x 32 ppc thermal workload kept under profiles/ (traffic
+# grows with the particle count).  Valid only for the kernel sources it was
+# taken on: the device header, the sort (its key sets the particle order the
+# kernel streams) and the part of pp_particles.cu that holds the particle
+# kernels (up to its charge-density section).
+PROFILED_BYTES_PER_PARTICLE = 908.550656e6 / 16777216
+_KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "6bf89df4b7a27e63f2f445318a437eed212d8a62f6b4adb088d509a6970a6b39",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "8daecefd83d3900ac9d04ed13b1c9b100583e3bc677e2a6ee4388832d3fd060e",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "c76df3f45ff3f9a7948ef6d5e5a35f4a0ff5dfb17ccd13df379d6548ed2e3883",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "33fbe4d172dede805a55432a29b6e43b0e876207361cc42374d517df7fd88bd7",
+    "paper_1211_4575_gb300/csrc/pp_sort.cu": "afba1e3d446de9e5ddbbde1047e965224b0e9e36a84f07db1d2c137e596077e7",
 }
 
 
@@ -46,9 +51,12 @@ def profiled_traffic(particles_per_launch):
     """ncu DRAM bytes per launch scaled to this launch, or None once the kernel changed."""
     import hashlib
     for rel, digest in PROFILED_SOURCES.items():
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != digest:
-                return None
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        if rel.endswith("pp_particles.cu"):
+            text = text[: text.index(_KERNEL_END)]
+        if hashlib.sha256(text.encode()).hexdigest() != digest:
+            return None
     return PROFILED_BYTES_PER_PARTICLE * particles_per_launch
 
 

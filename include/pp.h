@@ -72,7 +72,8 @@ extern "C" {
 typedef struct pp_ctx pp_ctx;
 
 /* Grid and solver parameters (Sec. III).  Validation (PP_EINVAL): n >= 1 per
- * axis and <= 1023; d > 0; dt > 0 with c*dt/d < 1 on every axis (a particle
+ * axis and <= 1023, at most 2^28 cells once each size is rounded up to a
+ * multiple of 8; d > 0; dt > 0 with c*dt/d < 1 on every axis (a particle
  * crosses at most one cell face per step); c = eps0 = 1; field_order in
  * {2,4,6}; 0.5 <= alpha < 1 (eq:bnplus1); shape_order in {1,2,3} (CIC, TSC,
  * PCS of Sec. II); pusher PP_VAY or PP_BORIS; precision PP_FP64 or

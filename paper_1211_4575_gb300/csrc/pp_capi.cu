@@ -143,6 +143,13 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
         if (!(d->dt > 0.0) || !(d->dt / h[a] < 1.0))
             return fail(c, PP_EINVAL, "need 0 < c dt / d < 1 on every axis (axis %d: %g)", a, d->dt / h[a]);
     }
+    {
+        // int32 sort keys: tile-padded cells times the octant sub-keys must stay below 2^31
+        int64_t padded = 1;
+        for (int a = 0; a < 3; ++a) padded *= (int64_t)((n[a] + 7) / 8 * 8);
+        if (padded * kSubKeys >= ((int64_t)1 << 31))
+            return fail(c, PP_EINVAL, "grid of %lld (tile-padded) cells above the 2^28 limit", (long long)padded);
+    }
     if (d->c != 1.0 || d->eps0 != 1.0) return fail(c, PP_EINVAL, "the library is normalised to c = eps0 = 1");
     if (d->field_order != 2 && d->field_order != 4 && d->field_order != 6)
         return fail(c, PP_EINVAL, "field_order must be 2, 4 or 6");

@@ -16,6 +16,7 @@ namespace pp {
 // Mesh geometry: every mesh array is padded by G ghost layers per side,
 // x fastest.  Interior index (i,j,k) in [0,n) maps to the padded offset below.
 // ---------------------------------------------------------------------------
+constexpr int kSubKeys = 8;  // sort sub-keys per cell: the octant of the particle inside it
 constexpr int kGhost = 5;   // covers the deposit reach of a particle sorted up to
                             // two cells outside its tile plus the PCS support
 

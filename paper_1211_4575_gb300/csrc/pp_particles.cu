@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int s = 0; s < T.ns; ++s) {
         const TiledSpecies &S = T.sp[s];
-        const int tb = S.cell_start[tile * kTileCells], te = S.cell_start[(tile + 1) * kTileCells];
+        const int tb = S.cell_start[tile * kTileCells * kSubKeys], te = S.cell_start[(tile + 1) * kTileCells * kSubKeys];
         for (int cb = tb; cb < te; cb += kChunk) {
             const int cn = min(kChunk, te - cb);
             if (threadIdx.x < 3) {
@@ -615,6 +615,88 @@ __global__ void k_rho(Geom g, double qw, int64_t n, Fp64Particles p64, MixedPart
     deposit_rho<O, double>(acc, xi, qw);
 }
 
+// Cell-sorted form: thread k owns cell k (its kSubKeys consecutive sort keys) and sums the eq:rho2
+// weights of that cell's particles in FP64 registers over a fixed frame of
+// nodes around the cell, then adds the frame to the mesh once, instead of
+// once per particle.  A particle that moved to another cell since the sort
+// is added directly.
+struct RhoCellGeom {
+    int T[3];
+    int nt[3];
+    int tile_vol;
+};
+
+// A (accumulation type) is double for FP64 contexts and float for the mixed
+// form, whose positions are FP32 already; the mesh sum stays FP64.
+template <int O, typename A>
+__global__ void __launch_bounds__(128) k_rho_cells(Geom g, RhoCellGeom kg, int64_t nkeys, const int32_t *cell_start,
+                                                   double qw, Fp64Particles p64, MixedParticles pm, int mixed,
+                                                   double *rho) {
+    constexpr bool odd = (O % 2) == 1;
+    constexpr int NF = odd ? O + 1 : O + 2;         // frame nodes per axis
+    constexpr int ST = odd ? -(O - 1) / 2 : -O / 2; // frame start relative to the cell
+    int64_t key = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= nkeys) return;
+    const int b = cell_start[key * kSubKeys], e = cell_start[(key + 1) * kSubKeys];
+    if (b == e) return;
+    int tile = (int)(key / kg.tile_vol), loc = (int)(key % kg.tile_vol);
+    int c0 = (tile % kg.nt[0]) * kg.T[0] + loc % kg.T[0];
+    int c1 = ((tile / kg.nt[0]) % kg.nt[1]) * kg.T[1] + (loc / kg.T[0]) % kg.T[1];
+    int c2 = (tile / (kg.nt[0] * kg.nt[1])) * kg.T[2] + loc / (kg.T[0] * kg.T[1]);
+    A acc[NF][NF][NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+#pragma unroll
+            for (int i = 0; i < NF; ++i) acc[k][j][i] = A(0);
+    for (int t = b; t < e; ++t) {
+        int cx, cy, cz;
+        double xi[3];
+        if (mixed) {
+            unpack_cell(pm.cell[t], cx, cy, cz);
+            xi[0] = pm.ox[t]; xi[1] = pm.oy[t]; xi[2] = pm.oz[t];
+        } else {
+            double X[3] = {p64.x[t], p64.y[t], p64.z[t]};
+            int cc[3];
+            for (int a = 0; a < 3; ++a) {
+                cc[a] = min(max((int)floor(X[a]), 0), g.n[a] - 1);
+                xi[a] = X[a] - cc[a];
+            }
+            cx = cc[0]; cy = cc[1]; cz = cc[2];
+        }
+        if (cx != c0 || cy != c1 || cz != c2) {   // left its sorted cell: add it directly
+            RhoAcc acc1{g, rho, cx, cy, cz};
+            deposit_rho<O, double>(acc1, xi, qw);
+            continue;
+        }
+        A w[3][NF];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            A ws[O + 1];
+            int sh = support<O, A>((A)xi[a], false, ws) - ST;   // 0, or 1 for even orders
+#pragma unroll
+            for (int m = 0; m < NF; ++m) w[a][m] = (m - sh >= 0 && m - sh <= O) ? ws[m - sh] : A(0);
+        }
+#pragma unroll
+        for (int k = 0; k < NF; ++k)
+#pragma unroll
+            for (int j = 0; j < NF; ++j) {
+                A wjk = w[1][j] * w[2][k];
+#pragma unroll
+                for (int i = 0; i < NF; ++i) acc[k][j][i] += w[0][i] * wjk;
+            }
+    }
+    RhoAcc out{g, rho, c0, c1, c2};
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+#pragma unroll
+            for (int i = 0; i < NF; ++i)
+                if (acc[k][j][i] != A(0)) out.addRho(ST + i, ST + j, ST + k, qw * (double)acc[k][j][i]);
+}
+
 cudaError_t launch_rho(Ctx &c) {
     cudaError_t e = cudaMemsetAsync(c.rho, 0, sizeof(double) * c.g.cells(), c.st);
     if (e != cudaSuccess) return e;
@@ -623,9 +705,29 @@ cudaError_t launch_rho(Ctx &c) {
         if (S.n == 0) continue;
         Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
         MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
-        unsigned blocks = (unsigned)(((S.n + 31) / 32 * 32 + 255) / 256);
         double qw = S.q * S.w;
         int mixed = c.fp64 ? 0 : 1;
+        if (S.sorted) {
+            RhoCellGeom kg;
+            for (int a = 0; a < 3; ++a) {
+                kg.T[a] = c.tile[a];
+                kg.nt[a] = c.ntile[a];
+            }
+            kg.tile_vol = c.tile[0] * c.tile[1] * c.tile[2];
+            int64_t ncell = c.nkeys / kSubKeys;
+            unsigned kb = (unsigned)((ncell + 127) / 128);
+#define PP_R(O, A) k_rho_cells<O, A><<<kb, 128, 0, c.st>>>(c.g, kg, ncell, S.cell_start, qw, p64, pm, mixed, c.rho)
+            if (mixed) {
+                if (c.d.shape_order == 1) PP_R(1, float); else if (c.d.shape_order == 2) PP_R(2, float); else PP_R(3, float);
+            } else {
+                if (c.d.shape_order == 1) PP_R(1, double); else if (c.d.shape_order == 2) PP_R(2, double); else PP_R(3, double);
+            }
+#undef PP_R
+            ++c.nlaunch;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            continue;
+        }
+        unsigned blocks = (unsigned)(((S.n + 31) / 32 * 32 + 255) / 256);
         if (c.d.shape_order == 1) k_rho<1><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);
         else if (c.d.shape_order == 2) k_rho<2><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);
         else k_rho<3><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);

@@ -4,7 +4,11 @@
 //
 // The key of a particle is its cell, numbered tile by tile (tiles of up to
 // 8x8x8 cells, x fastest inside a tile and across tiles), so that the sorted
-// arrays hold every tile as one contiguous range.  Pipeline: key + histogram
+// arrays hold every tile as one contiguous range, times kSubKeys plus the
+// octant of the particle inside its cell (which half of the cell on each
+// axis).  The octant order makes particles of equal rank in neighbouring
+// cells sit in the same half-cell, so that the lanes of a warp in the tiled
+// kernel use the same stencil offsets.  Pipeline: key + histogram
 // (warp-aggregated atomics) -> exclusive scan -> scatter through per-key
 // cursors.  The order inside a cell is not deterministic.
 #include "pp_internal.cuh"
@@ -52,16 +56,19 @@ __global__ void k_keys_fp64(KeyGeom kg, int64_t n, const double *x, const double
     cx = min(max(cx, 0), kg.n[0] - 1);
     cy = min(max(cy, 0), kg.n[1] - 1);
     cz = min(max(cz, 0), kg.n[2] - 1);
-    int32_t key = cell_key(kg, cx, cy, cz);
+    int oct = (x[t] - cx >= 0.5 ? 1 : 0) | (y[t] - cy >= 0.5 ? 2 : 0) | (z[t] - cz >= 0.5 ? 4 : 0);
+    int32_t key = cell_key(kg, cx, cy, cz) * kSubKeys + oct;
     keys[t] = key;
     aggregated_add(counts, key);
 }
 
-__global__ void k_keys_mixed(KeyGeom kg, int64_t n, const int32_t *cell, int32_t *keys, int32_t *counts) {
+__global__ void k_keys_mixed(KeyGeom kg, int64_t n, const int32_t *cell, const float *ox, const float *oy,
+                             const float *oz, int32_t *keys, int32_t *counts) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     int32_t c = cell[t];
-    int32_t key = cell_key(kg, c & 1023, (c >> 10) & 1023, (c >> 20) & 1023);
+    int oct = (ox[t] >= 0.5f ? 1 : 0) | (oy[t] >= 0.5f ? 2 : 0) | (oz[t] >= 0.5f ? 4 : 0);
+    int32_t key = cell_key(kg, c & 1023, (c >> 10) & 1023, (c >> 20) & 1023) * kSubKeys + oct;
     keys[t] = key;
     aggregated_add(counts, key);
 }
@@ -177,7 +184,7 @@ cudaError_t sort_setup(Ctx &c) {
         c.tile[a] = c.g.n[a] < 8 ? c.g.n[a] : 8;
         c.ntile[a] = (c.g.n[a] + c.tile[a] - 1) / c.tile[a];
     }
-    c.nkeys = (int64_t)c.ntile[0] * c.ntile[1] * c.ntile[2] * c.tile[0] * c.tile[1] * c.tile[2];
+    c.nkeys = (int64_t)c.ntile[0] * c.ntile[1] * c.ntile[2] * c.tile[0] * c.tile[1] * c.tile[2] * kSubKeys;
     cudaError_t e = cudaMalloc(&c.counts, sizeof(int32_t) * (c.nkeys + 1));
     if (e != cudaSuccess) return e;
     c.scan_tmp_bytes = sizeof(int32_t) * scan_tmp_count(c.nkeys + 1);
@@ -193,7 +200,7 @@ cudaError_t launch_sort(Ctx &c, int s) {
     KeyGeom kg = key_geom(c);
     unsigned blocks = (unsigned)((S.n + 255) / 256);
     if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
-    else k_keys_mixed<<<blocks, 256, 0, c.st>>>(kg, S.n, S.cell, S.keys, c.counts);
+    else k_keys_mixed<<<blocks, 256, 0, c.st>>>(kg, S.n, S.cell, S.ox, S.oy, S.oz, S.keys, c.counts);
     ++c.nlaunch;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // cell_start = exclusive scan of counts; counts then becomes the cursor
