@@ -48,7 +48,7 @@ class Grid(C.Structure):
 class Species(C.Structure):
     _fields_ = [("q", C.c_double), ("m", C.c_double), ("w", C.c_double), ("n", C.c_int64),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
-                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p)]
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p), ("rad", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -73,6 +73,7 @@ def lib():
         L.orc_gather.argtypes = [C.POINTER(Grid), P, P, P, P, P]
         L.orc_push_vay.argtypes = [C.c_double, P, P, P]
         L.orc_push_boris.argtypes = [C.c_double, P, P, P]
+        L.orc_radiate.argtypes = [C.c_double, C.c_double, P, P]
         L.orc_deposit_particle.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, P, P, P, P]
         L.orc_current_from_drho.argtypes = [C.POINTER(Grid), P, P, P]
         L.orc_field_update.argtypes = [C.POINTER(Grid), P, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -151,6 +152,14 @@ def push(qmdt: float, E, B, u, pusher=VAY) -> np.ndarray:
     return u
 
 
+def radiate(K: float, dt: float, um, u) -> np.ndarray:
+    """Radiative cooling of one push: p- = um, p+^EM = u; returns p+."""
+    um = np.asarray(um, dtype=np.float64).copy()
+    u = np.asarray(u, dtype=np.float64).copy()
+    lib().orc_radiate(float(K), float(dt), _ptr(um), _ptr(u))
+    return u
+
+
 def deposit_particle(g: Grid, q, w, x0, x1, Drho=None, lsum=None):
     """Accumulate one particle's D rho (3 mesh arrays) and line sums."""
     nx, ny, nz = g.n
@@ -208,16 +217,18 @@ class Simulation:
         self.relax_residual = 0.0
         self.nstep = 0
 
-    def add_species(self, q, m, w, x, y, z, ux, uy, uz) -> int:
+    def add_species(self, q, m, w, x, y, z, ux, uy, uz, rad=0.0) -> int:
+        """rad: coefficient mu0 q^2 / (6 pi m c) of radiative cooling (0 = off)."""
         arrs = {k: np.ascontiguousarray(v, dtype=np.float64).copy()
                 for k, v in dict(x=x, y=y, z=z, ux=ux, uy=uy, uz=uz).items()}
-        self.species.append(dict(q=float(q), m=float(m), w=float(w), **arrs))
+        self.species.append(dict(q=float(q), m=float(m), w=float(w), rad=float(rad), **arrs))
         return len(self.species) - 1
 
     def _sp(self):
         arr = (Species * max(1, len(self.species)))()
         for i, s in enumerate(self.species):
             arr[i].q, arr[i].m, arr[i].w, arr[i].n = s["q"], s["m"], s["w"], len(s["x"])
+            arr[i].rad = s["rad"]
             for k in ("x", "y", "z", "ux", "uy", "uz"):
                 setattr(arr[i], k, s[k].ctypes.data)
         return arr

@@ -37,6 +37,13 @@
  *   R5  "Successive relaxation" of eq:EllipticB is read as Jacobi iteration.
  *   R6  Each field component is gathered from its own staggered nodes with the
  *       same weight function as the deposit (eq:pfields, eq:rho2).
+ *   R7  Radiative cooling (Sec. "Radiative cooling") is the explicit form the
+ *       paper settles on: no iteration, so the proper acceleration inside the
+ *       radiated power of eq:prad is the Lorentz one, (p+^EM - p-)/dt, and
+ *       p0 = (p+^EM + p-)/2.  The coefficient mu0 q^2/(6 pi m c) is a species
+ *       parameter: in a normalised code it depends on the physical unit of
+ *       length, which the paper fixes elsewhere.  A particle with p0 = 0 does
+ *       not radiate (eq:udot has no direction there).
  */
 #include <math.h>
 #include <stdint.h>
@@ -60,6 +67,7 @@ typedef struct {
     int64_t n;           /* number of macro-particles */
     double *x, *y, *z;   /* positions */
     double *ux, *uy, *uz;/* proper velocity gamma*v, staggered to t - dt/2 */
+    double rad;          /* mu0 q^2 / (6 pi m c) of eq:udot; 0 = no radiative cooling */
 } orc_species;
 
 typedef struct {
@@ -284,6 +292,27 @@ void orc_push_boris(double qmdt, const double E[3], const double B[3], double u[
     double upxs[3];
     cross3(uprime, sv, upxs);
     for (int a = 0; a < 3; ++a) u[a] = um[a] + upxs[a] + 0.5 * qmdt * E[a];
+}
+
+/* Radiative cooling of one particle (Sec. "Radiative cooling"): um is the
+ * proper velocity p- at t - dt/2, u holds p+^EM from the Lorentz push and
+ * receives p+ = p+^EM + pdot_rad dt.  K = mu0 q^2 / (6 pi m c), c = 1.       */
+void orc_radiate(double K, double dt, const double um[3], double u[3])
+{
+    double p0[3], pdot[3];
+    for (int a = 0; a < 3; ++a) {
+        p0[a] = 0.5 * (u[a] + um[a]);      /* time-averaged proper velocity */
+        pdot[a] = (u[a] - um[a]) / dt;     /* time-centred proper acceleration */
+    }
+    double p2 = dot3(p0, p0);
+    if (p2 == 0.0) return;
+    double gamma0 = sqrt(1.0 + p2);
+    double pxp[3];
+    cross3(pdot, p0, pxp);
+    double bracket = dot3(pdot, pdot) + dot3(pxp, pxp);   /* eq:prad over mu0 q^2 / (6 pi c) */
+    double prad[3];
+    for (int a = 0; a < 3; ++a) prad[a] = -K * gamma0 / p2 * bracket * p0[a];   /* eq:udot */
+    for (int a = 0; a < 3; ++a) u[a] += prad[a] * dt;
 }
 
 /* ------------------------------------------------------------------ */
@@ -549,10 +578,12 @@ void orc_particles_deposit(const orc_grid *g, double *E[3], double *B[3], orc_sp
         for (int64_t p = 0; p < P->n; ++p) {
             double x0[3] = {P->x[p], P->y[p], P->z[p]};
             double u[3] = {P->ux[p], P->uy[p], P->uz[p]};
+            double um[3] = {u[0], u[1], u[2]};
             double Ep[3], Bp[3];
             orc_gather(g, E, B, x0, Ep, Bp);
             if (g->pusher == 1) orc_push_boris(qmdt, Ep, Bp, u);
             else orc_push_vay(qmdt, Ep, Bp, u);
+            if (P->rad != 0.0) orc_radiate(P->rad, g->dt, um, u);
             double gam = sqrt(1.0 + dot3(u, u));
             double x1[3];
             for (int a = 0; a < 3; ++a) x1[a] = x0[a] + g->dt * u[a] / gam;

@@ -466,3 +466,92 @@ def test_cold_two_stream_closed_form_values():
     ks = [2 * np.pi * m / 8.0 for m in (4, 5, 6)]
     got = [theory.cold_two_stream(k, beta) for k in ks]
     assert np.allclose(got, [0.452, 0.483, 0.477], atol=1.5e-3)
+
+
+# --------------------------------------------------------------------------
+# Radiative cooling (Sec. "Radiative cooling", eq:prad, eq:udot)
+# --------------------------------------------------------------------------
+
+def _synchrotron_gamma(orc, dt, pusher, T=45.0, K=0.01, g0=10.0, q=-1.0, m=1.0, B=1.0):
+    u = np.array([math.sqrt(g0 * g0 - 1.0), 0.0, 0.0])
+    n = int(round(T / dt))
+    for _ in range(n):
+        um = u.copy()
+        u = orc.push(q * dt / m, [0.0, 0.0, 0.0], [0.0, 0.0, B], u, pusher)
+        u = orc.radiate(K, dt, um, u)
+    # closed form: gamma' = -kappa (gamma^2 - 1), kappa = K (q/m)^2 B^2, so
+    # (gamma - 1)/(gamma + 1) decays as exp(-2 kappa t)
+    kappa = K * (q / m) ** 2 * B * B
+    C = (g0 - 1.0) / (g0 + 1.0) * math.exp(-2.0 * kappa * n * dt)
+    exact = (1.0 + C) / (1.0 - C)
+    return math.sqrt(1.0 + u @ u), exact
+
+
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_synchrotron_cooling_closed_form(orc, pusher):
+    """A particle gyrating perpendicular to a uniform B loses energy at the
+    synchrotron rate: with pdot perpendicular to p the bracket of eq:prad is
+    gamma^2 pdot^2, which gives gamma' = -kappa (gamma^2 - 1).  The explicit
+    scheme converges to that solution at first order in dt."""
+    g1, exact = _synchrotron_gamma(orc, 0.05, pusher)
+    g2, _ = _synchrotron_gamma(orc, 0.025, pusher)
+    e1 = abs(g1 - exact) / (exact - 1.0)
+    e2 = abs(g2 - exact) / (exact - 1.0)
+    assert exact < 2.1   # gamma fell from 10 to about 2: the cooling dominates the run
+    assert e1 < 3e-3 and e2 < 1.5e-3, (e1, e2)
+    assert 1.7 < e1 / e2 < 2.3, (e1, e2)
+
+
+def test_radiated_power_equals_lienard_form_in_three_velocities(orc):
+    """eq:prad (proper velocities) is a rewrite of eq:pradv (three-velocities).
+    With p- = p0 - pdot dt/2 and p+ = p0 + pdot dt/2 the oracle's p0 and pdot
+    are exact, and the energy it removes per step, m (p0 . dp)/(gamma0 dt),
+    must equal eq:pradv at v = p0/gamma0, vdot = d(p/gamma)/dt."""
+    rng = np.random.default_rng(42)
+    K, m, dt = 0.03, 1.0, 0.01
+    for _ in range(200):
+        g = 1.0 + 10.0 ** rng.uniform(-2, 3)
+        p0 = rng.normal(size=3)
+        p0 *= math.sqrt(g * g - 1.0) / np.linalg.norm(p0)
+        pdot = rng.normal(size=3) * 10.0 ** rng.uniform(-2, 1)
+        um, up = p0 - 0.5 * dt * pdot, p0 + 0.5 * dt * pdot
+        out = orc.radiate(K, dt, um, up)
+        dp = out - up
+        gamma0 = math.sqrt(1.0 + p0 @ p0)
+        # the change is along -p0 ...
+        # (dp is a difference of O(|p|) numbers: tolerances follow |p| eps)
+        assert np.linalg.norm(np.cross(dp, p0)) <= 1e-14 * np.linalg.norm(up) * np.linalg.norm(p0)
+        assert dp @ p0 < 0.0
+        power = -m * (p0 @ dp) / (gamma0 * dt)
+        # ... and carries the Lienard power of the three-velocity
+        v = p0 / gamma0
+        vdot = pdot / gamma0 - p0 * (p0 @ pdot) / gamma0 ** 3
+        lienard = K * m * (gamma0 ** 4 * (vdot @ vdot) + gamma0 ** 6 * (vdot @ v) ** 2)
+        # eq:pradv itself cancels to relative eps gamma^2 (the paper's reason for eq:prad)
+        tol = 1e-13 * np.linalg.norm(up) / np.linalg.norm(dp) + 1e-14 * gamma0 ** 2 + 1e-12
+        assert power == pytest.approx(lienard, rel=tol)
+
+
+def test_radiative_cooling_special_cases(orc):
+    u = np.array([0.3, -0.2, 0.5])
+    # no acceleration: no radiation; K = 0: no change; p0 = 0: no direction, no change
+    assert np.array_equal(orc.radiate(0.1, 0.05, u, u), u)
+    assert np.array_equal(orc.radiate(0.0, 0.05, u, 1.1 * u), 1.1 * u)
+    assert np.array_equal(orc.radiate(0.1, 0.05, -u, u), u)
+
+
+def test_cooling_off_leaves_the_step_bit_identical(orc):
+    """rad = 0 must not change a single bit of the step (the term is skipped)."""
+    from pp_synth import thermal
+    L = thermal((8, 8, 8), ppc=4, seed=3)
+    sims = []
+    for rad in (None, 0.0):
+        g = orc.Simulation(L.n, L.d, L.dt, shape_order=3)
+        for s in L.species:
+            kw = {} if rad is None else {"rad": rad}
+            g.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], **kw)
+        g.step(2)
+        sims.append(g)
+    for a in range(3):
+        assert np.array_equal(sims[0].E[a], sims[1].E[a])
+    assert np.array_equal(sims[0].species[0]["ux"], sims[1].species[0]["ux"])
