@@ -38,10 +38,10 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # taken on: the device header, the sort (its key sets the particle order the
 # kernel streams) and the part of pp_particles.cu that holds the particle
 # kernels (up to its charge-density section).
-PROFILED_BYTES_PER_PARTICLE = 908.550656e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 907.673600e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "c76df3f45ff3f9a7948ef6d5e5a35f4a0ff5dfb17ccd13df379d6548ed2e3883",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "b506e86b124f8573eac1967de6efb9a864b252bf52d3c806d6c10b549596e119",
     "paper_1211_4575_gb300/csrc/pp_internal.cuh": "33fbe4d172dede805a55432a29b6e43b0e876207361cc42374d517df7fd88bd7",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "afba1e3d446de9e5ddbbde1047e965224b0e9e36a84f07db1d2c137e596077e7",
 }

@@ -238,7 +238,15 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMargin = 2;                     // drift allowed before the fallback
 constexpr int kReachLo = 2, kReachHi = 3;      // deposit/gather reach around a cell
 constexpr int kWin = kTile + 2 * kMargin + kReachLo + kReachHi;   // 17 nodes per axis
-constexpr int kWin3 = kWin * kWin * kWin;
+// Window layout: x fastest, then z (stride kWin), then y (stride kWinPlane).
+// A warp's lanes take particles 32 sorted positions apart, i.e. one per cell
+// over an 8 x 4 block of cells in x and y.  With y strided by a plane of
+// 296 = 8 (mod 32) words those 32 cells start in 32 distinct banks; a plain
+// 17 x 17 plane folds the block's rows onto each other (2-way conflicts).
+constexpr int kWinPlane = 296;
+static_assert(kWinPlane >= kWin * kWin && kWinPlane % 32 == 8, "plane pitch must hold a 17 x 17 plane, 8 mod 32");
+constexpr int kWinVol = kWinPlane * kWin;      // words per window component
+__device__ __forceinline__ int win(int i, int j, int k) { return j * kWinPlane + k * kWin + i; }
 constexpr int kWinLo = kMargin + kReachLo;     // window node 0 = tile origin - kWinLo
 constexpr int kChunk = 1024;                   // particles staged per round
 constexpr int kPerThread = kChunk / kThreads;  // particles per thread per round
@@ -246,7 +254,8 @@ constexpr int kLaneStride = kChunk / 32;       // sorted-order distance between 
 static_assert(kChunk % kThreads == 0 && kLaneStride == kWarps * kPerThread, "chunk must split evenly over the CTA");
 constexpr int kStage = kChunk + kChunk / 32;   // one pad word per 32 (bank spread)
 constexpr int kStageArrays = 10;               // cell, 3 offsets, 3 momenta, 3 displacements
-constexpr size_t kTiledSmem = sizeof(float) * (9 * kWin3 + kStageArrays * kStage) + sizeof(int) * 16;
+constexpr size_t kTiledSmem = sizeof(float) * (9 * kWinVol + kStageArrays * kStage) + sizeof(int) * 16;
+static_assert(kTiledSmem <= 227 * 1024, "tile CTA must fit the opt-in shared memory");
 constexpr float kFixedRange = 1073741824.0f;   // 2^30
 static_assert(kChunk <= 1024, "the fixed-point bound allows at most 1024 rounding halves per flush");
 constexpr int kMaxTiledSpecies = PP_MAX_SPECIES;
@@ -255,14 +264,14 @@ struct SmemAcc {
     const float *Fw;  // 6 windows: E0 E1 E2 B0 B1 B2
     int *J;           // 3 fixed-point windows
     int base;         // window offset of the particle's cell
-    __device__ __forceinline__ int at(int i, int j, int k) const { return base + (k * kWin + j) * kWin + i; }
+    __device__ __forceinline__ int at(int i, int j, int k) const { return base + win(i, j, k); }
     __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
-        return Fw[(kind * 3 + comp) * kWin3 + at(i, j, k)];
+        return Fw[(kind * 3 + comp) * kWinVol + at(i, j, k)];
     }
     // v is pre-scaled by the fixed-point unit.  Zero contributions are added
     // too: a per-site test costs more than the extra shared-memory traffic.
     __device__ __forceinline__ void addJ(int comp, int i, int j, int k, float v) const {
-        atomicAdd(J + comp * kWin3 + at(i, j, k), __float2int_rn(v));
+        atomicAdd(J + comp * kWinVol + at(i, j, k), __float2int_rn(v));
     }
 };
 
@@ -297,8 +306,8 @@ template <int O, int PUSH>
 __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_constant__ TiledArgs T) {
     extern __shared__ float smem[];
     float *F = smem;
-    int *Jw = (int *)(smem + 6 * kWin3);
-    float *stg = smem + 9 * kWin3;
+    int *Jw = (int *)(smem + 6 * kWinVol);
+    float *stg = smem + 9 * kWinVol;
     int32_t *s_cell = (int32_t *)stg;
     float *s_o = stg + kStage;           // 3 arrays: offsets at t
     float *s_u = stg + 4 * kStage;       // 3 arrays: momenta
@@ -311,13 +320,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
     const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
     const int wx = ox - kWinLo, wy = oy - kWinLo, wz = oz - kWinLo;
     // stage E and B (ghost layers hold the periodic images), clear the current window
-    for (int idx = threadIdx.x; idx < 6 * kWin3; idx += kThreads) {
-        int comp = idx / kWin3, r = idx - comp * kWin3;
-        int i = r % kWin, j = (r / kWin) % kWin, k = r / (kWin * kWin);
+    for (int idx = threadIdx.x; idx < 6 * kWinVol; idx += kThreads) {
+        int comp = idx / kWinVol, r = idx - comp * kWinVol;
+        int j = r / kWinPlane, rem = r - j * kWinPlane;
+        if (rem >= kWin * kWin) continue;   // plane padding, never read
+        int i = rem % kWin, k = rem / kWin;
         const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
         F[idx] = __ldg(src + g.at(wx + i, wy + j, wz + k));
     }
-    for (int idx = threadIdx.x; idx < 3 * kWin3; idx += kThreads) Jw[idx] = 0;
+    for (int idx = threadIdx.x; idx < 3 * kWinVol; idx += kThreads) Jw[idx] = 0;
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                     continue;
                 }
                 float E[3], B[3];
-                SmemAcc sacc{F, Jw, ((rz + kWinLo) * kWin + (ry + kWinLo)) * kWin + (rx + kWinLo)};
+                SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
                 gather_EB<O, float>(sacc, xi0, E, B);
                 if (PUSH == PP_BORIS) push_boris<float>(S.qmdt, E, B, u);
                 else push_vay<float>(S.qmdt, E, B, u);
@@ -418,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 float xi0[3] = {s_o[sq], s_o[kStage + sq], s_o[2 * kStage + sq]};
                 float xi1[3] = {xi0[0] + dx0, xi0[1] + s_d[kStage + sq], xi0[2] + s_d[2 * kStage + sq]};
                 int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
-                SmemAcc sacc{F, Jw, ((rz + kWinLo) * kWin + (ry + kWinLo)) * kWin + (rx + kWinLo)};
+                SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
                 deposit_esirkepov<O, float>(sacc, xi0, xi1, jsc);
                 rebin(xi1[0], cx, g.n[0]);
                 rebin(xi1[1], cy, g.n[1]);
@@ -446,10 +457,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 for (int idx = threadIdx.x; idx < 3 * vol; idx += kThreads) {
                     int comp = idx / vol, r = idx - comp * vol;
                     int i = x0 + r % ex, j = y0 + (r / ex) % ey, k = z0 + r / (ex * ey);
-                    int w = (k * kWin + j) * kWin + i;
-                    int iv = Jw[comp * kWin3 + w];
+                    int w = win(i, j, k);
+                    int iv = Jw[comp * kWinVol + w];
                     if (iv == 0) continue;
-                    Jw[comp * kWin3 + w] = 0;
+                    Jw[comp * kWinVol + w] = 0;
                     float uc = comp == 0 ? unit[0] : (comp == 1 ? unit[1] : unit[2]);
                     atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), (float)iv / uc);
                 }
