@@ -38,11 +38,11 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # taken on: the device header, the sort (its key sets the particle order the
 # kernel streams) and the part of pp_particles.cu that holds the particle
 # kernels (up to its charge-density section).
-PROFILED_BYTES_PER_PARTICLE = 907.673600e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 906.362112e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "b506e86b124f8573eac1967de6efb9a864b252bf52d3c806d6c10b549596e119",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "33fbe4d172dede805a55432a29b6e43b0e876207361cc42374d517df7fd88bd7",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "fb61b196a6ae7c9a0b5a08e39f76c44260ab65e750eecc4c424c8dd04d516ddf",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "cf2c2a0fd8e7d130fa396700ecd19be42d26f281a5d1d9b58144bbff7fc1fab3",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "afba1e3d446de9e5ddbbde1047e965224b0e9e36a84f07db1d2c137e596077e7",
 }
 
@@ -70,6 +70,8 @@ def args():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--ppc", type=int, default=32, help="macro-particles per cell per species")
     ap.add_argument("--deposit", choices=["auto", "global", "tiled"], default="auto")
+    ap.add_argument("--radiation", type=float, default=0.0,
+                    help="radiative-cooling coefficient mu0 q^2/(6 pi m c) for every species (0 = off)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-n", type=int, default=16, help="cells per axis of the oracle sample")
@@ -92,7 +94,8 @@ def workload_name(a, nparticles):
     kind = "thermal pair plasma u_th=0.1c (numerical heating)" if a.workload == "thermal" else \
         "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
     return (f"{kind}, {a.n}^3 cells, dx=0.1, dt=0.05, {a.ppc} per cell per species ({nparticles} particles), "
-            f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset")
+            f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset"
+            + (f", radiative cooling K={a.radiation:g}" if a.radiation else ""))
 
 
 def measured_peak():
@@ -176,7 +179,7 @@ def oracle_rate(a, steps, warmup=0):
     sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
                             relax_max_iter=200)
     for s in L.species:
-        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], rad=a.radiation)
     if warmup:
         sim.step(warmup)
     t0 = time.perf_counter()
@@ -235,6 +238,7 @@ def run_gpu(a):
     sim = make()
     for s in L.species:
         sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+        sim.set_radiative_cooling(sid, a.radiation)
         sim.load_particles(sid, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
     for _ in range(a.warmup):
         sim.step(1)
@@ -285,6 +289,7 @@ def run_gpu(a):
         sim2 = make()
         for s, p in zip(L.species, pinned):
             sid = sim2.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+            sim2.set_radiative_cooling(sid, a.radiation)
             sim2.load_particles(sid, *[p[k].numpy() for k in ("x", "y", "z", "ux", "uy", "uz")])
         sim2.step(a.steps)
         d2 = sim2.diagnostics()

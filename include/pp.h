@@ -148,6 +148,19 @@ int pp_init_grid(pp_ctx **out, const pp_grid_desc *desc);
  * desc->capacity macro-particles.  *species_id receives its index 0, 1, ... */
 int pp_init_species(pp_ctx *ctx, const pp_species_desc *desc, int *species_id);
 
+/* Radiative cooling of species sid (Sec. "Radiative cooling", eq:prad,
+ * eq:udot): after each Lorentz push the proper velocity loses
+ *   pdot_rad dt = -coef gamma0 / p0^2 [pdot0^2 + |pdot0 x p0|^2] p0 dt,
+ * with p0 = (p+ + p-)/2, pdot0 = (p+ - p-)/dt of that push, gamma0 =
+ * sqrt(1 + p0^2), explicit and not iterated (the paper's choice).  coef is
+ * mu0 q^2 / (6 pi m c) of eq:udot in the library's units: it depends on the
+ * physical length unit of the run, so the caller supplies it.  0 (the
+ * default) turns cooling off.  The explicit form assumes that one step
+ * changes the energy by a small fraction.  Errors: PP_EINVAL for a bad sid
+ * or a coefficient that is negative or not finite.  Takes effect at the next
+ * pp_step / pp_deposit. */
+int pp_set_radiative_cooling(pp_ctx *ctx, int sid, double coef);
+
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
@@ -229,9 +242,10 @@ int pp_profile_enable(pp_ctx *ctx, int enable);
 /* Totals since the last pp_profile_enable(ctx, 1) (synchronises). */
 int pp_profile_read(pp_ctx *ctx, pp_profile *out);
 
-/* Checkpoint: write the descriptor, species parameters, step counter, FP64
- * fields and FP64 particle arrays to a file (Sec. IX, each attribute as one
- * 64-bit block so that a restart does not depend on the precision form). */
+/* Checkpoint: write the descriptor, species parameters (with the cooling
+ * coefficient), step counter, FP64 fields and FP64 particle arrays to a file
+ * (Sec. IX, each attribute as one 64-bit block so that a restart does not
+ * depend on the precision form). */
 int pp_save(pp_ctx *ctx, const char *path);
 
 /* Restore a checkpoint written by pp_save into a new context on `stream`. */

@@ -290,6 +290,15 @@ extern "C" int pp_init_species(pp_ctx *p, const pp_species_desc *sd, int *sid) {
     return PP_OK;
 }
 
+extern "C" int pp_set_radiative_cooling(pp_ctx *p, int sid, double coef) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "pp_set_radiative_cooling: NULL context");
+    if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    if (!isfinite(coef) || coef < 0.0) return fail(c, PP_EINVAL, "cooling coefficient must be finite and >= 0");
+    c->sp[sid].rad = coef;
+    return PP_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Loading
 // ---------------------------------------------------------------------------
@@ -708,7 +717,9 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // ---------------------------------------------------------------------------
 // Checkpoint / restart (FP64 blocks, independent of the precision form)
 // ---------------------------------------------------------------------------
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '1'};
+// Format 2 adds each species' radiative-cooling coefficient; format 1 files
+// (without it) restore with cooling off.
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '2'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
@@ -729,7 +740,8 @@ extern "C" int pp_save(pp_ctx *p, const char *path) {
     for (int s = 0; s < c->nspecies && ok; ++s) {
         Species &S = c->sp[s];
         pp_species_desc sd{S.q, S.m, S.w, S.limit};
-        ok = fwrite(&sd, sizeof sd, 1, f) == 1 && fwrite(&S.n, sizeof S.n, 1, f) == 1;
+        ok = fwrite(&sd, sizeof sd, 1, f) == 1 && fwrite(&S.n, sizeof S.n, 1, f) == 1 &&
+             fwrite(&S.rad, sizeof S.rad, 1, f) == 1;
         std::vector<double> pb((size_t)S.n * 6);
         if (ok && S.n) {
             rc = pp_get_particles(p, s, pb.data(), pb.data() + S.n, pb.data() + 2 * S.n, pb.data() + 3 * S.n,
@@ -752,7 +764,8 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     pp_grid_desc d;
     int64_t step = 0;
     int ns = 0;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(&d, sizeof d, 1, f) == 1 &&
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && (magic[7] == '1' || magic[7] == '2') &&
+              fread(&d, sizeof d, 1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
               ns <= PP_MAX_SPECIES;
     if (!ok) { fclose(f); return fail(c, PP_EINVAL, "%s is not a checkpoint of this library", path); }
@@ -771,9 +784,12 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
         pp_species_desc sd;
         int64_t n = 0;
         int sid = -1;
-        ok = fread(&sd, sizeof sd, 1, f) == 1 && fread(&n, sizeof n, 1, f) == 1 && n >= 0 && n <= sd.capacity;
+        double rad = 0.0;
+        ok = fread(&sd, sizeof sd, 1, f) == 1 && fread(&n, sizeof n, 1, f) == 1 && n >= 0 && n <= sd.capacity &&
+             (magic[7] == '1' || fread(&rad, sizeof rad, 1, f) == 1);
         if (!ok) break;
         rc = pp_init_species(p, &sd, &sid);
+        if (rc == PP_OK) rc = pp_set_radiative_cooling(p, sid, rad);
         std::vector<double> pb((size_t)n * 6);
         if (rc == PP_OK) ok = fread(pb.data(), sizeof(double), pb.size(), f) == pb.size();
         if (rc == PP_OK && ok && n)

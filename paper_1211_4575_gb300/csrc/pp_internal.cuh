@@ -121,6 +121,43 @@ __device__ __forceinline__ void push_boris(R qmdt, const R (&E)[3], const R (&B)
 }
 
 // ---------------------------------------------------------------------------
+// Radiative cooling (Sec. "Radiative cooling", eq:prad, eq:udot), explicit and
+// not iterated: with p- = um (t - dt/2) and p+^EM = u from the Lorentz push,
+// p0 = (p+^EM + p-)/2, gamma0 = sqrt(1 + p0^2) and D = p+^EM - p- = pdot0 dt,
+//   p+ = p+^EM - (K/dt) gamma0 (D^2 + |D x p0|^2) / p0^2 * p0,
+// K = mu0 q^2 / (6 pi m c) (c = 1); kdt = K / dt.  p0 = 0 does not radiate.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void radiate(R kdt, const R (&um)[3], R (&u)[3]) {
+    R px = R(0.5) * (u[0] + um[0]), py = R(0.5) * (u[1] + um[1]), pz = R(0.5) * (u[2] + um[2]);
+    R dx = u[0] - um[0], dy = u[1] - um[1], dz = u[2] - um[2];
+    R p2 = px * px + py * py + pz * pz;
+    if (p2 > R(0)) {
+        R cx = dy * pz - dz * py, cy = dz * px - dx * pz, cz = dx * py - dy * px;
+        R bracket = dx * dx + dy * dy + dz * dz + (cx * cx + cy * cy + cz * cz);
+        R f = -kdt * sqrt(R(1) + p2) * bracket / p2;
+        u[0] += f * px;
+        u[1] += f * py;
+        u[2] += f * pz;
+    }
+}
+
+// The particle's momentum update: Vay or Boris push, then radiative cooling
+// when the species radiates (kdt != 0, uniform over a launch).
+template <int PUSH, typename R>
+__device__ __forceinline__ void push_particle(R qmdt, R kdt, const R (&E)[3], const R (&B)[3], R (&u)[3]) {
+    if (kdt != R(0)) {
+        R um[3] = {u[0], u[1], u[2]};
+        if (PUSH == PP_BORIS) push_boris<R>(qmdt, E, B, u);
+        else push_vay<R>(qmdt, E, B, u);
+        radiate<R>(kdt, um, u);
+    } else {
+        if (PUSH == PP_BORIS) push_boris<R>(qmdt, E, B, u);
+        else push_vay<R>(qmdt, E, B, u);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Gather of one staggered component (eq:pfields): separable triple sum over
 // the (O+1)^3 support, x innermost.  Acc::F(kind, comp, i, j, k) reads the
 // field at frame indices; kind 0 = E, 1 = B.
@@ -258,6 +295,7 @@ __device__ __forceinline__ void deposit_rho(Acc &acc, const R (&xi)[3], R qw) {
 // ---------------------------------------------------------------------------
 struct Species {
     double q, m, w;
+    double rad = 0.0;         // radiative-cooling coefficient mu0 q^2 / (6 pi m c); 0 = off
     int64_t cap = 0, n = 0;   // allocated slots (rounded up to 64) and particles held
     int64_t limit = 0;        // capacity requested by the caller
     // PP_FP64: positions in cell units xi = x/dx in [0, n); momenta

@@ -32,6 +32,7 @@ struct StepArgs {
     const R *B[3];
     R *J[3];
     R qmdt;
+    R kdt;                       // radiative cooling K / dt (0 = off)
     R dtdx[3];
     R jscale[3];
     int64_t n;
@@ -56,8 +57,7 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
     GlobalAcc<double> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, 0, 0, 0};
     double E[3], B[3];
     gather_EB<O, double>(acc, xi0, E, B);
-    if (PUSH == PP_BORIS) push_boris<double>(a.qmdt, E, B, u);
-    else push_vay<double>(a.qmdt, E, B, u);
+    push_particle<PUSH, double>(a.qmdt, a.kdt, E, B, u);
     double gi = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double xi1[3];
     bool ok = true;
@@ -121,8 +121,7 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
     GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
     float E[3], B[3];
     gather_EB<O, float>(acc, xi0, E, B);
-    if (PUSH == PP_BORIS) push_boris<float>(a.qmdt, E, B, u);
-    else push_vay<float>(a.qmdt, E, B, u);
+    push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
     float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     float xi1[3];
     bool ok = true;
@@ -157,6 +156,7 @@ static StepArgs<R> step_args(Ctx &c, int s) {
     const Species &S = c.sp[s];
     double h[3] = {c.d.dx, c.d.dy, c.d.dz};
     a.qmdt = (R)(S.q * c.d.dt / S.m);
+    a.kdt = (R)(S.rad / c.d.dt);
     for (int d = 0; d < 3; ++d) {
         a.dtdx[d] = (R)(c.d.dt / h[d]);
         a.jscale[d] = (R)(-S.q * S.w * h[d] / c.d.dt);
@@ -281,6 +281,7 @@ struct TiledSpecies {
     int32_t *slow_list;          // indices of particles left to the global-mesh kernel
     unsigned *slow_count;
     float qmdt;
+    float kdt;                   // radiative cooling K / dt (0 = off)
     float jscale[3];             // -q w dx_a / dt
 };
 
@@ -373,8 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 float E[3], B[3];
                 SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
                 gather_EB<O, float>(sacc, xi0, E, B);
-                if (PUSH == PP_BORIS) push_boris<float>(S.qmdt, E, B, u);
-                else push_vay<float>(S.qmdt, E, B, u);
+                push_particle<PUSH, float>(S.qmdt, S.kdt, E, B, u);
                 float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 float dx[3];
                 bool ok = true;
@@ -486,8 +486,7 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
         GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
         float E[3], B[3];
         gather_EB<O, float>(acc, xi0, E, B);
-        if (PUSH == PP_BORIS) push_boris<float>(a.qmdt, E, B, u);
-        else push_vay<float>(a.qmdt, E, B, u);
+        push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
         float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         float xi1[3];
         bool ok = true;
@@ -547,6 +546,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         t.slow_list = S.keys;              // the sort keys are dead between sorts
         t.slow_count = c.d_slow_count + s;
         t.qmdt = (float)(S.q * c.d.dt / S.m);
+        t.kdt = (float)(S.rad / c.d.dt);
         for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.d.dt);
     }
     if (T.ns == 0) return cudaSuccess;
