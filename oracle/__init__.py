@@ -78,6 +78,9 @@ def lib():
         L.orc_current_from_drho.argtypes = [C.POINTER(Grid), P, P, P]
         L.orc_field_update.argtypes = [C.POINTER(Grid), P, P, P, C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.orc_particles_deposit.argtypes = [C.POINTER(Grid), P, P, C.POINTER(Species), C.c_int, P]
+        L.orc_step4.argtypes = [C.POINTER(Grid), P, P, P, C.POINTER(Species), C.c_int,
+                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.orc_step4_coeffs.argtypes = [P, P]
         L.orc_step.argtypes = [C.POINTER(Grid), P, P, P, C.POINTER(Species), C.c_int,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.orc_rho.argtypes = [C.POINTER(Grid), C.POINTER(Species), C.c_int, P]
@@ -160,6 +163,14 @@ def radiate(K: float, dt: float, um, u) -> np.ndarray:
     return u
 
 
+def step4_coeffs():
+    """Drift (a) and kick (b) fractions of the four substeps of the 4th-order step."""
+    a = np.zeros(4)
+    b = np.zeros(4)
+    lib().orc_step4_coeffs(_ptr(a), _ptr(b))
+    return a, b
+
+
 def deposit_particle(g: Grid, q, w, x0, x1, Drho=None, lsum=None):
     """Accumulate one particle's D rho (3 mesh arrays) and line sums."""
     nx, ny, nz = g.n
@@ -206,7 +217,11 @@ class Simulation:
     """The oracle's whole step over numpy-held state (one FP64 copy per array)."""
 
     def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
-                 relax_max_iter=200, relax_tol=1e-14):
+                 relax_max_iter=200, relax_tol=1e-14, integrator=2):
+        """integrator 2: leap-frog step; 4: the four-substep 4th-order step."""
+        if integrator not in (2, 4):
+            raise ValueError("integrator must be 2 or 4")
+        self.integrator = integrator
         self.g = make_grid(n, d, dt, field_order, alpha, shape_order, pusher, relax_max_iter, relax_tol)
         nx, ny, nz = n
         self.E = [np.zeros((nz, ny, nx)) for _ in range(3)]
@@ -249,9 +264,10 @@ class Simulation:
     def step(self, n: int = 1):
         it = C.c_int(0)
         res = C.c_double(0.0)
+        f = lib().orc_step4 if self.integrator == 4 else lib().orc_step
         for _ in range(n):
-            lib().orc_step(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), _ptr3(self.J), self._sp(),
-                           len(self.species), C.byref(it), C.byref(res))
+            f(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), _ptr3(self.J), self._sp(),
+              len(self.species), C.byref(it), C.byref(res))
             self.nstep += 1
         self.relax_iters, self.relax_residual = it.value, res.value
 

@@ -37,13 +37,23 @@
  *   R5  "Successive relaxation" of eq:EllipticB is read as Jacobi iteration.
  *   R6  Each field component is gathered from its own staggered nodes with the
  *       same weight function as the deposit (eq:pfields, eq:rho2).
- *   R7  Radiative cooling (Sec. "Radiative cooling") is the explicit form the
+ *   R16 Radiative cooling (Sec. "Radiative cooling") is the explicit form the
  *       paper settles on: no iteration, so the proper acceleration inside the
  *       radiated power of eq:prad is the Lorentz one, (p+^EM - p-)/dt, and
  *       p0 = (p+^EM + p-)/2.  The coefficient mu0 q^2/(6 pi m c) is a species
  *       parameter: in a normalised code it depends on the physical unit of
  *       length, which the paper fixes elsewhere.  A particle with p0 = 0 does
  *       not radiate (eq:udot has no direction there).
+ *   R17 The 4th-order symplectic step (Sec. III, the passage on the symmetric
+ *       fourth-order integrator of Yoshida / Forest & Ruth / Candy & Rozmus)
+ *       is four leap-frog substeps, each a kick of b_i dt followed by a drift
+ *       of a_i dt, with b = (0, w1, w0, w1), a = (w1/2, (w0+w1)/2, (w0+w1)/2,
+ *       w1/2), w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3) w1.  Each kick is then
+ *       centred on the position time, the condition the paper states.  The
+ *       fields, with positions and charge in the paper's pairing of conjugate
+ *       variables, advance in the drifts: the field update of eq:bnplus1 /
+ *       eq:enplus1 runs with dt -> a_i dt and the current of that drift.
+ *       Positions and proper velocities are both at t at a step boundary.
  */
 #include <math.h>
 #include <stdint.h>
@@ -561,8 +571,10 @@ static void wrap_pos(double *x, double L)
     if (*x >= L) *x -= L;   /* x + L rounded up to L */
 }
 
-void orc_particles_deposit(const orc_grid *g, double *E[3], double *B[3], orc_species *sp, int nsp,
-                           double *J[3])
+/* Gather, kick by kick_dt (push and cooling; none when kick_dt = 0), drift by
+ * g->dt, deposit.  The plain leap-frog step has kick_dt = g->dt. */
+void orc_particles_kick_drift(const orc_grid *g, double kick_dt, double *E[3], double *B[3], orc_species *sp,
+                              int nsp, double *J[3])
 {
     int64_t N = ncells(g);
     double *Drho[3], *lsum[3];
@@ -574,16 +586,18 @@ void orc_particles_deposit(const orc_grid *g, double *E[3], double *B[3], orc_sp
     double L[3] = {g->n[0] * g->d[0], g->n[1] * g->d[1], g->n[2] * g->d[2]};
     for (int s = 0; s < nsp; ++s) {
         orc_species *P = &sp[s];
-        double qmdt = P->q * g->dt / P->m;
+        double qmdt = P->q * kick_dt / P->m;
         for (int64_t p = 0; p < P->n; ++p) {
             double x0[3] = {P->x[p], P->y[p], P->z[p]};
             double u[3] = {P->ux[p], P->uy[p], P->uz[p]};
             double um[3] = {u[0], u[1], u[2]};
-            double Ep[3], Bp[3];
-            orc_gather(g, E, B, x0, Ep, Bp);
-            if (g->pusher == 1) orc_push_boris(qmdt, Ep, Bp, u);
-            else orc_push_vay(qmdt, Ep, Bp, u);
-            if (P->rad != 0.0) orc_radiate(P->rad, g->dt, um, u);
+            if (kick_dt != 0.0) {
+                double Ep[3], Bp[3];
+                orc_gather(g, E, B, x0, Ep, Bp);
+                if (g->pusher == 1) orc_push_boris(qmdt, Ep, Bp, u);
+                else orc_push_vay(qmdt, Ep, Bp, u);
+                if (P->rad != 0.0) orc_radiate(P->rad, kick_dt, um, u);
+            }
             double gam = sqrt(1.0 + dot3(u, u));
             double x1[3];
             for (int a = 0; a < 3; ++a) x1[a] = x0[a] + g->dt * u[a] / gam;
@@ -599,11 +613,44 @@ void orc_particles_deposit(const orc_grid *g, double *E[3], double *B[3], orc_sp
     for (int a = 0; a < 3; ++a) { free(Drho[a]); free(lsum[a]); }
 }
 
+void orc_particles_deposit(const orc_grid *g, double *E[3], double *B[3], orc_species *sp, int nsp,
+                           double *J[3])
+{
+    orc_particles_kick_drift(g, g->dt, E, B, sp, nsp, J);
+}
+
 void orc_step(const orc_grid *g, double *E[3], double *B[3], double *J[3], orc_species *sp, int nsp,
               int *iters_out, double *resid_out)
 {
     orc_particles_deposit(g, E, B, sp, nsp, J);
     orc_field_update(g, E, B, J, iters_out, resid_out);
+}
+
+/* Kick (b) and drift (a) fractions of the four substeps of reading R17. */
+void orc_step4_coeffs(double a[4], double b[4])
+{
+    double w1 = 1.0 / (2.0 - cbrt(2.0));
+    double w0 = -cbrt(2.0) * w1;
+    a[0] = a[3] = 0.5 * w1;
+    a[1] = a[2] = 0.5 * (w0 + w1);
+    b[0] = 0.0;
+    b[1] = b[3] = w1;
+    b[2] = w0;
+}
+
+/* One 4th-order step (reading R17): four kick-drift substeps, each followed by
+ * the field update over its drift. */
+void orc_step4(const orc_grid *g, double *E[3], double *B[3], double *J[3], orc_species *sp, int nsp,
+               int *iters_out, double *resid_out)
+{
+    double a[4], b[4];
+    orc_step4_coeffs(a, b);
+    for (int i = 0; i < 4; ++i) {
+        orc_grid sub = *g;
+        sub.dt = a[i] * g->dt;
+        orc_particles_kick_drift(&sub, b[i] * g->dt, E, B, sp, nsp, J);
+        orc_field_update(&sub, E, B, J, iters_out, resid_out);
+    }
 }
 
 /* ------------------------------------------------------------------ */

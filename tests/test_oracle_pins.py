@@ -555,3 +555,124 @@ def test_cooling_off_leaves_the_step_bit_identical(orc):
     for a in range(3):
         assert np.array_equal(sims[0].E[a], sims[1].E[a])
     assert np.array_equal(sims[0].species[0]["ux"], sims[1].species[0]["ux"])
+
+
+# --------------------------------------------------------------------------
+# 4th-order symplectic step (Sec. III, reading R17)
+# --------------------------------------------------------------------------
+
+def _solenoidal_fields(orc, L, seed):
+    import pp_synth
+    g = orc.make_grid(L.n, L.d, L.dt, field_order=6)
+    E, A = pp_synth.random_fields(L.n, seed, 0.05)
+    B = [orc.diff(g, A[(a + 2) % 3], (a + 1) % 3, +1) - orc.diff(g, A[(a + 1) % 3], (a + 2) % 3, +1)
+         for a in range(3)]
+    return E, B
+
+
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_step4_is_time_reversible(orc, pusher):
+    """The four substeps form a palindrome (b1 = 0, a1 = a4, a2 = a3, b2 = b4)
+    with symmetric kicks, and at alpha = 1/2 the field update is the implicit
+    midpoint rule, so three steps of +dt followed by three of -dt return
+    particles and fields to round-off.  The plain leap-frog step does not
+    (its velocities sit half a step away), which shows the test can tell."""
+    import pp_synth
+    L = pp_synth.thermal((8, 6, 5), ppc=2, u_th=0.3, dx=0.5, dt=0.25, seed=7)
+    E, B = _solenoidal_fields(orc, L, 3)   # eq:EllipticB equals the defining equations for div B = 0
+    errs = {}
+    for integ in (4, 2):
+        sim = orc.Simulation(L.n, L.d, L.dt, shape_order=3, alpha=0.5, pusher=pusher, relax_tol=1e-15,
+                             relax_max_iter=3000, integrator=integ)
+        for s in L.species:
+            sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+        sim.load_fields(E, B)
+        E0 = [v.copy() for v in sim.E]
+        B0 = [v.copy() for v in sim.B]
+        P0 = [{k: s[k].copy() for k in ("x", "y", "z", "ux", "uy", "uz")} for s in sim.species]
+        sim.step(3)
+        assert max(np.abs(sim.E[a] - E0[a]).max() for a in range(3)) > 0.1   # the state did move
+        sim.g.dt = -L.dt
+        sim.step(3)
+        e = max(max(np.abs(sim.E[a] - E0[a]).max(), np.abs(sim.B[a] - B0[a]).max()) for a in range(3))
+        for s, p0 in zip(sim.species, P0):
+            for k in ("ux", "uy", "uz"):
+                e = max(e, np.abs(s[k] - p0[k]).max())
+            for a, k in enumerate("xyz"):
+                Lb = L.n[a] * L.d[a]
+                e = max(e, np.abs((s[k] - p0[k] + Lb / 2) % Lb - Lb / 2).max())
+        errs[integ] = e
+    assert errs[4] < 1e-12, errs
+    assert errs[2] > 1e-3, errs
+
+
+def _gyration_error(orc, h, integrator, u0=0.5):
+    """Largest position / momentum error of a test particle (weight 1e-10) after
+    two gyrations in a uniform B_z = 1 (q = -1, m = 1: u turns counter-clockwise
+    at Omega = 1/gamma on a circle of radius u0)."""
+    g0 = math.sqrt(1.0 + u0 * u0)
+    om = 1.0 / g0
+    n = int(round(4.0 * math.pi * g0 / h))
+    T = n * h
+    sim = orc.Simulation((8, 8, 8), (1.0, 1.0, 1.0), h, shape_order=3, alpha=0.5, relax_tol=1e-14,
+                         relax_max_iter=400, integrator=integrator)
+    x0 = (3.3, 3.1, 4.2)
+    t0 = 0.0 if integrator == 4 else -0.5 * h     # leap-frog velocities lag half a step
+    sim.add_species(-1.0, 1.0, 1e-10, [x0[0]], [x0[1]], [x0[2]],
+                    [u0 * math.cos(om * t0)], [u0 * math.sin(om * t0)], [0.0])
+    E = [np.zeros((8, 8, 8)) for _ in range(3)]
+    B = [np.zeros((8, 8, 8)) for _ in range(3)]
+    B[2][...] = 1.0
+    sim.load_fields(E, B)
+    sim.step(n)
+    s = sim.species[0]
+    xe = x0[0] + u0 * math.sin(om * T)
+    ye = x0[1] + u0 * (1.0 - math.cos(om * T))
+    tu = T + t0
+    dpos = max(abs((s["x"][0] - xe + 4.0) % 8.0 - 4.0), abs((s["y"][0] - ye + 4.0) % 8.0 - 4.0))
+    du = max(abs(s["ux"][0] - u0 * math.cos(om * tu)), abs(s["uy"][0] - u0 * math.sin(om * tu)))
+    return dpos, du
+
+
+def test_step4_gyration_converges_at_fourth_order(orc):
+    """Against the exact circle, halving dt divides the 4th-order step's error
+    by about 16 (the leap-frog's by about 4): the kick sizes cancel the cubic
+    phase error of the Vay rotation, 2 w1^3 + w0^3 = 0."""
+    e4 = [_gyration_error(orc, h, 4) for h in (0.4, 0.2)]
+    e2 = [_gyration_error(orc, h, 2) for h in (0.4, 0.2)]
+    for k in range(2):
+        assert 13.0 < e4[0][k] / e4[1][k] < 17.0, e4
+        assert 3.5 < e2[0][k] / e2[1][k] < 4.5, e2
+    assert e4[1][0] < 0.05 * e2[1][0]
+
+
+@pytest.mark.parametrize("mode", [1, 3])
+def test_step4_vacuum_energy_is_product_of_substep_factors(orc, mode):
+    """With no particles a 4th-order step is four field updates with dt -> a_i dt:
+    the energy of a vacuum mode falls by the product of the theta-scheme's
+    closed-form factors (1 + beta^2 s_i^2)/(1 + alpha^2 s_i^2), s_i = a_i dt K(k).
+    The a_i are the published drift fractions of the fourth-order composition
+    (Forest & Ruth; Candy & Rozmus): w1/2, (w0+w1)/2, (w0+w1)/2, w1/2 with
+    w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3) w1."""
+    nx, dx, dt, alpha = 16, 0.5, 0.25, 0.55
+    sim = orc.Simulation((nx, 2, 2), (dx, dx, dx), dt, field_order=6, alpha=alpha, relax_tol=1e-15,
+                         relax_max_iter=500, integrator=4)
+    k = 2 * np.pi * mode / (nx * dx)
+    kc = orc.fd_coeffs(6)
+    K = (2 / dx) * (kc[0] * np.sin(k * dx / 2) + kc[1] * np.sin(3 * k * dx / 2) + kc[2] * np.sin(5 * k * dx / 2))
+    w1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    w0 = -(2.0 ** (1.0 / 3.0)) * w1
+    ratio = 1.0
+    for a in (w1 / 2, (w0 + w1) / 2, (w0 + w1) / 2, w1 / 2):
+        s = a * dt * K
+        ratio *= (1 + (1 - alpha) ** 2 * s * s) / (1 + alpha ** 2 * s * s)
+    x = np.arange(nx) * dx
+    E = [np.zeros((2, 2, nx)) for _ in range(3)]
+    B = [np.zeros((2, 2, nx)) for _ in range(3)]
+    E[1][...] = np.cos(k * x)
+    B[2][...] = 0.3 * np.sin(k * (x + dx / 2))
+    sim.load_fields(E, B)
+    W0 = sum((v ** 2).sum() for v in sim.E + sim.B)
+    sim.step(1)
+    W1 = sum((v ** 2).sum() for v in sim.E + sim.B)
+    assert W1 / W0 == pytest.approx(ratio, rel=1e-12)
