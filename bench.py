@@ -38,11 +38,11 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # taken on: the device header, the sort (its key sets the particle order the
 # kernel streams) and the part of pp_particles.cu that holds the particle
 # kernels (up to its charge-density section).
-PROFILED_BYTES_PER_PARTICLE = 906.362112e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 906.353920e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "fb61b196a6ae7c9a0b5a08e39f76c44260ab65e750eecc4c424c8dd04d516ddf",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "cf2c2a0fd8e7d130fa396700ecd19be42d26f281a5d1d9b58144bbff7fc1fab3",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "fbdb92befdb07090e1d0892cb670242f1c04512fe7b595ec2a896d45408bc24e",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "3e961bfd74147df7918ee81149e7a141f4bb8ed7100c8c394f7a708d270ae7a2",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "afba1e3d446de9e5ddbbde1047e965224b0e9e36a84f07db1d2c137e596077e7",
 }
 
@@ -70,6 +70,8 @@ def args():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--ppc", type=int, default=32, help="macro-particles per cell per species")
     ap.add_argument("--deposit", choices=["auto", "global", "tiled"], default="auto")
+    ap.add_argument("--integrator", type=int, choices=[2, 4], default=2,
+                    help="2: leap-frog step; 4: four-substep 4th-order symplectic step")
     ap.add_argument("--radiation", type=float, default=0.0,
                     help="radiative-cooling coefficient mu0 q^2/(6 pi m c) for every species (0 = off)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -95,7 +97,8 @@ def workload_name(a, nparticles):
         "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
     return (f"{kind}, {a.n}^3 cells, dx=0.1, dt=0.05, {a.ppc} per cell per species ({nparticles} particles), "
             f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset"
-            + (f", radiative cooling K={a.radiation:g}" if a.radiation else ""))
+            + (f", radiative cooling K={a.radiation:g}" if a.radiation else "")
+            + (", 4th-order symplectic step (4 kick-drift substeps)" if a.integrator == 4 else ""))
 
 
 def measured_peak():
@@ -177,7 +180,7 @@ def oracle_rate(a, steps, warmup=0):
          else pp_synth.weibel(n=n, ppc=a.ppc, seed=1213))
     oracle.build()
     sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
-                            relax_max_iter=200)
+                            relax_max_iter=200, integrator=a.integrator)
     for s in L.species:
         sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], rad=a.radiation)
     if warmup:
@@ -231,9 +234,11 @@ def run_gpu(a):
     stream = torch.cuda.current_stream()
 
     def make():
-        return pp.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, pusher=pp.PP_VAY,
-                             precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=100, relax_tol=1e-6,
-                             deposit_mode=mode, stream=stream.cuda_stream)
+        s = pp.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, pusher=pp.PP_VAY,
+                          precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=100, relax_tol=1e-6,
+                          deposit_mode=mode, stream=stream.cuda_stream)
+        s.set_integrator(a.integrator)
+        return s
 
     sim = make()
     for s in L.species:
@@ -270,7 +275,8 @@ def run_gpu(a):
     # roofline of the dominant kernel (the fused particle kernel)
     peak, peak_kind = measured_peak()
     part_ms = prof["particle_ms"]
-    achieved = BYTES_PER_PARTICLE_STEP * npart * a.steps / (part_ms * 1e-3) / 1e9 if part_ms > 0 else 0.0
+    bytes_per_step = BYTES_PER_PARTICLE_STEP * (4 if a.integrator == 4 else 1)   # one particle pass per substep
+    achieved = bytes_per_step * npart * a.steps / (part_ms * 1e-3) / 1e9 if part_ms > 0 else 0.0
     diag = sim.diagnostics()
 
     # ---- end to end through the C ABI with host buffers ----
@@ -320,7 +326,7 @@ def run_gpu(a):
                      "frac": achieved / peak if peak else None,
                      "traffic": profiled_traffic(npart * a.steps / max(1, prof["particle_launches"])),
                      "kernel": "fused particle step (gather+push+move+deposit)",
-                     "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP, "peak_kind": peak_kind,
+                     "bytes_per_particle_step": bytes_per_step, "peak_kind": peak_kind,
                      "kernel_ms_per_step": part_ms / a.steps},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -161,6 +161,21 @@ int pp_init_species(pp_ctx *ctx, const pp_species_desc *desc, int *species_id);
  * pp_step / pp_deposit. */
 int pp_set_radiative_cooling(pp_ctx *ctx, int sid, double coef);
 
+/* Time integrator of pp_step (Sec. III, the symmetric fourth-order
+ * symplectic integrator of Yoshida / Forest & Ruth / Candy & Rozmus).
+ * order 2 (default): the leap-frog step; proper velocities are staggered
+ * half a step behind the positions.  order 4: each step is four kick-drift
+ * substeps, kick b_i dt then drift a_i dt with b = (0, w1, w0, w1) and
+ * a = (w1/2, (w0+w1)/2, (w0+w1)/2, w1/2), w1 = 1/(2 - 2^(1/3)),
+ * w0 = -2^(1/3) w1, so that every kick is centred on the position time.  The
+ * fields advance with the drifts (field update with dt -> a_i dt and the
+ * current of that drift).  In order 4 the proper velocities are synchronous
+ * with the positions at step boundaries (load u at t, read back u at the new
+ * t).  A step costs four particle passes and four field solves.  Errors:
+ * PP_EINVAL for another order.  Takes effect at the next pp_step; pp_deposit
+ * and pp_field_update always take one leap-frog step. */
+int pp_set_integrator(pp_ctx *ctx, int order);
+
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
@@ -242,8 +257,9 @@ int pp_profile_enable(pp_ctx *ctx, int enable);
 /* Totals since the last pp_profile_enable(ctx, 1) (synchronises). */
 int pp_profile_read(pp_ctx *ctx, pp_profile *out);
 
-/* Checkpoint: write the descriptor, species parameters (with the cooling
- * coefficient), step counter, FP64 fields and FP64 particle arrays to a file
+/* Checkpoint: write the descriptor, integrator order, species parameters
+ * (with the cooling coefficient), step counter, FP64 fields and FP64 particle
+ * arrays to a file
  * (Sec. IX, each attribute as one 64-bit block so that a restart does not
  * depend on the precision form). */
 int pp_save(pp_ctx *ctx, const char *path);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "pp_init_grid": (C.c_int, [_PP, C.POINTER(GridDesc)]),
     "pp_init_species": (C.c_int, [_P, C.POINTER(SpeciesDesc), C.POINTER(C.c_int)]),
     "pp_set_radiative_cooling": (C.c_int, [_P, C.c_int, C.c_double]),
+    "pp_set_integrator": (C.c_int, [_P, C.c_int]),
     "pp_load_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int]),
     "pp_load_fields": (C.c_int, [_P, _PP, _PP, C.c_int]),
     "pp_step": (C.c_int, [_P, C.c_int]),
@@ -213,6 +214,10 @@ class Simulation:
         self._c(lib().pp_init_species(self._ctx, C.byref(SpeciesDesc(q, m, w, int(capacity))), C.byref(sid)))
         self.nspecies += 1
         return sid.value
+
+    def set_integrator(self, order):
+        """2: leap-frog step; 4: four-substep 4th-order symplectic step (u synchronous with x)."""
+        self._c(lib().pp_set_integrator(self._ctx, int(order)))
 
     def set_radiative_cooling(self, sid, coef):
         """Radiative cooling coefficient mu0 q^2 / (6 pi m c) of species sid (0 = off)."""

@@ -60,6 +60,51 @@ static void circulant_inverse(int n, const double k[3], std::vector<double> &g) 
     for (int q = 0; q < n; ++q) g[q] /= n;
 }
 
+// Drift (a) and kick (b) fractions of the four substeps of the symmetric
+// fourth-order integrator (Sec. III; Forest & Ruth 1990, Candy & Rozmus
+// 1991): kick b_i dt, then drift a_i dt, so that every kick is centred on the
+// position time.  w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3) w1.
+static void step4_fractions(double a[4], double b[4]) {
+    const double r = cbrt(2.0);
+    const double w1 = 1.0 / (2.0 - r), w0 = -r * w1;
+    a[0] = a[3] = 0.5 * w1;
+    a[1] = a[2] = 0.5 * (w0 + w1);
+    b[0] = 0.0;
+    b[1] = b[3] = w1;
+    b[2] = w0;
+}
+
+// Chebyshev bounds of A = 1 - alpha^2 dt^2 L (spectrum in [1, 1 + kk sum_a
+// max K_a^2]) and the iteration count that reaches relax_tol.
+static void cheb_setup(const Ctx *c, double dt, Ctx::Cheb &out) {
+    double h[3] = {c->d.dx, c->d.dy, c->d.dz};
+    double kk = c->d.alpha * c->d.alpha * dt * dt;
+    double lmax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double best = 0.0;
+        for (int s = 0; s <= 4000; ++s) {
+            double th = M_PI * s / 4000.0;
+            double K = 2.0 * (c->fd[0] * sin(0.5 * th) + c->fd[1] * sin(1.5 * th) + c->fd[2] * sin(2.5 * th));
+            best = fmax(best, K * K);
+        }
+        lmax += kk * best * 1.0005 / (h[a] * h[a]);
+    }
+    out.theta = 0.5 * (lmax + 1.0);
+    out.delta = 0.5 * (lmax - 1.0);
+    double sk = sqrt(lmax);
+    double rho = (sk - 1.0) / (sk + 1.0);
+    double target = c->d.relax_tol / sqrt(3.0 * (double)c->g.cells()) / sk;
+    int it = 1;
+    if (out.delta > 0.0) {
+        double rk = rho;
+        while (it < 10000 && 2.0 * rk / (1.0 + rk * rk) > target) {
+            rk *= rho;
+            ++it;
+        }
+    }
+    out.iters = it < c->d.relax_max_iter ? it : c->d.relax_max_iter;
+}
+
 static int setup_operators(Ctx *c) {
     fd_coeffs(c->d.field_order, c->fd);
     // 1D stencil of d^+ d^-: autocorrelation of the half-offset kernel
@@ -98,33 +143,15 @@ static int setup_operators(Ctx *c) {
     if (e != cudaSuccess) return fail(c, PP_ECUDA, "taps: %s", cudaGetErrorString(e));
     e = cudaMemcpy(c->taps, host.data(), sizeof(double) * 3 * kMaxTaps, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(c, PP_ECUDA, "taps copy: %s", cudaGetErrorString(e));
-    // Chebyshev bounds of A = 1 - alpha^2 dt^2 L: spectrum in [1, 1 + kk sum_a max K_a^2]
-    double h[3] = {c->d.dx, c->d.dy, c->d.dz};
-    double kk = c->d.alpha * c->d.alpha * c->d.dt * c->d.dt;
-    double lmax = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        double best = 0.0;
-        for (int s = 0; s <= 4000; ++s) {
-            double th = M_PI * s / 4000.0;
-            double K = 2.0 * (c->fd[0] * sin(0.5 * th) + c->fd[1] * sin(1.5 * th) + c->fd[2] * sin(2.5 * th));
-            best = fmax(best, K * K);
-        }
-        lmax += kk * best * 1.0005 / (h[a] * h[a]);
-    }
-    c->cheb_theta = 0.5 * (lmax + 1.0);
-    c->cheb_delta = 0.5 * (lmax - 1.0);
-    double sk = sqrt(lmax);
-    double rho = (sk - 1.0) / (sk + 1.0);
-    double target = c->d.relax_tol / sqrt(3.0 * (double)c->g.cells()) / sk;
-    int it = 1;
-    if (c->cheb_delta > 0.0) {
-        double rk = rho;
-        while (it < 10000 && 2.0 * rk / (1.0 + rk * rk) > target) {
-            rk *= rho;
-            ++it;
-        }
-    }
-    c->cheb_iters = it < c->d.relax_max_iter ? it : c->d.relax_max_iter;
+    // Chebyshev bounds of A = 1 - alpha^2 dt^2 L for every solve step the
+    // context takes: the step dt and the drifts of the 4th-order substeps
+    double a[4], b[4];
+    step4_fractions(a, b);
+    const double dts[3] = {c->d.dt, fabs(a[0]) * c->d.dt, fabs(a[1]) * c->d.dt};
+    for (int q = 0; q < 3; ++q) cheb_setup(c, dts[q], c->cheb[q]);
+    c->cheb_sel = 0;
+    c->kick_dt = c->drift_dt = c->d.dt;
+    c->last_kk = c->d.alpha * c->d.alpha * c->d.dt * c->d.dt;
     return PP_OK;
 }
 
@@ -549,13 +576,35 @@ extern "C" int pp_step(pp_ctx *p, int nsteps) {
             int r = pp_sort(p);
             if (r) return r;
         }
-        int r = particle_phase(c, -1);
-        if (r) return r;
-        r = field_phase(c);
+        int r = PP_OK;
+        if (c->order == 4) {
+            double a[4], b[4];
+            step4_fractions(a, b);
+            for (int i = 0; i < 4 && r == PP_OK; ++i) {
+                c->kick_dt = b[i] * c->d.dt;
+                c->drift_dt = a[i] * c->d.dt;
+                c->cheb_sel = (i == 0 || i == 3) ? 1 : 2;
+                r = particle_phase(c, -1);
+                if (r == PP_OK) r = field_phase(c);
+            }
+            c->kick_dt = c->drift_dt = c->d.dt;
+            c->cheb_sel = 0;
+        } else {
+            r = particle_phase(c, -1);
+            if (r == PP_OK) r = field_phase(c);
+        }
         if (r) return r;
         ++c->step;
         ++c->since_sort;
     }
+    return PP_OK;
+}
+
+extern "C" int pp_set_integrator(pp_ctx *p, int order) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (order != 2 && order != 4) return fail(c, PP_EINVAL, "integrator order must be 2 or 4");
+    c->order = order;
     return PP_OK;
 }
 
@@ -717,9 +766,9 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // ---------------------------------------------------------------------------
 // Checkpoint / restart (FP64 blocks, independent of the precision form)
 // ---------------------------------------------------------------------------
-// Format 2 adds each species' radiative-cooling coefficient; format 1 files
-// (without it) restore with cooling off.
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '2'};
+// Format 2 adds each species' radiative-cooling coefficient, format 3 the
+// integrator order; older files restore with cooling off and order 2.
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '3'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
@@ -735,7 +784,8 @@ extern "C" int pp_save(pp_ctx *p, const char *path) {
     d.stream = nullptr;
     bool ok = rc == PP_OK;
     ok = ok && fwrite(kMagic, 1, 8, f) == 8 && fwrite(&d, sizeof d, 1, f) == 1;
-    ok = ok && fwrite(&c->step, sizeof c->step, 1, f) == 1 && fwrite(&c->nspecies, sizeof(int), 1, f) == 1;
+    ok = ok && fwrite(&c->step, sizeof c->step, 1, f) == 1 && fwrite(&c->nspecies, sizeof(int), 1, f) == 1 &&
+         fwrite(&c->order, sizeof(int), 1, f) == 1;
     ok = ok && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
     for (int s = 0; s < c->nspecies && ok; ++s) {
         Species &S = c->sp[s];
@@ -764,19 +814,21 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     pp_grid_desc d;
     int64_t step = 0;
     int ns = 0;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && (magic[7] == '1' || magic[7] == '2') &&
+    int order = 2;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '3' &&
               fread(&d, sizeof d, 1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
-              ns <= PP_MAX_SPECIES;
+              ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1);
     if (!ok) { fclose(f); return fail(c, PP_EINVAL, "%s is not a checkpoint of this library", path); }
     d.stream = stream;
     pp_ctx *p = nullptr;
     int rc = pp_init_grid(&p, &d);
     if (rc != PP_OK && rc != PP_WSTAB) { fclose(f); return rc; }
     c = p;
+    rc = pp_set_integrator(p, order);
     int64_t N = c->g.cells();
     std::vector<double> buf((size_t)N * 6);
-    ok = fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+    ok = rc == PP_OK && fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
     const double *E[3] = {buf.data(), buf.data() + N, buf.data() + 2 * N};
     const double *B[3] = {buf.data() + 3 * N, buf.data() + 4 * N, buf.data() + 5 * N};
     if (ok) rc = pp_load_fields(p, E, B, 0);
@@ -786,7 +838,7 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
         int sid = -1;
         double rad = 0.0;
         ok = fread(&sd, sizeof sd, 1, f) == 1 && fread(&n, sizeof n, 1, f) == 1 && n >= 0 && n <= sd.capacity &&
-             (magic[7] == '1' || fread(&rad, sizeof rad, 1, f) == 1);
+             (magic[7] < '2' || fread(&rad, sizeof rad, 1, f) == 1);
         if (!ok) break;
         rc = pp_init_species(p, &sd, &sid);
         if (rc == PP_OK) rc = pp_set_radiative_cooling(p, sid, rad);

@@ -336,9 +336,20 @@ struct Ctx {
     // field solve
     double fd[3];            // a, b, c
     double lap[6];           // 1D stencil of d^+ d^- at offsets 0..5
-    int cheb_iters = 0;
-    double cheb_theta = 1, cheb_delta = 0;
+    struct Cheb {            // Chebyshev semi-iteration on the spectrum [1, 2 theta - 1]
+        double theta = 1, delta = 0;
+        int iters = 0;
+    };
+    Cheb cheb[3];            // solve step |dt|, |a_1| dt, |a_2| dt (4th-order substeps)
+    int cheb_sel = 0;        // the set the next field update uses
     int last_iters = 0;
+    double last_kk = 0;      // alpha^2 dt^2 of the last solve
+    // time integration: order 2 = leap-frog step; 4 = four kick-drift substeps
+    // (Sec. III, symmetric fourth-order integrator).  kick_dt / drift_dt are
+    // the sizes of the (sub)step being taken; both equal dt outside a
+    // 4th-order step.
+    int order = 2;
+    double kick_dt = 0, drift_dt = 0;
     // sort
     int tile[3] = {8, 8, 8};
     int ntile[3] = {1, 1, 1};

@@ -304,8 +304,10 @@ static cudaError_t field_update_impl(Ctx &c) {
     const Geom &g = c.g;
     FieldCoef k = field_coef(c);
     unsigned blocks = (unsigned)((g.cells() + 255) / 256);
-    double al = c.d.alpha, be = 1.0 - c.d.alpha, dt = c.d.dt;
+    // dt of this solve: the step, or the drift of a 4th-order substep
+    double al = c.d.alpha, be = 1.0 - c.d.alpha, dt = c.drift_dt;
     double kk = al * al * dt * dt;
+    const Ctx::Cheb &ch = c.cheb[c.cheb_sel];
     cudaError_t e;
     k_rhs<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.J), (R *)c.R[0], (R *)c.R[1], (R *)c.R[2],
                                        (R)(al * be * dt * dt), (R)dt, (R)(al * dt * dt));
@@ -313,12 +315,12 @@ static cudaError_t field_update_impl(Ctx &c) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Chebyshev semi-iteration on the spectrum [1, lmax] of the SPD operator,
     // starting from B^n (Saad, Iterative Methods, Alg. 12.1 in 3-term form).
-    double theta = c.cheb_theta, delta = c.cheb_delta;
+    double theta = ch.theta, delta = ch.delta;
     void **cur = c.B, **prev = c.B;
     void **bufs[2] = {c.Xa, c.Xb};
     int nb = 0;
     double rho_prev = delta > 0 ? delta / theta : 0.0;
-    for (int it = 0; it < c.cheb_iters; ++it) {
+    for (int it = 0; it < ch.iters; ++it) {
         double c1, c2;
         if (it == 0) {
             c1 = 0.0;
@@ -341,7 +343,8 @@ static cudaError_t field_update_impl(Ctx &c) {
         cur = out;
         nb = (out == bufs[0]) ? 1 : 0;
     }
-    c.last_iters = c.cheb_iters;
+    c.last_iters = ch.iters;
+    c.last_kk = kk;
     // eq:enplus1 with B^{n+1} = cur, B^n = B
     k_e_update<R><<<blocks, 256, 0, c.st>>>(g, k, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], v3<R>(cur), v3<R>(c.B),
                                             v3<R>(c.J), (R)al, (R)be, (R)dt);
@@ -443,7 +446,7 @@ template <typename R>
 static cudaError_t mesh_diag_impl(Ctx &c, double *host_out) {
     FieldCoef k = field_coef(c);
     int capture = c.have_G0 ? 0 : 1;
-    double kk = c.d.alpha * c.d.alpha * c.d.dt * c.d.dt;
+    double kk = c.last_kk;   // residual of the last solve
     int64_t want = (c.g.cells() + 255) / 256;
     int nblk = (int)(want < kDiagBlocks ? want : kDiagBlocks);
     k_mesh_diag<R><<<nblk, 256, 0, c.st>>>(c.g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.R), c.rho, c.G0, capture, kk, c.d_red);

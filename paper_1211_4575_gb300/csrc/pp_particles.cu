@@ -55,9 +55,11 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
     double xi0[3] = {p.x[t], p.y[t], p.z[t]};
     double u[3] = {p.ux[t], p.uy[t], p.uz[t]};
     GlobalAcc<double> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, 0, 0, 0};
-    double E[3], B[3];
-    gather_EB<O, double>(acc, xi0, E, B);
-    push_particle<PUSH, double>(a.qmdt, a.kdt, E, B, u);
+    if (a.qmdt != 0.0) {   // no kick (a 4th-order drift-only substep, or q = 0): no force
+        double E[3], B[3];
+        gather_EB<O, double>(acc, xi0, E, B);
+        push_particle<PUSH, double>(a.qmdt, a.kdt, E, B, u);
+    }
     double gi = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double xi1[3];
     bool ok = true;
@@ -119,9 +121,11 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
     float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
     float u[3] = {p.ux[t], p.uy[t], p.uz[t]};
     GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
-    float E[3], B[3];
-    gather_EB<O, float>(acc, xi0, E, B);
-    push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
+    if (a.qmdt != 0.0f) {   // no kick (a 4th-order drift-only substep, or q = 0): no force
+        float E[3], B[3];
+        gather_EB<O, float>(acc, xi0, E, B);
+        push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
+    }
     float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     float xi1[3];
     bool ok = true;
@@ -155,11 +159,11 @@ static StepArgs<R> step_args(Ctx &c, int s) {
     }
     const Species &S = c.sp[s];
     double h[3] = {c.d.dx, c.d.dy, c.d.dz};
-    a.qmdt = (R)(S.q * c.d.dt / S.m);
-    a.kdt = (R)(S.rad / c.d.dt);
+    a.qmdt = (R)(S.q * c.kick_dt / S.m);
+    a.kdt = (R)(c.kick_dt != 0.0 ? S.rad / c.kick_dt : 0.0);
     for (int d = 0; d < 3; ++d) {
-        a.dtdx[d] = (R)(c.d.dt / h[d]);
-        a.jscale[d] = (R)(-S.q * S.w * h[d] / c.d.dt);
+        a.dtdx[d] = (R)(c.drift_dt / h[d]);
+        a.jscale[d] = (R)(-S.q * S.w * h[d] / c.drift_dt);
     }
     a.n = S.n;
     a.status = c.d_status;
@@ -371,10 +375,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                     S.slow_list[slot] = cb + q;
                     continue;
                 }
-                float E[3], B[3];
-                SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
-                gather_EB<O, float>(sacc, xi0, E, B);
-                push_particle<PUSH, float>(S.qmdt, S.kdt, E, B, u);
+                if (S.qmdt != 0.0f) {   // uniform: no kick, no force
+                    float E[3], B[3];
+                    SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
+                    gather_EB<O, float>(sacc, xi0, E, B);
+                    push_particle<PUSH, float>(S.qmdt, S.kdt, E, B, u);
+                }
                 float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 float dx[3];
                 bool ok = true;
@@ -484,9 +490,11 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
         float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
         float u[3] = {p.ux[t], p.uy[t], p.uz[t]};
         GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
-        float E[3], B[3];
-        gather_EB<O, float>(acc, xi0, E, B);
-        push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
+        if (a.qmdt != 0.0f) {
+            float E[3], B[3];
+            gather_EB<O, float>(acc, xi0, E, B);
+            push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
+        }
         float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         float xi1[3];
         bool ok = true;
@@ -528,7 +536,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         T.E[d] = (const float *)c.E[d];
         T.B[d] = (const float *)c.B[d];
         T.J[d] = (float *)c.J[d];
-        T.dtdx[d] = (float)(c.d.dt / h[d]);
+        T.dtdx[d] = (float)(c.drift_dt / h[d]);
         T.nt[d] = c.ntile[d];
     }
     T.ns = 0;
@@ -545,9 +553,9 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         t.cell_start = S.cell_start;
         t.slow_list = S.keys;              // the sort keys are dead between sorts
         t.slow_count = c.d_slow_count + s;
-        t.qmdt = (float)(S.q * c.d.dt / S.m);
-        t.kdt = (float)(S.rad / c.d.dt);
-        for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.d.dt);
+        t.qmdt = (float)(S.q * c.kick_dt / S.m);
+        t.kdt = (float)(c.kick_dt != 0.0 ? S.rad / c.kick_dt : 0.0);
+        for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.drift_dt);
     }
     if (T.ns == 0) return cudaSuccess;
     T.status = c.d_status;
