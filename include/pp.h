@@ -176,6 +176,24 @@ int pp_set_radiative_cooling(pp_ctx *ctx, int sid, double coef);
  * and pp_field_update always take one leap-frog step. */
 int pp_set_integrator(pp_ctx *ctx, int order);
 
+/* Step graphs (no counterpart in the paper: a launch-overhead measure for
+ * small runs).  With enable = 1, pp_step captures each step as a CUDA graph
+ * the first time the context is in that state, and replays the capture
+ * afterwards.  A state is whether the step sorts, which of the two current
+ * buffers holds J, and which of its two buffers holds each species; at most
+ * 8 captures are kept, the oldest replaced first.  Results equal those of
+ * the eager path.  Every call that changes what a step launches (species,
+ * particle loads, cooling, integrator, tuning) drops the captures.  Graphs
+ * are not used while profiling is enabled.  Needs a context stream other
+ * than the legacy default (PP_EINVAL otherwise).  If a capture fails the
+ * context returns to eager steps for good.  enable = 0 frees the captures.
+ * A runtime setting: checkpoints do not keep it. */
+int pp_set_graphs(pp_ctx *ctx, int enable);
+
+/* Steps captured as graphs and steps replayed from a capture since
+ * pp_init_grid (either pointer may be NULL). */
+int pp_get_graph_stats(pp_ctx *ctx, int64_t *captures, int64_t *replays);
+
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,

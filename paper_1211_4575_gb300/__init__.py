@@ -72,6 +72,8 @@ SIGNATURES = {
     "pp_init_species": (C.c_int, [_P, C.POINTER(SpeciesDesc), C.POINTER(C.c_int)]),
     "pp_set_radiative_cooling": (C.c_int, [_P, C.c_int, C.c_double]),
     "pp_set_integrator": (C.c_int, [_P, C.c_int]),
+    "pp_set_graphs": (C.c_int, [_P, C.c_int]),
+    "pp_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pp_load_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int]),
     "pp_load_fields": (C.c_int, [_P, _PP, _PP, C.c_int]),
     "pp_step": (C.c_int, [_P, C.c_int]),
@@ -218,6 +220,16 @@ class Simulation:
     def set_integrator(self, order):
         """2: leap-frog step; 4: four-substep 4th-order symplectic step (u synchronous with x)."""
         self._c(lib().pp_set_integrator(self._ctx, int(order)))
+
+    def set_graphs(self, enable=True):
+        """Capture steps as CUDA graphs and replay them (needs a non-default stream)."""
+        self._c(lib().pp_set_graphs(self._ctx, int(bool(enable))))
+
+    def graph_stats(self):
+        """(captures, replays) of the step graphs."""
+        cap, rep = C.c_int64(0), C.c_int64(0)
+        self._c(lib().pp_get_graph_stats(self._ctx, C.byref(cap), C.byref(rep)))
+        return cap.value, rep.value
 
     def set_radiative_cooling(self, sid, coef):
         """Radiative cooling coefficient mu0 q^2 / (6 pi m c) of species sid (0 = off)."""

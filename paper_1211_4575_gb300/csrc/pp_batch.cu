@@ -4,7 +4,9 @@
 // Each admitted context keeps its own particles, fields and stream on the
 // device; pp_batch_advance enqueues up to max_steps steps of every active slot
 // on that slot's stream, so the runs of different sizes overlap on the GPU,
-// and records an event per slot.  pp_batch_poll reads the event without
+// and records an event per slot.  Slots whose context has its own stream step
+// through captured CUDA graphs (pp_set_graphs), one graph launch per step
+// instead of ~25 kernel launches.  pp_batch_poll reads the event without
 // blocking; a slot whose steps are all enqueued and whose event has completed
 // reports PP_BATCH_DONE once and is released (its memory returns to the budget;
 // the context itself stays with the caller).
@@ -77,6 +79,8 @@ extern "C" int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot
     pp_batch::Slot &S = b->slot[k];
     if (!S.ev && cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming) != cudaSuccess)
         return bfail(b, PP_ECUDA, "event creation failed");
+    // slots step through captured graphs where the context has its own stream
+    if (static_cast<Ctx *>(ctx)->st) pp_set_graphs(ctx, 1);
     S.ctx = ctx;
     S.left = steps;
     S.done = 0;

@@ -245,11 +245,21 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     return PP_OK;
 }
 
+// Drop every captured step graph (their launch arguments no longer hold).
+static void graphs_clear(Ctx *c) {
+    for (int q = 0; q < kGraphSlots; ++q) {
+        if (c->graphs[q].exec) cudaGraphExecDestroy(c->graphs[q].exec);
+        c->graphs[q] = StepGraph();
+    }
+    c->graph_next = 0;
+}
+
 extern "C" int pp_destroy(pp_ctx *p) {
     if (!p) return PP_OK;
     Ctx *c = p;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
+    graphs_clear(c);
     for (int s = 0; s < c->nspecies; ++s) {
         cudaFree(c->sp[s].buf);
         cudaFree(c->sp[s].alt);
@@ -304,15 +314,8 @@ extern "C" int pp_init_species(pp_ctx *p, const pp_species_desc *sd, int *sid) {
         S = Species();
         return fail(c, PP_ENOMEM, "species storage of %zu bytes x 2", bytes);
     }
-    if (c->fp64) {
-        double *b = (double *)S.buf;
-        S.x = b; S.y = b + S.cap; S.z = b + 2 * S.cap; S.ux = b + 3 * S.cap; S.uy = b + 4 * S.cap; S.uz = b + 5 * S.cap;
-    } else {
-        int32_t *ci = (int32_t *)S.buf;
-        float *f = (float *)(ci + S.cap);
-        S.cell = ci; S.ox = f; S.oy = f + S.cap; S.oz = f + 2 * S.cap;
-        S.fux = f + 3 * S.cap; S.fuy = f + 4 * S.cap; S.fuz = f + 5 * S.cap;
-    }
+    S.bind(c->fp64);
+    graphs_clear(c);
     *sid = c->nspecies++;
     return PP_OK;
 }
@@ -323,6 +326,7 @@ extern "C" int pp_set_radiative_cooling(pp_ctx *p, int sid, double coef) {
     if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
     if (!isfinite(coef) || coef < 0.0) return fail(c, PP_EINVAL, "cooling coefficient must be finite and >= 0");
     c->sp[sid].rad = coef;
+    graphs_clear(c);
     return PP_OK;
 }
 
@@ -347,6 +351,7 @@ extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x,
     if (n < 0) return fail(c, PP_EINVAL, "negative count");
     if (n > 0 && (!x || !y || !z || !ux || !uy || !uz)) return fail(c, PP_EINVAL, "NULL particle array");
     if (S.n + n > S.limit) return fail(c, PP_ENOMEM, "species %d capacity %lld exceeded", sid, (long long)S.limit);
+    graphs_clear(c);   // particle counts set launch sizes
     const int64_t chunk = (int64_t)1 << 24;
     double *stage = nullptr;
     if (!on_device && n > 0) CU(cudaMalloc(&stage, sizeof(double) * 6 * (size_t)(n < chunk ? n : chunk)));
@@ -567,36 +572,165 @@ extern "C" int pp_sort(pp_ctx *p) {
     return PP_OK;
 }
 
+// The device work of one step: the sort when `sort`, then the particle and
+// field phases (four kick-drift substeps for the 4th-order integrator).  Only
+// enqueues work; the host state it changes is the J / J' and particle buffer
+// swaps, the sorted flags and the last solve's iteration data.
+static int step_body(Ctx *c, bool sort) {
+    if (sort) {
+        int r = pp_sort(static_cast<pp_ctx *>(c));
+        if (r) return r;
+    }
+    int r = PP_OK;
+    if (c->order == 4) {
+        double a[4], b[4];
+        step4_fractions(a, b);
+        for (int i = 0; i < 4 && r == PP_OK; ++i) {
+            c->kick_dt = b[i] * c->d.dt;
+            c->drift_dt = a[i] * c->d.dt;
+            c->cheb_sel = (i == 0 || i == 3) ? 1 : 2;
+            r = particle_phase(c, -1);
+            if (r == PP_OK) r = field_phase(c);
+        }
+        c->kick_dt = c->drift_dt = c->d.dt;
+        c->cheb_sel = 0;
+    } else {
+        r = particle_phase(c, -1);
+        if (r == PP_OK) r = field_phase(c);
+    }
+    return r;
+}
+
+static bool graph_matches(const Ctx *c, const StepGraph &G, bool sort) {
+    if (!G.valid || G.sort != sort || G.J0 != c->J[0]) return false;
+    for (int s = 0; s < c->nspecies; ++s)
+        if (G.buf[s] != c->sp[s].buf || G.sorted[s] != c->sp[s].sorted) return false;
+    return true;
+}
+
+// Host state a step leaves behind, taken after a capture and re-applied after
+// each replay of that capture.
+static void graph_save_after(const Ctx *c, StepGraph &G) {
+    for (int a = 0; a < 3; ++a) {
+        G.J_after[a] = c->J[a];
+        G.Jt_after[a] = c->Jt[a];
+    }
+    for (int s = 0; s < c->nspecies; ++s) {
+        G.buf_after[s] = c->sp[s].buf;
+        G.alt_after[s] = c->sp[s].alt;
+    }
+    G.last_iters = c->last_iters;
+    G.last_kk = c->last_kk;
+}
+
+static void graph_apply_after(Ctx *c, const StepGraph &G) {
+    for (int a = 0; a < 3; ++a) {
+        c->J[a] = G.J_after[a];
+        c->Jt[a] = G.Jt_after[a];
+    }
+    for (int s = 0; s < c->nspecies; ++s) {
+        Species &S = c->sp[s];
+        S.buf = G.buf_after[s];
+        S.alt = G.alt_after[s];
+        S.bind(c->fp64);
+        if (G.sort) S.sorted = true;
+    }
+    c->last_iters = G.last_iters;
+    c->last_kk = G.last_kk;
+    if (G.sort) c->since_sort = 0;
+}
+
+// One step through the graph cache: replay the capture that starts from the
+// current state, or capture it (and launch the capture).  A capture that fails
+// leaves the host state as it was and the step runs eagerly.
+static int step_graph(Ctx *c, bool sort) {
+    for (int q = 0; q < kGraphSlots; ++q) {
+        StepGraph &G = c->graphs[q];
+        if (!graph_matches(c, G, sort)) continue;
+        CU(cudaGraphLaunch(G.exec, c->st));
+        graph_apply_after(c, G);
+        c->nlaunch += G.launches;
+        ++c->graph_replays;
+        return PP_OK;
+    }
+    int q = -1;
+    for (int k = 0; k < kGraphSlots; ++k)
+        if (!c->graphs[k].valid) { q = k; break; }
+    if (q < 0) {
+        q = c->graph_next;
+        c->graph_next = (c->graph_next + 1) % kGraphSlots;
+    }
+    StepGraph &G = c->graphs[q];
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G = StepGraph();
+    G.sort = sort;
+    G.J0 = c->J[0];
+    for (int s = 0; s < c->nspecies; ++s) {
+        G.buf[s] = c->sp[s].buf;
+        G.sorted[s] = c->sp[s].sorted;
+    }
+    // host state before, for a failed capture
+    StepGraph before;
+    graph_save_after(c, before);
+    bool sorted0[PP_MAX_SPECIES];
+    for (int s = 0; s < c->nspecies; ++s) sorted0[s] = c->sp[s].sorted;
+    int since0 = c->since_sort;
+    int64_t nl0 = c->nlaunch;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed);
+    int r = e == cudaSuccess ? step_body(c, sort) : PP_ECUDA;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(c->st, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (r == PP_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (r != PP_OK || e != cudaSuccess || !exec) {
+        cudaGetLastError();   // clear a capture error
+        if (exec) cudaGraphExecDestroy(exec);
+        graph_apply_after(c, before);   // undo the pointer swaps of the capture
+        for (int s = 0; s < c->nspecies; ++s) c->sp[s].sorted = sorted0[s];
+        c->since_sort = since0;
+        c->nlaunch = nl0;
+        G = StepGraph();
+        c->use_graphs = false;   // do not try again on this context
+        return step_body(c, sort);
+    }
+    G.exec = exec;
+    G.launches = (int)(c->nlaunch - nl0);
+    graph_save_after(c, G);
+    G.valid = true;
+    ++c->graph_captures;
+    CU(cudaGraphLaunch(exec, c->st));
+    return PP_OK;
+}
+
 extern "C" int pp_step(pp_ctx *p, int nsteps) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (nsteps < 0) return fail(c, PP_EINVAL, "negative step count");
     for (int it = 0; it < nsteps; ++it) {
-        if (c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval) {
-            int r = pp_sort(p);
-            if (r) return r;
-        }
-        int r = PP_OK;
-        if (c->order == 4) {
-            double a[4], b[4];
-            step4_fractions(a, b);
-            for (int i = 0; i < 4 && r == PP_OK; ++i) {
-                c->kick_dt = b[i] * c->d.dt;
-                c->drift_dt = a[i] * c->d.dt;
-                c->cheb_sel = (i == 0 || i == 3) ? 1 : 2;
-                r = particle_phase(c, -1);
-                if (r == PP_OK) r = field_phase(c);
-            }
-            c->kick_dt = c->drift_dt = c->d.dt;
-            c->cheb_sel = 0;
-        } else {
-            r = particle_phase(c, -1);
-            if (r == PP_OK) r = field_phase(c);
-        }
+        bool sort = c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval;
+        int r = (c->use_graphs && !c->prof && c->st) ? step_graph(c, sort) : step_body(c, sort);
         if (r) return r;
         ++c->step;
         ++c->since_sort;
     }
+    return PP_OK;
+}
+
+extern "C" int pp_set_graphs(pp_ctx *p, int enable) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (enable && !c->st) return fail(c, PP_EINVAL, "step graphs need a context stream other than the legacy default");
+    c->use_graphs = enable != 0;
+    if (!enable) graphs_clear(c);
+    return PP_OK;
+}
+
+extern "C" int pp_get_graph_stats(pp_ctx *p, int64_t *captures, int64_t *replays) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (captures) *captures = c->graph_captures;
+    if (replays) *replays = c->graph_replays;
     return PP_OK;
 }
 
@@ -605,6 +739,7 @@ extern "C" int pp_set_integrator(pp_ctx *p, int order) {
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (order != 2 && order != 4) return fail(c, PP_EINVAL, "integrator order must be 2 or 4");
     c->order = order;
+    graphs_clear(c);
     return PP_OK;
 }
 
@@ -632,6 +767,7 @@ extern "C" int pp_set_tuning(pp_ctx *p, int sort_interval, int deposit_mode) {
         return fail(c, PP_EINVAL, "the tiled deposit needs PP_MIXED32 and grid sizes that are multiples of 8");
     c->d.sort_interval = sort_interval;
     c->d.deposit_mode = deposit_mode;
+    graphs_clear(c);
     return PP_OK;
 }
 

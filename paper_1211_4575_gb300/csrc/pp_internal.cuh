@@ -308,7 +308,38 @@ struct Species {
     int32_t *keys = nullptr;  // sort keys
     int32_t *cell_start = nullptr; // offsets per sort key (nkeys + 1), valid after a sort
     bool sorted = false;
+    // Point the SoA arrays into buf (the sort swaps buf and alt).
+    void bind(bool fp64) {
+        if (fp64) {
+            double *b = (double *)buf;
+            x = b; y = b + cap; z = b + 2 * cap; ux = b + 3 * cap; uy = b + 4 * cap; uz = b + 5 * cap;
+        } else {
+            int32_t *ci = (int32_t *)buf;
+            float *f = (float *)(ci + cap);
+            cell = ci; ox = f; oy = f + cap; oz = f + 2 * cap; fux = f + 3 * cap; fuy = f + 4 * cap; fuz = f + 5 * cap;
+        }
+    }
 };
+
+// One step captured as a CUDA graph (pp_set_graphs).  A step's launches and
+// their pointer arguments are fixed by the state it starts from: whether it
+// sorts, which of J / J' holds the current, and which buffer holds each
+// species (the sort swaps them).  The host-side state the step leaves behind
+// is stored with it and re-applied on every replay.
+struct StepGraph {
+    bool valid = false;
+    bool sort = false;
+    void *J0 = nullptr;
+    void *buf[PP_MAX_SPECIES] = {};
+    bool sorted[PP_MAX_SPECIES] = {};
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    void *J_after[3] = {}, *Jt_after[3] = {};
+    void *buf_after[PP_MAX_SPECIES] = {}, *alt_after[PP_MAX_SPECIES] = {};
+    int last_iters = 0;
+    double last_kk = 0;
+};
+constexpr int kGraphSlots = 8;
 
 enum Phase { PH_PARTICLE = 0, PH_CURRENT = 1, PH_FIELD = 2, PH_SORT = 3, PH_N = 4 };
 
@@ -350,6 +381,11 @@ struct Ctx {
     // 4th-order step.
     int order = 2;
     double kick_dt = 0, drift_dt = 0;
+    // step graphs
+    bool use_graphs = false;
+    StepGraph graphs[kGraphSlots];
+    int graph_next = 0;          // slot replaced on the next miss when all are valid
+    int64_t graph_captures = 0, graph_replays = 0;
     // sort
     int tile[3] = {8, 8, 8};
     int ntile[3] = {1, 1, 1};

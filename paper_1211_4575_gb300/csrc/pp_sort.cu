@@ -217,8 +217,7 @@ cudaError_t launch_sort(Ctx &c, int s) {
         void *old = S.buf;
         S.buf = S.alt;
         S.alt = old;
-        double *p = (double *)S.buf;
-        S.x = p; S.y = p + cp; S.z = p + 2 * cp; S.ux = p + 3 * cp; S.uy = p + 4 * cp; S.uz = p + 5 * cp;
+        S.bind(true);
     } else {
         int64_t cp = S.cap;
         int32_t *c2 = (int32_t *)S.alt;
@@ -230,9 +229,7 @@ cudaError_t launch_sort(Ctx &c, int s) {
         void *old = S.buf;
         S.buf = S.alt;
         S.alt = old;
-        int32_t *ci = (int32_t *)S.buf;
-        float *f = (float *)(ci + cp);
-        S.cell = ci; S.ox = f; S.oy = f + cp; S.oz = f + 2 * cp; S.fux = f + 3 * cp; S.fuy = f + 4 * cp; S.fuz = f + 5 * cp;
+        S.bind(false);
     }
     return cudaSuccess;
 }

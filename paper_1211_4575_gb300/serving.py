@@ -99,3 +99,65 @@ def sequential(requests, precision=PP_MIXED32, keep=False):
             sim.close()
     makespan = time.perf_counter() - t0
     return _summary(lat, work, makespan), results
+
+
+def build_all(requests, precision=PP_MIXED32):
+    """Build every run of a batched workload (seeded load, resident on the
+    device), each with its own stream: [(request, Simulation, particles, stream)]."""
+    import torch
+    built = []
+    for req in requests:
+        stream = torch.cuda.Stream()
+        sim, npart = _build(req, precision, stream.cuda_stream)
+        built.append((req, sim, npart, stream))
+    torch.cuda.synchronize()
+    return built
+
+
+def batched(built, budget_bytes, max_slots=64, chunk=4, graphs=True):
+    """Batched form on runs already resident (build_all): all runs admitted
+    into slots as budget and slots allow and advanced together, one stream
+    each, each step replayed from a captured CUDA graph unless graphs=False,
+    until every run has taken its steps.  Summary of the timed region."""
+    batch = Batch(budget_bytes, max_slots)
+    waiting = list(built)
+    active = {}
+    lat, work = [], 0
+    t0 = time.perf_counter()
+    while waiting or active:
+        while waiting:
+            req, sim, npart, stream = waiting[0]
+            slot = batch.admit(sim, req["steps"])
+            if slot is None:
+                break
+            if not graphs:
+                sim.set_graphs(False)
+            waiting.pop(0)
+            active[slot] = (req, sim, npart, stream)
+        batch.advance(chunk)
+        for slot in list(active):
+            state, _ = batch.poll(slot)
+            if state in (PP_BATCH_DONE, PP_BATCH_FAILED):
+                req, sim, npart, stream = active.pop(slot)
+                if state == PP_BATCH_FAILED:
+                    raise PPError(state, f"run {req.get('seed')} failed")
+                lat.append(time.perf_counter() - t0)
+                work += npart * req["steps"]
+    makespan = time.perf_counter() - t0
+    batch.close()
+    return _summary(lat, work, makespan)
+
+
+def one_at_a_time(built):
+    """The same resident runs stepped one after another with plain (uncaptured)
+    steps, each run to its end before the next starts."""
+    lat, work = [], 0
+    t0 = time.perf_counter()
+    for req, sim, npart, _ in built:
+        sim.set_graphs(False)
+        sim.step(req["steps"])
+        sim.sync()
+        lat.append(time.perf_counter() - t0)
+        work += npart * req["steps"]
+    makespan = time.perf_counter() - t0
+    return _summary(lat, work, makespan)
