@@ -38,11 +38,11 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # taken on: the device header, the sort (its key sets the particle order the
 # kernel streams) and the part of pp_particles.cu that holds the particle
 # kernels (up to its charge-density section).
-PROFILED_BYTES_PER_PARTICLE = 906.933760e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 901.710848e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "fbdb92befdb07090e1d0892cb670242f1c04512fe7b595ec2a896d45408bc24e",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "7a1005e6fce878184c5489791878a81bd89a30dde19bc6d5745fcb39a7212881",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "096c0f083a3ddac4fbd3f8964377829535703a37db32aafeb2651b730c2509b9",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "22e55bbcd96d3a08dbc32137c21494075357308a26bb05c4d1b03b8fe4748a57",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "504fa77f0cf5c710b397512493380b8b75448c917235096f104992b782818ec3",
 }
 

@@ -208,12 +208,12 @@ __device__ __forceinline__ void gather_EB(const Acc &acc, const R (&xi)[3], R (&
 // jscale_a = -q w dx_a / dt.  xi0/xi1: old/new position in the frame of Acc.
 // Acc::addJ(comp, i, j, k, v) accumulates into the current of the frame.
 // ---------------------------------------------------------------------------
-template <int O, typename R, class Acc>
-__device__ __forceinline__ void deposit_esirkepov(Acc &acc, const R (&xi0)[3], const R (&xi1)[3],
-                                                  const R (&jscale)[3]) {
+// Weights of one particle's move on the union support of its old and new
+// positions: S0 (old) and DS (new - old), O+2 points per axis from lo.
+template <int O, typename R>
+__device__ __forceinline__ void esirkepov_weights(const R (&xi0)[3], const R (&xi1)[3], R (&S0)[3][O + 2],
+                                                  R (&DS)[3][O + 2], int (&lo)[3]) {
     constexpr int S = O + 2;
-    R S0[3][S], DS[3][S];
-    int lo[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         R wo[O + 1], wn[O + 1];
@@ -230,49 +230,132 @@ __device__ __forceinline__ void deposit_esirkepov(Acc &acc, const R (&xi0)[3], c
         }
         lo[a] = l;
     }
+}
+
+// Component A of the current of one particle from its weights.
+template <int O, typename R, int A, class Acc>
+__device__ __forceinline__ void esirkepov_component(Acc &acc, const R (&S0)[3][O + 2], const R (&DS)[3][O + 2],
+                                                    const int (&lo)[3], R jscale) {
+    constexpr int S = O + 2;
+    constexpr int B = (A + 1) % 3, Cc = (A + 2) % 3;
+    // C[m] = sum_{m' <= m} dS[m'] = -sum_{m' > m} dS[m'] (the support sums
+    // to zero): the upper faces use the suffix form, so a particle that
+    // stays inside its cell gets exact zeros there.
+    R C[O + 1];
+    R run = R(0);
+#pragma unroll
+    for (int m = 0; m <= O; ++m) {
+        if (2 * m < O + 1) {
+            run += DS[A][m];
+            C[m] = run * jscale;
+        }
+    }
+    run = R(0);
+#pragma unroll
+    for (int m = O; m >= 0; --m) {
+        if (2 * m >= O + 1) {
+            run -= DS[A][m + 1];
+            C[m] = run * jscale;
+        }
+    }
+#pragma unroll
+    for (int mc = 0; mc < S; ++mc) {
+        R p = S0[Cc][mc] + R(0.5) * DS[Cc][mc];
+        R q = R(0.5) * S0[Cc][mc] + R(1.0 / 3.0) * DS[Cc][mc];
+#pragma unroll
+        for (int mb = 0; mb < S; ++mb) {
+            R Y = S0[B][mb] * p + DS[B][mb] * q;
+#pragma unroll
+            for (int m = 0; m <= O; ++m) {
+                R v = C[m] * Y;
+                if (v == R(0)) continue;
+                int idx[3];
+                idx[A] = lo[A] + m;
+                idx[B] = lo[B] + mb;
+                idx[Cc] = lo[Cc] + mc;
+                acc.addJ(A, idx[0], idx[1], idx[2], v);
+            }
+        }
+    }
+}
+
+template <int O, typename R, class Acc>
+__device__ __forceinline__ void deposit_esirkepov(Acc &acc, const R (&xi0)[3], const R (&xi1)[3],
+                                                  const R (&jscale)[3]) {
+    R S0[3][O + 2], DS[3][O + 2];
+    int lo[3];
+    esirkepov_weights<O, R>(xi0, xi1, S0, DS, lo);
+    esirkepov_component<O, R, 0>(acc, S0, DS, lo, jscale[0]);
+    esirkepov_component<O, R, 1>(acc, S0, DS, lo, jscale[1]);
+    esirkepov_component<O, R, 2>(acc, S0, DS, lo, jscale[2]);
+}
+
+// deposit_esirkepov for a particle whose old and new positions share the
+// support start on every axis (it crosses no support boundary in the step):
+// the union support is the O+1 points of both, the prefix C vanishes on the
+// last face, and each component has O (O+1)^2 sites.  The products are those
+// of deposit_esirkepov site by site (its zero sites are left out here, its
+// skipped exact zeros are added here).  Returns false, depositing nothing,
+// for any other particle.
+template <int O, typename R, class Acc>
+__device__ __forceinline__ bool deposit_esirkepov_inner(Acc &acc, const R (&xi0)[3], const R (&xi1)[3],
+                                                        const R (&jscale)[3]) {
+    R S0[3][O + 1], DS[3][O + 1];
+    int lo[3];
+    bool same = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R wo[O + 1], wn[O + 1];
+        int io = support<O, R>(xi0[a], false, wo);
+        int in = support<O, R>(xi1[a], false, wn);
+        same = same && io == in;
+        lo[a] = io;
+#pragma unroll
+        for (int m = 0; m <= O; ++m) {
+            S0[a][m] = wo[m];
+            DS[a][m] = wn[m] - wo[m];
+        }
+    }
+    if (!same) return false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
-        // C[m] = sum_{m' <= m} dS[m'] = -sum_{m' > m} dS[m'] (the support sums
-        // to zero): the upper faces use the suffix form, so a particle that
-        // stays inside its cell gets exact zeros there.
-        R C[O + 1];
+        R C[O];
         R run = R(0);
 #pragma unroll
-        for (int m = 0; m <= O; ++m) {
+        for (int m = 0; m < O; ++m) {
             if (2 * m < O + 1) {
                 run += DS[a][m];
                 C[m] = run * jscale[a];
             }
         }
-        run = R(0);
+        run = R(0);   // C[O] = -DS[O+1] = 0: the suffix starts below it
 #pragma unroll
-        for (int m = O; m >= 0; --m) {
+        for (int m = O - 1; m >= 0; --m) {
             if (2 * m >= O + 1) {
                 run -= DS[a][m + 1];
                 C[m] = run * jscale[a];
             }
         }
 #pragma unroll
-        for (int mc = 0; mc < S; ++mc) {
+        for (int mc = 0; mc <= O; ++mc) {
             R p = S0[c][mc] + R(0.5) * DS[c][mc];
             R q = R(0.5) * S0[c][mc] + R(1.0 / 3.0) * DS[c][mc];
 #pragma unroll
-            for (int mb = 0; mb < S; ++mb) {
+            for (int mb = 0; mb <= O; ++mb) {
                 R Y = S0[b][mb] * p + DS[b][mb] * q;
 #pragma unroll
-                for (int m = 0; m <= O; ++m) {
-                    R v = C[m] * Y;
-                    if (v == R(0)) continue;
+                for (int m = 0; m < O; ++m) {
                     int idx[3];
                     idx[a] = lo[a] + m;
                     idx[b] = lo[b] + mb;
                     idx[c] = lo[c] + mc;
-                    acc.addJ(a, idx[0], idx[1], idx[2], v);
+                    acc.addJ(a, idx[0], idx[1], idx[2], C[m] * Y);
                 }
             }
         }
     }
+    return true;
 }
 
 // Charge weights of one particle on the integer nodes (eq:rho2).

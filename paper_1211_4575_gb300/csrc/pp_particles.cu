@@ -258,9 +258,11 @@ constexpr int kLaneStride = kChunk / 32;       // sorted-order distance between 
 static_assert(kChunk % kThreads == 0 && kLaneStride == kWarps * kPerThread, "chunk must split evenly over the CTA");
 constexpr int kStage = kChunk + kChunk / 32;   // one pad word per 32 (bank spread)
 constexpr int kStageArrays = 10;               // cell, 3 offsets, 3 momenta, 3 displacements
-constexpr size_t kTiledSmem = sizeof(float) * (9 * kWinVol + kStageArrays * kStage) + sizeof(int) * 16;
+constexpr size_t kTiledSmem = sizeof(float) * (9 * kWinVol + kStageArrays * kStage) + sizeof(int) * (16 + kChunk);
 static_assert(kTiledSmem <= 227 * 1024, "tile CTA must fit the opt-in shared memory");
 constexpr float kFixedRange = 1073741824.0f;   // 2^30
+constexpr int32_t kQueued = 1 << 30;           // staging flag on a packed cell (bits 0-29 hold x, y, z)
+static_assert(kWarps >= 3, "the queue pass needs three warps per group");
 static_assert(kChunk <= 1024, "the fixed-point bound allows at most 1024 rounding halves per flush");
 constexpr int kMaxTiledSpecies = PP_MAX_SPECIES;
 
@@ -318,7 +320,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
     float *s_u = stg + 4 * kStage;       // 3 arrays: momenta
     float *s_d = stg + 7 * kStage;       // 3 arrays: displacement of the step (NaN: not deposited here)
     int *bbox = (int *)(stg + kStageArrays * kStage);   // min x,y,z, max x,y,z of the deposited cells
+    int *nqueue = bbox + 6;                               // particles queued for the general deposit
     float *tot = (float *)(bbox + 8);                     // sum |dxi| per axis
+    int *s_queue = bbox + 16;                             // their staging indices (kChunk)
     const Geom &g = T.g;
     const int tile = blockIdx.x;
     const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
@@ -347,6 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 bbox[3 + threadIdx.x] = -(1 << 20);   // running maximum
                 tot[threadIdx.x] = 0.0f;
             }
+            if (threadIdx.x == 0) *nqueue = 0;
             for (int q = threadIdx.x; q < cn; q += kThreads) {
                 int sq = q + (q >> 5);
                 s_cell[sq] = S.p.cell[cb + q];
@@ -423,29 +428,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 unit[d] = bound > 0.0f ? kFixedRange / bound : 0.0f;
                 jsc[d] = S.jscale[d] * unit[d];
             }
-#pragma unroll 1
-            for (int r = 0; r < kPerThread; ++r) {
-                const int q = lane * kLaneStride + warp + kWarps * r;
-                if (q >= cn) continue;
-                const int sq = q + (q >> 5);
-                float dx0 = s_d[sq];
-                if (isnan(dx0)) continue;
-                int cx, cy, cz;
+            // The particle at staging index sq in the frame of its cell: old and
+            // new offsets, and the accessor of its window position.
+            auto frame = [&](int sq, float (&xi0)[3], float (&xi1)[3], int &cx, int &cy, int &cz) {
                 unpack_cell(s_cell[sq], cx, cy, cz);
-                float xi0[3] = {s_o[sq], s_o[kStage + sq], s_o[2 * kStage + sq]};
-                float xi1[3] = {xi0[0] + dx0, xi0[1] + s_d[kStage + sq], xi0[2] + s_d[2 * kStage + sq]};
+                for (int d = 0; d < 3; ++d) {
+                    xi0[d] = s_o[d * kStage + sq];
+                    xi1[d] = xi0[d] + s_d[d * kStage + sq];
+                }
                 int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
-                SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
-                deposit_esirkepov<O, float>(sacc, xi0, xi1, jsc);
+                return SmemAcc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
+            };
+            auto finish = [&](int sq, float (&xi1)[3], int cx, int cy, int cz) {
                 rebin(xi1[0], cx, g.n[0]);
                 rebin(xi1[1], cy, g.n[1]);
                 rebin(xi1[2], cz, g.n[2]);
                 s_cell[sq] = pack_cell(cx, cy, cz);
                 s_o[sq] = xi1[0]; s_o[kStage + sq] = xi1[1]; s_o[2 * kStage + sq] = xi1[2];
+            };
+            // Most particles cross no support boundary in a step: they deposit
+            // through the O (O+1)^2-site form.  The others are queued and then
+            // deposited by all threads together, so that a warp's lanes take one
+            // form at a time instead of every warp taking the union of both.
+#pragma unroll 1
+            for (int r = 0; r < kPerThread; ++r) {
+                const int q = lane * kLaneStride + warp + kWarps * r;
+                if (q >= cn) continue;
+                const int sq = q + (q >> 5);
+                if (isnan(s_d[sq])) continue;
+                float xi0[3], xi1[3];
+                int cx, cy, cz;
+                SmemAcc sacc = frame(sq, xi0, xi1, cx, cy, cz);
+                if (!deposit_esirkepov_inner<O, float>(sacc, xi0, xi1, jsc)) {
+                    s_queue[atomicAdd(nqueue, 1)] = sq;
+                    s_cell[sq] |= kQueued;   // re-binned when written back
+                    continue;
+                }
+                finish(sq, xi1, cx, cy, cz);
+            }
+            __syncthreads();
+            // The queue: groups of three warps take 32 particles per round, one
+            // current component per warp (warp 15 rests), so that the pass lasts
+            // about a third of a deposit and no warp diverges over components.
+            const int nq = *nqueue;
+            const int group = warp / 3, comp = warp - 3 * group;
+            if (group < kWarps / 3) {
+#pragma unroll 1
+                for (int k = 32 * group + lane; k < nq; k += 32 * (kWarps / 3)) {
+                    const int sq = s_queue[k];
+                    float xi0[3], xi1[3];
+                    int cx, cy, cz;
+                    SmemAcc sacc = frame(sq, xi0, xi1, cx, cy, cz);
+                    float S0[3][O + 2], DS[3][O + 2];
+                    int lo[3];
+                    esirkepov_weights<O, float>(xi0, xi1, S0, DS, lo);
+                    if (comp == 0) esirkepov_component<O, float, 0>(sacc, S0, DS, lo, jsc[0]);
+                    else if (comp == 1) esirkepov_component<O, float, 1>(sacc, S0, DS, lo, jsc[1]);
+                    else esirkepov_component<O, float, 2>(sacc, S0, DS, lo, jsc[2]);
+                }
             }
             __syncthreads();
             for (int q = threadIdx.x; q < cn; q += kThreads) {
                 int sq = q + (q >> 5);
+                if (s_cell[sq] & kQueued) {   // deposited from the queue: move it now
+                    float xi0[3], xi1[3];
+                    int cx, cy, cz;
+                    frame(sq, xi0, xi1, cx, cy, cz);
+                    finish(sq, xi1, cx, cy, cz);
+                }
                 S.p.cell[cb + q] = s_cell[sq];
                 S.p.ox[cb + q] = s_o[sq]; S.p.oy[cb + q] = s_o[kStage + sq]; S.p.oz[cb + q] = s_o[2 * kStage + sq];
                 S.p.ux[cb + q] = s_u[sq]; S.p.uy[cb + q] = s_u[kStage + sq]; S.p.uz[cb + q] = s_u[2 * kStage + sq];
