@@ -38,10 +38,10 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # taken on: the device header, the sort (its key sets the particle order the
 # kernel streams) and the part of pp_particles.cu that holds the particle
 # kernels (up to its charge-density section).
-PROFILED_BYTES_PER_PARTICLE = 901.710848e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 901.399552e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "096c0f083a3ddac4fbd3f8964377829535703a37db32aafeb2651b730c2509b9",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "9f54073428da81ba06fff7c2bab70dfcfc5c9ab2996f1791b674a996a7eba308",
     "paper_1211_4575_gb300/csrc/pp_internal.cuh": "22e55bbcd96d3a08dbc32137c21494075357308a26bb05c4d1b03b8fe4748a57",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "504fa77f0cf5c710b397512493380b8b75448c917235096f104992b782818ec3",
 }

@@ -243,8 +243,8 @@ constexpr int kMargin = 2;                     // drift allowed before the fallb
 constexpr int kReachLo = 2, kReachHi = 3;      // deposit/gather reach around a cell
 constexpr int kWin = kTile + 2 * kMargin + kReachLo + kReachHi;   // 17 nodes per axis
 // Window layout: x fastest, then z (stride kWin), then y (stride kWinPlane).
-// A warp's lanes take particles 32 sorted positions apart, i.e. one per cell
-// over an 8 x 4 block of cells in x and y.  With y strided by a plane of
+// A warp's lanes take particles about one cell apart in sorted order (lane_q),
+// i.e. one per cell over an 8 x 4 block of cells in x and y.  With y strided by a plane of
 // 296 = 8 (mod 32) words those 32 cells start in 32 distinct banks; a plain
 // 17 x 17 plane folds the block's rows onto each other (2-way conflicts).
 constexpr int kWinPlane = 296;
@@ -254,8 +254,8 @@ __device__ __forceinline__ int win(int i, int j, int k) { return j * kWinPlane +
 constexpr int kWinLo = kMargin + kReachLo;     // window node 0 = tile origin - kWinLo
 constexpr int kChunk = 1024;                   // particles staged per round
 constexpr int kPerThread = kChunk / kThreads;  // particles per thread per round
-constexpr int kLaneStride = kChunk / 32;       // sorted-order distance between lanes
-static_assert(kChunk % kThreads == 0 && kLaneStride == kWarps * kPerThread, "chunk must split evenly over the CTA");
+constexpr int kRounds = kChunk / 32;           // warp-rounds per chunk
+static_assert(kChunk % kThreads == 0 && kRounds == kWarps * kPerThread, "chunk must split evenly over the CTA");
 constexpr int kStage = kChunk + kChunk / 32;   // one pad word per 32 (bank spread)
 constexpr int kStageArrays = 10;               // cell, 3 offsets, 3 momenta, 3 displacements
 constexpr size_t kTiledSmem = sizeof(float) * (9 * kWinVol + kStageArrays * kStage) + sizeof(int) * (16 + kChunk);
@@ -265,6 +265,15 @@ constexpr int32_t kQueued = 1 << 30;           // staging flag on a packed cell 
 static_assert(kWarps >= 3, "the queue pass needs three warps per group");
 static_assert(kChunk <= 1024, "the fixed-point bound allows at most 1024 rounding halves per flush");
 constexpr int kMaxTiledSpecies = PP_MAX_SPECIES;
+
+// Chunk position of the particle that `lane` takes in warp-round j (0..31):
+// lanes 2^sh apart in sorted order, j choosing the offset inside that stride
+// and the block of 32 * 2^sh particles.  With 2^sh about the number of
+// particles per cell, the lanes of a warp sit in 32 consecutive cells.  A
+// bijection of (lane, j) onto 0..1023 for sh in 0..5.
+__device__ __forceinline__ int lane_q(int lane, int j, int sh) {
+    return ((j >> sh) << (sh + 5)) + (lane << sh) + (j & ((1 << sh) - 1));
+}
 
 struct SmemAcc {
     const float *Fw;  // 6 windows: E0 E1 E2 B0 B1 B2
@@ -289,6 +298,7 @@ struct TiledSpecies {
     float qmdt;
     float kdt;                   // radiative cooling K / dt (0 = off)
     float jscale[3];             // -q w dx_a / dt
+    int lane_shift;              // log2 of the sorted-order distance between lanes
 };
 
 struct TiledArgs {
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
             int lo[3] = {1 << 20, 1 << 20, 1 << 20}, hi[3] = {-(1 << 20), -(1 << 20), -(1 << 20)};
 #pragma unroll 1
             for (int r = 0; r < kPerThread; ++r) {
-                const int q = lane * kLaneStride + warp + kWarps * r;
+                const int q = lane_q(lane, warp + kWarps * r, S.lane_shift);
                 if (q >= cn) continue;
                 const int sq = q + (q >> 5);
                 int cx, cy, cz;
@@ -452,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
             // form at a time instead of every warp taking the union of both.
 #pragma unroll 1
             for (int r = 0; r < kPerThread; ++r) {
-                const int q = lane * kLaneStride + warp + kWarps * r;
+                const int q = lane_q(lane, warp + kWarps * r, S.lane_shift);
                 if (q >= cn) continue;
                 const int sq = q + (q >> 5);
                 if (isnan(s_d[sq])) continue;
@@ -605,6 +615,12 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         t.slow_count = c.d_slow_count + s;
         t.qmdt = (float)(S.q * c.kick_dt / S.m);
         t.kdt = (float)(c.kick_dt != 0.0 ? S.rad / c.kick_dt : 0.0);
+        // lanes about one cell apart: the nearest power of two to the
+        // species' mean particles per cell, 1..32
+        double per_cell = (double)S.n / (double)c.g.cells();
+        int sh = 0;
+        while (sh < 5 && per_cell >= 1.5 * (double)(1 << sh)) ++sh;
+        t.lane_shift = sh;
         for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.drift_dt);
     }
     if (T.ns == 0) return cudaSuccess;
