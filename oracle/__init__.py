@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
 class Grid(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double),
                 ("field_order", C.c_int), ("alpha", C.c_double), ("shape_order", C.c_int),
-                ("pusher", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double)]
+                ("pusher", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double),
+                ("field_solver", C.c_int)]
 
 
 class Species(C.Structure):
@@ -102,8 +103,11 @@ def _ptr3(arrs):
     return t
 
 
+IMPLICIT, EXPLICIT = 0, 1
+
+
 def make_grid(n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
-              relax_max_iter=200, relax_tol=1e-14) -> Grid:
+              relax_max_iter=200, relax_tol=1e-14, field_solver=IMPLICIT) -> Grid:
     g = Grid()
     g.n[:] = list(n)
     g.d[:] = [float(v) for v in d]
@@ -114,6 +118,7 @@ def make_grid(n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
     g.pusher = int(pusher)
     g.relax_max_iter = int(relax_max_iter)
     g.relax_tol = float(relax_tol)
+    g.field_solver = int(field_solver)
     return g
 
 
@@ -217,12 +222,14 @@ class Simulation:
     """The oracle's whole step over numpy-held state (one FP64 copy per array)."""
 
     def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
-                 relax_max_iter=200, relax_tol=1e-14, integrator=2):
-        """integrator 2: leap-frog step; 4: the four-substep 4th-order step."""
+                 relax_max_iter=200, relax_tol=1e-14, integrator=2, field_solver=IMPLICIT):
+        """integrator 2: leap-frog step; 4: the four-substep 4th-order step.
+        field_solver IMPLICIT (eq:EllipticB) or EXPLICIT (6th-order FDTD)."""
         if integrator not in (2, 4):
             raise ValueError("integrator must be 2 or 4")
         self.integrator = integrator
-        self.g = make_grid(n, d, dt, field_order, alpha, shape_order, pusher, relax_max_iter, relax_tol)
+        self.g = make_grid(n, d, dt, field_order, alpha, shape_order, pusher, relax_max_iter, relax_tol,
+                           field_solver)
         nx, ny, nz = n
         self.E = [np.zeros((nz, ny, nx)) for _ in range(3)]
         self.B = [np.zeros((nz, ny, nx)) for _ in range(3)]

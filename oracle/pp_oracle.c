@@ -54,6 +54,13 @@
  *       variables, advance in the drifts: the field update of eq:bnplus1 /
  *       eq:enplus1 runs with dt -> a_i dt and the current of that drift.
  *       Positions and proper velocities are both at t at a step boundary.
+ *   R18 The explicit 6th-order FDTD solver of the cold-beam comparison (Sec.
+ *       VIII, fig:coldbeam) is Yee's leap-frog with the same staggered
+ *       differences, B split into two half steps so that E and B stay at the
+ *       same time as in the implicit scheme:
+ *         B^{n+1/2} = B^n - dt/2 curl^+ E^n,
+ *         E^{n+1}   = E^n + dt (curl^- B^{n+1/2} - J),
+ *         B^{n+1}   = B^{n+1/2} - dt/2 curl^+ E^{n+1}.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,6 +77,7 @@ typedef struct {
     int pusher;          /* 0 Vay, 1 Boris */
     int relax_max_iter;  /* iteration cap of the relaxation */
     double relax_tol;    /* relative max-norm residual target */
+    int field_solver;    /* 0: implicit (eq:EllipticB); 1: explicit FDTD (reading R18) */
 } orc_grid;
 
 typedef struct {
@@ -490,9 +498,34 @@ void orc_current_from_drho(const orc_grid *g, double *const Drho[3], double *con
 /* eq:EllipticB with reading R3, relaxation reading R5).               */
 /* E, B are advanced in place; J is J^{n+1}.                           */
 /* ------------------------------------------------------------------ */
+/* The explicit FDTD field update (reading R18). */
+static void field_update_explicit(const orc_grid *g, double *E[3], double *B[3], double *const J[3])
+{
+    int64_t N = ncells(g);
+    double dt = g->dt;
+    double *buf = (double *)calloc((size_t)N * 4, sizeof(double));
+    double *c[3] = {buf, buf + N, buf + 2 * N}, *tmp = buf + 3 * N;
+    curl_plus(g, E, c, tmp);
+    for (int a = 0; a < 3; ++a)
+        for (int64_t q = 0; q < N; ++q) B[a][q] -= 0.5 * dt * c[a][q];
+    curl_minus(g, B, c, tmp);
+    for (int a = 0; a < 3; ++a)
+        for (int64_t q = 0; q < N; ++q) E[a][q] += dt * (c[a][q] - J[a][q]);
+    curl_plus(g, E, c, tmp);
+    for (int a = 0; a < 3; ++a)
+        for (int64_t q = 0; q < N; ++q) B[a][q] -= 0.5 * dt * c[a][q];
+    free(buf);
+}
+
 void orc_field_update(const orc_grid *g, double *E[3], double *B[3], double *const J[3],
                       int *iters_out, double *resid_out)
 {
+    if (g->field_solver == 1) {
+        field_update_explicit(g, E, B, J);
+        if (iters_out) *iters_out = 0;
+        if (resid_out) *resid_out = 0.0;
+        return;
+    }
     int64_t N = ncells(g);
     double alpha = g->alpha, beta = 1.0 - alpha, dt = g->dt;
     double kc[3];

@@ -676,3 +676,83 @@ def test_step4_vacuum_energy_is_product_of_substep_factors(orc, mode):
     sim.step(1)
     W1 = sum((v ** 2).sum() for v in sim.E + sim.B)
     assert W1 / W0 == pytest.approx(ratio, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Explicit 6th-order FDTD variant (Sec. VIII cold-beam study, reading R18)
+# --------------------------------------------------------------------------
+
+def _K(orc, order, dx, theta):
+    kc = orc.fd_coeffs(order)
+    return (2 / dx) * (kc[0] * np.sin(theta / 2) + kc[1] * np.sin(3 * theta / 2) + kc[2] * np.sin(5 * theta / 2))
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+@pytest.mark.parametrize("mode", [1, 3, 6])
+def test_explicit_fdtd_vacuum_dispersion_closed_form(orc, order, mode):
+    """A standing vacuum mode E_y ~ cos(kx) under the leap-frog obeys the
+    three-term recurrence e(n+1) + e(n-1) = 2 cos(phi) e(n) with the closed-form
+    cos(phi) = 1 - (dt K(k))^2 / 2 of the staggered difference symbol K: no
+    damping, and the discrete phase speed of the scheme."""
+    nx, dx, dt = 16, 0.5, 0.2
+    sim = orc.Simulation((nx, 2, 2), (dx, dx, dx), dt, field_order=order, field_solver=orc.EXPLICIT)
+    k = 2 * np.pi * mode / (nx * dx)
+    x = np.arange(nx) * dx
+    E = [np.zeros((2, 2, nx)) for _ in range(3)]
+    B = [np.zeros((2, 2, nx)) for _ in range(3)]
+    E[1][...] = np.cos(k * x)
+    sim.load_fields(E, B)
+    basis = np.broadcast_to(np.cos(k * x), (2, 2, nx))
+    e = []
+    for _ in range(40):
+        e.append((sim.E[1] * basis).sum() / (basis * basis).sum())
+        sim.step(1)
+    e = np.array(e)
+    cphi = 1.0 - (dt * _K(orc, order, dx, k * dx)) ** 2 / 2.0
+    assert abs(cphi) < 1.0
+    assert np.abs(e[2:] + e[:-2] - 2 * cphi * e[1:-1]).max() < 1e-12 * np.abs(e).max()
+    assert np.abs(e).max() <= 1.0 + 1e-12 and np.abs(e).max() > 0.5
+
+
+def test_explicit_fdtd_stability_limit(orc):
+    """The leap-frog is stable for dt sqrt(sum_a Kmax_a^2) < 2 and blows up
+    just above: random fields (white-noise content reaches the Nyquist mode)
+    stay bounded 1% below the limit and grow by orders 1% above it."""
+    n, d = (8, 8, 8), (0.5, 0.4, 0.45)
+    theta = np.linspace(0, np.pi, 4001)
+    kmax2 = sum(np.max(_K(orc, 6, h, theta) ** 2) for h in d)
+    dt_c = 2.0 / np.sqrt(kmax2)
+    import pp_synth
+    E, B = pp_synth.random_fields(n, 5, 1.0)
+    W = {}
+    for f in (0.99, 1.01):
+        sim = orc.Simulation(n, d, f * dt_c, field_order=6, field_solver=orc.EXPLICIT)
+        sim.load_fields(E, B)
+        W0 = sum((v ** 2).sum() for v in sim.E + sim.B)
+        sim.step(150)
+        W[f] = sum((v ** 2).sum() for v in sim.E + sim.B) / W0
+    assert W[0.99] < 3.0, W
+    assert W[1.01] > 1e6, W
+
+
+@pytest.mark.parametrize("shape", [2, 3])
+def test_explicit_fdtd_keeps_gauss_and_divB_with_particles(orc, shape):
+    """With the charge-conserving current the explicit update keeps div^- E - rho
+    and div^+ B at their initial values (curl and divergence commute on the
+    staggered mesh), like the implicit one."""
+    import pp_synth
+    L = pp_synth.thermal(n=(8, 6, 5), ppc=2, u_th=0.3, dx=0.5, dt=0.1, seed=7)
+    sim = orc.Simulation(L.n, L.d, L.dt, field_order=6, shape_order=shape, field_solver=orc.EXPLICIT)
+    for s in L.species:
+        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    E, B = _solenoidal_fields(orc, L, 4)
+    sim.load_fields(E, B)
+    g0 = orc.div_minus(sim.g, sim.E) - sim.rho()
+    b0 = orc.div_plus(sim.g, sim.B)
+    moved = 0.0
+    for _ in range(6):
+        sim.step(1)
+        moved = max(moved, np.abs(orc.div_minus(sim.g, sim.E) - g0).max())
+        assert np.abs(orc.div_minus(sim.g, sim.E) - sim.rho() - g0).max() < 1e-12 * max(1.0, np.abs(g0).max())
+        assert np.abs(orc.div_plus(sim.g, sim.B) - b0).max() < 1e-12
+    assert moved > 1e-4     # the charge did move
