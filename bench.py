@@ -35,14 +35,16 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # DRAM traffic of the fused particle kernel per particle, from the committed ncu
 # capture of the 64^3 x 32 ppc thermal workload kept under profiles/ (traffic
 # grows with the particle count).  Valid only for the kernel sources it was
-# taken on: the device header, the sort (its key sets the particle order the
-# kernel streams) and the part of pp_particles.cu that holds the particle
-# kernels (up to its charge-density section).
+# taken on: the device part of the header (up to its host-side context), the
+# sort (its key sets the particle order the kernel streams) and the part of
+# pp_particles.cu that holds the particle kernels (up to its charge-density
+# section).
 PROFILED_BYTES_PER_PARTICLE = 901.399552e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
+_HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
 PROFILED_SOURCES = {
     "paper_1211_4575_gb300/csrc/pp_particles.cu": "9f54073428da81ba06fff7c2bab70dfcfc5c9ab2996f1791b674a996a7eba308",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "22e55bbcd96d3a08dbc32137c21494075357308a26bb05c4d1b03b8fe4748a57",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "c56159587544efc868ec20265dbea5f40615495920ea98b8caa55e574bfc65d6",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "504fa77f0cf5c710b397512493380b8b75448c917235096f104992b782818ec3",
 }
 
@@ -55,6 +57,8 @@ def profiled_traffic(particles_per_launch):
             text = f.read()
         if rel.endswith("pp_particles.cu"):
             text = text[: text.index(_KERNEL_END)]
+        elif rel.endswith("pp_internal.cuh"):
+            text = text[: text.index(_HOST_START)]
         if hashlib.sha256(text.encode()).hexdigest() != digest:
             return None
     return PROFILED_BYTES_PER_PARTICLE * particles_per_launch
@@ -70,6 +74,9 @@ def args():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--ppc", type=int, default=32, help="macro-particles per cell per species")
     ap.add_argument("--deposit", choices=["auto", "global", "tiled"], default="auto")
+    ap.add_argument("--field-solver", choices=["implicit", "explicit"], default="implicit",
+                    help="implicit (eq:EllipticB) or the explicit FDTD leap-frog; explicit runs at dt=0.04, "
+                         "under its stability limit 0.0466 at dx=0.1")
     ap.add_argument("--integrator", type=int, choices=[2, 4], default=2,
                     help="2: leap-frog step; 4: four-substep 4th-order symplectic step")
     ap.add_argument("--radiation", type=float, default=0.0,
@@ -90,18 +97,24 @@ def args():
 def workload_load(a, seed_offset=0):
     import pp_synth
     n = (a.n, a.n, a.n)
+    dt = workload_dt(a)
     if a.workload == "thermal":
-        return pp_synth.thermal(n=n, ppc=a.ppc, seed=1212 + seed_offset)
-    return pp_synth.weibel(n=n, ppc=a.ppc, seed=1213 + seed_offset)
+        return pp_synth.thermal(n=n, ppc=a.ppc, seed=1212 + seed_offset, dt=dt)
+    return pp_synth.weibel(n=n, ppc=a.ppc, seed=1213 + seed_offset, dt=dt)
+
+
+def workload_dt(a):
+    return 0.04 if a.field_solver == "explicit" else 0.05
 
 
 def workload_name(a, nparticles):
     kind = "thermal pair plasma u_th=0.1c (numerical heating)" if a.workload == "thermal" else \
         "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
-    return (f"{kind}, {a.n}^3 cells, dx=0.1, dt=0.05, {a.ppc} per cell per species ({nparticles} particles), "
+    return (f"{kind}, {a.n}^3 cells, dx=0.1, dt={workload_dt(a):g}, {a.ppc} per cell per species ({nparticles} particles), "
             f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset"
             + (f", radiative cooling K={a.radiation:g}" if a.radiation else "")
-            + (", 4th-order symplectic step (4 kick-drift substeps)" if a.integrator == 4 else ""))
+            + (", 4th-order symplectic step (4 kick-drift substeps)" if a.integrator == 4 else "")
+            + (", explicit FDTD field solver" if a.field_solver == "explicit" else ""))
 
 
 def measured_peak():
@@ -179,11 +192,12 @@ def oracle_rate(a, steps, warmup=0):
     import oracle
     import pp_synth
     n = (a.sample_n,) * 3
-    L = (pp_synth.thermal(n=n, ppc=a.ppc, seed=1212) if a.workload == "thermal"
-         else pp_synth.weibel(n=n, ppc=a.ppc, seed=1213))
+    L = (pp_synth.thermal(n=n, ppc=a.ppc, seed=1212, dt=workload_dt(a)) if a.workload == "thermal"
+         else pp_synth.weibel(n=n, ppc=a.ppc, seed=1213, dt=workload_dt(a)))
     oracle.build()
     sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
-                            relax_max_iter=200, integrator=a.integrator)
+                            relax_max_iter=200, integrator=a.integrator,
+                            field_solver=oracle.EXPLICIT if a.field_solver == "explicit" else oracle.IMPLICIT)
     for s in L.species:
         sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], rad=a.radiation)
     if warmup:
@@ -241,6 +255,7 @@ def run_gpu(a):
                           precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=100, relax_tol=1e-6,
                           deposit_mode=mode, stream=stream.cuda_stream)
         s.set_integrator(a.integrator)
+        s.set_field_solver(pp.PP_FIELD_EXPLICIT if a.field_solver == "explicit" else pp.PP_FIELD_IMPLICIT)
         return s
 
     sim = make()

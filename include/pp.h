@@ -67,6 +67,9 @@ extern "C" {
 #define PP_DEPOSIT_GLOBAL 1  /* one thread per particle, L2 atomics                */
 #define PP_DEPOSIT_TILED 2   /* cell tiles staged in shared memory (PP_MIXED32)     */
 
+#define PP_FIELD_IMPLICIT 0  /* de-centred implicit update, eq:EllipticB (default)    */
+#define PP_FIELD_EXPLICIT 1  /* explicit FDTD leap-frog (cold-beam comparison)         */
+
 #define PP_MAX_SPECIES 8
 
 typedef struct pp_ctx pp_ctx;
@@ -194,6 +197,22 @@ int pp_set_graphs(pp_ctx *ctx, int enable);
  * pp_init_grid (either pointer may be NULL). */
 int pp_get_graph_stats(pp_ctx *ctx, int64_t *captures, int64_t *replays);
 
+/* Field solver of pp_step / pp_field_update.  PP_FIELD_IMPLICIT (default)
+ * is the de-centred implicit update of eq:bnplus1 / eq:enplus1 relaxed
+ * through eq:EllipticB.  PP_FIELD_EXPLICIT is the explicit FDTD solver the
+ * paper compares against in its cold-beam test (Sec. VIII, fig:coldbeam):
+ * Yee's leap-frog with the same staggered differences of field_order, B in
+ * two half steps so that E and B stay at the same time level,
+ *   B^{n+1/2} = B^n - dt/2 curl^+ E^n,
+ *   E^{n+1} = E^n + dt (curl^- B^{n+1/2} - J),
+ *   B^{n+1} = B^{n+1/2} - dt/2 curl^+ E^{n+1}.
+ * It has no damping (alpha plays no part) and is stable only for
+ * dt sqrt(sum_a Kmax_a^2) < 2, Kmax_a the largest symbol of the staggered
+ * difference along axis a.  Errors: PP_EINVAL for another solver, or for
+ * PP_FIELD_EXPLICIT when dt breaks that limit (the message gives the
+ * largest stable dt).  Takes effect at the next field update. */
+int pp_set_field_solver(pp_ctx *ctx, int solver);
+
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
@@ -275,7 +294,7 @@ int pp_profile_enable(pp_ctx *ctx, int enable);
 /* Totals since the last pp_profile_enable(ctx, 1) (synchronises). */
 int pp_profile_read(pp_ctx *ctx, pp_profile *out);
 
-/* Checkpoint: write the descriptor, integrator order, species parameters
+/* Checkpoint: write the descriptor, integrator order, field solver, species parameters
  * (with the cooling coefficient), step counter, FP64 fields and FP64 particle
  * arrays to a file
  * (Sec. IX, each attribute as one 64-bit block so that a restart does not

@@ -25,6 +25,7 @@ PP_OK, PP_EINVAL, PP_ENOMEM, PP_EBUSY, PP_ECUDA, PP_ETIMEOUT, PP_ENOCONV, PP_ECF
 PP_VAY, PP_BORIS = 0, 1
 PP_FP64, PP_MIXED32 = 0, 1
 PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
+PP_FIELD_IMPLICIT, PP_FIELD_EXPLICIT = 0, 1
 PP_MAX_SPECIES = 8
 PP_BATCH_FREE, PP_BATCH_RUNNING, PP_BATCH_DONE, PP_BATCH_FAILED = 0, 1, 2, 3
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
@@ -72,6 +73,7 @@ SIGNATURES = {
     "pp_init_species": (C.c_int, [_P, C.POINTER(SpeciesDesc), C.POINTER(C.c_int)]),
     "pp_set_radiative_cooling": (C.c_int, [_P, C.c_int, C.c_double]),
     "pp_set_integrator": (C.c_int, [_P, C.c_int]),
+    "pp_set_field_solver": (C.c_int, [_P, C.c_int]),
     "pp_set_graphs": (C.c_int, [_P, C.c_int]),
     "pp_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pp_load_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int]),
@@ -230,6 +232,10 @@ class Simulation:
         cap, rep = C.c_int64(0), C.c_int64(0)
         self._c(lib().pp_get_graph_stats(self._ctx, C.byref(cap), C.byref(rep)))
         return cap.value, rep.value
+
+    def set_field_solver(self, solver):
+        """PP_FIELD_IMPLICIT (eq:EllipticB, default) or PP_FIELD_EXPLICIT (FDTD leap-frog)."""
+        self._c(lib().pp_set_field_solver(self._ctx, int(solver)))
 
     def set_radiative_cooling(self, sid, coef):
         """Radiative cooling coefficient mu0 q^2 / (6 pi m c) of species sid (0 = off)."""

@@ -717,6 +717,31 @@ extern "C" int pp_step(pp_ctx *p, int nsteps) {
     return PP_OK;
 }
 
+extern "C" int pp_set_field_solver(pp_ctx *p, int solver) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (solver != PP_FIELD_IMPLICIT && solver != PP_FIELD_EXPLICIT) return fail(c, PP_EINVAL, "unknown field solver");
+    if (solver == PP_FIELD_EXPLICIT) {
+        // leap-frog stability: dt^2 sum_a Kmax_a^2 < 4
+        double h[3] = {c->d.dx, c->d.dy, c->d.dz}, sum = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double best = 0.0;
+            for (int s = 0; s <= 4000; ++s) {
+                double th = M_PI * s / 4000.0;
+                double K = 2.0 * (c->fd[0] * sin(0.5 * th) + c->fd[1] * sin(1.5 * th) + c->fd[2] * sin(2.5 * th));
+                best = fmax(best, K * K);
+            }
+            sum += best / (h[a] * h[a]);
+        }
+        double dt_max = 2.0 / sqrt(sum);
+        if (!(c->d.dt < dt_max))
+            return fail(c, PP_EINVAL, "the explicit solver needs dt < %.6g on this grid", dt_max);
+    }
+    c->field_solver = solver;
+    graphs_clear(c);
+    return PP_OK;
+}
+
 extern "C" int pp_set_graphs(pp_ctx *p, int enable) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
@@ -903,8 +928,9 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // Checkpoint / restart (FP64 blocks, independent of the precision form)
 // ---------------------------------------------------------------------------
 // Format 2 adds each species' radiative-cooling coefficient, format 3 the
-// integrator order; older files restore with cooling off and order 2.
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '3'};
+// integrator order, format 4 the field solver; older files restore with
+// cooling off, order 2 and the implicit solver.
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '4'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
@@ -921,7 +947,7 @@ extern "C" int pp_save(pp_ctx *p, const char *path) {
     bool ok = rc == PP_OK;
     ok = ok && fwrite(kMagic, 1, 8, f) == 8 && fwrite(&d, sizeof d, 1, f) == 1;
     ok = ok && fwrite(&c->step, sizeof c->step, 1, f) == 1 && fwrite(&c->nspecies, sizeof(int), 1, f) == 1 &&
-         fwrite(&c->order, sizeof(int), 1, f) == 1;
+         fwrite(&c->order, sizeof(int), 1, f) == 1 && fwrite(&c->field_solver, sizeof(int), 1, f) == 1;
     ok = ok && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
     for (int s = 0; s < c->nspecies && ok; ++s) {
         Species &S = c->sp[s];
@@ -950,11 +976,12 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     pp_grid_desc d;
     int64_t step = 0;
     int ns = 0;
-    int order = 2;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '3' &&
+    int order = 2, solver = PP_FIELD_IMPLICIT;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '4' &&
               fread(&d, sizeof d, 1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
-              ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1);
+              ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1) &&
+              (magic[7] < '4' || fread(&solver, sizeof solver, 1, f) == 1);
     if (!ok) { fclose(f); return fail(c, PP_EINVAL, "%s is not a checkpoint of this library", path); }
     d.stream = stream;
     pp_ctx *p = nullptr;
@@ -962,6 +989,7 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     if (rc != PP_OK && rc != PP_WSTAB) { fclose(f); return rc; }
     c = p;
     rc = pp_set_integrator(p, order);
+    if (rc == PP_OK) rc = pp_set_field_solver(p, solver);
     int64_t N = c->g.cells();
     std::vector<double> buf((size_t)N * 6);
     ok = rc == PP_OK && fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();

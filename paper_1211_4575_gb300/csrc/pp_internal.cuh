@@ -464,6 +464,7 @@ struct Ctx {
     // 4th-order step.
     int order = 2;
     double kick_dt = 0, drift_dt = 0;
+    int field_solver = 0;    // PP_FIELD_IMPLICIT or PP_FIELD_EXPLICIT
     // step graphs
     bool use_graphs = false;
     StepGraph graphs[kGraphSlots];

@@ -358,7 +358,54 @@ static cudaError_t field_update_impl(Ctx &c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_update(Ctx &c) { return c.fp64 ? field_update_impl<double>(c) : field_update_impl<float>(c); }
+// Explicit FDTD variant (the cold-beam comparison of Sec. VIII): Yee's
+// leap-frog with the same staggered differences, B in two half steps so that
+// E and B stay at one time level:
+//   B^{n+1/2} = B^n - dt/2 curl^+ E^n,  E^{n+1} = E^n + dt (curl^- B^{n+1/2} - J),
+//   B^{n+1} = B^{n+1/2} - dt/2 curl^+ E^{n+1}.
+// The half steps are k_rhs with alpha = 0, the full step k_e_update with
+// alpha = 1.
+template <typename R>
+static cudaError_t field_update_explicit_impl(Ctx &c) {
+    const Geom &g = c.g;
+    FieldCoef k = field_coef(c);
+    unsigned blocks = (unsigned)((g.cells() + 255) / 256);
+    unsigned pblocks = (unsigned)((g.padded_size() + 255) / 256);
+    const R half = (R)(0.5 * c.drift_dt);
+    cudaError_t e;
+    for (int pass = 0; pass < 2; ++pass) {
+        // B half step into the scratch R, then B := R with its ghost layers
+        k_rhs<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.J), (R *)c.R[0], (R *)c.R[1],
+                                           (R *)c.R[2], (R)0, half, (R)0);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_ghost_fill<R><<<pblocks, 256, 0, c.st>>>(g, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], (const R *)c.R[0],
+                                                   (const R *)c.R[1], (const R *)c.R[2], (R *)c.B[0], (R *)c.B[1],
+                                                   (R *)c.B[2], 1);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (pass == 1) break;
+        // E full step with B^{n+1/2}, then E's ghost layers (B copies onto itself)
+        k_e_update<R><<<blocks, 256, 0, c.st>>>(g, k, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], v3<R>(c.B), v3<R>(c.B),
+                                                v3<R>(c.J), (R)1, (R)0, (R)c.drift_dt);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_ghost_fill<R><<<pblocks, 256, 0, c.st>>>(g, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], (const R *)c.B[0],
+                                                   (const R *)c.B[1], (const R *)c.B[2], (R *)c.B[0], (R *)c.B[1],
+                                                   (R *)c.B[2], 1);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    c.last_iters = 0;   // no relaxation
+    c.last_kk = 0.0;
+    return cudaSuccess;
+}
+
+cudaError_t launch_field_update(Ctx &c) {
+    if (c.field_solver == PP_FIELD_EXPLICIT)
+        return c.fp64 ? field_update_explicit_impl<double>(c) : field_update_explicit_impl<float>(c);
+    return c.fp64 ? field_update_impl<double>(c) : field_update_impl<float>(c);
+}
 
 template <typename R>
 static cudaError_t ghost_fill_impl(Ctx &c, void *const sE[3], void *const sB[3]) {
