@@ -43,7 +43,7 @@ class Grid(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double),
                 ("field_order", C.c_int), ("alpha", C.c_double), ("shape_order", C.c_int),
                 ("pusher", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double),
-                ("field_solver", C.c_int)]
+                ("field_solver", C.c_int), ("current_mode", C.c_int)]
 
 
 class Species(C.Structure):
@@ -87,6 +87,7 @@ def lib():
         L.orc_rho.argtypes = [C.POINTER(Grid), C.POINTER(Species), C.c_int, P]
         L.orc_div_minus.argtypes = [C.POINTER(Grid), P, P]
         L.orc_div_plus.argtypes = [C.POINTER(Grid), P, P]
+        L.orc_divergence_filter.argtypes = [C.POINTER(Grid), P, P, P, C.c_int]
         L.orc_diagnostics.argtypes = [C.POINTER(Grid), P, P, C.POINTER(Species), C.c_int, C.POINTER(Diag)]
         _lib = L
     return _lib
@@ -104,10 +105,11 @@ def _ptr3(arrs):
 
 
 IMPLICIT, EXPLICIT = 0, 1
+CHARGE_CONSERVING, DIRECT = 0, 1
 
 
 def make_grid(n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
-              relax_max_iter=200, relax_tol=1e-14, field_solver=IMPLICIT) -> Grid:
+              relax_max_iter=200, relax_tol=1e-14, field_solver=IMPLICIT, current_mode=CHARGE_CONSERVING) -> Grid:
     g = Grid()
     g.n[:] = list(n)
     g.d[:] = [float(v) for v in d]
@@ -119,6 +121,7 @@ def make_grid(n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
     g.relax_max_iter = int(relax_max_iter)
     g.relax_tol = float(relax_tol)
     g.field_solver = int(field_solver)
+    g.current_mode = int(current_mode)
     return g
 
 
@@ -222,14 +225,19 @@ class Simulation:
     """The oracle's whole step over numpy-held state (one FP64 copy per array)."""
 
     def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=2, pusher=VAY,
-                 relax_max_iter=200, relax_tol=1e-14, integrator=2, field_solver=IMPLICIT):
+                 relax_max_iter=200, relax_tol=1e-14, integrator=2, field_solver=IMPLICIT,
+                 current_mode=CHARGE_CONSERVING, filter_passes=0, filter_interval=1):
         """integrator 2: leap-frog step; 4: the four-substep 4th-order step.
-        field_solver IMPLICIT (eq:EllipticB) or EXPLICIT (6th-order FDTD)."""
+        field_solver IMPLICIT (eq:EllipticB) or EXPLICIT (6th-order FDTD).
+        current_mode CHARGE_CONSERVING (eq:jj6) or DIRECT (eq:jj2).  After every
+        filter_interval-th step, filter_passes divergence-filter passes."""
+        self.filter_passes = int(filter_passes)
+        self.filter_interval = max(1, int(filter_interval))
         if integrator not in (2, 4):
             raise ValueError("integrator must be 2 or 4")
         self.integrator = integrator
         self.g = make_grid(n, d, dt, field_order, alpha, shape_order, pusher, relax_max_iter, relax_tol,
-                           field_solver)
+                           field_solver, current_mode)
         nx, ny, nz = n
         self.E = [np.zeros((nz, ny, nx)) for _ in range(3)]
         self.B = [np.zeros((nz, ny, nx)) for _ in range(3)]
@@ -276,7 +284,13 @@ class Simulation:
             f(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), _ptr3(self.J), self._sp(),
               len(self.species), C.byref(it), C.byref(res))
             self.nstep += 1
+            if self.filter_passes and self.nstep % self.filter_interval == 0:
+                self.divergence_filter(self.filter_passes)
         self.relax_iters, self.relax_residual = it.value, res.value
+
+    def divergence_filter(self, passes: int):
+        """passes smoothing steps of E towards div E = rho and of B towards div B = 0."""
+        lib().orc_divergence_filter(C.byref(self.g), _ptr3(self.E), _ptr3(self.B), _ptr(self.rho()), int(passes))
 
     def rho(self) -> np.ndarray:
         nx, ny, nz = self.g.n

@@ -61,6 +61,18 @@
  *         B^{n+1/2} = B^n - dt/2 curl^+ E^n,
  *         E^{n+1}   = E^n + dt (curl^- B^{n+1/2} - J),
  *         B^{n+1}   = B^{n+1/2} - dt/2 curl^+ E^{n+1}.
+ *   R19 The direct current eq:jj2 (the original code's method, Sec. III after
+ *       eq:penta) sums q w v W over particles with each component on its own
+ *       staggered nodes (like E), W taken at the middle of the move,
+ *       (x^n + x^{n+1})/2, and v = u^{n+1/2}/gamma: J^{n+1/2} without the
+ *       high-order current solve, which belongs to the charge-conserving form.
+ *   R20 The divergence filter ("Gauss-Seidel filtering" of E, and the
+ *       periodic filter of E and B of long FP32 runs): each pass is one
+ *       simultaneous smoothing step E += tau grad^+(div^- E - rho),
+ *       B += tau grad^-(div^+ B), tau = 1 / max(sum_a K_a^2), the largest
+ *       eigenvalue of -div grad, which removes the Nyquist-scale error in one
+ *       pass and damps every other non-constant mode.  Gauss-Seidel ordering
+ *       is sequential; the simultaneous form damps the same error.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +90,7 @@ typedef struct {
     int relax_max_iter;  /* iteration cap of the relaxation */
     double relax_tol;    /* relative max-norm residual target */
     int field_solver;    /* 0: implicit (eq:EllipticB); 1: explicit FDTD (reading R18) */
+    int current_mode;    /* 0: charge-conserving (eq:jj6); 1: direct eq:jj2 (reading R19) */
 } orc_grid;
 
 typedef struct {
@@ -604,6 +617,36 @@ static void wrap_pos(double *x, double L)
     if (*x >= L) *x -= L;   /* x + L rounded up to L */
 }
 
+/* Direct current eq:jj2 of one particle (reading R19): adds q w v W(xm - x_c)
+ * to each component on its staggered nodes. */
+static void deposit_direct(const orc_grid *g, double qw, const double xm[3], const double v[3], double *J[3])
+{
+    int o = g->shape_order;
+    for (int a = 0; a < 3; ++a) {
+        int s[3];
+        stag_E(a, s);
+        int lo[3], hi[3];
+        for (int b = 0; b < 3; ++b) {
+            double xi = xm[b] / g->d[b];
+            lo[b] = (int)floor(xi) - 2;
+            hi[b] = (int)floor(xi) + 2;
+        }
+        for (int k = lo[2]; k <= hi[2]; ++k) {
+            double wz = orc_weight(o, ((k + 0.5 * s[2]) * g->d[2] - xm[2]) / g->d[2]);
+            if (wz == 0.0) continue;
+            for (int j = lo[1]; j <= hi[1]; ++j) {
+                double wy = orc_weight(o, ((j + 0.5 * s[1]) * g->d[1] - xm[1]) / g->d[1]);
+                if (wy == 0.0) continue;
+                for (int i = lo[0]; i <= hi[0]; ++i) {
+                    double wx = orc_weight(o, ((i + 0.5 * s[0]) * g->d[0] - xm[0]) / g->d[0]);
+                    if (wx == 0.0) continue;
+                    J[a][idx3(g, i, j, k)] += qw * v[a] * wx * wy * wz;
+                }
+            }
+        }
+    }
+}
+
 /* Gather, kick by kick_dt (push and cooling; none when kick_dt = 0), drift by
  * g->dt, deposit.  The plain leap-frog step has kick_dt = g->dt. */
 void orc_particles_kick_drift(const orc_grid *g, double kick_dt, double *E[3], double *B[3], orc_species *sp,
@@ -617,6 +660,8 @@ void orc_particles_kick_drift(const orc_grid *g, double kick_dt, double *E[3], d
         lsum[a] = (double *)calloc((size_t)g->n[b] * g->n[c], sizeof(double));
     }
     double L[3] = {g->n[0] * g->d[0], g->n[1] * g->d[1], g->n[2] * g->d[2]};
+    if (g->current_mode == 1)
+        for (int a = 0; a < 3; ++a) memset(J[a], 0, sizeof(double) * (size_t)N);
     for (int s = 0; s < nsp; ++s) {
         orc_species *P = &sp[s];
         double qmdt = P->q * kick_dt / P->m;
@@ -634,7 +679,16 @@ void orc_particles_kick_drift(const orc_grid *g, double kick_dt, double *E[3], d
             double gam = sqrt(1.0 + dot3(u, u));
             double x1[3];
             for (int a = 0; a < 3; ++a) x1[a] = x0[a] + g->dt * u[a] / gam;
-            orc_deposit_particle(g, P->q, P->w, x0, x1, Drho, lsum);
+            if (g->current_mode == 1) {
+                double xm[3], v[3];
+                for (int a = 0; a < 3; ++a) {
+                    xm[a] = 0.5 * (x0[a] + x1[a]);
+                    v[a] = u[a] / gam;
+                }
+                deposit_direct(g, P->q * P->w, xm, v, J);
+            } else {
+                orc_deposit_particle(g, P->q, P->w, x0, x1, Drho, lsum);
+            }
             wrap_pos(&x1[0], L[0]);
             wrap_pos(&x1[1], L[1]);
             wrap_pos(&x1[2], L[2]);
@@ -642,7 +696,7 @@ void orc_particles_kick_drift(const orc_grid *g, double kick_dt, double *E[3], d
             P->ux[p] = u[0]; P->uy[p] = u[1]; P->uz[p] = u[2];
         }
     }
-    orc_current_from_drho(g, Drho, lsum, J);
+    if (g->current_mode != 1) orc_current_from_drho(g, Drho, lsum, J);
     for (int a = 0; a < 3; ++a) { free(Drho[a]); free(lsum[a]); }
 }
 
@@ -741,6 +795,42 @@ void orc_div_plus(const orc_grid *g, double *const F[3], double *out)
         for (int64_t q = 0; q < N; ++q) out[q] += t[q];
     }
     free(t);
+}
+
+/* Divergence filter (reading R20): `passes` simultaneous smoothing steps of E
+ * towards div^- E = rho and of B towards div^+ B = 0. */
+void orc_divergence_filter(const orc_grid *g, double *E[3], double *B[3], const double *rho, int passes)
+{
+    int64_t N = ncells(g);
+    double kc[3];
+    orc_fd_coeffs(g->field_order, kc);
+    double lam = 0.0;   /* max over wave numbers of sum_a K_a^2 */
+    for (int a = 0; a < 3; ++a) {
+        double best = 0.0;
+        for (int s = 0; s <= 4000; ++s) {
+            double th = 3.14159265358979323846 * s / 4000.0;
+            double K = (2.0 / g->d[a]) * (kc[0] * sin(0.5 * th) + kc[1] * sin(1.5 * th) + kc[2] * sin(2.5 * th));
+            if (K * K > best) best = K * K;
+        }
+        lam += best;
+    }
+    double tau = 1.0 / lam;
+    double *r = (double *)malloc(sizeof(double) * (size_t)N), *d = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int p = 0; p < passes; ++p) {
+        orc_div_minus(g, E, r);
+        for (int64_t q = 0; q < N; ++q) r[q] -= rho[q];
+        for (int a = 0; a < 3; ++a) {
+            orc_diff(g, g->field_order, a, +1, r, d);
+            for (int64_t q = 0; q < N; ++q) E[a][q] += tau * d[q];
+        }
+        orc_div_plus(g, B, r);
+        for (int a = 0; a < 3; ++a) {
+            orc_diff(g, g->field_order, a, -1, r, d);
+            for (int64_t q = 0; q < N; ++q) B[a][q] += tau * d[q];
+        }
+    }
+    free(r);
+    free(d);
 }
 
 /* Global diagnostics (energies, total charge, Gauss and div B residuals). */

@@ -756,3 +756,107 @@ def test_explicit_fdtd_keeps_gauss_and_divB_with_particles(orc, shape):
         assert np.abs(orc.div_minus(sim.g, sim.E) - sim.rho() - g0).max() < 1e-12 * max(1.0, np.abs(g0).max())
         assert np.abs(orc.div_plus(sim.g, sim.B) - b0).max() < 1e-12
     assert moved > 1e-4     # the charge did move
+
+
+# --------------------------------------------------------------------------
+# Direct current eq:jj2 (reading R19) and the divergence filter (reading R20)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_direct_current_moments(orc, shape):
+    """With J = sum q w v W(x_mid - x_c) on the staggered nodes, the total of
+    each component is sum q w v_a (partition of unity) and its first moment
+    along every axis is sum q w v_a x_mid (B-splines of order >= 1 reproduce
+    linear functions).  Particles stay clear of the periodic seam."""
+    n, d, dt = (12, 10, 11), (0.5, 0.4, 0.45), 0.2
+    rng = np.random.default_rng(shape)
+    m = 400
+    x0 = [rng.uniform(3.5, n[a] - 3.5, m) * d[a] for a in range(3)]
+    u = [rng.normal(0, 0.4, m) for _ in range(3)]
+    sim = orc.Simulation(n, d, dt, shape_order=shape, current_mode=orc.DIRECT)
+    sim.add_species(-1.0, 1.0, 0.3, x0[0], x0[1], x0[2], u[0], u[1], u[2])
+    sim.deposit()   # E = B = 0: the momenta do not change
+    g = np.sqrt(1 + u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+    v = [u[a] / g for a in range(3)]
+    xm = [x0[a] + 0.5 * dt * v[a] for a in range(3)]
+    qw = -0.3
+    nz, ny, nx = n[2], n[1], n[0]
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for a in range(3):
+        J = sim.J[a]
+        assert J.sum() == pytest.approx(qw * v[a].sum(), rel=1e-12)
+        for b, idx in enumerate((i, j, k)):
+            xn = (idx + (0.5 if b == a else 0.0)) * d[b]     # J_a sits half a cell up along a
+            assert (J * xn).sum() == pytest.approx((qw * v[a] * xm[b]).sum(), rel=1e-11, abs=1e-12)
+
+
+def test_direct_current_breaks_gauss_law_charge_conserving_keeps_it(orc):
+    """The reason the paper replaced eq:jj2: with it div^- E - rho drifts from
+    its initial value; with the charge-conserving current it stays put."""
+    import pp_synth
+    L = pp_synth.thermal(n=(8, 6, 5), ppc=2, u_th=0.3, dx=0.5, dt=0.25, seed=7)
+    drift = {}
+    for mode in (orc.CHARGE_CONSERVING, orc.DIRECT):
+        sim = orc.Simulation(L.n, L.d, L.dt, shape_order=2, current_mode=mode)
+        for s in L.species:
+            sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+        g0 = orc.div_minus(sim.g, sim.E) - sim.rho()
+        sim.step(3)
+        drift[mode] = np.abs(orc.div_minus(sim.g, sim.E) - sim.rho() - g0).max() / np.abs(sim.rho()).max()
+    assert drift[orc.CHARGE_CONSERVING] < 1e-12
+    assert drift[orc.DIRECT] > 1e-4
+
+
+def test_divergence_filter_removes_nyquist_error_in_one_pass(orc):
+    """tau = 1/max(sum K^2): the checkerboard error is the eigenmode of the
+    largest eigenvalue of -div grad, so one pass removes it from E and B."""
+    n, d = (8, 8, 8), (0.5, 0.4, 0.45)
+    sim = orc.Simulation(n, d, 0.1, field_order=6)
+    k, j, i = np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij")
+    cb = (-1.0) ** (i + j + k)
+    # E with div^- E = checkerboard and rho = 0; B with div^+ B = checkerboard
+    g = sim.g
+    E = [np.zeros((8, 8, 8)) for _ in range(3)]
+    E[0] = cb.copy()
+    B = [np.zeros((8, 8, 8)) for _ in range(3)]
+    B[2] = cb.copy()
+    sim.load_fields(E, B)
+    e0 = np.abs(orc.div_minus(g, sim.E)).max()
+    b0 = np.abs(orc.div_plus(g, sim.B)).max()
+    sim.divergence_filter(1)
+    assert e0 > 1.0 and b0 > 1.0
+    assert np.abs(orc.div_minus(g, sim.E)).max() < 1e-12 * e0
+    assert np.abs(orc.div_plus(g, sim.B)).max() < 1e-12 * b0
+
+
+def test_divergence_filter_converges_by_gradients_only(orc):
+    """Many passes drive div^- E - rho to its (unremovable) mean and div^+ B to
+    zero, and change E and B by discrete gradients only: the curls of the
+    changes vanish, so the filter leaves the induction equations alone."""
+    import pp_synth
+    n, d = (6, 6, 6), (0.5, 0.5, 0.5)
+    L = pp_synth.thermal(n=n, ppc=2, u_th=0.3, dx=0.5, dt=0.1, seed=3)
+    sim = orc.Simulation(n, d, 0.1, field_order=6)
+    sim.add_species(L.species[0]["q"], 1.0, L.species[0]["w"], *(L.species[0][k] for k in ("x", "y", "z", "ux", "uy", "uz")))
+    E, B = pp_synth.random_fields(n, 2, 1.0)
+    sim.load_fields(E, B)
+    E0 = [v.copy() for v in sim.E]
+    B0 = [v.copy() for v in sim.B]
+    g = sim.g
+    rho = sim.rho()
+    e_start = orc.div_minus(g, sim.E) - rho
+    sim.divergence_filter(600)
+    e = orc.div_minus(g, sim.E) - rho
+    assert np.abs(e - e.mean()).max() < 1e-10 * np.abs(e_start).max()
+    assert e.mean() == pytest.approx(e_start.mean(), abs=1e-12)
+    assert np.abs(orc.div_plus(g, sim.B)).max() < 1e-10 * np.abs(orc.div_plus(g, B0)).max()
+    def curl(F, sign):
+        out = []
+        for a in range(3):
+            b, c = (a + 1) % 3, (a + 2) % 3
+            out.append(orc.diff(g, F[c], b, sign) - orc.diff(g, F[b], c, sign))
+        return out
+    dE = [sim.E[a] - E0[a] for a in range(3)]
+    dB = [sim.B[a] - B0[a] for a in range(3)]
+    assert max(np.abs(c).max() for c in curl(dE, +1)) < 1e-12 * max(np.abs(x).max() for x in dE)
+    assert max(np.abs(c).max() for c in curl(dB, -1)) < 1e-12 * max(np.abs(x).max() for x in dB)
