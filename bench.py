@@ -77,6 +77,9 @@ def args():
     ap.add_argument("--field-solver", choices=["implicit", "explicit"], default="implicit",
                     help="implicit (eq:EllipticB) or the explicit FDTD leap-frog; explicit runs at dt=0.04, "
                          "under its stability limit 0.0466 at dx=0.1")
+    ap.add_argument("--current", choices=["conserving", "direct"], default="conserving",
+                    help="charge-conserving high-order current, or the direct current eq:jj2")
+    ap.add_argument("--filter", type=int, default=0, help="divergence-filter passes after every step (0 = off)")
     ap.add_argument("--integrator", type=int, choices=[2, 4], default=2,
                     help="2: leap-frog step; 4: four-substep 4th-order symplectic step")
     ap.add_argument("--radiation", type=float, default=0.0,
@@ -114,7 +117,9 @@ def workload_name(a, nparticles):
             f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset"
             + (f", radiative cooling K={a.radiation:g}" if a.radiation else "")
             + (", 4th-order symplectic step (4 kick-drift substeps)" if a.integrator == 4 else "")
-            + (", explicit FDTD field solver" if a.field_solver == "explicit" else ""))
+            + (", explicit FDTD field solver" if a.field_solver == "explicit" else "")
+            + (", direct current eq:jj2" if a.current == "direct" else "")
+            + (f", {a.filter} divergence-filter passes per step" if a.filter else ""))
 
 
 def measured_peak():
@@ -197,7 +202,9 @@ def oracle_rate(a, steps, warmup=0):
     oracle.build()
     sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
                             relax_max_iter=200, integrator=a.integrator,
-                            field_solver=oracle.EXPLICIT if a.field_solver == "explicit" else oracle.IMPLICIT)
+                            field_solver=oracle.EXPLICIT if a.field_solver == "explicit" else oracle.IMPLICIT,
+                            current_mode=oracle.DIRECT if a.current == "direct" else oracle.CHARGE_CONSERVING,
+                            filter_passes=a.filter, filter_interval=1)
     for s in L.species:
         sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], rad=a.radiation)
     if warmup:
@@ -256,6 +263,8 @@ def run_gpu(a):
                           deposit_mode=mode, stream=stream.cuda_stream)
         s.set_integrator(a.integrator)
         s.set_field_solver(pp.PP_FIELD_EXPLICIT if a.field_solver == "explicit" else pp.PP_FIELD_IMPLICIT)
+        s.set_current_deposit(pp.PP_CURRENT_DIRECT if a.current == "direct" else pp.PP_CURRENT_CONSERVING)
+        s.set_divergence_filter(a.filter, 1)
         return s
 
     sim = make()

@@ -69,6 +69,8 @@ extern "C" {
 
 #define PP_FIELD_IMPLICIT 0  /* de-centred implicit update, eq:EllipticB (default)    */
 #define PP_FIELD_EXPLICIT 1  /* explicit FDTD leap-frog (cold-beam comparison)         */
+#define PP_CURRENT_CONSERVING 0  /* charge-conserving high-order current (default)    */
+#define PP_CURRENT_DIRECT 1      /* direct current eq:jj2 (the original method)        */
 
 #define PP_MAX_SPECIES 8
 
@@ -122,7 +124,8 @@ typedef struct {
     double gauss_max;          /* max |div^- E - rho/eps0|                         */
     double gauss_drift_max;    /* max |G - G_0|, G_0 taken at the first load      */
     double divB_max;           /* max |div^+ B|                                    */
-    double relax_residual;     /* max|(1 - a^2 dt^2 L)B - rhs| / max|rhs|, last solve */
+    double relax_residual;     /* max|(1 - a^2 dt^2 L)B - rhs| / max|rhs|, last solve
+                                  (with the B a divergence filter left after it)    */
     int relax_iters;           /* relaxation sweeps of the last solve             */
     int status;                /* PP_* code of the device status word             */
     int64_t n_particles;       /* all species                                      */
@@ -213,6 +216,27 @@ int pp_get_graph_stats(pp_ctx *ctx, int64_t *captures, int64_t *replays);
  * largest stable dt).  Takes effect at the next field update. */
 int pp_set_field_solver(pp_ctx *ctx, int solver);
 
+/* Current deposit.  PP_CURRENT_CONSERVING (default) is the charge-conserving
+ * high-order current of Sec. III (eq:cc1 .. eq:penta).  PP_CURRENT_DIRECT is
+ * eq:jj2, the paper's original method: J = sum q w v W(x - x_c) with each
+ * component on its staggered nodes, W at the middle of the move and v the
+ * new velocity, with no high-order current solve.  It does not satisfy the
+ * discrete continuity equation; the paper pairs it with a divergence filter
+ * of E (pp_set_divergence_filter).  Errors: PP_EINVAL for another mode. */
+int pp_set_current_deposit(pp_ctx *ctx, int mode);
+
+/* Divergence filter (Sec. III after eq:penta: the filtering of E that the
+ * direct current needs, and the occasional filtering of E and B in long FP32
+ * runs).  After every interval-th step, `passes` simultaneous smoothing steps
+ *   E += tau grad^+ (div^- E - rho),   B += tau grad^- (div^+ B),
+ * tau = 1 / max(sum_a K_a^2) (the largest eigenvalue of -div grad), rho
+ * deposited from the particles' positions at that time.  A pass removes the
+ * Nyquist-scale error and damps every other non-constant mode; it changes E
+ * and B by gradients only.  The paper describes a Gauss-Seidel sweep; the
+ * simultaneous form damps the same error in parallel.  passes = 0 (the
+ * default) turns it off.  Errors: PP_EINVAL for passes < 0 or interval < 1. */
+int pp_set_divergence_filter(pp_ctx *ctx, int passes, int interval);
+
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
@@ -294,9 +318,9 @@ int pp_profile_enable(pp_ctx *ctx, int enable);
 /* Totals since the last pp_profile_enable(ctx, 1) (synchronises). */
 int pp_profile_read(pp_ctx *ctx, pp_profile *out);
 
-/* Checkpoint: write the descriptor, integrator order, field solver, species parameters
- * (with the cooling coefficient), step counter, FP64 fields and FP64 particle
- * arrays to a file
+/* Checkpoint: write the descriptor, integrator order, field solver, current
+ * deposit and divergence filter, species parameters (with the cooling
+ * coefficient), step counter, FP64 fields and FP64 particle arrays to a file
  * (Sec. IX, each attribute as one 64-bit block so that a restart does not
  * depend on the precision form). */
 int pp_save(pp_ctx *ctx, const char *path);

@@ -26,6 +26,7 @@ PP_VAY, PP_BORIS = 0, 1
 PP_FP64, PP_MIXED32 = 0, 1
 PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
 PP_FIELD_IMPLICIT, PP_FIELD_EXPLICIT = 0, 1
+PP_CURRENT_CONSERVING, PP_CURRENT_DIRECT = 0, 1
 PP_MAX_SPECIES = 8
 PP_BATCH_FREE, PP_BATCH_RUNNING, PP_BATCH_DONE, PP_BATCH_FAILED = 0, 1, 2, 3
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
@@ -74,6 +75,8 @@ SIGNATURES = {
     "pp_set_radiative_cooling": (C.c_int, [_P, C.c_int, C.c_double]),
     "pp_set_integrator": (C.c_int, [_P, C.c_int]),
     "pp_set_field_solver": (C.c_int, [_P, C.c_int]),
+    "pp_set_current_deposit": (C.c_int, [_P, C.c_int]),
+    "pp_set_divergence_filter": (C.c_int, [_P, C.c_int, C.c_int]),
     "pp_set_graphs": (C.c_int, [_P, C.c_int]),
     "pp_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pp_load_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int]),
@@ -236,6 +239,14 @@ class Simulation:
     def set_field_solver(self, solver):
         """PP_FIELD_IMPLICIT (eq:EllipticB, default) or PP_FIELD_EXPLICIT (FDTD leap-frog)."""
         self._c(lib().pp_set_field_solver(self._ctx, int(solver)))
+
+    def set_current_deposit(self, mode):
+        """PP_CURRENT_CONSERVING (default) or PP_CURRENT_DIRECT (eq:jj2)."""
+        self._c(lib().pp_set_current_deposit(self._ctx, int(mode)))
+
+    def set_divergence_filter(self, passes, interval=1):
+        """passes filter passes on E and B after every interval-th step (0 = off)."""
+        self._c(lib().pp_set_divergence_filter(self._ctx, int(passes), int(interval)))
 
     def set_radiative_cooling(self, sid, coef):
         """Radiative cooling coefficient mu0 q^2 / (6 pi m c) of species sid (0 = off)."""

@@ -151,6 +151,20 @@ static int setup_operators(Ctx *c) {
     for (int q = 0; q < 3; ++q) cheb_setup(c, dts[q], c->cheb[q]);
     c->cheb_sel = 0;
     c->kick_dt = c->drift_dt = c->d.dt;
+    // divergence filter step: 1 / max over wave numbers of sum_a K_a^2
+    {
+        double h[3] = {c->d.dx, c->d.dy, c->d.dz}, lam = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double best = 0.0;
+            for (int s = 0; s <= 4000; ++s) {
+                double th = M_PI * s / 4000.0;
+                double K = 2.0 * (c->fd[0] * sin(0.5 * th) + c->fd[1] * sin(1.5 * th) + c->fd[2] * sin(2.5 * th));
+                best = fmax(best, K * K);
+            }
+            lam += best / (h[a] * h[a]);
+        }
+        c->filter_tau = 1.0 / lam;
+    }
     c->last_kk = c->d.alpha * c->d.alpha * c->d.dt * c->d.dt;
     return PP_OK;
 }
@@ -516,7 +530,7 @@ static int particle_phase(Ctx *c, int only) {
     CU(prof_mark(c, PH_PARTICLE, false));
     CU(prof_mark(c, PH_CURRENT, true));
     CU(launch_fold_J(*c));
-    CU(launch_current_solve(*c));
+    if (c->current_mode == PP_CURRENT_CONSERVING) CU(launch_current_solve(*c));   // eq:jj2 is final
     CU(prof_mark(c, PH_CURRENT, false));
     if (c->prof) ++c->prof_steps;
     if (c->prof && c->prof_n > 4096) {
@@ -576,7 +590,7 @@ extern "C" int pp_sort(pp_ctx *p) {
 // field phases (four kick-drift substeps for the 4th-order integrator).  Only
 // enqueues work; the host state it changes is the J / J' and particle buffer
 // swaps, the sorted flags and the last solve's iteration data.
-static int step_body(Ctx *c, bool sort) {
+static int step_body(Ctx *c, bool sort, bool filter) {
     if (sort) {
         int r = pp_sort(static_cast<pp_ctx *>(c));
         if (r) return r;
@@ -598,11 +612,12 @@ static int step_body(Ctx *c, bool sort) {
         r = particle_phase(c, -1);
         if (r == PP_OK) r = field_phase(c);
     }
+    if (r == PP_OK && filter) CU(launch_divergence_filter(*c));
     return r;
 }
 
-static bool graph_matches(const Ctx *c, const StepGraph &G, bool sort) {
-    if (!G.valid || G.sort != sort || G.J0 != c->J[0]) return false;
+static bool graph_matches(const Ctx *c, const StepGraph &G, bool sort, bool filter) {
+    if (!G.valid || G.sort != sort || G.filter != filter || G.J0 != c->J[0]) return false;
     for (int s = 0; s < c->nspecies; ++s)
         if (G.buf[s] != c->sp[s].buf || G.sorted[s] != c->sp[s].sorted) return false;
     return true;
@@ -621,6 +636,7 @@ static void graph_save_after(const Ctx *c, StepGraph &G) {
     }
     G.last_iters = c->last_iters;
     G.last_kk = c->last_kk;
+    G.filtered_after_solve = c->filtered_after_solve;
 }
 
 static void graph_apply_after(Ctx *c, const StepGraph &G) {
@@ -637,16 +653,17 @@ static void graph_apply_after(Ctx *c, const StepGraph &G) {
     }
     c->last_iters = G.last_iters;
     c->last_kk = G.last_kk;
+    c->filtered_after_solve = G.filtered_after_solve;
     if (G.sort) c->since_sort = 0;
 }
 
 // One step through the graph cache: replay the capture that starts from the
 // current state, or capture it (and launch the capture).  A capture that fails
 // leaves the host state as it was and the step runs eagerly.
-static int step_graph(Ctx *c, bool sort) {
+static int step_graph(Ctx *c, bool sort, bool filter) {
     for (int q = 0; q < kGraphSlots; ++q) {
         StepGraph &G = c->graphs[q];
-        if (!graph_matches(c, G, sort)) continue;
+        if (!graph_matches(c, G, sort, filter)) continue;
         CU(cudaGraphLaunch(G.exec, c->st));
         graph_apply_after(c, G);
         c->nlaunch += G.launches;
@@ -664,6 +681,7 @@ static int step_graph(Ctx *c, bool sort) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     G = StepGraph();
     G.sort = sort;
+    G.filter = filter;
     G.J0 = c->J[0];
     for (int s = 0; s < c->nspecies; ++s) {
         G.buf[s] = c->sp[s].buf;
@@ -678,7 +696,7 @@ static int step_graph(Ctx *c, bool sort) {
     int64_t nl0 = c->nlaunch;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed);
-    int r = e == cudaSuccess ? step_body(c, sort) : PP_ECUDA;
+    int r = e == cudaSuccess ? step_body(c, sort, filter) : PP_ECUDA;
     if (e == cudaSuccess) e = cudaStreamEndCapture(c->st, &graph);
     cudaGraphExec_t exec = nullptr;
     if (r == PP_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -692,7 +710,7 @@ static int step_graph(Ctx *c, bool sort) {
         c->nlaunch = nl0;
         G = StepGraph();
         c->use_graphs = false;   // do not try again on this context
-        return step_body(c, sort);
+        return step_body(c, sort, filter);
     }
     G.exec = exec;
     G.launches = (int)(c->nlaunch - nl0);
@@ -709,7 +727,8 @@ extern "C" int pp_step(pp_ctx *p, int nsteps) {
     if (nsteps < 0) return fail(c, PP_EINVAL, "negative step count");
     for (int it = 0; it < nsteps; ++it) {
         bool sort = c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval;
-        int r = (c->use_graphs && !c->prof && c->st) ? step_graph(c, sort) : step_body(c, sort);
+        bool filter = c->filter_passes > 0 && (c->step + 1) % c->filter_interval == 0;
+        int r = (c->use_graphs && !c->prof && c->st) ? step_graph(c, sort, filter) : step_body(c, sort, filter);
         if (r) return r;
         ++c->step;
         ++c->since_sort;
@@ -738,6 +757,25 @@ extern "C" int pp_set_field_solver(pp_ctx *p, int solver) {
             return fail(c, PP_EINVAL, "the explicit solver needs dt < %.6g on this grid", dt_max);
     }
     c->field_solver = solver;
+    graphs_clear(c);
+    return PP_OK;
+}
+
+extern "C" int pp_set_current_deposit(pp_ctx *p, int mode) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (mode != PP_CURRENT_CONSERVING && mode != PP_CURRENT_DIRECT) return fail(c, PP_EINVAL, "unknown current deposit");
+    c->current_mode = mode;
+    graphs_clear(c);
+    return PP_OK;
+}
+
+extern "C" int pp_set_divergence_filter(pp_ctx *p, int passes, int interval) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (passes < 0 || interval < 1) return fail(c, PP_EINVAL, "filter needs passes >= 0 and interval >= 1");
+    c->filter_passes = passes;
+    c->filter_interval = interval;
     graphs_clear(c);
     return PP_OK;
 }
@@ -848,7 +886,10 @@ extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
         out->n_particles += c->sp[s].n;
     }
     out->n_slow = (int64_t)nslow;
-    if (c->last_iters > 0 && out->relax_residual > 10.0 * c->d.relax_tol && out->status == PP_OK)
+    // a divergence filter moves B after the solve: the residual then includes
+    // the filter's correction and is reported but not checked
+    if (c->last_iters > 0 && !c->filtered_after_solve && out->relax_residual > 10.0 * c->d.relax_tol &&
+        out->status == PP_OK)
         out->status = PP_ENOCONV;
     return PP_OK;
 }
@@ -928,9 +969,9 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // Checkpoint / restart (FP64 blocks, independent of the precision form)
 // ---------------------------------------------------------------------------
 // Format 2 adds each species' radiative-cooling coefficient, format 3 the
-// integrator order, format 4 the field solver; older files restore with
-// cooling off, order 2 and the implicit solver.
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '4'};
+// integrator order, format 4 the field solver, format 5 the current deposit
+// and the divergence filter; older files restore with the defaults.
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '5'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
@@ -947,7 +988,9 @@ extern "C" int pp_save(pp_ctx *p, const char *path) {
     bool ok = rc == PP_OK;
     ok = ok && fwrite(kMagic, 1, 8, f) == 8 && fwrite(&d, sizeof d, 1, f) == 1;
     ok = ok && fwrite(&c->step, sizeof c->step, 1, f) == 1 && fwrite(&c->nspecies, sizeof(int), 1, f) == 1 &&
-         fwrite(&c->order, sizeof(int), 1, f) == 1 && fwrite(&c->field_solver, sizeof(int), 1, f) == 1;
+         fwrite(&c->order, sizeof(int), 1, f) == 1 && fwrite(&c->field_solver, sizeof(int), 1, f) == 1 &&
+         fwrite(&c->current_mode, sizeof(int), 1, f) == 1 && fwrite(&c->filter_passes, sizeof(int), 1, f) == 1 &&
+         fwrite(&c->filter_interval, sizeof(int), 1, f) == 1;
     ok = ok && fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
     for (int s = 0; s < c->nspecies && ok; ++s) {
         Species &S = c->sp[s];
@@ -976,12 +1019,14 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     pp_grid_desc d;
     int64_t step = 0;
     int ns = 0;
-    int order = 2, solver = PP_FIELD_IMPLICIT;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '4' &&
+    int order = 2, solver = PP_FIELD_IMPLICIT, cmode = PP_CURRENT_CONSERVING, fpasses = 0, finterval = 1;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '5' &&
               fread(&d, sizeof d, 1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
               ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1) &&
-              (magic[7] < '4' || fread(&solver, sizeof solver, 1, f) == 1);
+              (magic[7] < '4' || fread(&solver, sizeof solver, 1, f) == 1) &&
+              (magic[7] < '5' || (fread(&cmode, sizeof cmode, 1, f) == 1 && fread(&fpasses, sizeof fpasses, 1, f) == 1 &&
+                                  fread(&finterval, sizeof finterval, 1, f) == 1));
     if (!ok) { fclose(f); return fail(c, PP_EINVAL, "%s is not a checkpoint of this library", path); }
     d.stream = stream;
     pp_ctx *p = nullptr;
@@ -990,6 +1035,8 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     c = p;
     rc = pp_set_integrator(p, order);
     if (rc == PP_OK) rc = pp_set_field_solver(p, solver);
+    if (rc == PP_OK) rc = pp_set_current_deposit(p, cmode);
+    if (rc == PP_OK) rc = pp_set_divergence_filter(p, fpasses, finterval);
     int64_t N = c->g.cells();
     std::vector<double> buf((size_t)N * 6);
     ok = rc == PP_OK && fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();

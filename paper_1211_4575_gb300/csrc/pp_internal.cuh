@@ -358,6 +358,39 @@ __device__ __forceinline__ bool deposit_esirkepov_inner(Acc &acc, const R (&xi0)
     return true;
 }
 
+// Direct current of one particle (eq:jj2, the paper's original method):
+// q w v W(x_mid - x_c) on each component's staggered nodes (staggered like E),
+// with x_mid = xi0 + dxi / 2 in the frame of Acc and q w v_a = -jscale_a dxi_a
+// (jscale_a = -q w dx_a / dt).  No continuity: see eq:cc1 for why the paper
+// replaced it.
+template <int O, typename R, class Acc>
+__device__ __forceinline__ void deposit_direct(Acc &acc, const R (&xi0)[3], const R (&dxi)[3], const R (&jscale)[3]) {
+    R wI[3][O + 1], wH[3][O + 1];
+    int iI[3], iH[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R xm = xi0[a] + R(0.5) * dxi[a];
+        iI[a] = support<O, R>(xm, false, wI[a]);
+        iH[a] = support<O, R>(xm, true, wH[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R vs = -jscale[a] * dxi[a];
+        const R *wx = a == 0 ? wH[0] : wI[0], *wy = a == 1 ? wH[1] : wI[1], *wz = a == 2 ? wH[2] : wI[2];
+        const int i0 = a == 0 ? iH[0] : iI[0], j0 = a == 1 ? iH[1] : iI[1], k0 = a == 2 ? iH[2] : iI[2];
+#pragma unroll
+        for (int k = 0; k <= O; ++k) {
+            R vz = vs * wz[k];
+#pragma unroll
+            for (int j = 0; j <= O; ++j) {
+                R vyz = vz * wy[j];
+#pragma unroll
+                for (int i = 0; i <= O; ++i) acc.addJ(a, i0 + i, j0 + j, k0 + k, vyz * wx[i]);
+            }
+        }
+    }
+}
+
 // Charge weights of one particle on the integer nodes (eq:rho2).
 template <int O, typename R, class Acc>
 __device__ __forceinline__ void deposit_rho(Acc &acc, const R (&xi)[3], R qw) {
@@ -417,10 +450,12 @@ struct StepGraph {
     bool sorted[PP_MAX_SPECIES] = {};
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
+    bool filter = false;
     void *J_after[3] = {}, *Jt_after[3] = {};
     void *buf_after[PP_MAX_SPECIES] = {}, *alt_after[PP_MAX_SPECIES] = {};
     int last_iters = 0;
     double last_kk = 0;
+    bool filtered_after_solve = false;
 };
 constexpr int kGraphSlots = 8;
 
@@ -465,6 +500,11 @@ struct Ctx {
     int order = 2;
     double kick_dt = 0, drift_dt = 0;
     int field_solver = 0;    // PP_FIELD_IMPLICIT or PP_FIELD_EXPLICIT
+    int current_mode = 0;    // PP_CURRENT_CONSERVING or PP_CURRENT_DIRECT
+    int filter_passes = 0;   // divergence-filter passes every filter_interval steps
+    int filter_interval = 1;
+    double filter_tau = 0;   // 1 / largest eigenvalue of -div grad
+    bool filtered_after_solve = false;   // a filter changed B after the last relaxation
     // step graphs
     bool use_graphs = false;
     StepGraph graphs[kGraphSlots];
@@ -515,6 +555,7 @@ cudaError_t launch_zero_J(Ctx &c);
 cudaError_t launch_fold_J(Ctx &c);
 cudaError_t launch_current_solve(Ctx &c);
 cudaError_t launch_field_update(Ctx &c);
+cudaError_t launch_divergence_filter(Ctx &c);
 cudaError_t launch_ghost_fill(Ctx &c, void *const src_E[3], void *const src_B[3]);
 cudaError_t launch_mesh_diag(Ctx &c, double *host_out /* 9 values */);
 

@@ -345,6 +345,7 @@ static cudaError_t field_update_impl(Ctx &c) {
     }
     c.last_iters = ch.iters;
     c.last_kk = kk;
+    c.filtered_after_solve = false;
     // eq:enplus1 with B^{n+1} = cur, B^n = B
     k_e_update<R><<<blocks, 256, 0, c.st>>>(g, k, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], v3<R>(cur), v3<R>(c.B),
                                             v3<R>(c.J), (R)al, (R)be, (R)dt);
@@ -399,6 +400,69 @@ static cudaError_t field_update_explicit_impl(Ctx &c) {
     c.last_iters = 0;   // no relaxation
     c.last_kk = 0.0;
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Divergence filter (the paper's divergence cleaning of E for the direct
+// current, and the periodic filter of E and B in long FP32 runs): each pass is
+// one simultaneous smoothing step
+//   E += tau grad^+ (div^- E - rho),   B += tau grad^- (div^+ B),
+// tau = 1 / max(sum_a K_a^2), which removes the Nyquist-scale error in one
+// pass and damps every other non-constant mode.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_div_error(Geom g, FieldCoef k, Vec3<R> F, const double *rho, int plus, R *out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    Nb<R> nb{g, {0, 0, 0}};
+    unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
+    R d = plus ? nb.dplus(F.p[0], 0, k) + nb.dplus(F.p[1], 1, k) + nb.dplus(F.p[2], 2, k)
+               : nb.dminus(F.p[0], 0, k) + nb.dminus(F.p[1], 1, k) + nb.dminus(F.p[2], 2, k);
+    out[g.at(nb.c[0], nb.c[1], nb.c[2])] = rho ? d - (R)rho[t] : d;
+}
+
+template <typename R>
+__global__ void k_grad_add(Geom g, FieldCoef k, const R *r, R *F0, R *F1, R *F2, R tau, int plus) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.cells()) return;
+    Nb<R> nb{g, {0, 0, 0}};
+    unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
+    int64_t q = g.at(nb.c[0], nb.c[1], nb.c[2]);
+    R *F[3] = {F0, F1, F2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a][q] += tau * (plus ? nb.dplus(r, a, k) : nb.dminus(r, a, k));
+}
+
+template <typename R>
+static cudaError_t divergence_filter_impl(Ctx &c) {
+    cudaError_t e = launch_rho(c);   // rho at the particles' current positions
+    if (e != cudaSuccess) return e;
+    const Geom &g = c.g;
+    FieldCoef k = field_coef(c);
+    unsigned blocks = (unsigned)((g.cells() + 255) / 256);
+    const R tau = (R)c.filter_tau;
+    // scratch: the relaxation iterates (free after a solve); the solve's
+    // right-hand side in R stays for the residual diagnostics
+    R *eE = (R *)c.Xa[0], *eB = (R *)c.Xa[1];
+    for (int p = 0; p < c.filter_passes; ++p) {
+        k_div_error<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(c.E), c.rho, 0, eE);
+        k_grad_add<R><<<blocks, 256, 0, c.st>>>(g, k, eE, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], tau, 1);
+        k_div_error<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(c.B), nullptr, 1, eB);
+        k_grad_add<R><<<blocks, 256, 0, c.st>>>(g, k, eB, (R *)c.B[0], (R *)c.B[1], (R *)c.B[2], tau, 0);
+        c.nlaunch += 4;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    unsigned pblocks = (unsigned)((g.padded_size() + 255) / 256);
+    k_ghost_fill<R><<<pblocks, 256, 0, c.st>>>(g, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], (const R *)c.B[0],
+                                               (const R *)c.B[1], (const R *)c.B[2], (R *)c.B[0], (R *)c.B[1],
+                                               (R *)c.B[2], 1);
+    ++c.nlaunch;
+    c.filtered_after_solve = true;   // B moved since the last solve: its residual no longer measures it
+    return cudaGetLastError();
+}
+
+cudaError_t launch_divergence_filter(Ctx &c) {
+    return c.fp64 ? divergence_filter_impl<double>(c) : divergence_filter_impl<float>(c);
 }
 
 cudaError_t launch_field_update(Ctx &c) {

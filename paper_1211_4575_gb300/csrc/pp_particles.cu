@@ -37,6 +37,7 @@ struct StepArgs {
     R jscale[3];
     int64_t n;
     int *status;
+    int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
 };
 
 struct Fp64Particles {
@@ -61,11 +62,12 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
         push_particle<PUSH, double>(a.qmdt, a.kdt, E, B, u);
     }
     double gi = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    double xi1[3];
+    double xi1[3], dxs[3];
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double dx = a.dtdx[d] * u[d] * gi;
+        dxs[d] = dx;
         xi1[d] = xi0[d] + dx;
         ok = ok && (fabs(dx) < 1.0);   // also false for NaN
     }
@@ -73,7 +75,8 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
         atomicOr(a.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
         return;
     }
-    deposit_esirkepov<O, double>(acc, xi0, xi1, a.jscale);
+    if (a.direct) deposit_direct<O, double>(acc, xi0, dxs, a.jscale);
+    else deposit_esirkepov<O, double>(acc, xi0, xi1, a.jscale);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double L = (double)a.g.n[d], v = xi1[d];
@@ -127,11 +130,12 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
         push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
     }
     float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    float xi1[3];
+    float xi1[3], dxs[3];
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         float dx = a.dtdx[d] * u[d] * gi;
+        dxs[d] = dx;
         xi1[d] = xi0[d] + dx;
         ok = ok && (fabsf(dx) < 1.0f);
     }
@@ -139,7 +143,8 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
         atomicOr(a.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
         return;
     }
-    deposit_esirkepov<O, float>(acc, xi0, xi1, a.jscale);
+    if (a.direct) deposit_direct<O, float>(acc, xi0, dxs, a.jscale);
+    else deposit_esirkepov<O, float>(acc, xi0, xi1, a.jscale);
     rebin(xi1[0], cx, a.g.n[0]);
     rebin(xi1[1], cy, a.g.n[1]);
     rebin(xi1[2], cz, a.g.n[2]);
@@ -167,6 +172,7 @@ static StepArgs<R> step_args(Ctx &c, int s) {
     }
     a.n = S.n;
     a.status = c.d_status;
+    a.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
     return a;
 }
 
@@ -311,6 +317,7 @@ struct TiledArgs {
     int ns;
     TiledSpecies sp[kMaxTiledSpecies];
     int *status;
+    int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
 };
 
 __device__ __forceinline__ int min_image(int d, int n) {
@@ -469,6 +476,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 float xi0[3], xi1[3];
                 int cx, cy, cz;
                 SmemAcc sacc = frame(sq, xi0, xi1, cx, cy, cz);
+                if (T.direct) {   // uniform: the direct current has one form for every particle
+                    float dxs[3] = {s_d[sq], s_d[kStage + sq], s_d[2 * kStage + sq]};
+                    deposit_direct<O, float>(sacc, xi0, dxs, jsc);
+                    finish(sq, xi1, cx, cy, cz);
+                    continue;
+                }
                 if (!deposit_esirkepov_inner<O, float>(sacc, xi0, xi1, jsc)) {
                     s_queue[atomicAdd(nqueue, 1)] = sq;
                     s_cell[sq] |= kQueued;   // re-binned when written back
@@ -556,11 +569,12 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
             push_particle<PUSH, float>(a.qmdt, a.kdt, E, B, u);
         }
         float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        float xi1[3];
+        float xi1[3], dxs[3];
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             float dx = a.dtdx[d] * u[d] * gi;
+            dxs[d] = dx;
             xi1[d] = xi0[d] + dx;
             ok = ok && (fabsf(dx) < 1.0f);
         }
@@ -568,7 +582,8 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
             atomicOr(a.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
             continue;
         }
-        deposit_esirkepov<O, float>(acc, xi0, xi1, a.jscale);
+        if (a.direct) deposit_direct<O, float>(acc, xi0, dxs, a.jscale);
+        else deposit_esirkepov<O, float>(acc, xi0, xi1, a.jscale);
         rebin(xi1[0], cx, a.g.n[0]);
         rebin(xi1[1], cy, a.g.n[1]);
         rebin(xi1[2], cz, a.g.n[2]);
@@ -625,6 +640,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
     }
     if (T.ns == 0) return cudaSuccess;
     T.status = c.d_status;
+    T.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
     static bool attr_done[2][4] = {{false}};
