@@ -39,12 +39,12 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # sort (its key sets the particle order the kernel streams) and the part of
 # pp_particles.cu that holds the particle kernels (up to its charge-density
 # section).
-PROFILED_BYTES_PER_PARTICLE = 901.399552e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 901.752320e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 _HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "9f54073428da81ba06fff7c2bab70dfcfc5c9ab2996f1791b674a996a7eba308",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "c56159587544efc868ec20265dbea5f40615495920ea98b8caa55e574bfc65d6",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "1cb64f6cf4b1b580652e88f7f64cf2caf14233b819b8d8b9b447be8e203943b5",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "e7ee42772ec328e139a4a55c235e8c666871ee42d634d2839b3bb4c6f964891d",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "504fa77f0cf5c710b397512493380b8b75448c917235096f104992b782818ec3",
 }
 
