@@ -56,6 +56,8 @@ extern "C" {
 #define PP_ECFL 7       /* a particle moved a cell or more in one step           */
 #define PP_ENAN 8       /* a non-finite particle value was met                   */
 #define PP_WSTAB 9      /* warning: alpha < 0.525 with 6th order + PCS (Sec. III) */
+#define PP_EBOUNDS 10   /* checked build (-DPP_CHECKED) only: a kernel index left its
+                           array; that access was skipped                          */
 
 /* ---- enumerations ---- */
 #define PP_VAY 0

@@ -19,9 +19,13 @@ import warnings
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libpp_gb300.so")
+# PP_GB300_CHECKED=1 selects the bounds-checked build (python -m
+# paper_1211_4575_gb300.build --checked), whose kernels report an index that
+# leaves its array as PP_EBOUNDS instead of touching memory outside it.
+LIB_PATH = os.path.join(_HERE, "lib", "libpp_gb300_checked.so" if os.environ.get("PP_GB300_CHECKED") == "1"
+                        else "libpp_gb300.so")
 
-PP_OK, PP_EINVAL, PP_ENOMEM, PP_EBUSY, PP_ECUDA, PP_ETIMEOUT, PP_ENOCONV, PP_ECFL, PP_ENAN, PP_WSTAB = range(10)
+PP_OK, PP_EINVAL, PP_ENOMEM, PP_EBUSY, PP_ECUDA, PP_ETIMEOUT, PP_ENOCONV, PP_ECFL, PP_ENAN, PP_WSTAB, PP_EBOUNDS = range(11)
 PP_VAY, PP_BORIS = 0, 1
 PP_FP64, PP_MIXED32 = 0, 1
 PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
@@ -30,7 +34,7 @@ PP_CURRENT_CONSERVING, PP_CURRENT_DIRECT = 0, 1
 PP_MAX_SPECIES = 8
 PP_BATCH_FREE, PP_BATCH_RUNNING, PP_BATCH_DONE, PP_BATCH_FAILED = 0, 1, 2, 3
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
-          9: "WSTAB"}
+          9: "WSTAB", 10: "EBOUNDS"}
 
 
 class PPError(RuntimeError):

@@ -12,7 +12,16 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pp_ctx.cuh"
+
+// NVTX range over a host scope: each phase of a step shows up by name in a
+// profiler timeline (ncu --nvtx, Nsight Systems).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 using namespace pp;
 
@@ -508,6 +517,7 @@ static cudaError_t prof_collect(Ctx *c) {
 // The step
 // ---------------------------------------------------------------------------
 static int particle_phase(Ctx *c, int only) {
+    NvtxRange nvtx("pp particle phase");
     CU(launch_zero_J(*c));
     CU(cudaMemsetAsync(c->d_nslow, 0, sizeof(unsigned long long), c->st));
     CU(prof_mark(c, PH_PARTICLE, true));
@@ -541,6 +551,7 @@ static int particle_phase(Ctx *c, int only) {
 }
 
 static int field_phase(Ctx *c) {
+    NvtxRange nvtx("pp field update");
     CU(prof_mark(c, PH_FIELD, true));
     CU(launch_field_update(*c));
     CU(prof_mark(c, PH_FIELD, false));
@@ -577,6 +588,7 @@ extern "C" int pp_profile_read(pp_ctx *p, pp_profile *out) {
 }
 
 extern "C" int pp_sort(pp_ctx *p) {
+    NvtxRange nvtx("pp sort");
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     CU(prof_mark(c, PH_SORT, true));
@@ -612,7 +624,10 @@ static int step_body(Ctx *c, bool sort, bool filter) {
         r = particle_phase(c, -1);
         if (r == PP_OK) r = field_phase(c);
     }
-    if (r == PP_OK && filter) CU(launch_divergence_filter(*c));
+    if (r == PP_OK && filter) {
+        NvtxRange nvtx("pp divergence filter");
+        CU(launch_divergence_filter(*c));
+    }
     return r;
 }
 
@@ -835,6 +850,7 @@ extern "C" int pp_set_tuning(pp_ctx *p, int sort_interval, int deposit_mode) {
 }
 
 static int status_code(int bits) {
+    if (bits & ST_BOUNDS) return PP_EBOUNDS;
     if (bits & ST_NAN) return PP_ENAN;
     if (bits & ST_CFL) return PP_ECFL;
     if (bits & ST_NOCONV) return PP_ENOCONV;

@@ -39,7 +39,16 @@ __host__ __device__ __forceinline__ int wrap(int i, int n) {
 }
 
 // Device status bits (collected into one word, mapped to PP_* on the host).
-enum : int { ST_NAN = 1, ST_CFL = 2, ST_NOCONV = 4, ST_RANGE = 8 };
+enum : int { ST_NAN = 1, ST_CFL = 2, ST_NOCONV = 4, ST_RANGE = 8, ST_BOUNDS = 16 };
+
+// Checked build (-DPP_CHECKED): the particle kernels test every mesh and
+// shared-memory index against its array; a violation sets ST_BOUNDS in the
+// status word and the access is skipped (a read returns 0), with no trap.
+#ifdef PP_CHECKED
+#define PP_IF_CHECKED(...) __VA_ARGS__
+#else
+#define PP_IF_CHECKED(...)
+#endif
 
 // ---------------------------------------------------------------------------
 // B-spline weights of order O (Sec. II, W^1..W^3) written in the fractional

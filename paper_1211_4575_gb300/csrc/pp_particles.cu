@@ -16,11 +16,22 @@ struct GlobalAcc {
     const R *B[3];
     R *J[3];
     int ox, oy, oz;
+    PP_IF_CHECKED(int *st = nullptr; mutable int bad = 0;)
+#ifdef PP_CHECKED
+    __device__ __forceinline__ bool inside(int x, int y, int z) const {
+        return x >= -g.G && x < g.n[0] + g.G && y >= -g.G && y < g.n[1] + g.G && z >= -g.G && z < g.n[2] + g.G;
+    }
+    __device__ ~GlobalAcc() {   // one report per particle
+        if (bad && st) atomicOr(st, ST_BOUNDS);
+    }
+#endif
     __device__ __forceinline__ R F(int kind, int comp, int i, int j, int k) const {
+        PP_IF_CHECKED(if (!inside(ox + i, oy + j, oz + k)) { bad = 1; return R(0); })
         const R *p = kind ? B[comp] : E[comp];
         return __ldg(p + g.at(ox + i, oy + j, oz + k));
     }
     __device__ __forceinline__ void addJ(int comp, int i, int j, int k, R v) const {
+        PP_IF_CHECKED(if (!inside(ox + i, oy + j, oz + k)) { bad = 1; return; })
         atomicAdd(J[comp] + g.at(ox + i, oy + j, oz + k), v);
     }
 };
@@ -56,6 +67,7 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
     double xi0[3] = {p.x[t], p.y[t], p.z[t]};
     double u[3] = {p.ux[t], p.uy[t], p.uz[t]};
     GlobalAcc<double> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, 0, 0, 0};
+    PP_IF_CHECKED(acc.st = a.status;)
     if (a.qmdt != 0.0) {   // no kick (a 4th-order drift-only substep, or q = 0): no force
         double E[3], B[3];
         gather_EB<O, double>(acc, xi0, E, B);
@@ -124,6 +136,7 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
     float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
     float u[3] = {p.ux[t], p.uy[t], p.uz[t]};
     GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
+    PP_IF_CHECKED(acc.st = a.status;)
     if (a.qmdt != 0.0f) {   // no kick (a 4th-order drift-only substep, or q = 0): no force
         float E[3], B[3];
         gather_EB<O, float>(acc, xi0, E, B);
@@ -285,13 +298,24 @@ struct SmemAcc {
     const float *Fw;  // 6 windows: E0 E1 E2 B0 B1 B2
     int *J;           // 3 fixed-point windows
     int base;         // window offset of the particle's cell
+    PP_IF_CHECKED(int wx = 0, wy = 0, wz = 0; int *st = nullptr; mutable int bad = 0;)   // its window coordinates
+#ifdef PP_CHECKED
+    __device__ __forceinline__ bool inside(int i, int j, int k) const {
+        return wx + i >= 0 && wx + i < kWin && wy + j >= 0 && wy + j < kWin && wz + k >= 0 && wz + k < kWin;
+    }
+    __device__ ~SmemAcc() {   // one report per particle
+        if (bad && st) atomicOr(st, ST_BOUNDS);
+    }
+#endif
     __device__ __forceinline__ int at(int i, int j, int k) const { return base + win(i, j, k); }
     __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
+        PP_IF_CHECKED(if (!inside(i, j, k)) { bad = 1; return 0.0f; })
         return Fw[(kind * 3 + comp) * kWinVol + at(i, j, k)];
     }
     // v is pre-scaled by the fixed-point unit.  Zero contributions are added
     // too: a per-site test costs more than the extra shared-memory traffic.
     __device__ __forceinline__ void addJ(int comp, int i, int j, int k, float v) const {
+        PP_IF_CHECKED(if (!inside(i, j, k)) { bad = 1; return; })
         atomicAdd(J + comp * kWinVol + at(i, j, k), __float2int_rn(v));
     }
 };
@@ -352,6 +376,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
         if (rem >= kWin * kWin) continue;   // plane padding, never read
         int i = rem % kWin, k = rem / kWin;
         const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
+#ifdef PP_CHECKED
+        if (wx + i < -g.G || wx + i >= g.n[0] + g.G || wy + j < -g.G || wy + j >= g.n[1] + g.G || wz + k < -g.G ||
+            wz + k >= g.n[2] + g.G) {
+            atomicOr(T.status, ST_BOUNDS);
+            F[idx] = 0.0f;
+            continue;
+        }
+#endif
         F[idx] = __ldg(src + g.at(wx + i, wy + j, wz + k));
     }
     for (int idx = threadIdx.x; idx < 3 * kWinVol; idx += kThreads) Jw[idx] = 0;
@@ -400,6 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 if (S.qmdt != 0.0f) {   // uniform: no kick, no force
                     float E[3], B[3];
                     SmemAcc sacc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
+                    PP_IF_CHECKED(sacc.wx = rx + kWinLo; sacc.wy = ry + kWinLo; sacc.wz = rz + kWinLo; sacc.st = T.status;)
                     gather_EB<O, float>(sacc, xi0, E, B);
                     push_particle<PUSH, float>(S.qmdt, S.kdt, E, B, u);
                 }
@@ -454,7 +487,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                     xi1[d] = xi0[d] + s_d[d * kStage + sq];
                 }
                 int rx = min_image(cx - ox, g.n[0]), ry = min_image(cy - oy, g.n[1]), rz = min_image(cz - oz, g.n[2]);
-                return SmemAcc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
+                SmemAcc acc{F, Jw, win(rx + kWinLo, ry + kWinLo, rz + kWinLo)};
+                PP_IF_CHECKED(acc.wx = rx + kWinLo; acc.wy = ry + kWinLo; acc.wz = rz + kWinLo; acc.st = T.status;)
+                return acc;
             };
             auto finish = [&](int sq, float (&xi1)[3], int cx, int cy, int cz) {
                 rebin(xi1[0], cx, g.n[0]);
@@ -563,6 +598,7 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
         float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
         float u[3] = {p.ux[t], p.uy[t], p.uz[t]};
         GlobalAcc<float> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, cx, cy, cz};
+        PP_IF_CHECKED(acc.st = a.status;)
         if (a.qmdt != 0.0f) {
             float E[3], B[3];
             gather_EB<O, float>(acc, xi0, E, B);
