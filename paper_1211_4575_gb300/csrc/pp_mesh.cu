@@ -3,9 +3,10 @@
 // implicit de-centred field update (eq:bnplus1, eq:enplus1, eq:EllipticB),
 // the periodic ghost fill of E and B, and the FP64 mesh diagnostics.
 //
-// Mesh arrays are padded (Geom::at); stencils read interior values through
-// periodic wrapping, so only E and B (read by the particle gather) need their
-// ghost layers filled.
+// Mesh arrays are padded (Geom::at).  E and B keep their periodic ghost layers
+// filled (the particle gather reads them), and so do the relaxation iterates:
+// the implicit solver's stencils read those through linear offsets (NbLin).
+// Other stencils read interior values through periodic wrapping (Nb).
 #include "pp_internal.cuh"
 
 namespace pp {
@@ -196,6 +197,66 @@ struct Vec3 {
     const R *p[3];
 };
 
+// Neighbours by linear offsets into a padded array whose periodic ghost
+// layers (width kGhost >= the stencil reach 5) hold valid images: no index
+// wrapping.  Same stencils as Nb.
+template <typename R>
+struct NbLin {
+    int64_t q;      // padded index of the cell
+    int64_t s[3];   // strides of x, y, z
+    __device__ __forceinline__ R at(const R *f, int axis, int o) const { return f[q + o * s[axis]]; }
+    __device__ __forceinline__ R dplus(const R *f, int axis, const FieldCoef &k) const {
+        R v = R(0);
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) v += (R)k.k[m - 1] * (at(f, axis, m) - at(f, axis, 1 - m));
+        return v * (R)k.ih[axis];
+    }
+    __device__ __forceinline__ R dminus(const R *f, int axis, const FieldCoef &k) const {
+        R v = R(0);
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) v += (R)k.k[m - 1] * (at(f, axis, m - 1) - at(f, axis, -m));
+        return v * (R)k.ih[axis];
+    }
+    __device__ __forceinline__ R lap(const R *f, const FieldCoef &k) const {
+        R center = f[q];
+        R v = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R sa = (R)k.lap[0] * center;
+#pragma unroll
+            for (int o = 1; o <= 5; ++o) sa += (R)k.lap[o] * (at(f, a, o) + at(f, a, -o));
+            v += sa * (R)k.ih2[a];
+        }
+        return v;
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ NbLin<R> nb_lin(const Geom &g, int i, int j, int k) {
+    return NbLin<R>{g.at(i, j, k), {1, (int64_t)g.P[0], (int64_t)g.P[0] * g.P[1]}};
+}
+
+// Store v at interior cell (i, j, k) and at every periodic image of it inside
+// the ghost layers, so that the array stays readable through NbLin.  Every
+// ghost cell is the image of exactly one interior cell.
+template <typename R>
+__device__ __forceinline__ void store_periodic(R *f, const Geom &g, int i, int j, int k, R v) {
+    int x0 = i, y0 = j, z0 = k;
+    while (x0 - g.n[0] >= -g.G) x0 -= g.n[0];
+    while (y0 - g.n[1] >= -g.G) y0 -= g.n[1];
+    while (z0 - g.n[2] >= -g.G) z0 -= g.n[2];
+    for (int z = z0; z < g.n[2] + g.G; z += g.n[2])
+        for (int y = y0; y < g.n[1] + g.G; y += g.n[1])
+            for (int x = x0; x < g.n[0] + g.G; x += g.n[0]) f[g.at(x, y, z)] = v;
+}
+
+// Launch shape of the cell kernels below: x along threads, y and z along the
+// grid (no division to recover the cell).
+constexpr int kCellThreads = 128;
+static inline dim3 cell_grid(const Geom &g) {
+    return dim3((unsigned)((g.n[0] + kCellThreads - 1) / kCellThreads), (unsigned)g.n[1], (unsigned)g.n[2]);
+}
+
 // rhs_a = B_a + alpha beta dt^2 (L B)_a - dt (curl^+ E)_a + alpha dt^2 (curl^+ J)_a
 // (eq:EllipticB; the current term's sign follows from eq:bnplus1 + eq:enplus1)
 template <typename R>
@@ -216,6 +277,45 @@ __global__ void k_rhs(Geom g, FieldCoef k, Vec3<R> E, Vec3<R> B, Vec3<R> J, R *O
     }
 }
 
+// k_rhs for B and E with valid ghost layers (the implicit solver): B and E
+// through linear offsets, J (ghosts cleared by the fold) through wrapping.
+template <typename R>
+__global__ void k_rhs_lin(Geom g, FieldCoef k, Vec3<R> E, Vec3<R> B, Vec3<R> J, R *O0, R *O1, R *O2, R ab_dt2,
+                          R dt, R a_dt2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n[0]) return;
+    int j = blockIdx.y, kz = blockIdx.z;
+    NbLin<R> nl = nb_lin<R>(g, i, j, kz);
+    Nb<R> nb{g, {i, j, kz}};
+    R *out[3] = {O0, O1, O2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        R curlE = nl.dplus(E.p[c], b, k) - nl.dplus(E.p[b], c, k);
+        R curlJ = nb.dplus(J.p[c], b, k) - nb.dplus(J.p[b], c, k);
+        out[a][nl.q] = B.p[a][nl.q] + ab_dt2 * nl.lap(B.p[a], k) - dt * curlE + a_dt2 * curlJ;
+    }
+}
+
+// k_cheb on an iterate X with valid ghost layers; writes the new iterate with
+// its ghost images (so the next sweep reads it the same way).
+template <typename R>
+__global__ void k_cheb_lin(Geom g, FieldCoef k, Vec3<R> X, Vec3<R> Xp, Vec3<R> Rh, R *O0, R *O1, R *O2, R kk, R c1,
+                           R c2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n[0]) return;
+    int j = blockIdx.y, kz = blockIdx.z;
+    NbLin<R> nl = nb_lin<R>(g, i, j, kz);
+    R *out[3] = {O0, O1, O2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R x = X.p[a][nl.q];
+        R r = Rh.p[a][nl.q] - x + kk * nl.lap(X.p[a], k);
+        R xp = Xp.p[a][nl.q];
+        store_periodic(out[a], g, i, j, kz, x + c1 * (x - xp) + c2 * r);
+    }
+}
+
 // One Chebyshev semi-iteration step for (1 - kk L) x = rhs:
 // x_new = x + c1 (x - x_prev) + c2 (rhs - x + kk L x); x_new may alias x_prev.
 template <typename R>
@@ -233,6 +333,24 @@ __global__ void k_cheb(Geom g, FieldCoef k, Vec3<R> X, Vec3<R> Xp, Vec3<R> Rh, R
         R r = Rh.p[a][q] - x + kk * nb.lap(X.p[a], k);
         R xp = Xp.p[a][q];
         out[a][q] = x + c1 * (x - xp) + c2 * r;
+    }
+}
+
+// k_e_update with Bn and Bo ghost-valid (linear offsets).
+template <typename R>
+__global__ void k_e_update_lin(Geom g, FieldCoef k, R *E0, R *E1, R *E2, Vec3<R> Bn, Vec3<R> Bo, Vec3<R> J, R alpha,
+                               R beta, R dt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n[0]) return;
+    int j = blockIdx.y, kz = blockIdx.z;
+    NbLin<R> nl = nb_lin<R>(g, i, j, kz);
+    R *E[3] = {E0, E1, E2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        R cur = alpha * (nl.dminus(Bn.p[c], b, k) - nl.dminus(Bn.p[b], c, k)) +
+                beta * (nl.dminus(Bo.p[c], b, k) - nl.dminus(Bo.p[b], c, k));
+        E[a][nl.q] = E[a][nl.q] + dt * (cur - J.p[a][nl.q]);
     }
 }
 
@@ -303,14 +421,17 @@ template <typename R>
 static cudaError_t field_update_impl(Ctx &c) {
     const Geom &g = c.g;
     FieldCoef k = field_coef(c);
-    unsigned blocks = (unsigned)((g.cells() + 255) / 256);
     // dt of this solve: the step, or the drift of a 4th-order substep
     double al = c.d.alpha, be = 1.0 - c.d.alpha, dt = c.drift_dt;
     double kk = al * al * dt * dt;
     const Ctx::Cheb &ch = c.cheb[c.cheb_sel];
     cudaError_t e;
-    k_rhs<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.J), (R *)c.R[0], (R *)c.R[1], (R *)c.R[2],
-                                       (R)(al * be * dt * dt), (R)dt, (R)(al * dt * dt));
+    // B and E arrive with valid ghost layers (every writer of them fills
+    // them), and each sweep writes its iterate with ghosts: the stencils read
+    // through linear offsets.
+    const dim3 cg = cell_grid(g);
+    k_rhs_lin<R><<<cg, kCellThreads, 0, c.st>>>(g, k, v3<R>(c.E), v3<R>(c.B), v3<R>(c.J), (R *)c.R[0], (R *)c.R[1],
+                                                (R *)c.R[2], (R)(al * be * dt * dt), (R)dt, (R)(al * dt * dt));
     ++c.nlaunch;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Chebyshev semi-iteration on the spectrum [1, lmax] of the SPD operator,
@@ -335,8 +456,8 @@ static cudaError_t field_update_impl(Ctx &c) {
         // output: a scratch buffer that is neither cur nor (when prev is B) B
         void **out = (prev == c.B || prev == cur) ? bufs[nb] : prev;
         if (out == cur) out = bufs[1 - nb];
-        k_cheb<R><<<blocks, 256, 0, c.st>>>(g, k, v3<R>(cur), v3<R>(prev), v3<R>(c.R), (R *)out[0], (R *)out[1],
-                                            (R *)out[2], (R)kk, (R)c1, (R)c2);
+        k_cheb_lin<R><<<cg, kCellThreads, 0, c.st>>>(g, k, v3<R>(cur), v3<R>(prev), v3<R>(c.R), (R *)out[0],
+                                                     (R *)out[1], (R *)out[2], (R)kk, (R)c1, (R)c2);
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         prev = cur;
@@ -347,8 +468,8 @@ static cudaError_t field_update_impl(Ctx &c) {
     c.last_kk = kk;
     c.filtered_after_solve = false;
     // eq:enplus1 with B^{n+1} = cur, B^n = B
-    k_e_update<R><<<blocks, 256, 0, c.st>>>(g, k, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], v3<R>(cur), v3<R>(c.B),
-                                            v3<R>(c.J), (R)al, (R)be, (R)dt);
+    k_e_update_lin<R><<<cg, kCellThreads, 0, c.st>>>(g, k, (R *)c.E[0], (R *)c.E[1], (R *)c.E[2], v3<R>(cur),
+                                                     v3<R>(c.B), v3<R>(c.J), (R)al, (R)be, (R)dt);
     ++c.nlaunch;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     unsigned pblocks = (unsigned)((g.padded_size() + 255) / 256);
