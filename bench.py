@@ -70,9 +70,12 @@ def args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["thermal", "weibel"], default="thermal")
+    ap.add_argument("--workload", choices=["thermal", "weibel", "beam"], default="thermal",
+                    help="thermal / weibel: n^3 pair plasma; beam: cold Gamma=10 beam through an electron-ion "
+                         "background on 2n x n x n")
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
-    ap.add_argument("--ppc", type=int, default=32, help="macro-particles per cell per species")
+    ap.add_argument("--ppc", type=int, default=None,
+                    help="macro-particles per cell per species (per population for beam); default 32, beam 16")
     ap.add_argument("--deposit", choices=["auto", "global", "tiled"], default="auto")
     ap.add_argument("--field-solver", choices=["implicit", "explicit"], default="implicit",
                     help="implicit (eq:EllipticB) or the explicit FDTD leap-frog; explicit runs at dt=0.04, "
@@ -94,26 +97,55 @@ def args():
     ap.add_argument("--batch-steps", type=int, default=30, help="steps per run of the batched form")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=20.0)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.ppc is None:
+        a.ppc = 16 if a.workload == "beam" else 32
+    return a
 
 
-def workload_load(a, seed_offset=0):
-    import pp_synth
-    n = (a.n, a.n, a.n)
-    dt = workload_dt(a)
-    if a.workload == "thermal":
-        return pp_synth.thermal(n=n, ppc=a.ppc, seed=1212 + seed_offset, dt=dt)
-    return pp_synth.weibel(n=n, ppc=a.ppc, seed=1213 + seed_offset, dt=dt)
+def workload_grid(a, edge):
+    return (2 * edge, edge, edge) if a.workload == "beam" else (edge, edge, edge)
 
 
 def workload_dt(a):
+    if a.workload == "beam":   # dx = 0.5; the explicit solver's limit there is 0.233
+        return 0.2 if a.field_solver == "explicit" else 0.25
     return 0.04 if a.field_solver == "explicit" else 0.05
 
 
+def make_load(a, edge, seed_offset=0):
+    import pp_synth
+    n = workload_grid(a, edge)
+    if a.workload == "beam":
+        L = pp_synth.beam_background(n=n, ppc=a.ppc, seed=1214 + seed_offset)
+        L.dt = workload_dt(a)
+        return L
+    if a.workload == "thermal":
+        return pp_synth.thermal(n=n, ppc=a.ppc, seed=1212 + seed_offset, dt=workload_dt(a))
+    return pp_synth.weibel(n=n, ppc=a.ppc, seed=1213 + seed_offset, dt=workload_dt(a))
+
+
+def workload_load(a, seed_offset=0):
+    return make_load(a, a.n, seed_offset)
+
+
+def nominal_particles(a):
+    nx, ny, nz = workload_grid(a, a.n)
+    return nx * ny * nz * a.ppc * 2 * (2 if a.workload == "beam" else 1)
+
+
 def workload_name(a, nparticles):
-    kind = "thermal pair plasma u_th=0.1c (numerical heating)" if a.workload == "thermal" else \
-        "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
-    return (f"{kind}, {a.n}^3 cells, dx=0.1, dt={workload_dt(a):g}, {a.ppc} per cell per species ({nparticles} particles), "
+    nx, ny, nz = workload_grid(a, a.n)
+    if a.workload == "beam":
+        head = (f"cold Gamma=10 beam through an electron-ion background (m_i/m_e=25, u_th=0.01c), "
+                f"{nx}x{ny}x{nz} cells, dx=0.5, dt={workload_dt(a):g}, {a.ppc} per cell per species per population "
+                f"({nparticles} particles)")
+    else:
+        kind = "thermal pair plasma u_th=0.1c (numerical heating)" if a.workload == "thermal" else \
+            "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
+        head = (f"{kind}, {a.n}^3 cells, dx=0.1, dt={workload_dt(a):g}, {a.ppc} per cell per species "
+                f"({nparticles} particles)")
+    return (f"{head}, "
             f"PCS, 6th-order fields, alpha=0.55, Vay, sort every 20 steps, int32 cell + fp32 offset"
             + (f", radiative cooling K={a.radiation:g}" if a.radiation else "")
             + (", 4th-order symplectic step (4 kick-drift substeps)" if a.integrator == 4 else "")
@@ -196,9 +228,7 @@ def oracle_rate(a, steps, warmup=0):
     same physics and per-cell loading on a sample_n^3 periodic box."""
     import oracle
     import pp_synth
-    n = (a.sample_n,) * 3
-    L = (pp_synth.thermal(n=n, ppc=a.ppc, seed=1212, dt=workload_dt(a)) if a.workload == "thermal"
-         else pp_synth.weibel(n=n, ppc=a.ppc, seed=1213, dt=workload_dt(a)))
+    L = make_load(a, a.sample_n)
     oracle.build()
     sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
                             relax_max_iter=200, integrator=a.integrator,
@@ -212,7 +242,8 @@ def oracle_rate(a, steps, warmup=0):
     t0 = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t0
-    sample = (f"{a.sample_n}^3 cells x {a.ppc} per cell per species = {L.n_particles} particles, "
+    sample = (f"{'x'.join(str(v) for v in L.n)} cells, {a.ppc} per cell per species"
+              f"{' per population' if a.workload == 'beam' else ''} = {L.n_particles} particles, "
               f"{steps} steps, same per-cell load and parameters as the workload, single-threaded C")
     return L.n_particles * steps / dt, sample, dt
 
@@ -226,7 +257,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a, (a.n ** 3) * a.ppc * 2), "oracle_sample": sample},
+            "config": {"workload": workload_name(a, nominal_particles(a)), "oracle_sample": sample},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -345,7 +376,7 @@ def run_gpu(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(a, npart), "grid": [a.n] * 3, "particles_per_gpu": npart,
+        "config": {"workload": workload_name(a, npart), "grid": list(workload_grid(a, a.n)), "particles_per_gpu": npart,
                    "precision": "mixed (int32 cell + fp32 offset; fp32 fields and current; fp64 reductions)",
                    "deposit": a.deposit, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state 28 B x particles, read and written every step)"},
