@@ -39,11 +39,11 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # sort (its key sets the particle order the kernel streams) and the part of
 # pp_particles.cu that holds the particle kernels (up to its charge-density
 # section).
-PROFILED_BYTES_PER_PARTICLE = 902.275584e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 901.271040e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 _HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "bb3dcc893b737c0ae067d913fd363d213d86077cf6d88c55920fede3c211eece",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "cbb895123efa8f3252ff1cb8882f1e24bcc350214df43a96c7b177a64e9f3307",
     "paper_1211_4575_gb300/csrc/pp_internal.cuh": "cd803c585dfd58b2b48107b461c5b79ce07b701c6300d987b84ef6c30cf506a1",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "504fa77f0cf5c710b397512493380b8b75448c917235096f104992b782818ec3",
 }

@@ -413,7 +413,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
             int lo[3] = {1 << 20, 1 << 20, 1 << 20}, hi[3] = {-(1 << 20), -(1 << 20), -(1 << 20)};
 #pragma unroll 1
             for (int r = 0; r < kPerThread; ++r) {
-                const int q = lane_q(lane, warp + kWarps * r, S.lane_shift);
+                // consecutive particles: a warp's lanes sit in one to three cells,
+                // so the gather reads the same or neighbouring window addresses
+                const int q = 32 * (warp + kWarps * r) + lane;
                 if (q >= cn) continue;
                 const int sq = q + (q >> 5);
                 int cx, cy, cz;
