@@ -242,10 +242,12 @@ int pp_set_divergence_filter(pp_ctx *ctx, int passes, int interval);
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
- * host memory (on_device = 0) or device memory (on_device = 1).  Errors:
- * PP_ENOMEM if the count would exceed the capacity, PP_ENAN if a value is
- * not finite (nothing is appended then).  Loading resets the Gauss reference
- * G_0 of pp_diagnostics and re-sorts the species by cell. */
+ * host memory (on_device = 0) or device memory (on_device = 1); page-locked
+ * host arrays are read in place by the device, pageable ones are staged.
+ * Errors: PP_ENOMEM if the count would exceed the capacity, PP_ENAN if a
+ * value is not finite (nothing is appended then).  Loading re-sorts the
+ * species by cell and resets the Gauss reference G_0 of pp_diagnostics (taken
+ * from the loaded state before the next step or diagnostics). */
 int pp_load_particles(pp_ctx *ctx, int sid, int64_t n, const double *x, const double *y, const double *z,
                       const double *ux, const double *uy, const double *uz, int on_device);
 

@@ -362,7 +362,23 @@ static int refresh_gauss_reference(Ctx *c) {
     c->have_G0 = false;
     CU(launch_mesh_diag(*c, tmp));
     CU(cudaStreamSynchronize(c->st));
+    c->g0_pending = false;
     return PP_OK;
+}
+
+// Loads mark the Gauss reference G_0 as due; it is taken before the next call
+// that moves or reads the state, i.e. from the state the loads left (one rho
+// deposit however many species and field loads came before).
+static int ensure_gauss_reference(Ctx *c) { return c->g0_pending ? refresh_gauss_reference(c) : PP_OK; }
+
+// True when p points to page-locked host memory the device can read directly.
+static bool pinned_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
 }
 
 extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x, const double *y, const double *z,
@@ -375,33 +391,45 @@ extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x,
     if (n > 0 && (!x || !y || !z || !ux || !uy || !uz)) return fail(c, PP_EINVAL, "NULL particle array");
     if (S.n + n > S.limit) return fail(c, PP_ENOMEM, "species %d capacity %lld exceeded", sid, (long long)S.limit);
     graphs_clear(c);   // particle counts set launch sizes
-    const int64_t chunk = (int64_t)1 << 24;
-    double *stage = nullptr;
-    if (!on_device && n > 0) CU(cudaMalloc(&stage, sizeof(double) * 6 * (size_t)(n < chunk ? n : chunk)));
-    int rc = PP_OK;
+    // Device arrays and page-locked host arrays are read in place by the
+    // convert kernel (host memory over the host link); pageable host arrays
+    // go through a device staging buffer in chunks.
     const double *src[6] = {x, y, z, ux, uy, uz};
+    bool direct = on_device != 0;
+    if (!direct && n > 0) {
+        direct = true;
+        for (int k = 0; k < 6; ++k) direct = direct && pinned_host(src[k]);
+    }
+    const int64_t chunk = direct ? (n > 0 ? n : 1) : ((int64_t)1 << 24);
+    double *stage = nullptr;
+    if (!direct && n > 0) CU(cudaMalloc(&stage, sizeof(double) * 6 * (size_t)(n < chunk ? n : chunk)));
+    int rc = PP_OK;
+    cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
+    if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle load: %s", cudaGetErrorString(e));
     for (int64_t off = 0; off < n && rc == PP_OK; off += chunk) {
         int64_t m = n - off < chunk ? n - off : chunk;
         const double *a[6];
         for (int k = 0; k < 6; ++k) {
-            if (on_device) {
+            if (direct) {
                 a[k] = src[k] + off;
             } else {
                 double *dst = stage + (size_t)k * (size_t)(n < chunk ? n : chunk);
-                cudaError_t e = cudaMemcpyAsync(dst, src[k] + off, sizeof(double) * m, cudaMemcpyHostToDevice, c->st);
+                e = cudaMemcpyAsync(dst, src[k] + off, sizeof(double) * m, cudaMemcpyHostToDevice, c->st);
                 if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "particle upload: %s", cudaGetErrorString(e)); break; }
                 a[k] = dst;
             }
         }
         if (rc != PP_OK) break;
-        cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
-        if (e == cudaSuccess) e = launch_check_finite(*c, m, a, 6, c->d_status);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-        if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "particle check: %s", cudaGetErrorString(e)); break; }
-        if (*c->h_status) { rc = fail(c, PP_ENAN, "non-finite particle value in rows %lld..%lld", (long long)off, (long long)(off + m)); break; }
-        e = launch_convert_in(*c, sid, S.n + off, m, a[0], a[1], a[2], a[3], a[4], a[5]);
+        // converted past the species' count: nothing is appended unless every row is finite
+        e = launch_convert_in(*c, sid, S.n + off, m, a[0], a[1], a[2], a[3], a[4], a[5], c->d_status);
         if (e != cudaSuccess) { rc = fail(c, PP_ECUDA, "particle convert: %s", cudaGetErrorString(e)); break; }
+    }
+    if (rc == PP_OK) {
+        e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle load: %s", cudaGetErrorString(e));
+        else if (*c->h_status) rc = fail(c, PP_ENAN, "non-finite particle value: nothing appended");
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
     }
     if (stage) {
         cudaStreamSynchronize(c->st);
@@ -410,7 +438,8 @@ extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x,
     if (rc != PP_OK) return rc;
     S.n += n;
     CU(launch_sort(*c, sid));
-    return refresh_gauss_reference(c);
+    c->g0_pending = true;
+    return PP_OK;
 }
 
 template <typename R>
@@ -471,7 +500,8 @@ extern "C" int pp_load_fields(pp_ctx *p, const double *const E[3], const double 
     CU(launch_ghost_fill(*c, c->E, c->B));
     CU(cudaStreamSynchronize(c->st));
     if (stage) cudaFree(stage);
-    return refresh_gauss_reference(c);
+    c->g0_pending = true;
+    return PP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -740,6 +770,7 @@ extern "C" int pp_step(pp_ctx *p, int nsteps) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (nsteps < 0) return fail(c, PP_EINVAL, "negative step count");
+    if (int r = ensure_gauss_reference(c)) return r;
     for (int it = 0; it < nsteps; ++it) {
         bool sort = c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval;
         bool filter = c->filter_passes > 0 && (c->step + 1) % c->filter_interval == 0;
@@ -825,6 +856,7 @@ extern "C" int pp_deposit(pp_ctx *p, int sid) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (sid < -1 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    if (int r0 = ensure_gauss_reference(c)) return r0;
     int r = particle_phase(c, sid);
     if (r == PP_OK) ++c->since_sort;
     return r;
@@ -833,6 +865,7 @@ extern "C" int pp_deposit(pp_ctx *p, int sid) {
 extern "C" int pp_field_update(pp_ctx *p) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (int r = ensure_gauss_reference(c)) return r;
     return field_phase(c);
 }
 
@@ -872,6 +905,7 @@ extern "C" int pp_sync(pp_ctx *p) {
 extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
     Ctx *c = p;
     if (!c || !out) return fail(c, PP_EINVAL, "pp_diagnostics: NULL argument");
+    if (int r = ensure_gauss_reference(c)) return r;
     int st = pp_sync(p);
     memset(out, 0, sizeof(*out));
     out->status = st;

@@ -509,6 +509,7 @@ struct Ctx {
     int order = 2;
     double kick_dt = 0, drift_dt = 0;
     int field_solver = 0;    // PP_FIELD_IMPLICIT or PP_FIELD_EXPLICIT
+    bool g0_pending = false; // a load changed rho or E: take the Gauss reference before the next use
     int current_mode = 0;    // PP_CURRENT_CONSERVING or PP_CURRENT_DIRECT
     int filter_passes = 0;   // divergence-filter passes every filter_interval steps
     int filter_interval = 1;
@@ -572,9 +573,8 @@ cudaError_t launch_sort(Ctx &c, int s);
 cudaError_t sort_setup(Ctx &c);
 
 cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const double *x, const double *y,
-                              const double *z, const double *ux, const double *uy, const double *uz);
+                              const double *z, const double *ux, const double *uy, const double *uz, int *bad);
 cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, double *ux, double *uy,
                                double *uz);
-cudaError_t launch_check_finite(Ctx &c, int64_t n, const double *const *arrs, int narr, int *flag);
 
 }  // namespace pp

@@ -921,12 +921,20 @@ cudaError_t launch_kinetic(Ctx &c, double *out) {
 // ---------------------------------------------------------------------------
 // Conversions between the ABI's FP64 physical arrays and the storage forms.
 // ---------------------------------------------------------------------------
+// Reads each input once (from device memory, or from pinned host memory over
+// the host link) and flags a non-finite value in *bad instead of storing it.
 __global__ void k_convert_in(int64_t n, int64_t off, const double *x, const double *y, const double *z,
                              const double *ux, const double *uy, const double *uz, double hx, double hy,
-                             double hz, int nx, int ny, int nz, int mixed, Fp64Particles p64, MixedParticles pm) {
+                             double hz, int nx, int ny, int nz, int mixed, Fp64Particles p64, MixedParticles pm,
+                             int *bad) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     double in[3] = {x[t], y[t], z[t]};
+    const double vx = ux[t], vy = uy[t], vz = uz[t];
+    if (!isfinite(in[0]) || !isfinite(in[1]) || !isfinite(in[2]) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz)) {
+        atomicOr(bad, 1);
+        return;
+    }
     double h[3] = {hx, hy, hz};
     int N[3] = {nx, ny, nz};
     double xi[3];
@@ -949,21 +957,22 @@ __global__ void k_convert_in(int64_t n, int64_t off, const double *x, const doub
     if (mixed) {
         pm.cell[q] = pack_cell(cell[0], cell[1], cell[2]);
         pm.ox[q] = o[0]; pm.oy[q] = o[1]; pm.oz[q] = o[2];
-        pm.ux[q] = (float)ux[t]; pm.uy[q] = (float)uy[t]; pm.uz[q] = (float)uz[t];
+        pm.ux[q] = (float)vx; pm.uy[q] = (float)vy; pm.uz[q] = (float)vz;
     } else {
         p64.x[q] = xi[0]; p64.y[q] = xi[1]; p64.z[q] = xi[2];
-        p64.ux[q] = ux[t]; p64.uy[q] = uy[t]; p64.uz[q] = uz[t];
+        p64.ux[q] = vx; p64.uy[q] = vy; p64.uz[q] = vz;
     }
 }
 
 cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const double *x, const double *y,
-                              const double *z, const double *ux, const double *uy, const double *uz) {
+                              const double *z, const double *ux, const double *uy, const double *uz, int *bad) {
     if (n == 0) return cudaSuccess;
     Species &S = c.sp[s];
     Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_convert_in<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(n, off, x, y, z, ux, uy, uz, c.d.dx, c.d.dy, c.d.dz,
-                                                               c.g.n[0], c.g.n[1], c.g.n[2], c.fp64 ? 0 : 1, p64, pm);
+                                                               c.g.n[0], c.g.n[1], c.g.n[2], c.fp64 ? 0 : 1, p64, pm,
+                                                               bad);
     ++c.nlaunch;
     return cudaGetLastError();
 }
@@ -996,22 +1005,5 @@ cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, d
     return cudaGetLastError();
 }
 
-__global__ void k_check_finite(int64_t n, const double *a0, const double *a1, const double *a2, const double *a3,
-                               const double *a4, const double *a5, int *flag) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    double s = a0[t] + a1[t] + a2[t] + a3[t] + a4[t] + a5[t];
-    if (!isfinite(s) || !isfinite(a0[t]) || !isfinite(a1[t]) || !isfinite(a2[t]) || !isfinite(a3[t]) ||
-        !isfinite(a4[t]) || !isfinite(a5[t]))
-        atomicOr(flag, 1);
-}
-
-cudaError_t launch_check_finite(Ctx &c, int64_t n, const double *const *arrs, int narr, int *flag) {
-    if (n == 0 || narr != 6) return cudaSuccess;
-    k_check_finite<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(n, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4],
-                                                                 arrs[5], flag);
-    ++c.nlaunch;
-    return cudaGetLastError();
-}
 
 }  // namespace pp
