@@ -6,8 +6,11 @@ product library never imports, links or calls it, and it imports nothing from
 the product package.
 
 The arithmetic lives in ``pp_oracle.c`` (plain C, one literal loop per
-definition of the paper, cited per function).  This module only compiles that
-file with gcc and marshals numpy arrays to it with ctypes.
+definition of the paper, cited per function).  This module compiles that
+file with gcc and marshals numpy arrays to it with ctypes.  The one piece of
+method written here, in numpy, is the reflecting wall's construction by
+virtual images (WallSimulation, at the end): it adds particles and mirrors
+arrays, and every step still runs in the C code.
 
 Array conventions: fields are numpy float64 arrays of shape (nz, ny, nx)
 (x fastest in memory), with the Yee staggering of the paper's Sec. III:
@@ -306,3 +309,116 @@ class Simulation:
         out["relax_iters"] = self.relax_iters
         out["relax_residual"] = self.relax_residual
         return out
+
+
+# ---------------------------------------------------------------------------
+# Reflecting walls (Sec. II "Boundary conditions"): walls at x = 0 and
+# x = L = n_x dx, both on integer (charge-density) nodes.  The paper defines
+# the wall through virtual particles: every particle inside has a mirror
+# image outside, x -> 2 x_b - x with the normal momentum reversed, and the
+# fields obey the symmetries of the Maxwell equations across the wall.  Taken
+# literally, that is the periodic system of the particles and their images in
+# the mirror-extended box of 2 n_x cells in x (mirror planes at 0 and L;
+# periodicity 2L makes each one the image of the other).  This oracle runs
+# exactly that system: the images are real particles of the periodic oracle,
+# nothing is folded or reflected.  A physical particle is, after any step, the
+# member of its pair that lies in [0, L].
+#
+# Parities across a wall with normal x (the paper's table): quantities
+# staggered in x (E_x, J_x at i+1/2; B_y, B_z at i+1/2) are odd, quantities on
+# integer x nodes (rho, E_y, E_z, J_y, J_z, B_x) are even.
+# ---------------------------------------------------------------------------
+WALL_PARITY = {"E": ((True, -1.0), (False, 1.0), (False, 1.0)),
+               "B": ((False, 1.0), (True, -1.0), (True, -1.0)),
+               "J": ((True, -1.0), (False, 1.0), (False, 1.0))}
+
+
+def mirror_x(f: np.ndarray, half: bool, sign: float) -> np.ndarray:
+    """The mirror image across x = 0 of a mesh array of the extended box: node i
+    maps to -i, node i+1/2 to -(i+1/2), i.e. index -1-i (all mod 2 n_x)."""
+    N = f.shape[-1]
+    i = np.arange(N)
+    idx = (N - 1 - i) if half else (-i) % N
+    return sign * f[..., idx]
+
+
+def wall_symmetrise(F, kind: str):
+    """Projection of three mesh arrays of the extended box onto the mirror-
+    symmetric state of the table above: f -> (f + P f(mirror)) / 2."""
+    return [0.5 * (np.asarray(F[a], dtype=np.float64) + mirror_x(np.asarray(F[a], dtype=np.float64), *WALL_PARITY[kind][a]))
+            for a in range(3)]
+
+
+class WallSimulation:
+    """Reflecting walls in x at 0 and L = n[0] d[0] (periodic in y and z): the
+    periodic oracle on the mirror-extended box of 2 n[0] cells, with every
+    particle's virtual image loaded as a particle.  Mesh arrays (fields,
+    J, rho) are those of the extended box, shape (nz, ny, 2 nx).  Energies,
+    charge and kinetic energy in diagnostics() are those of the physical box
+    [0, L] (half the extended box's sums)."""
+
+    def __init__(self, n, d, dt, **kw):
+        nx, ny, nz = n
+        self.nx = int(nx)
+        self.L = nx * float(d[0])
+        self.sim = Simulation((2 * nx, ny, nz), d, dt, **kw)
+        self.counts: list[int] = []
+
+    @property
+    def g(self):
+        return self.sim.g
+
+    @property
+    def E(self):
+        return self.sim.E
+
+    @property
+    def B(self):
+        return self.sim.B
+
+    @property
+    def J(self):
+        return self.sim.J
+
+    @property
+    def species(self):
+        """Physical particles of each species (see particles())."""
+        return [self.particles(s) for s in range(len(self.counts))]
+
+    def add_species(self, q, m, w, x, y, z, ux, uy, uz, rad=0.0) -> int:
+        x = np.asarray(x, dtype=np.float64)
+        if np.any(x < 0.0) or np.any(x > self.L):
+            raise ValueError("positions must lie between the walls")
+        ux = np.asarray(ux, dtype=np.float64)
+        image = np.where(x > 0.0, 2.0 * self.L - x, 0.0)
+        cat = np.concatenate
+        self.sim.add_species(q, m, w, cat([x, image]), cat([y, y]), cat([z, z]), cat([ux, -ux]), cat([uy, uy]),
+                             cat([uz, uz]), rad=rad)
+        self.counts.append(len(x))
+        return len(self.counts) - 1
+
+    def load_fields(self, E, B):
+        """Extended-box arrays, projected onto the mirror-symmetric state."""
+        self.sim.load_fields(wall_symmetrise(E, "E"), wall_symmetrise(B, "B"))
+
+    def step(self, n: int = 1):
+        self.sim.step(n)
+
+    def particles(self, sid: int) -> dict:
+        """The member of each (particle, image) pair that lies in [0, L]."""
+        s = self.sim.species[sid]
+        n = self.counts[sid]
+        inside = s["x"][:n] <= self.L
+        out = {}
+        for k in ("x", "y", "z", "ux", "uy", "uz"):
+            out[k] = np.where(inside, s[k][:n], s[k][n:])
+        return out
+
+    def rho(self) -> np.ndarray:
+        return self.sim.rho()
+
+    def diagnostics(self) -> dict:
+        d = self.sim.diagnostics()
+        for k in ("energy_E", "energy_B", "energy_Ex", "kinetic", "charge"):
+            d[k] *= 0.5
+        return d
