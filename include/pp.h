@@ -73,6 +73,8 @@ extern "C" {
 #define PP_FIELD_EXPLICIT 1  /* explicit FDTD leap-frog (cold-beam comparison)         */
 #define PP_CURRENT_CONSERVING 0  /* charge-conserving high-order current (default)    */
 #define PP_CURRENT_DIRECT 1      /* direct current eq:jj2 (the original method)        */
+#define PP_BOUNDARY_PERIODIC 0   /* x periodic like y and z (default)                  */
+#define PP_BOUNDARY_WALLS 1      /* reflecting walls at x = 0 and x = nx*dx            */
 
 #define PP_MAX_SPECIES 8
 
@@ -85,7 +87,23 @@ typedef struct pp_ctx pp_ctx;
  * {2,4,6}; 0.5 <= alpha < 1 (eq:bnplus1); shape_order in {1,2,3} (CIC, TSC,
  * PCS of Sec. II); pusher PP_VAY or PP_BORIS; precision PP_FP64 or
  * PP_MIXED32.  alpha < 0.525 with field_order 6 and PCS returns PP_WSTAB but
- * still creates the context (the paper reports instability below 0.525). */
+ * still creates the context (the paper reports instability below 0.525).
+ *
+ * boundary_x = PP_BOUNDARY_WALLS puts reflecting walls at x = 0 and
+ * x = L = nx*dx (Sec. II "Boundary conditions"; y and z stay periodic).  The
+ * walls sit on integer (charge-density) nodes.  A particle that crosses a wall
+ * deposits its current as if streaming freely, its virtual mirror image
+ * deposits the mirrored current (rho and J_y, J_z added across the wall, J_x
+ * subtracted), and only then is it reflected: x -> 2 x_b - x, u_x -> -u_x.  The
+ * fields keep the paper's parities across each wall: E_x, B_y, B_z (staggered
+ * in x) odd, E_y, E_z, B_x even.  The library holds the mesh as the
+ * mirror-extended periodic box of 2*nx cells in x, whose second half is the
+ * mirror image of the first, and every mesh array of the ABI (pp_load_fields,
+ * pp_get_fields, pp_get_rho) has that shape: 2*nx*ny*nz values, x fastest.
+ * pp_load_fields projects its arrays onto the mirror-symmetric state (each
+ * value and its image replaced by their parity-signed mean).  Particle
+ * positions stay physical: x in [0, L].  Needs 2*nx <= 1023 (and 2*nx a
+ * multiple of 8 for the tiled deposit). */
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz;
@@ -101,6 +119,7 @@ typedef struct {
     double relax_tol;     /* target relative residual of eq:EllipticB            */
     int deposit_mode;     /* PP_DEPOSIT_*                                         */
     void *stream;         /* cudaStream_t                                          */
+    int boundary_x;       /* PP_BOUNDARY_PERIODIC or PP_BOUNDARY_WALLS             */
 } pp_grid_desc;
 
 /* One particle species: charge q, mass m, and w = number density represented
@@ -112,7 +131,10 @@ typedef struct {
 } pp_species_desc;
 
 /* FP64 global diagnostics (Sec. III eq:gauss, eq:divb, eq:rho2; Sec. VIII
- * field-energy series).  dV = dx*dy*dz. */
+ * field-energy series).  dV = dx*dy*dz.  Between walls the field energies and
+ * the charge are those of the physical box [0, L] (half the sums over the
+ * mirror-extended mesh); maxima are taken over the extended mesh, which holds
+ * the same values twice. */
 typedef struct {
     int64_t step;              /* steps taken since pp_init_grid                 */
     double time;               /* step * dt                                       */
@@ -244,8 +266,10 @@ int pp_set_divergence_filter(pp_ctx *ctx, int passes, int interval);
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
  * host memory (on_device = 0) or device memory (on_device = 1); page-locked
  * host arrays are read in place by the device, pageable ones are staged.
+ * Between walls (PP_BOUNDARY_WALLS) x must lie in [0, nx*dx].
  * Errors: PP_ENOMEM if the count would exceed the capacity, PP_ENAN if a
- * value is not finite (nothing is appended then).  Loading re-sorts the
+ * value is not finite, PP_EINVAL for an x outside the walls (nothing is
+ * appended then).  Loading re-sorts the
  * species by cell and resets the Gauss reference G_0 of pp_diagnostics (taken
  * from the loaded state before the next step or diagnostics). */
 int pp_load_particles(pp_ctx *ctx, int sid, int64_t n, const double *x, const double *y, const double *z,

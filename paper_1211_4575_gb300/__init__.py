@@ -31,6 +31,7 @@ PP_FP64, PP_MIXED32 = 0, 1
 PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
 PP_FIELD_IMPLICIT, PP_FIELD_EXPLICIT = 0, 1
 PP_CURRENT_CONSERVING, PP_CURRENT_DIRECT = 0, 1
+PP_BOUNDARY_PERIODIC, PP_BOUNDARY_WALLS = 0, 1
 PP_MAX_SPECIES = 8
 PP_BATCH_FREE, PP_BATCH_RUNNING, PP_BATCH_DONE, PP_BATCH_FAILED = 0, 1, 2, 3
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
@@ -49,7 +50,7 @@ class GridDesc(C.Structure):
                 ("c", C.c_double), ("eps0", C.c_double), ("field_order", C.c_int), ("alpha", C.c_double),
                 ("shape_order", C.c_int), ("pusher", C.c_int), ("precision", C.c_int),
                 ("sort_interval", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double),
-                ("deposit_mode", C.c_int), ("stream", C.c_void_p)]
+                ("deposit_mode", C.c_int), ("stream", C.c_void_p), ("boundary_x", C.c_int)]
 
 
 class SpeciesDesc(C.Structure):
@@ -183,7 +184,10 @@ class Simulation:
 
     def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=3, pusher=PP_VAY, precision=PP_FP64,
                  sort_interval=20, relax_max_iter=200, relax_tol=1e-6, deposit_mode=PP_DEPOSIT_AUTO, stream=None,
-                 _handle=None):
+                 boundary_x=PP_BOUNDARY_PERIODIC, _handle=None):
+        """boundary_x = PP_BOUNDARY_WALLS: reflecting walls at x = 0 and n[0] d[0];
+        mesh arrays (fields(), rho(), load_fields()) then span the mirror-extended
+        box, shape (nz, ny, 2 nx)."""
         self._ctx = C.c_void_p()
         if _handle is not None:
             self._ctx = _handle
@@ -192,10 +196,11 @@ class Simulation:
                          field_order=field_order, alpha=alpha, shape_order=shape_order, pusher=pusher,
                          precision=precision, sort_interval=sort_interval, relax_max_iter=relax_max_iter,
                          relax_tol=relax_tol, deposit_mode=deposit_mode,
-                         stream=stream if stream is not None else _current_stream())
+                         stream=stream if stream is not None else _current_stream(), boundary_x=boundary_x)
             rc = lib().pp_init_grid(C.byref(self._ctx), C.byref(g))
             _check(rc, self._ctx if self._ctx.value else None)
         self.n = tuple(n)
+        self.walls = boundary_x == PP_BOUNDARY_WALLS
         self.nspecies = 0
 
     # -- lifecycle --------------------------------------------------------
@@ -274,6 +279,9 @@ class Simulation:
     def load_fields(self, E, B):
         E = [_f64(a) for a in E]
         B = [_f64(a) for a in B]
+        size = int(np.prod(self.mesh_shape))
+        if any(a.size != size for a in E + B):
+            raise ValueError(f"field arrays must hold {size} values (mesh shape {self.mesh_shape})")
         self._c(lib().pp_load_fields(self._ctx, _ptr_array(E), _ptr_array(B), 0))
 
     # -- the step -----------------------------------------------------------
@@ -303,9 +311,14 @@ class Simulation:
         out["kinetic"] = list(d.kinetic)[: self.nspecies]
         return out
 
-    def _mesh(self):
+    @property
+    def mesh_shape(self):
+        """(nz, ny, nx) of the mesh arrays; nx doubled between walls."""
         nx, ny, nz = self.n
-        return np.zeros((nz, ny, nx))
+        return (nz, ny, 2 * nx if self.walls else nx)
+
+    def _mesh(self):
+        return np.zeros(self.mesh_shape)
 
     def fields(self):
         E = [self._mesh() for _ in range(3)]
@@ -353,6 +366,7 @@ class Simulation:
         sim._ctx = h
         g, ns = sim.grid()
         sim.n = (g.nx, g.ny, g.nz)
+        sim.walls = g.boundary_x == PP_BOUNDARY_WALLS
         sim.nspecies = ns
         return sim
 

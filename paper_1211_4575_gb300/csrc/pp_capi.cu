@@ -5,6 +5,7 @@
 // or field update runs on the host.
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -185,10 +186,17 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     Ctx *c = nullptr;
     if (!out || !d) return fail(c, PP_EINVAL, "pp_init_grid: NULL argument");
     *out = nullptr;
-    int n[3] = {d->nx, d->ny, d->nz};
+    if (d->boundary_x != PP_BOUNDARY_PERIODIC && d->boundary_x != PP_BOUNDARY_WALLS)
+        return fail(c, PP_EINVAL, "unknown boundary_x %d", d->boundary_x);
+    const bool walls = d->boundary_x == PP_BOUNDARY_WALLS;
+    // between walls the mesh is the mirror-extended box: 2 nx cells in x
+    int n[3] = {walls ? 2 * d->nx : d->nx, d->ny, d->nz};
     double h[3] = {d->dx, d->dy, d->dz};
+    if (walls && d->nx < 1) return fail(c, PP_EINVAL, "grid size %d on axis 0 below 1", d->nx);
     for (int a = 0; a < 3; ++a) {
-        if (n[a] < 1 || n[a] > 1023) return fail(c, PP_EINVAL, "grid size %d on axis %d outside [1, 1023]", n[a], a);
+        if (n[a] < 1 || n[a] > 1023)
+            return fail(c, PP_EINVAL, "grid size %d on axis %d outside [1, 1023]%s", n[a], a,
+                        walls && a == 0 ? " (between walls the mesh holds 2 nx cells in x)" : "");
         if (!(h[a] > 0.0)) return fail(c, PP_EINVAL, "cell size on axis %d must be > 0", a);
         if (!(d->dt > 0.0) || !(d->dt / h[a] < 1.0))
             return fail(c, PP_EINVAL, "need 0 < c dt / d < 1 on every axis (axis %d: %g)", a, d->dt / h[a]);
@@ -212,8 +220,9 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     if (d->deposit_mode < 0 || d->deposit_mode > 2) return fail(c, PP_EINVAL, "unknown deposit_mode");
     if (d->deposit_mode == PP_DEPOSIT_TILED && d->precision != PP_MIXED32)
         return fail(c, PP_EINVAL, "the tiled deposit exists for PP_MIXED32 only");
-    if (d->deposit_mode == PP_DEPOSIT_TILED && (d->nx % 8 || d->ny % 8 || d->nz % 8))
-        return fail(c, PP_EINVAL, "the tiled deposit needs every grid size to be a multiple of 8");
+    if (d->deposit_mode == PP_DEPOSIT_TILED && (n[0] % 8 || n[1] % 8 || n[2] % 8))
+        return fail(c, PP_EINVAL, "the tiled deposit needs every mesh size to be a multiple of 8%s",
+                    walls ? " (2 nx between walls)" : "");
 
     pp_ctx *p = new (std::nothrow) pp_ctx();
     if (!p) return fail(c, PP_ENOMEM, "host allocation failed");
@@ -222,6 +231,7 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     c->st = (cudaStream_t)d->stream;
     c->fp64 = d->precision == PP_FP64;
     c->rsz = c->fp64 ? 8 : 4;
+    c->mirror = walls ? d->nx : 0;
     for (int a = 0; a < 3; ++a) {
         c->g.n[a] = n[a];
         c->g.P[a] = n[a] + 2 * kGhost;
@@ -428,7 +438,9 @@ extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x,
         e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle load: %s", cudaGetErrorString(e));
-        else if (*c->h_status) rc = fail(c, PP_ENAN, "non-finite particle value: nothing appended");
+        else if (*c->h_status & 1) rc = fail(c, PP_ENAN, "non-finite particle value: nothing appended");
+        else if (*c->h_status) rc = fail(c, PP_EINVAL, "particle x outside the walls [0, %g]: nothing appended",
+                                         c->mirror * c->d.dx);
         cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
     }
     if (stage) {
@@ -497,6 +509,7 @@ extern "C" int pp_load_fields(pp_ctx *p, const double *const E[3], const double 
             }
             CU(to_padded(c, s, dsts[f][a]));
         }
+    CU(launch_mirror_fields(*c));   // between walls: the mirror-symmetric part
     CU(launch_ghost_fill(*c, c->E, c->B));
     CU(cudaStreamSynchronize(c->st));
     if (stage) cudaFree(stage);
@@ -570,6 +583,7 @@ static int particle_phase(Ctx *c, int only) {
     CU(prof_mark(c, PH_PARTICLE, false));
     CU(prof_mark(c, PH_CURRENT, true));
     CU(launch_fold_J(*c));
+    CU(launch_mirror_J(*c));   // between walls: the virtual images' current
     if (c->current_mode == PP_CURRENT_CONSERVING) CU(launch_current_solve(*c));   // eq:jj2 is final
     CU(prof_mark(c, PH_CURRENT, false));
     if (c->prof) ++c->prof_steps;
@@ -918,12 +932,13 @@ extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
     CU(cudaMemcpyAsync(kin, c->d_out + 16, sizeof(double) * PP_MAX_SPECIES, cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
     double dV = c->d.dx * c->d.dy * c->d.dz;
+    const double box = c->mirror ? 0.5 : 1.0;   // between walls: the physical half of the extended mesh
     out->step = c->step;
     out->time = c->step * c->d.dt;
-    out->energy_E = mesh[0] * dV;
-    out->energy_B = mesh[1] * dV;
-    out->energy_Ex = mesh[2] * dV;
-    out->charge = mesh[3] * dV;
+    out->energy_E = mesh[0] * dV * box;
+    out->energy_B = mesh[1] * dV * box;
+    out->energy_Ex = mesh[2] * dV * box;
+    out->charge = mesh[3] * dV * box;
     out->rho_max = mesh[4];
     out->gauss_max = mesh[5];
     out->gauss_drift_max = mesh[6];
@@ -1021,7 +1036,7 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // Format 2 adds each species' radiative-cooling coefficient, format 3 the
 // integrator order, format 4 the field solver, format 5 the current deposit
 // and the divergence filter; older files restore with the defaults.
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '5'};
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '6'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
@@ -1070,8 +1085,10 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     int64_t step = 0;
     int ns = 0;
     int order = 2, solver = PP_FIELD_IMPLICIT, cmode = PP_CURRENT_CONSERVING, fpasses = 0, finterval = 1;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '5' &&
-              fread(&d, sizeof d, 1, f) == 1 &&
+    // formats 1-5 wrote the descriptor without its last member (boundary_x)
+    memset(&d, 0, sizeof d);
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '6' &&
+              fread(&d, magic[7] >= '6' ? sizeof d : offsetof(pp_grid_desc, boundary_x), 1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
               ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1) &&
               (magic[7] < '4' || fread(&solver, sizeof solver, 1, f) == 1) &&

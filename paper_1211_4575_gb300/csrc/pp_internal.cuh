@@ -511,6 +511,9 @@ struct Ctx {
     int field_solver = 0;    // PP_FIELD_IMPLICIT or PP_FIELD_EXPLICIT
     bool g0_pending = false; // a load changed rho or E: take the Gauss reference before the next use
     int current_mode = 0;    // PP_CURRENT_CONSERVING or PP_CURRENT_DIRECT
+    // Reflecting walls at x = 0 and x = mirror (cells): the mesh is the
+    // mirror-extended box, g.n[0] = 2 * mirror.  0 = periodic in x.
+    int mirror = 0;
     int filter_passes = 0;   // divergence-filter passes every filter_interval steps
     int filter_interval = 1;
     double filter_tau = 0;   // 1 / largest eigenvalue of -div grad
@@ -563,6 +566,9 @@ cudaError_t launch_kinetic(Ctx &c, double *out_per_species);
 
 cudaError_t launch_zero_J(Ctx &c);
 cudaError_t launch_fold_J(Ctx &c);
+cudaError_t launch_mirror_J(Ctx &c);
+cudaError_t launch_mirror_fields(Ctx &c);
+cudaError_t launch_mirror_rho(Ctx &c, double *rho);
 cudaError_t launch_current_solve(Ctx &c);
 cudaError_t launch_field_update(Ctx &c);
 cudaError_t launch_divergence_filter(Ctx &c);

@@ -85,6 +85,88 @@ cudaError_t launch_zero_J(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------
+// Reflecting walls (Sec. II "Boundary conditions").  Between walls the mesh is
+// the mirror-extended box of n0 = 2 nx cells in x, the walls on the integer
+// nodes 0 and nx.  Along x, integer node i has the image (n0 - i) mod n0 and
+// half node i+1/2 (index i) the image index n0 - 1 - i.  Components staggered
+// in x are odd across a wall and the others even: component 0 of E and J,
+// components 1 and 2 of B.
+//
+// avg = 0 (a deposit): the virtual images contribute the mirror of what the
+// particles deposited, f(i) <- f(i) + P f(m(i)), and the image node receives
+// P times that sum; a wall node, its own image, doubles.  avg = 1 (a load):
+// f(i) <- (f(i) + P f(m(i))) / 2 on both nodes of the pair.  One thread per
+// pair: i in [0, nx] along a row (odd components stop at nx - 1).
+// ---------------------------------------------------------------------------
+struct PaddedIndex {
+    Geom g;
+    __device__ __forceinline__ int64_t operator()(int i, int j, int k) const { return g.at(i, j, k); }
+};
+struct CompactIndex {
+    int n0, n1;
+    __device__ __forceinline__ int64_t operator()(int i, int j, int k) const {
+        return i + (int64_t)n0 * (j + (int64_t)n1 * k);
+    }
+};
+
+template <typename R, class Ix>
+__global__ void k_mirror(Ix ix, int nx, int ny, int nz, R *F0, R *F1, R *F2, int odd_mask, int avg) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int comp = blockIdx.y;
+    if (t >= (int64_t)(nx + 1) * ny * nz) return;
+    const int i = (int)(t % (nx + 1));
+    const int64_t r = t / (nx + 1);
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const bool odd = (odd_mask >> comp) & 1;
+    int m;
+    if (odd) {
+        if (i == nx) return;
+        m = 2 * nx - 1 - i;
+    } else {
+        m = i == 0 ? 0 : 2 * nx - i;
+    }
+    R *F = comp == 0 ? F0 : (comp == 1 ? F1 : F2);
+    const int64_t a = ix(i, j, k), b = ix(m, j, k);
+    const R P = odd ? R(-1) : R(1);
+    R v = F[a] + P * F[b];
+    if (avg) v *= R(0.5);
+    F[a] = v;
+    if (b != a) F[b] = P * v;
+}
+
+template <typename R>
+static cudaError_t mirror_padded(Ctx &c, void *const F[3], int odd_mask, int avg) {
+    const int nx = c.mirror, ny = c.g.n[1], nz = c.g.n[2];
+    dim3 grid((unsigned)(((int64_t)(nx + 1) * ny * nz + 255) / 256), 3);
+    k_mirror<R, PaddedIndex><<<grid, 256, 0, c.st>>>(PaddedIndex{c.g}, nx, ny, nz, (R *)F[0], (R *)F[1], (R *)F[2],
+                                                     odd_mask, avg);
+    ++c.nlaunch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_J(Ctx &c) {
+    if (!c.mirror) return cudaSuccess;
+    return c.fp64 ? mirror_padded<double>(c, c.J, 1, 0) : mirror_padded<float>(c, c.J, 1, 0);
+}
+
+cudaError_t launch_mirror_fields(Ctx &c) {
+    if (!c.mirror) return cudaSuccess;
+    cudaError_t e = c.fp64 ? mirror_padded<double>(c, c.E, 1, 1) : mirror_padded<float>(c, c.E, 1, 1);
+    if (e != cudaSuccess) return e;
+    return c.fp64 ? mirror_padded<double>(c, c.B, 6, 1) : mirror_padded<float>(c, c.B, 6, 1);
+}
+
+cudaError_t launch_mirror_rho(Ctx &c, double *rho) {
+    if (!c.mirror) return cudaSuccess;
+    const int nx = c.mirror, ny = c.g.n[1], nz = c.g.n[2];
+    dim3 grid((unsigned)(((int64_t)(nx + 1) * ny * nz + 255) / 256), 1);
+    k_mirror<double, CompactIndex><<<grid, 256, 0, c.st>>>(CompactIndex{c.g.n[0], c.g.n[1]}, nx, ny, nz, rho, rho, rho,
+                                                            0, 0);
+    ++c.nlaunch;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // High-order current: along the axis of each component, J_out = P^{-1} J_in
 // with P the symmetric cyclic line operator (c, b+c, a+b+c, b+c, c) that
 // turns the 2nd-order difference into the high-order one; applied as the

@@ -49,6 +49,7 @@ struct StepArgs {
     int64_t n;
     int *status;
     int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
+    int mirror;                  // walls at x = 0 and x = mirror cells; 0 = periodic
 };
 
 struct Fp64Particles {
@@ -59,6 +60,37 @@ struct MixedParticles {
     int32_t *cell;
     float *ox, *oy, *oz, *ux, *uy, *uz;
 };
+
+// Reflecting walls at x = 0 and x = nw cells (Sec. II "Boundary conditions"),
+// applied after the particle deposited its step as if streaming freely: a
+// particle that ended the move beyond a wall (in (nw, 2 nw) of the
+// mirror-extended box, which the periodic wrap also gives for x < 0) is
+// replaced by its virtual image, x -> 2 nw - x and u_x -> -u_x.  nw = 0: no
+// walls.
+__device__ __forceinline__ void reflect(double &xi, double &ux, int nw) {
+    if (nw && xi > (double)nw) {
+        xi = 2.0 * (double)nw - xi;
+        ux = -ux;
+    }
+}
+// Mixed form: cell cx and offset o in [0, 1).  2 nw - (cx + o) is cell
+// 2 nw - 1 - cx with offset 1 - o, or cell 2 nw - cx when o = 0; an offset
+// that rounds to 1 moves to the cell above.
+__device__ __forceinline__ void reflect(int &cx, float &o, float &ux, int nw) {
+    if (nw && (cx > nw || (cx == nw && o > 0.0f))) {
+        if (o > 0.0f) {
+            cx = 2 * nw - 1 - cx;
+            o = 1.0f - o;
+            if (o >= 1.0f) {
+                o = 0.0f;
+                ++cx;
+            }
+        } else {
+            cx = 2 * nw - cx;
+        }
+        ux = -ux;
+    }
+}
 
 template <int O, int PUSH>
 __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64Particles p) {
@@ -97,6 +129,7 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
         if (v >= L) v -= L;
         xi1[d] = v;
     }
+    reflect(xi1[0], u[0], a.mirror);
     p.x[t] = xi1[0]; p.y[t] = xi1[1]; p.z[t] = xi1[2];
     p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
 }
@@ -161,6 +194,7 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
     rebin(xi1[0], cx, a.g.n[0]);
     rebin(xi1[1], cy, a.g.n[1]);
     rebin(xi1[2], cz, a.g.n[2]);
+    reflect(cx, xi1[0], u[0], a.mirror);
     p.cell[t] = pack_cell(cx, cy, cz);
     p.ox[t] = xi1[0]; p.oy[t] = xi1[1]; p.oz[t] = xi1[2];
     p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
@@ -186,6 +220,7 @@ static StepArgs<R> step_args(Ctx &c, int s) {
     a.n = S.n;
     a.status = c.d_status;
     a.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
+    a.mirror = c.mirror;
     return a;
 }
 
@@ -342,6 +377,7 @@ struct TiledArgs {
     TiledSpecies sp[kMaxTiledSpecies];
     int *status;
     int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
+    int mirror;                  // walls at x = 0 and x = mirror cells; 0 = periodic
 };
 
 __device__ __forceinline__ int min_image(int d, int n) {
@@ -369,6 +405,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
     const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
     const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
     const int wx = ox - kWinLo, wy = oy - kWinLo, wz = oz - kWinLo;
+    {   // a tile that holds no particle (the mirror half of a box between walls) stages nothing
+        int held = 0;
+        for (int s = 0; s < T.ns; ++s)
+            held |= T.sp[s].cell_start[(tile + 1) * kTileCells * kSubKeys] - T.sp[s].cell_start[tile * kTileCells * kSubKeys];
+        if (!held) return;
+    }
     // stage E and B (ghost layers hold the periodic images), clear the current window
     for (int idx = threadIdx.x; idx < 6 * kWinVol; idx += kThreads) {
         int comp = idx / kWinVol, r = idx - comp * kWinVol;
@@ -497,6 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 rebin(xi1[0], cx, g.n[0]);
                 rebin(xi1[1], cy, g.n[1]);
                 rebin(xi1[2], cz, g.n[2]);
+                if (T.mirror) reflect(cx, xi1[0], s_u[sq], T.mirror);
                 s_cell[sq] = pack_cell(cx, cy, cz);
                 s_o[sq] = xi1[0]; s_o[kStage + sq] = xi1[1]; s_o[2 * kStage + sq] = xi1[2];
             };
@@ -625,6 +668,7 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
         rebin(xi1[0], cx, a.g.n[0]);
         rebin(xi1[1], cy, a.g.n[1]);
         rebin(xi1[2], cz, a.g.n[2]);
+        reflect(cx, xi1[0], u[0], a.mirror);
         p.cell[t] = pack_cell(cx, cy, cz);
         p.ox[t] = xi1[0]; p.oy[t] = xi1[1]; p.oz[t] = xi1[2];
         p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
@@ -679,6 +723,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
     if (T.ns == 0) return cudaSuccess;
     T.status = c.d_status;
     T.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
+    T.mirror = c.mirror;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
     static bool attr_done[2][4] = {{false}};
@@ -873,7 +918,7 @@ cudaError_t launch_rho(Ctx &c) {
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return launch_mirror_rho(c, c.rho);   // between walls: add the virtual images' charge
 }
 
 // ---------------------------------------------------------------------------
@@ -926,13 +971,17 @@ cudaError_t launch_kinetic(Ctx &c, double *out) {
 __global__ void k_convert_in(int64_t n, int64_t off, const double *x, const double *y, const double *z,
                              const double *ux, const double *uy, const double *uz, double hx, double hy,
                              double hz, int nx, int ny, int nz, int mixed, Fp64Particles p64, MixedParticles pm,
-                             int *bad) {
+                             int *bad, double wall) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     double in[3] = {x[t], y[t], z[t]};
     const double vx = ux[t], vy = uy[t], vz = uz[t];
     if (!isfinite(in[0]) || !isfinite(in[1]) || !isfinite(in[2]) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz)) {
         atomicOr(bad, 1);
+        return;
+    }
+    if (wall > 0.0 && !(in[0] >= 0.0 && in[0] <= wall)) {   // between walls: x in [0, L]
+        atomicOr(bad, 2);
         return;
     }
     double h[3] = {hx, hy, hz};
@@ -972,7 +1021,7 @@ cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const doubl
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_convert_in<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(n, off, x, y, z, ux, uy, uz, c.d.dx, c.d.dy, c.d.dz,
                                                                c.g.n[0], c.g.n[1], c.g.n[2], c.fp64 ? 0 : 1, p64, pm,
-                                                               bad);
+                                                               bad, c.mirror ? c.mirror * c.d.dx : 0.0);
     ++c.nlaunch;
     return cudaGetLastError();
 }

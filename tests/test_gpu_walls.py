@@ -1,0 +1,194 @@
+"""GPU parity of the reflecting walls (Sec. II "Boundary conditions",
+boundary_x = PP_BOUNDARY_WALLS) against the oracle's virtual-image system.
+
+The library deposits the particles alone, folds the images' share into the
+mirror-extended mesh and reflects the particles that crossed; the oracle
+carries every image as a particle and reflects nothing.  Both see the same
+unsymmetrised random fields and project them by their own code."""
+import math
+
+import numpy as np
+import pytest
+
+import pp_synth
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1211_4575_gb300 as m
+    from paper_1211_4575_gb300 import build
+    build.build()
+    return m
+
+
+def _pair(pp, orc, L, precision, shape, pusher=0, mode=0, fields_seed=31, gpu_kw=None, orc_kw=None, setup=None):
+    gpu = H.gpu_sim(pp, L, precision, shape, pusher=pusher, deposit_mode=mode, boundary_x=pp.PP_BOUNDARY_WALLS,
+                    **(gpu_kw or {}))
+    if setup:
+        setup(gpu)
+    osim = orc.WallSimulation(L.n, L.d, L.dt, shape_order=shape, pusher=pusher, relax_tol=1e-14, relax_max_iter=2000,
+                              **(orc_kw or {}))
+    for s in L.species:
+        osim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    E, B = pp_synth.random_fields((2 * L.n[0], L.n[1], L.n[2]), fields_seed, 0.05)
+    gpu.load_fields(E, B)
+    osim.load_fields(E, B)
+    return gpu, osim
+
+
+def _box(L):
+    return (2 * L.n[0] * L.d[0], L.n[1] * L.d[1], L.n[2] * L.d[2])
+
+
+def _compare(gpu, osim, L, tol_f, tol_x, tol_u):
+    assert gpu.diagnostics()["status"] == 0
+    for s in range(len(L.species)):
+        p = gpu.particles(s)
+        assert p["x"].min() >= 0.0 and p["x"].max() <= L.n[0] * L.d[0]
+        dpos, du = H.particle_errors(p, osim.particles(s), _box(L))
+        assert dpos <= tol_x and du <= tol_u, (s, dpos, du)
+    fe = H.field_errors(gpu, osim)
+    for k, v in fe.items():
+        assert v <= tol_f, (k, v, fe)
+
+
+def _load(n=(10, 12, 9), count=3001, seed=140, u_scale=0.6):
+    # particles fast enough that many cross a wall in a few steps
+    return pp_synth.random_particles(n, (0.5, 0.4, 0.45), 0.2, count, seed=seed, u_scale=u_scale)
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("pusher", [0, 1])
+def test_walls_fp64_parity(pp, orc, shape, pusher):
+    """Ragged 3001 random particles between walls on 10x12x9 (mesh 20x12x9),
+    random fields, four steps: FP64 to 1e-12 against the oracle's images."""
+    L = _load(seed=140 + shape + 3 * pusher)
+    gpu, osim = _pair(pp, orc, L, pp.PP_FP64, shape, pusher)
+    gpu.step(4)
+    osim.step(4)
+    _compare(gpu, osim, L, 1e-12, 1e-12, 1e-12)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_walls_mixed_parity(pp, orc, mode):
+    """Mixed form, global (1) and tiled (2) deposits, 12x16x16 between walls
+    (mesh 24x16x16), three steps: fields 3e-5, positions and momenta 2e-6."""
+    L = _load((12, 16, 16), seed=151)
+    gpu, osim = _pair(pp, orc, L, pp.PP_MIXED32, 3, mode=mode)
+    gpu.step(3)
+    osim.step(3)
+    _compare(gpu, osim, L, 3e-5, 2e-6, 2e-6)
+
+
+@pytest.mark.parametrize("variant", ["explicit", "direct_filter", "step4"])
+def test_walls_with_the_variants(pp, orc, variant):
+    """The walls under the explicit FDTD solver, the direct current with the
+    divergence filter, and the 4th-order step: FP64 to 1e-12."""
+    L = _load(seed=160)
+    if variant == "explicit":
+        L.dt = 0.1
+        setup = lambda g: g.set_field_solver(pp.PP_FIELD_EXPLICIT)
+        okw = dict(field_solver=orc.EXPLICIT)
+    elif variant == "direct_filter":
+        def setup(g):
+            g.set_current_deposit(pp.PP_CURRENT_DIRECT)
+            g.set_divergence_filter(2, 1)
+        okw = dict(current_mode=orc.DIRECT, filter_passes=2, filter_interval=1)
+    else:
+        setup = lambda g: g.set_integrator(4)
+        okw = dict(integrator=4)
+    gpu, osim = _pair(pp, orc, L, pp.PP_FP64, 3, setup=setup, orc_kw=okw)
+    gpu.step(2)
+    osim.step(2)
+    _compare(gpu, osim, L, 1e-12, 1e-12, 1e-12)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_free_particle_bounces_on_gpu(pp, precision):
+    """One light particle per wall in empty fields, 100 steps: the folded
+    straight path, u_x reversed on the odd legs (closed form)."""
+    n, d, dt = (16, 8, 8), (0.5, 0.5, 0.5), 0.2
+    Lx = n[0] * d[0]
+    sim = pp.Simulation(n, d, dt, shape_order=3, precision=precision, boundary_x=pp.PP_BOUNDARY_WALLS,
+                        relax_tol=1e-14 if precision == 0 else 1e-6)
+    x0 = np.array([6.7, 1.1])
+    u0 = np.array([[2.0, 0.3, -0.1], [-1.5, -0.2, 0.4]])
+    sid = sim.add_species(-1.0, 1.0, 1e-13, 2)
+    sim.load_particles(sid, x0, np.array([1.3, 2.2]), np.array([0.7, 3.1]), u0[:, 0], u0[:, 1], u0[:, 2])
+    v = u0 / np.sqrt(1.0 + (u0 ** 2).sum(1))[:, None]
+    tol = 1e-9 if precision == 0 else 2e-4
+    for k in range(10, 101, 10):
+        sim.step(10)
+        p = sim.particles(sid)
+        o = np.argsort(p["uy"])[::-1]   # uy 0.3 first, -0.2 second
+        X = x0 + k * dt * v[:, 0]
+        s = np.mod(X, 2 * Lx)
+        xe = np.where(s <= Lx, s, 2 * Lx - s)
+        uxe = np.where(s <= Lx, u0[:, 0], -u0[:, 0])
+        assert np.abs(p["x"][o] - xe).max() < tol, (k, p["x"][o], xe)
+        assert np.abs(p["ux"][o] - uxe).max() < tol, (k, p["ux"][o], uxe)
+
+
+def test_walls_keep_symmetry_and_charge_tiled(pp):
+    """Thermal pair plasma between walls, tiled mixed form, 30 steps: the
+    extended mesh stays mirror-symmetric (E_x odd, E_y even, B_x even, B_y odd),
+    the charge equals the particles' and the Gauss drift stays at FP32 level."""
+    L = pp_synth.thermal(n=(16, 16, 16), ppc=8, u_th=0.3, dx=0.1, dt=0.05, seed=1217)
+    sim = H.gpu_sim(pp, L, pp.PP_MIXED32, 3, deposit_mode=2, boundary_x=pp.PP_BOUNDARY_WALLS)
+    sim.step(30)
+    d = sim.diagnostics()
+    assert d["status"] == 0
+    q = sum(s["q"] * s["w"] * len(s["x"]) for s in L.species) * 0.1 ** 3
+    qe = sum(abs(s["q"]) * s["w"] * len(s["x"]) for s in L.species) * 0.1 ** 3
+    assert abs(d["charge"] - q) <= 1e-6 * qe
+    assert d["gauss_drift_max"] <= 1e-4 * d["rho_max"]
+    E, B, J = sim.fields()
+    N = E[0].shape[-1]
+    i = np.arange(N)
+    for F, half, sign in ((E[0], True, -1), (E[1], False, 1), (B[0], False, 1), (B[1], True, -1), (J[0], True, -1),
+                          (J[2], False, 1)):
+        img = sign * F[..., (N - 1 - i) if half else (-i) % N]
+        assert np.abs(F - img).max() <= 1e-4 * np.abs(F).max()
+    for s in range(2):
+        p = sim.particles(s)
+        assert p["x"].min() >= 0.0 and p["x"].max() <= 1.6
+
+
+def test_walls_arguments_and_checkpoint(pp, tmp_path):
+    with pytest.raises(pp.PPError):   # mesh 2 * 600 > 1023
+        pp.Simulation((600, 8, 8), (0.5, 0.5, 0.5), 0.2, boundary_x=pp.PP_BOUNDARY_WALLS)
+    with pytest.raises(pp.PPError):
+        pp.Simulation((8, 8, 8), (0.5, 0.5, 0.5), 0.2, boundary_x=2)
+    with pytest.raises(pp.PPError):   # mesh 2 * 12 = 24 is a multiple of 8, 2 * 10 is not
+        pp.Simulation((10, 8, 8), (0.5, 0.5, 0.5), 0.2, precision=pp.PP_MIXED32, deposit_mode=pp.PP_DEPOSIT_TILED,
+                      boundary_x=pp.PP_BOUNDARY_WALLS)
+    sim = pp.Simulation((12, 8, 8), (0.5, 0.5, 0.5), 0.2, precision=pp.PP_FP64, boundary_x=pp.PP_BOUNDARY_WALLS)
+    sid = sim.add_species(-1.0, 1.0, 0.1, 10)
+    one = np.array([1.0])
+    with pytest.raises(pp.PPError):   # x beyond the upper wall at 6
+        sim.load_particles(sid, np.array([6.5]), one, one, one, one, one)
+    with pytest.raises(ValueError):   # field arrays of the physical box instead of the extended one
+        sim.load_fields([np.zeros((8, 8, 12))] * 3, [np.zeros((8, 8, 12))] * 3)
+    assert sim.count(sid) == 0
+    L = _load((12, 8, 8), count=500, seed=171)
+    s = L.species[0]
+    a = pp.Simulation(L.n, L.d, L.dt, shape_order=2, precision=pp.PP_FP64, boundary_x=pp.PP_BOUNDARY_WALLS,
+                      relax_tol=1e-14)
+    sid = a.add_species(s["q"], s["m"], s["w"], 500)
+    a.load_particles(sid, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    a.step(2)
+    path = str(tmp_path / "walls.ckpt")
+    a.save(path)
+    b = pp.Simulation.restore(path)
+    assert b.walls and b.mesh_shape == (8, 8, 24)
+    a.step(2)
+    b.step(2)
+    Ea, _, _ = a.fields()
+    Eb, _, _ = b.fields()
+    assert max(H.rel_err(Eb[k], Ea[k]) for k in range(3)) <= 1e-12
