@@ -92,6 +92,8 @@ def lib():
         L.orc_div_plus.argtypes = [C.POINTER(Grid), P, P]
         L.orc_divergence_filter.argtypes = [C.POINTER(Grid), P, P, P, C.c_int]
         L.orc_diagnostics.argtypes = [C.POINTER(Grid), P, P, C.POINTER(Species), C.c_int, C.POINTER(Diag)]
+        L.orc_philox4x32.argtypes = [P, P, P]
+        L.orc_draws.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, P]
         _lib = L
     return _lib
 
@@ -349,6 +351,38 @@ def wall_symmetrise(F, kind: str):
             for a in range(3)]
 
 
+def philox4x32(ctr, key):
+    """Philox4x32-10 of a 4-word counter under a 2-word key (reading R23)."""
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32(C.cast(c, C.c_void_p), C.cast(k, C.c_void_p), C.cast(o, C.c_void_p))
+    return tuple(o)
+
+
+def draws(seed: int, step: int, stream: int, n: int) -> np.ndarray:
+    """(n, 4) uniforms in (0, 1): draw i = Philox of counter (i, 0, step, stream)."""
+    out = np.zeros((max(int(n), 0), 4))
+    if n > 0:
+        lib().orc_draws(int(seed) & (2 ** 64 - 1), int(step) & 0xFFFFFFFF, int(stream) & 0xFFFFFFFF, int(n),
+                        _ptr(out))
+    return out
+
+
+def gaussians(D: np.ndarray) -> np.ndarray:
+    """Three standard normals per row of four uniforms (Box-Muller on (u0, u1)
+    and (u2, u3))."""
+    r0 = np.sqrt(-2.0 * np.log(D[:, 0]))
+    r1 = np.sqrt(-2.0 * np.log(D[:, 2]))
+    return np.stack([r0 * np.cos(2 * np.pi * D[:, 1]), r0 * np.sin(2 * np.pi * D[:, 1]),
+                     r1 * np.cos(2 * np.pi * D[:, 3])], 1)
+
+
+# Damped components of the outflow layer, bit a for E_a and 3 + a for B_a:
+# by default those transverse to the wall normal x (reading R22).
+TRANSVERSE = (1 << 1) | (1 << 2) | (1 << 4) | (1 << 5)
+
+
 class WallSimulation:
     """Reflecting walls in x at 0 and L = n[0] d[0] (periodic in y and z): the
     periodic oracle on the mirror-extended box of 2 n[0] cells, with every
@@ -363,6 +397,14 @@ class WallSimulation:
         self.L = nx * float(d[0])
         self.sim = Simulation((2 * nx, ny, nz), d, dt, **kw)
         self.counts: list[int] = []
+        self.d = tuple(float(v) for v in d)
+        self.dt = float(dt)
+        self.nyz = (int(ny), int(nz))
+        self.nstep = 0
+        self.open = None
+        self.injectors: dict = {}
+        self.window = None
+        self.shifts = 0
 
     @property
     def g(self):
@@ -401,8 +443,118 @@ class WallSimulation:
         """Extended-box arrays, projected onto the mirror-symmetric state."""
         self.sim.load_fields(wall_symmetrise(E, "E"), wall_symmetrise(B, "B"))
 
+    # -- open lower end, injector, sliding window (readings R22-R24) ---------
+    def set_open_boundary(self, cells: int, damping: float, escape: float, components: int = TRANSVERSE):
+        """Outflow layer of `cells` cells at x = 0 (the other wall stays)."""
+        self.open = dict(cells=int(cells), damping=float(damping), escape=float(escape), mask=int(components))
+
+    def set_injector(self, sid: int, ppc: float, u, u_th: float, seed: int):
+        """Inflow through x = 0 of species sid: ppc particles per cell, drift
+        proper velocity u (u[0] > 0), thermal spread u_th, Philox seed."""
+        self.injectors[sid] = dict(ppc=float(ppc), u=np.asarray(u, dtype=np.float64), u_th=float(u_th),
+                                   seed=int(seed), k0=self.nstep)
+
+    def set_window(self, v: float):
+        """Sliding window at speed v against x (content moves one cell up)."""
+        self.window = dict(v=float(v), k0=self.nstep)
+
+    def _pairs(self, sid):
+        s = self.sim.species[sid]
+        n = self.counts[sid]
+        return s, n, s["x"][:n] <= self.L
+
+    def _set_pairs(self, sid, phys: dict, keep=None):
+        """Replace species sid by the given physical particles and their images."""
+        if keep is not None:
+            phys = {k: v[keep] for k, v in phys.items()}
+        x = phys["x"]
+        image = np.where(x > 0.0, 2.0 * self.L - x, 0.0)
+        s = self.sim.species[sid]
+        cat = np.concatenate
+        s["x"] = cat([x, image])
+        s["ux"] = cat([phys["ux"], -phys["ux"]])
+        for k in ("y", "z", "uy", "uz"):
+            s[k] = cat([phys[k], phys[k]])
+        self.counts[sid] = len(x)
+
+    def _damp(self):
+        o = self.open
+        N = 2 * self.nx
+        for kind, F in (("E", self.sim.E), ("B", self.sim.B)):
+            for a in range(3):
+                if not (o["mask"] >> (a + (3 if kind == "B" else 0))) & 1:
+                    continue
+                pos = np.arange(N) + (0.5 if WALL_PARITY[kind][a][0] else 0.0)
+                dist = np.minimum(pos, N - pos)
+                f = np.where(dist < o["cells"], 1.0 - o["damping"] * ((o["cells"] - dist) / o["cells"]) ** 2, 1.0)
+                F[a] *= f
+
+    def _escape(self):
+        lim = self.open["escape"] * self.d[0]
+        for sid in range(len(self.counts)):
+            p = self.particles(sid)
+            self._set_pairs(sid, p, keep=~((p["x"] < lim) & (p["ux"] < 0.0)))
+
+    def _append(self, sid, new: dict):
+        p = self.particles(sid)
+        self._set_pairs(sid, {k: np.concatenate([p[k], new[k]]) for k in p})
+
+    def _draw_particles(self, inj, sid, count, step, stream, thick):
+        D = draws(inj["seed"], step, stream, count)
+        G = gaussians(draws(inj["seed"], step, stream + 1 + sid, count))
+        ny, nz = self.nyz
+        return dict(x=thick * D[:, 0], y=(ny * self.d[1]) * D[:, 1], z=(nz * self.d[2]) * D[:, 2],
+                    ux=inj["u"][0] + inj["u_th"] * G[:, 0], uy=inj["u"][1] + inj["u_th"] * G[:, 1],
+                    uz=inj["u"][2] + inj["u_th"] * G[:, 2])
+
+    def _inject(self, sid):
+        inj = self.injectors[sid]
+        k = self.nstep - inj["k0"]
+        u = inj["u"]
+        vx = u[0] / np.sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
+        ny, nz = self.nyz
+        rate = inj["ppc"] * ny * nz * vx * self.dt / self.d[0]
+        count = int(np.floor(k * rate) - np.floor((k - 1) * rate))
+        self._append(sid, self._draw_particles(inj, sid, count, self.nstep, 0, vx * self.dt))
+
+    def _slide(self):
+        w = self.window
+        k = self.nstep - w["k0"]
+        step_frac = w["v"] * self.dt / self.d[0]
+        if np.floor(k * step_frac) <= np.floor((k - 1) * step_frac):
+            return
+        self.shifts += 1
+        nx, N = self.nx, 2 * self.nx
+        for kind, F in (("E", self.sim.E), ("B", self.sim.B)):
+            for a in range(3):
+                half, sign = WALL_PARITY[kind][a]
+                top = nx - 1 if half else nx          # last node of the physical half
+                f = F[a]
+                f[..., 1:top + 1] = f[..., 0:top].copy()
+                f[..., 0] = 0.0
+                i = np.arange(0 if half else 1, nx)
+                f[..., (N - 1 - i) if half else (N - i)] = sign * f[..., i]
+        for sid in range(len(self.counts)):
+            p = self.particles(sid)
+            p["x"] = p["x"] + self.d[0]
+            self._set_pairs(sid, p, keep=p["x"] <= self.L)
+        ny, nz = self.nyz
+        for sid in sorted(self.injectors):
+            inj = self.injectors[sid]
+            count = int(np.floor(inj["ppc"] * ny * nz + 0.5))
+            self._append(sid, self._draw_particles(inj, sid, count, self.shifts, 16, self.d[0]))
+
     def step(self, n: int = 1):
-        self.sim.step(n)
+        for _ in range(n):
+            self.sim.step(1)
+            self.nstep += 1
+            if self.open is not None:
+                self._damp()
+                self._escape()
+            for sid in sorted(self.injectors):
+                self._inject(sid)
+            if self.window is not None:
+                self._slide()
 
     def particles(self, sid: int) -> dict:
         """The member of each (particle, image) pair that lies in [0, L]."""

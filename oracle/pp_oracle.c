@@ -73,6 +73,35 @@
  *       eigenvalue of -div grad, which removes the Nyquist-scale error in one
  *       pass and damps every other non-constant mode.  Gauss-Seidel ordering
  *       is sequential; the simultaneous form damps the same error.
+ *   R21 Reflecting walls (Sec. II "Boundary conditions") are the virtual-image
+ *       system in the mirror-extended box (oracle/__init__.py, WallSimulation).
+ *   R22 The outflow layer (same section): the paper gives no profile.  Each
+ *       step the chosen field components are multiplied by
+ *       1 - damping ((cells - d) / cells)^2 at distance d < cells (in cells,
+ *       at the component's own staggered position) from the open end.  The
+ *       paper's "perpendicular components" is read as those transverse to the
+ *       boundary normal (E_y, E_z, B_y, B_z), the fields of waves leaving along
+ *       x; the component set is a parameter.  A particle leaves the box when
+ *       a step ends with it moving outward (u_x < 0) closer than `escape`
+ *       cells to the open end: until then it deposits like any other.
+ *   R23 The injector (Sec. II "Sliding window and injection of particles") is
+ *       fed by Philox4x32-10 draws (Salmon et al., SC'11), counter
+ *       (index, 0, step, stream), key = the 64-bit seed.  Per step it adds the
+ *       inflow that crossed the open end during the step: floor(k r) -
+ *       floor((k-1) r) particles at the k-th step since it was set, r = ppc ny
+ *       nz v_x dt / dx, v the drift velocity; positions uniform in the slab
+ *       [0, v_x dt) x [0, Ly) x [0, Lz), proper velocity = drift + u_th times
+ *       three standard normals (Box-Muller).  Positions come from stream 0,
+ *       shared by every species, so that species injected with the same seed
+ *       and density land on the same points (neutral pairs); velocities from
+ *       stream 1 + species.
+ *   R24 The sliding window moves the box one cell against x (its content one
+ *       cell up) at the k-th step since it was set whenever floor(k v dt / dx)
+ *       grows: v (t - t_old) > dx with t_old advanced by dx / v, so that the
+ *       window keeps speed v on average.  The top layer and the particles in it
+ *       leave, fields of the new bottom layer are zero, and every species with
+ *       an injector gets a layer of round(ppc ny nz) particles uniform in
+ *       [0, dx) (streams 16 and 17 + species, the shift count as the step).
  */
 #include <math.h>
 #include <stdint.h>
@@ -867,4 +896,46 @@ void orc_diagnostics(const orc_grid *g, double *const E[3], double *const B[3], 
         if (fabs(dv[q]) > out->divB_max) out->divB_max = fabs(dv[q]);
     free(rho);
     free(dv);
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random        */
+/* numbers: as easy as 1, 2, 3", SC'11): ten rounds of                 */
+/*   (x0, x1, x2, x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2),             */
+/*                        hi(M0 x0) ^ x3 ^ k1, lo(M0 x0))              */
+/* with M0 = 0xD2511F53, M1 = 0xCD9E8D57, the key bumped by the Weyl   */
+/* constants (0x9E3779B9, 0xBB67AE85) between rounds.  Reading R23.    */
+/* ------------------------------------------------------------------ */
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * x[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * x[2];
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x[1] ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x[3] ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3;
+    }
+    for (int m = 0; m < 4; ++m) out[m] = x[m];
+}
+
+/* n draws of four uniforms in (0, 1): draw i is Philox of counter
+ * (i, 0, step, stream) under key (seed low, seed high), each word r mapped to
+ * (r + 1/2) 2^-32.  out holds 4 n values. */
+void orc_draws(uint64_t seed, uint32_t step, uint32_t stream, int64_t n, double *out)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t ctr[4] = {(uint32_t)i, 0u, step, stream};
+        uint32_t r[4];
+        orc_philox4x32(ctr, key, r);
+        for (int m = 0; m < 4; ++m) out[4 * i + m] = ((double)r[m] + 0.5) * (1.0 / 4294967296.0);
+    }
 }

@@ -10,6 +10,8 @@ folding rules for rho, J_par and J_perp, which must reproduce the images'
 deposit.
 """
 
+import math
+
 import numpy as np
 import pytest
 
@@ -141,3 +143,172 @@ def test_paper_folding_rules_reproduce_the_images(orc, shape):
         half, sign = orc.WALL_PARITY["J"][a]
         jf = _fold(alone.J[a], half, sign)
         assert np.abs(jf - walls.J[a]).max() <= 1e-12 * np.abs(walls.J[a]).max(), a
+
+
+# --------------------------------------------------------------------------
+# Open lower end, injector and sliding window (readings R22-R24)
+# --------------------------------------------------------------------------
+
+def test_philox_draws_are_uniform_and_mix(orc):
+    """The counter-based generator of the injector: its words are uniform
+    (chi-square over 16 bins), its Box-Muller normals have mean 0 and variance
+    1, and one flipped counter or key bit changes about half of the 128 output
+    bits (avalanche), for every word of the counter."""
+    D = orc.draws(12345, 7, 3, 20000)
+    assert D.min() > 0.0 and D.max() < 1.0
+    for m in range(4):
+        h, _ = np.histogram(D[:, m], bins=16, range=(0.0, 1.0))
+        chi2 = ((h - 1250.0) ** 2 / 1250.0).sum()
+        assert chi2 < 45.0, (m, chi2)   # 15 degrees of freedom: p ~ 1e-4
+    G = orc.gaussians(D)
+    assert np.abs(G.mean(0)).max() < 0.03 and np.abs(G.var(0) - 1.0).max() < 0.05
+    rng = np.random.default_rng(3)
+    flips = []
+    for _ in range(200):
+        ctr = [int(v) for v in rng.integers(0, 2 ** 32, 4)]
+        key = [int(v) for v in rng.integers(0, 2 ** 32, 2)]
+        a = orc.philox4x32(ctr, key)
+        w, b = int(rng.integers(0, 6)), int(rng.integers(0, 32))
+        if w < 4:
+            ctr[w] ^= 1 << b
+        else:
+            key[w - 4] ^= 1 << b
+        c = orc.philox4x32(ctr, key)
+        flips.append(sum(bin(x ^ y).count("1") for x, y in zip(a, c)))
+    assert 60.0 < np.mean(flips) < 68.0 and min(flips) > 35
+
+
+def _inject_sim(orc, n=(16, 4, 4), ppc=3.0, u=(1.2, 0.0, 0.0), u_th=0.0, w=1e-12, seeds=(9, 9)):
+    d, dt = (0.5, 0.5, 0.5), 0.2
+    sim = orc.WallSimulation(n, d, dt, shape_order=2)
+    e = np.zeros(0)
+    for q, s in zip((-1.0, 1.0), seeds):
+        sid = sim.add_species(q, 1.0, w, e, e, e, e, e, e)
+        sim.set_injector(sid, ppc, u, u_th, s)
+    return sim, n, d, dt
+
+
+def test_injector_counts_and_free_streaming_slab(orc):
+    """A cold light beam injected for k steps: exactly floor(k r) particles,
+    r = ppc ny nz v dt / dx; each batch sits where free streaming puts it (the
+    whole inflow fills [0, k v dt) uniformly, no particle outside it), every
+    momentum is the drift, and two species with one seed land on the same
+    points (a neutral inflow)."""
+    sim, n, d, dt = _inject_sim(orc)
+    u = 1.2
+    v = u / math.sqrt(1 + u * u)
+    r = 3.0 * n[1] * n[2] * v * dt / d[0]
+    for k in range(1, 21):
+        sim.step(1)
+        p0, p1 = sim.particles(0), sim.particles(1)
+        assert len(p0["x"]) == len(p1["x"]) == math.floor(k * r)
+    p0, p1 = sim.particles(0), sim.particles(1)
+    assert np.abs(p0["ux"] - u).max() < 1e-9 and np.abs(p0["uy"]).max() < 1e-9
+    assert p0["x"].min() > 0.0 and p0["x"].max() < 20 * v * dt + 1e-9
+    # uniform fill: the count below every depth is proportional to it
+    for depth in (0.25, 0.5, 0.75):
+        frac = (p0["x"] < depth * 20 * v * dt).mean()
+        assert abs(frac - depth) < 0.05, (depth, frac)
+    o0 = np.lexsort((p0["z"], p0["y"], p0["x"]))
+    o1 = np.lexsort((p1["z"], p1["y"], p1["x"]))
+    for k in ("x", "y", "z"):
+        assert np.abs(p0[k][o0] - p1[k][o1]).max() < 1e-9
+    dg = sim.diagnostics()
+    assert abs(dg["charge"]) < 1e-20
+
+
+def test_open_layer_absorbs_an_outgoing_wave(orc):
+    """A transverse vacuum pulse (E_y, B_z) running towards x = 0: with a
+    20-cell layer most of its energy is gone once it has been and come back;
+    with the bare mirror (no layer) the energy stays."""
+    n, d, dt = (48, 4, 4), (0.5, 0.5, 0.5), 0.1
+    out = {}
+    for layer in (False, True):
+        sim = orc.WallSimulation(n, d, dt, shape_order=1, field_solver=orc.EXPLICIT)
+        N = 2 * n[0]
+        xi = np.arange(N, dtype=float)
+        xh = xi + 0.5
+        pulse = lambda x: np.exp(-((x - 30.0) / 3.0) ** 2) * (x < n[0])
+        E = [np.zeros((n[2], n[1], N)) for _ in range(3)]
+        B = [np.zeros((n[2], n[1], N)) for _ in range(3)]
+        E[1][...] = pulse(xi)
+        B[2][...] = -pulse(xh)          # E x B along -x
+        sim.load_fields(E, B)
+        if layer:
+            sim.set_open_boundary(20, 0.3, 0.0)
+        e0 = sim.diagnostics()
+        sim.step(int(round(2 * 30 * d[0] / dt)) + 40)
+        e1 = sim.diagnostics()
+        out[layer] = (e1["energy_E"] + e1["energy_B"]) / (e0["energy_E"] + e0["energy_B"])
+    assert out[False] > 0.95 and out[True] < 0.1, out
+
+
+def test_escape_takes_outgoing_particles_only(orc):
+    """Light particles in empty fields near the open end: those moving out
+    leave at the first step that ends below `escape` cells; those moving in,
+    and everything while no open end is set, stay."""
+    n, d, dt = (16, 4, 4), (0.5, 0.5, 0.5), 0.2
+    sim = orc.WallSimulation(n, d, dt, shape_order=2)
+    x0 = np.array([2.0, 2.0, 3.0])
+    ux = np.array([-1.0, 1.0, -0.5])
+    o = np.array([1.0, 1.0, 1.0])
+    sim.add_species(-1.0, 1.0, 1e-12, x0, o, o, ux, 0 * o, 0 * o)
+    sim.set_open_boundary(8, 0.0, 3.0)
+    v = ux / np.sqrt(1 + ux * ux)
+    for k in range(1, 25):
+        sim.step(1)
+        x = x0 + k * dt * v
+        alive = ~((x < 3.0 * d[0]) & (v < 0))
+        # a particle once gone stays gone
+        if k > 1:
+            alive &= prev
+        assert len(sim.particles(0)["x"]) == alive.sum(), k
+        prev = alive
+    assert alive.tolist() == [False, True, False]
+
+
+def test_window_shifts_content_and_adds_a_layer(orc):
+    """Window at v = 0.6: shifts happen exactly when floor(k v dt / dx) grows;
+    at a shift the fields equal those of an identical run without the window
+    moved up one cell (zero in the new bottom layer), particles moved up by
+    dx, the top layer's particles gone, and a new layer of round(ppc ny nz)
+    injected particles in [0, dx)."""
+    n, d, dt = (12, 4, 4), (0.5, 0.5, 0.5), 0.2
+    L = pp_synth.random_particles(n, d, dt, 300, seed=5, u_scale=0.2)
+    s = L.species[0]
+    runs = []
+    for window in (False, True):
+        sim = orc.WallSimulation(n, d, dt, shape_order=2)
+        sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+        sid = sim.add_species(1.0, 1.0, 0.05, np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0),
+                              np.zeros(0))
+        sim.injectors[sid] = dict(ppc=2.0, u=np.array([0.3, 0.0, 0.0]), u_th=0.1, seed=4, k0=0)
+        E, B = pp_synth.random_fields((2 * n[0], n[1], n[2]), 6, 0.05)
+        sim.load_fields(E, B)
+        if window:
+            sim.set_window(0.6)
+        runs.append(sim)
+    plain, win = runs
+    frac = 0.6 * dt / d[0]
+    shifts = 0
+    for k in range(1, 12):
+        plain.step(1)
+        win.step(1)
+        if math.floor(k * frac) > math.floor((k - 1) * frac):
+            shifts += 1
+            assert win.shifts == shifts
+            # fields: the plain run's, one cell up (physical half), zero at the bottom
+            assert np.abs(win.sim.E[1][..., 1:n[0] + 1] - plain.sim.E[1][..., 0:n[0]]).max() < 1e-12
+            assert np.abs(win.sim.E[1][..., 0]).max() == 0.0
+            assert np.abs(win.sim.E[0][..., 1:n[0]] - plain.sim.E[0][..., 0:n[0] - 1]).max() < 1e-12
+            # the new layer
+            p1 = win.particles(1)
+            fresh = p1["x"] < d[0]
+            assert fresh.sum() >= round(2.0 * n[1] * n[2])
+            break
+    assert shifts == 1
+    # after the shift the window run's particles are the plain run's moved up by dx
+    pw, pp_ = win.particles(0), plain.particles(0)
+    xs = np.sort(pp_["x"] + d[0])
+    xs = xs[xs <= n[0] * d[0]]
+    assert np.abs(np.sort(pw["x"]) - xs).max() < 1e-12
