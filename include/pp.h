@@ -149,7 +149,9 @@ typedef struct {
     double gauss_drift_max;    /* max |G - G_0|, G_0 taken at the first load      */
     double divB_max;           /* max |div^+ B|                                    */
     double relax_residual;     /* max|(1 - a^2 dt^2 L)B - rhs| / max|rhs|, last solve
-                                  (with the B a divergence filter left after it)    */
+                                  (with the B a divergence filter, an outflow layer
+                                  or a window shift left after it; PP_ENOCONV is
+                                  then not raised from it)                          */
     int relax_iters;           /* relaxation sweeps of the last solve             */
     int status;                /* PP_* code of the device status word             */
     int64_t n_particles;       /* all species                                      */
@@ -261,6 +263,51 @@ int pp_set_current_deposit(pp_ctx *ctx, int mode);
  * default) turns it off.  Errors: PP_EINVAL for passes < 0 or interval < 1. */
 int pp_set_divergence_filter(pp_ctx *ctx, int passes, int interval);
 
+/* ---- open end, injector and sliding window (PP_BOUNDARY_WALLS only) -------
+ * Sec. II "Boundary conditions" (outflow) and "Sliding window and injection
+ * of particles".  The upper wall at x = L stays a reflecting wall; the lower
+ * end x = 0 becomes open.  pp_step applies them after each full step, in this
+ * order: damping of the layer, injection, window shift (the particles that
+ * leave through the open end do so in the step's own particle pass).  Steps of
+ * a context that uses any of them run eagerly (no step graphs) and
+ * synchronise at every sort.  A particle that leaves keeps its slot until the
+ * next sort; pp_get_count, pp_get_particles, pp_diagnostics and pp_save sort
+ * first when one may have left.  Errors of all three: PP_EINVAL without walls
+ * or for a value outside the stated range. */
+
+/* Outflow layer at x = 0: every step the field components chosen by
+ * `components` (bit a = E_a, bit 3 + a = B_a; the paper damps those
+ * perpendicular to the boundary normal, E_y E_z B_y B_z = 0x36) are multiplied
+ * by 1 - damping ((cells - d) / cells)^2 at distance d < cells from x = 0,
+ * taken at each component's staggered position; a particle that ends a step
+ * closer than `escape` cells to x = 0 and moving outward (u_x < 0) leaves the
+ * box; until then it deposits like any other.  The paper gives no profile and
+ * uses about 20 cells.  cells in [0, nx] (0 = closed again: the reflecting
+ * wall), damping in [0, 1], escape in [0, nx] (cells), components < 64. */
+int pp_set_open_boundary(pp_ctx *ctx, int cells, double damping, double escape, int components);
+
+/* Inflow of species sid through the open end x = 0: at the k-th step after
+ * this call, floor(k r) - floor((k-1) r) particles, r = ppc ny nz v_x dt / dx
+ * with v the drift velocity (the flux of a density of ppc per cell), uniform
+ * in [0, v_x dt) x [0, Ly) x [0, Lz), with proper velocity u + u_th (three
+ * standard normals).  Draws: Philox4x32-10 (Salmon et al., SC'11) keyed by
+ * the seed; positions come from one stream for all species, so two species
+ * injected with the same ppc, drift and seed enter at the same points (a
+ * neutral inflow keeps Gauss's law).  The sliding window also fills its new
+ * bottom layer from the injectors: round(ppc ny nz) particles uniform in
+ * [0, dx) per species.  ppc = 0 turns it off.  PP_ENOMEM from pp_step when an
+ * injection would exceed the species' capacity. */
+int pp_set_injector(pp_ctx *ctx, int sid, double ppc, const double u[3], double u_th, uint64_t seed);
+
+/* Sliding window moving at speed v (0 <= v < c) against x: whenever the
+ * window has travelled a further cell, v (t - t_set) / dx passing an integer
+ * (so its mean speed is v), the content of the box moves one cell up in x:
+ * fields shift (zero in the new bottom layer), particles move up by dx, those
+ * that pass the top wall leave, the injectors fill the bottom layer, and the
+ * species are re-sorted.  The current J is left as the last deposit made it.
+ * v = 0 turns it off. */
+int pp_set_sliding_window(pp_ctx *ctx, double v);
+
 /* Append n macro-particles to species sid (eq:pseudop): positions x,y,z
  * (physical, any real value: wrapped periodically into the box) and proper
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
@@ -334,7 +381,9 @@ int pp_get_count(pp_ctx *ctx, int sid, int64_t *n);
 
 /* FP64 host copies of species sid (positions physical in [0, L), proper
  * velocities), each array of pp_get_count values, in the library's current
- * (cell-sorted) order. */
+ * (cell-sorted) order.  Particles that left through an open end or a sliding
+ * window are dropped first (a sort), so call pp_get_count before sizing the
+ * arrays. */
 int pp_get_particles(pp_ctx *ctx, int sid, double *x, double *y, double *z, double *ux, double *uy,
                      double *uz);
 

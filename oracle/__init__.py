@@ -545,12 +545,22 @@ class WallSimulation:
             self._append(sid, self._draw_particles(inj, sid, count, self.shifts, 16, self.d[0]))
 
     def step(self, n: int = 1):
+        """Each step: the periodic step of the extended box, then the particles
+        that left through the open end go (they moved out in this step's push),
+        then the divergence filter when due (its rho without them), the layer's
+        damping, the inflow, and the window shift."""
         for _ in range(n):
+            passes = self.sim.filter_passes
+            self.sim.filter_passes = 0
             self.sim.step(1)
+            self.sim.filter_passes = passes
             self.nstep += 1
             if self.open is not None:
-                self._damp()
                 self._escape()
+            if passes and self.sim.nstep % self.sim.filter_interval == 0:
+                self.sim.divergence_filter(passes)
+            if self.open is not None:
+                self._damp()
             for sid in sorted(self.injectors):
                 self._inject(sid)
             if self.window is not None:

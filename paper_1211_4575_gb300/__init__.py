@@ -32,6 +32,7 @@ PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
 PP_FIELD_IMPLICIT, PP_FIELD_EXPLICIT = 0, 1
 PP_CURRENT_CONSERVING, PP_CURRENT_DIRECT = 0, 1
 PP_BOUNDARY_PERIODIC, PP_BOUNDARY_WALLS = 0, 1
+TRANSVERSE = 0x36   # damped components of the outflow layer: E_y, E_z, B_y, B_z
 PP_MAX_SPECIES = 8
 PP_BATCH_FREE, PP_BATCH_RUNNING, PP_BATCH_DONE, PP_BATCH_FAILED = 0, 1, 2, 3
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOCONV", 7: "ECFL", 8: "ENAN",
@@ -82,6 +83,9 @@ SIGNATURES = {
     "pp_set_field_solver": (C.c_int, [_P, C.c_int]),
     "pp_set_current_deposit": (C.c_int, [_P, C.c_int]),
     "pp_set_divergence_filter": (C.c_int, [_P, C.c_int, C.c_int]),
+    "pp_set_open_boundary": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int]),
+    "pp_set_injector": (C.c_int, [_P, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_double, C.c_uint64]),
+    "pp_set_sliding_window": (C.c_int, [_P, C.c_double]),
     "pp_set_graphs": (C.c_int, [_P, C.c_int]),
     "pp_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pp_load_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int]),
@@ -256,6 +260,20 @@ class Simulation:
     def set_divergence_filter(self, passes, interval=1):
         """passes filter passes on E and B after every interval-th step (0 = off)."""
         self._c(lib().pp_set_divergence_filter(self._ctx, int(passes), int(interval)))
+
+    def set_open_boundary(self, cells, damping, escape, components=TRANSVERSE):
+        """Outflow layer of `cells` cells at x = 0 between walls (0 = closed)."""
+        self._c(lib().pp_set_open_boundary(self._ctx, int(cells), float(damping), float(escape), int(components)))
+
+    def set_injector(self, sid, ppc, u, u_th=0.0, seed=0):
+        """Inflow of species sid through x = 0: ppc per cell, drift proper
+        velocity u (u[0] > 0), thermal spread u_th, Philox seed (0 ppc = off)."""
+        uu = (C.c_double * 3)(*[float(v) for v in u])
+        self._c(lib().pp_set_injector(self._ctx, int(sid), float(ppc), uu, float(u_th), int(seed) & (2 ** 64 - 1)))
+
+    def set_sliding_window(self, v):
+        """Sliding window at speed v against x (0 = off)."""
+        self._c(lib().pp_set_sliding_window(self._ctx, float(v)))
 
     def set_radiative_cooling(self, sid, coef):
         """Radiative cooling coefficient mu0 q^2 / (6 pi m c) of species sid (0 = off)."""

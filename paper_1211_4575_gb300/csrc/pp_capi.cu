@@ -260,6 +260,7 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     chk(cudaMalloc(&c->d_status, sizeof(int)), "status");
     if (rc == PP_OK) chk(cudaMemset(c->d_status, 0, sizeof(int)), "status clear");
     chk(cudaMallocHost(&c->h_status, sizeof(int)), "status mirror");
+    chk(cudaMallocHost(&c->h_count, sizeof(int32_t)), "count mirror");
     chk(cudaMalloc(&c->d_red, sizeof(double) * 512 * 16), "reduction partials");
     chk(cudaMalloc(&c->d_out, sizeof(double) * (16 + PP_MAX_SPECIES)), "reduction results");
     chk(cudaMalloc(&c->d_nslow, sizeof(unsigned long long)), "fallback counter");
@@ -311,6 +312,7 @@ extern "C" int pp_destroy(pp_ctx *p) {
     cudaFree(c->d_nslow);
     cudaFree(c->d_slow_count);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_count) cudaFreeHost(c->h_count);
     for (int q = 0; q < c->prof_cap; ++q) {
         cudaEventDestroy(c->prof_ev[q].a);
         cudaEventDestroy(c->prof_ev[q].b);
@@ -646,12 +648,91 @@ extern "C" int pp_sort(pp_ctx *p) {
 // field phases (four kick-drift substeps for the 4th-order integrator).  Only
 // enqueues work; the host state it changes is the J / J' and particle buffer
 // swaps, the sorted flags and the last solve's iteration data.
+// Open end, injectors or a sliding window: steps change the particle count on
+// the host and synchronise at sorts, so they run eagerly.
+static bool boundary_dynamic(const Ctx *c) {
+    if (!c->mirror) return false;
+    if (c->open.cells > 0 || c->window.v > 0.0) return true;
+    for (int s = 0; s < c->nspecies; ++s)
+        if (c->inj[s].ppc > 0.0) return true;
+    return false;
+}
+
+// Drop the particles that left the box (a sort of each species that may hold
+// some; synchronises).
+static int compact(Ctx *c) {
+    for (int s = 0; s < c->nspecies; ++s)
+        if (c->sp[s].may_hold_dead) CU(launch_sort(*c, s));
+    return PP_OK;
+}
+
+// Drift velocity along x of injector s.
+static double inj_vx(const Ctx::Injector &I) {
+    return I.u[0] / sqrt(1.0 + I.u[0] * I.u[0] + I.u[1] * I.u[1] + I.u[2] * I.u[2]);
+}
+
+// What the open end, the injectors and the window do after a step (Sec. II,
+// outflow and injection; readings of the outflow layer, the injector and the
+// window in the header): damp the layer (outgoing particles already left in
+// the particle pass), inject the inflow of the step, and shift the window when
+// it has moved a cell.
+static int boundary_step(Ctx *c) {
+    if (c->open.cells > 0 && c->open.mask) {
+        CU(launch_damp(*c));
+        c->filtered_after_solve = true;   // B moved since the solve: its residual no longer measures it
+    }
+    const double ny = c->g.n[1], nz = c->g.n[2];
+    for (int s = 0; s < c->nspecies; ++s) {
+        const Ctx::Injector &I = c->inj[s];
+        if (!(I.ppc > 0.0)) continue;
+        const double vx = inj_vx(I);
+        const double rate = I.ppc * ny * nz * vx * c->d.dt / c->d.dx;
+        const int64_t k = c->step - I.k0;
+        const int64_t count = (int64_t)(floor((double)k * rate) - floor((double)(k - 1) * rate));
+        Species &S = c->sp[s];
+        if (S.n + count > S.limit)
+            return fail(c, PP_ENOMEM, "injector of species %d: capacity %lld exceeded", s, (long long)S.limit);
+        CU(launch_inject(*c, s, S.n, count, (uint32_t)c->step, 0u, vx * c->d.dt));
+        S.n += count;
+    }
+    if (c->window.v > 0.0) {
+        const double f = c->window.v * c->d.dt / c->d.dx;
+        const int64_t k = c->step - c->window.k0;
+        if (floor((double)k * f) > floor((double)(k - 1) * f)) {
+            ++c->window.shifts;
+            CU(launch_window_fields(*c));
+            c->filtered_after_solve = true;
+            for (int s = 0; s < c->nspecies; ++s) {
+                CU(launch_window_particles(*c, s));
+                c->sp[s].may_hold_dead = true;
+            }
+            for (int s = 0; s < c->nspecies; ++s) {
+                const Ctx::Injector &I = c->inj[s];
+                if (!(I.ppc > 0.0)) continue;
+                const int64_t count = (int64_t)floor(I.ppc * ny * nz + 0.5);
+                Species &S = c->sp[s];
+                if (S.n + count > S.limit)
+                    return fail(c, PP_ENOMEM, "window layer of species %d: capacity %lld exceeded", s,
+                                (long long)S.limit);
+                CU(launch_inject(*c, s, S.n, count, (uint32_t)c->window.shifts, 16u, c->d.dx));
+                S.n += count;
+            }
+            if (int r = pp_sort(static_cast<pp_ctx *>(c))) return r;   // cells moved: re-tile
+        }
+    }
+    return PP_OK;
+}
+
 static int step_body(Ctx *c, bool sort, bool filter) {
     if (sort) {
         int r = pp_sort(static_cast<pp_ctx *>(c));
         if (r) return r;
     }
     int r = PP_OK;
+    // the open end takes outgoing particles at the end of a full step
+    const double esc = (c->mirror && c->open.cells > 0) ? c->open.escape : 0.0;
+    if (esc > 0.0)
+        for (int s = 0; s < c->nspecies; ++s) c->sp[s].may_hold_dead = true;
     if (c->order == 4) {
         double a[4], b[4];
         step4_fractions(a, b);
@@ -659,15 +740,18 @@ static int step_body(Ctx *c, bool sort, bool filter) {
             c->kick_dt = b[i] * c->d.dt;
             c->drift_dt = a[i] * c->d.dt;
             c->cheb_sel = (i == 0 || i == 3) ? 1 : 2;
+            c->escape_now = i == 3 ? esc : 0.0;
             r = particle_phase(c, -1);
             if (r == PP_OK) r = field_phase(c);
         }
         c->kick_dt = c->drift_dt = c->d.dt;
         c->cheb_sel = 0;
     } else {
+        c->escape_now = esc;
         r = particle_phase(c, -1);
         if (r == PP_OK) r = field_phase(c);
     }
+    c->escape_now = 0.0;
     if (r == PP_OK && filter) {
         NvtxRange nvtx("pp divergence filter");
         CU(launch_divergence_filter(*c));
@@ -788,10 +872,12 @@ extern "C" int pp_step(pp_ctx *p, int nsteps) {
     for (int it = 0; it < nsteps; ++it) {
         bool sort = c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval;
         bool filter = c->filter_passes > 0 && (c->step + 1) % c->filter_interval == 0;
-        int r = (c->use_graphs && !c->prof && c->st) ? step_graph(c, sort, filter) : step_body(c, sort, filter);
+        const bool dyn = boundary_dynamic(c);
+        int r = (c->use_graphs && !c->prof && c->st && !dyn) ? step_graph(c, sort, filter) : step_body(c, sort, filter);
         if (r) return r;
         ++c->step;
         ++c->since_sort;
+        if (dyn && (r = boundary_step(c)) != PP_OK) return r;
     }
     return PP_OK;
 }
@@ -840,10 +926,57 @@ extern "C" int pp_set_divergence_filter(pp_ctx *p, int passes, int interval) {
     return PP_OK;
 }
 
+extern "C" int pp_set_open_boundary(pp_ctx *p, int cells, double damping, double escape, int components) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (!c->mirror) return fail(c, PP_EINVAL, "an open end needs boundary_x = PP_BOUNDARY_WALLS");
+    if (cells < 0 || cells > c->mirror) return fail(c, PP_EINVAL, "layer of %d cells outside [0, nx]", cells);
+    if (!(damping >= 0.0 && damping <= 1.0)) return fail(c, PP_EINVAL, "damping must lie in [0, 1]");
+    if (!(escape >= 0.0 && escape <= (double)c->mirror)) return fail(c, PP_EINVAL, "escape must lie in [0, nx]");
+    if (components < 0 || components > 63) return fail(c, PP_EINVAL, "components is a 6-bit mask");
+    c->open.cells = cells;
+    c->open.damping = damping;
+    c->open.escape = escape;
+    c->open.mask = components;
+    graphs_clear(c);
+    return PP_OK;
+}
+
+extern "C" int pp_set_injector(pp_ctx *p, int sid, double ppc, const double u[3], double u_th, uint64_t seed) {
+    Ctx *c = p;
+    if (!c || !u) return fail(c, PP_EINVAL, "pp_set_injector: NULL argument");
+    if (!c->mirror) return fail(c, PP_EINVAL, "an injector needs boundary_x = PP_BOUNDARY_WALLS");
+    if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    if (!(ppc >= 0.0 && ppc < 1e6) || !(u_th >= 0.0 && u_th < 1e6) || !isfinite(u[0]) || !isfinite(u[1]) ||
+        !isfinite(u[2]))
+        return fail(c, PP_EINVAL, "injector needs 0 <= ppc, 0 <= u_th and a finite drift");
+    if (ppc > 0.0 && !(u[0] > 0.0)) return fail(c, PP_EINVAL, "the inflow must move into the box (u_x > 0)");
+    Ctx::Injector &I = c->inj[sid];
+    I.ppc = ppc;
+    for (int a = 0; a < 3; ++a) I.u[a] = u[a];
+    I.u_th = u_th;
+    I.seed = seed;
+    I.k0 = c->step;
+    graphs_clear(c);
+    return PP_OK;
+}
+
+extern "C" int pp_set_sliding_window(pp_ctx *p, double v) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (!c->mirror) return fail(c, PP_EINVAL, "a sliding window needs boundary_x = PP_BOUNDARY_WALLS");
+    if (!(v >= 0.0 && v < 1.0)) return fail(c, PP_EINVAL, "window speed must lie in [0, c)");
+    c->window.v = v;
+    c->window.k0 = c->step;
+    graphs_clear(c);
+    return PP_OK;
+}
+
 extern "C" int pp_set_graphs(pp_ctx *p, int enable) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (enable && !c->st) return fail(c, PP_EINVAL, "step graphs need a context stream other than the legacy default");
+    if (int r = compact(c)) return r;   // a capture holds no synchronisation
     c->use_graphs = enable != 0;
     if (!enable) graphs_clear(c);
     return PP_OK;
@@ -920,6 +1053,7 @@ extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
     Ctx *c = p;
     if (!c || !out) return fail(c, PP_EINVAL, "pp_diagnostics: NULL argument");
     if (int r = ensure_gauss_reference(c)) return r;
+    if (int r = compact(c)) return r;
     int st = pp_sync(p);
     memset(out, 0, sizeof(*out));
     out->status = st;
@@ -1003,6 +1137,7 @@ extern "C" int pp_get_count(pp_ctx *p, int sid, int64_t *n) {
     Ctx *c = p;
     if (!c || !n) return fail(c, PP_EINVAL, "pp_get_count: NULL argument");
     if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    if (int r = compact(c)) return r;
     *n = c->sp[sid].n;
     return PP_OK;
 }
@@ -1012,6 +1147,7 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    if (int r = compact(c)) return r;
     Species &S = c->sp[sid];
     if (S.n == 0) return PP_OK;
     if (!x || !y || !z || !ux || !uy || !uz) return fail(c, PP_EINVAL, "NULL particle array");
@@ -1036,11 +1172,12 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // Format 2 adds each species' radiative-cooling coefficient, format 3 the
 // integrator order, format 4 the field solver, format 5 the current deposit
 // and the divergence filter; older files restore with the defaults.
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '6'};
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '7'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
     if (!c || !path) return fail(c, PP_EINVAL, "pp_save: NULL argument");
+    if (int r = compact(c)) return r;   // counts written below must be final
     FILE *f = fopen(path, "wb");
     if (!f) return fail(c, PP_EINVAL, "cannot open %s for writing", path);
     int64_t N = c->g.cells();
@@ -1069,6 +1206,9 @@ extern "C" int pp_save(pp_ctx *p, const char *path) {
             ok = rc == PP_OK && fwrite(pb.data(), sizeof(double), pb.size(), f) == pb.size();
         }
     }
+    // format 7: open end, window and injectors
+    ok = ok && fwrite(&c->open, sizeof c->open, 1, f) == 1 && fwrite(&c->window, sizeof c->window, 1, f) == 1;
+    for (int s = 0; s < c->nspecies && ok; ++s) ok = fwrite(&c->inj[s], sizeof c->inj[s], 1, f) == 1;
     if (fclose(f) != 0) ok = false;
     if (!ok) return rc != PP_OK ? rc : fail(c, PP_EINVAL, "write to %s failed", path);
     return PP_OK;
@@ -1087,7 +1227,7 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     int order = 2, solver = PP_FIELD_IMPLICIT, cmode = PP_CURRENT_CONSERVING, fpasses = 0, finterval = 1;
     // formats 1-5 wrote the descriptor without its last member (boundary_x)
     memset(&d, 0, sizeof d);
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '6' &&
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '7' &&
               fread(&d, magic[7] >= '6' ? sizeof d : offsetof(pp_grid_desc, boundary_x), 1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
               ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1) &&
@@ -1125,6 +1265,24 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
         if (rc == PP_OK && ok && n)
             rc = pp_load_particles(p, sid, n, pb.data(), pb.data() + n, pb.data() + 2 * n, pb.data() + 3 * n,
                                    pb.data() + 4 * n, pb.data() + 5 * n, 0);
+    }
+    if (ok && rc == PP_OK && magic[7] >= '7') {
+        Ctx::OpenEnd open;
+        Ctx::Window window;
+        ok = fread(&open, sizeof open, 1, f) == 1 && fread(&window, sizeof window, 1, f) == 1;
+        if (ok && c->mirror) {   // validated through the setters, then the run's state taken over
+            rc = pp_set_open_boundary(p, open.cells, open.damping, open.escape, open.mask);
+            if (rc == PP_OK) rc = pp_set_sliding_window(p, window.v);
+            c->window = window;
+        }
+        for (int s = 0; s < ns && ok && rc == PP_OK; ++s) {
+            Ctx::Injector I;
+            ok = fread(&I, sizeof I, 1, f) == 1;
+            if (ok && c->mirror) {
+                rc = pp_set_injector(p, s, I.ppc, I.u, I.u_th, I.seed);
+                c->inj[s] = I;
+            }
+        }
     }
     fclose(f);
     if (!ok || rc != PP_OK) {

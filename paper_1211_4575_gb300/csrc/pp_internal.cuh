@@ -31,6 +31,12 @@ struct Geom {
     __host__ __device__ __forceinline__ int64_t cells() const { return (int64_t)n[0] * n[1] * n[2]; }
 };
 
+// A particle that left the box (through an open end or the top layer of a
+// sliding window) stays in its slot until the next sort drops it: the mixed
+// form sets the sign bit of its packed cell, the FP64 form a negative x.
+constexpr int32_t kDeadBit = (int32_t)0x80000000u;
+constexpr double kDeadX = -1.0;
+
 // Wrap an index that lies within a few periods of [0, n).
 __host__ __device__ __forceinline__ int wrap(int i, int n) {
     while (i < 0) i += n;
@@ -428,6 +434,9 @@ struct Species {
     // PP_MIXED32: packed cell (x | y << 10 | z << 20) + FP32 offsets and momenta
     int32_t *cell = nullptr;
     float *ox = nullptr, *oy = nullptr, *oz = nullptr, *fux = nullptr, *fuy = nullptr, *fuz = nullptr;
+    int64_t nsorted = 0;      // particles [0, nsorted) are in cell_start's ranges; the rest
+                              // (injected since the last sort) form an unsorted tail
+    bool may_hold_dead = false;   // particles may have left (escape, window) since the last sort
     void *buf = nullptr;      // primary particle storage
     void *alt = nullptr;      // sort target of the same layout
     int32_t *keys = nullptr;  // sort keys
@@ -514,6 +523,29 @@ struct Ctx {
     // Reflecting walls at x = 0 and x = mirror (cells): the mesh is the
     // mirror-extended box, g.n[0] = 2 * mirror.  0 = periodic in x.
     int mirror = 0;
+    // Open lower end between walls (outflow layer, escape), injectors and the
+    // sliding window (Sec. II "Boundary conditions", "Sliding window and
+    // injection of particles").
+    struct OpenEnd {
+        int cells = 0;           // damping layer width; 0 = no open end
+        double damping = 0.0;    // factor 1 - damping ((cells - d) / cells)^2 per step
+        double escape = 0.0;     // outgoing particles closer than this (cells) leave
+        int mask = 0;            // damped components: bit a = E_a, bit 3 + a = B_a
+    } open;
+    struct Injector {
+        double ppc = 0.0;        // particles per cell of the inflow; 0 = off
+        double u[3] = {0, 0, 0}; // drift proper velocity
+        double u_th = 0.0;
+        uint64_t seed = 0;
+        int64_t k0 = 0;          // step at which it was set
+    } inj[PP_MAX_SPECIES];
+    struct Window {
+        double v = 0.0;          // speed against x; 0 = off
+        int64_t k0 = 0;
+        int64_t shifts = 0;
+    } window;
+    int32_t *h_count = nullptr;  // pinned: live count read back after a compacting sort
+    double escape_now = 0.0;     // escape distance the particle kernels apply (0: none this pass)
     int filter_passes = 0;   // divergence-filter passes every filter_interval steps
     int filter_interval = 1;
     double filter_tau = 0;   // 1 / largest eigenvalue of -div grad
@@ -576,6 +608,10 @@ cudaError_t launch_ghost_fill(Ctx &c, void *const src_E[3], void *const src_B[3]
 cudaError_t launch_mesh_diag(Ctx &c, double *host_out /* 9 values */);
 
 cudaError_t launch_sort(Ctx &c, int s);
+cudaError_t launch_damp(Ctx &c);
+cudaError_t launch_inject(Ctx &c, int s, int64_t off, int64_t count, uint32_t step, uint32_t pstream, double thick);
+cudaError_t launch_window_fields(Ctx &c);
+cudaError_t launch_window_particles(Ctx &c, int s);
 cudaError_t sort_setup(Ctx &c);
 
 cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const double *x, const double *y,

@@ -167,6 +167,109 @@ cudaError_t launch_mirror_rho(Ctx &c, double *rho) {
 }
 
 // ---------------------------------------------------------------------------
+// Open lower end (Sec. II "Boundary conditions", outflow): each step the
+// chosen components are multiplied by 1 - damping ((cells - d) / cells)^2 at
+// distance d < cells from x = 0, d taken at the component's staggered
+// position, on both sides of that mirror plane so that the extended mesh stays
+// symmetric.  Columns: the first `cells` x-indices and the last `cells`.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_damp(Geom g, R *F, int half, int cells, double damping) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cols = 2 * cells;
+    if (t >= (int64_t)cols * g.n[1] * g.n[2]) return;
+    const int c = (int)(t % cols);
+    const int64_t r = t / cols;
+    const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+    const int N = g.n[0];
+    const int i = c < cells ? c : N - 2 * cells + c;
+    const double pos = i + (half ? 0.5 : 0.0);
+    const double d = fmin(pos, N - pos);
+    if (d >= cells) return;
+    const double s = (cells - d) / cells;
+    F[g.at(i, j, k)] *= (R)(1.0 - damping * s * s);
+}
+
+template <typename R>
+static cudaError_t damp_impl(Ctx &c) {
+    const int cells = c.open.cells;
+    void **groups[2] = {c.E, c.B};
+    const int half[2] = {1, 6};   // staggered in x: E_x; B_y, B_z
+    const unsigned blocks = (unsigned)(((int64_t)2 * cells * c.g.n[1] * c.g.n[2] + 255) / 256);
+    for (int f = 0; f < 2; ++f)
+        for (int comp = 0; comp < 3; ++comp) {
+            if (!((c.open.mask >> (3 * f + comp)) & 1)) continue;
+            k_damp<R><<<blocks, 256, 0, c.st>>>(c.g, (R *)groups[f][comp], (half[f] >> comp) & 1, cells,
+                                                c.open.damping);
+            ++c.nlaunch;
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    return launch_ghost_fill(c, c.E, c.B);
+}
+
+cudaError_t launch_damp(Ctx &c) {
+    if (!c.mirror || c.open.cells <= 0 || !c.open.mask) return cudaSuccess;
+    return c.fp64 ? damp_impl<double>(c) : damp_impl<float>(c);
+}
+
+// ---------------------------------------------------------------------------
+// Sliding window (Sec. II "Sliding window and injection of particles"): the
+// content of the box moves one cell up in x.  In the physical half a node takes
+// the value of the node one cell below (zero for the new bottom node); a node
+// of the mirror half takes P times the new value of its image.  Written into
+// scratch arrays, which then swap with E and B.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_window_fields(Geom g, int nw, const R *I0, const R *I1, const R *I2, R *O0, R *O1, R *O2,
+                                int odd_mask) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int comp = blockIdx.y;
+    if (t >= g.cells()) return;
+    const int i = (int)(t % g.n[0]);
+    const int64_t r = t / g.n[0];
+    const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+    const bool odd = (odd_mask >> comp) & 1;
+    const R *in = comp == 0 ? I0 : (comp == 1 ? I1 : I2);
+    R *out = comp == 0 ? O0 : (comp == 1 ? O1 : O2);
+    const int top = odd ? nw - 1 : nw;   // last node of the physical half
+    int src = i;
+    R sign = R(1);
+    if (i > top) {                        // mirror half: the image node
+        src = odd ? 2 * nw - 1 - i : 2 * nw - i;
+        sign = odd ? R(-1) : R(1);
+    }
+    out[g.at(i, j, k)] = src == 0 ? R(0) : sign * in[g.at(src - 1, j, k)];
+}
+
+template <typename R>
+static cudaError_t window_fields_impl(Ctx &c) {
+    dim3 grid((unsigned)((c.g.cells() + 255) / 256), 3);
+    void **F[2] = {c.E, c.B};
+    void **S[2] = {c.Xa, c.Xb};
+    const int odd[2] = {1, 6};
+    for (int f = 0; f < 2; ++f) {
+        k_window_fields<R><<<grid, 256, 0, c.st>>>(c.g, c.mirror, (const R *)F[f][0], (const R *)F[f][1],
+                                                   (const R *)F[f][2], (R *)S[f][0], (R *)S[f][1], (R *)S[f][2],
+                                                   odd[f]);
+        ++c.nlaunch;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        for (int a = 0; a < 3; ++a) {
+            void *t = F[f][a];
+            F[f][a] = S[f][a];
+            S[f][a] = t;
+        }
+    }
+    return launch_ghost_fill(c, c.E, c.B);
+}
+
+cudaError_t launch_window_fields(Ctx &c) {
+    if (!c.mirror) return cudaSuccess;
+    return c.fp64 ? window_fields_impl<double>(c) : window_fields_impl<float>(c);
+}
+
+// ---------------------------------------------------------------------------
 // High-order current: along the axis of each component, J_out = P^{-1} J_in
 // with P the symmetric cyclic line operator (c, b+c, a+b+c, b+c, c) that
 // turns the 2nd-order difference into the high-order one; applied as the

@@ -50,6 +50,8 @@ struct StepArgs {
     int *status;
     int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
     int mirror;                  // walls at x = 0 and x = mirror cells; 0 = periodic
+    double esc;                  // open end: outgoing particles below x = esc cells leave; 0 = off
+    int64_t off;                 // first particle of the launch
 };
 
 struct Fp64Particles {
@@ -96,6 +98,8 @@ template <int O, int PUSH>
 __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64Particles p) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.n) return;
+    t += a.off;
+    if (p.x[t] < 0.0) return;   // left the box
     double xi0[3] = {p.x[t], p.y[t], p.z[t]};
     double u[3] = {p.ux[t], p.uy[t], p.uz[t]};
     GlobalAcc<double> acc{a.g, {a.E[0], a.E[1], a.E[2]}, {a.B[0], a.B[1], a.B[2]}, {a.J[0], a.J[1], a.J[2]}, 0, 0, 0};
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
         xi1[d] = v;
     }
     reflect(xi1[0], u[0], a.mirror);
+    if (a.esc > 0.0 && xi1[0] < a.esc && u[0] < 0.0) xi1[0] = kDeadX;   // out through the open end
     p.x[t] = xi1[0]; p.y[t] = xi1[1]; p.z[t] = xi1[2];
     p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
 }
@@ -164,6 +169,8 @@ template <int O, int PUSH>
 __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, MixedParticles p) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.n) return;
+    t += a.off;
+    if (p.cell[t] < 0) return;   // left the box
     int cx, cy, cz;
     unpack_cell(p.cell[t], cx, cy, cz);
     float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
@@ -195,7 +202,9 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
     rebin(xi1[1], cy, a.g.n[1]);
     rebin(xi1[2], cz, a.g.n[2]);
     reflect(cx, xi1[0], u[0], a.mirror);
-    p.cell[t] = pack_cell(cx, cy, cz);
+    int32_t cw = pack_cell(cx, cy, cz);
+    if (a.esc > 0.0 && (double)cx + (double)xi1[0] < a.esc && u[0] < 0.0f) cw |= kDeadBit;
+    p.cell[t] = cw;
     p.ox[t] = xi1[0]; p.oy[t] = xi1[1]; p.oz[t] = xi1[2];
     p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
 }
@@ -221,6 +230,8 @@ static StepArgs<R> step_args(Ctx &c, int s) {
     a.status = c.d_status;
     a.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
     a.mirror = c.mirror;
+    a.esc = c.escape_now;
+    a.off = 0;
     return a;
 }
 
@@ -378,6 +389,7 @@ struct TiledArgs {
     int *status;
     int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
     int mirror;                  // walls at x = 0 and x = mirror cells; 0 = periodic
+    double esc;                  // open end: outgoing particles below x = esc cells leave; 0 = off
 };
 
 __device__ __forceinline__ int min_image(int d, int n) {
@@ -460,6 +472,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 const int q = 32 * (warp + kWarps * r) + lane;
                 if (q >= cn) continue;
                 const int sq = q + (q >> 5);
+                if (s_cell[sq] < 0) {   // left the box: kept as it is until the next sort
+                    s_d[sq] = __int_as_float(0x7fc00000);
+                    continue;
+                }
                 int cx, cy, cz;
                 unpack_cell(s_cell[sq], cx, cy, cz);
                 float xi0[3] = {s_o[sq], s_o[kStage + sq], s_o[2 * kStage + sq]};
@@ -540,7 +556,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 rebin(xi1[1], cy, g.n[1]);
                 rebin(xi1[2], cz, g.n[2]);
                 if (T.mirror) reflect(cx, xi1[0], s_u[sq], T.mirror);
-                s_cell[sq] = pack_cell(cx, cy, cz);
+                int32_t cw = pack_cell(cx, cy, cz);
+                if (T.esc > 0.0 && (double)cx + (double)xi1[0] < T.esc && s_u[sq] < 0.0f) cw |= kDeadBit;
+                s_cell[sq] = cw;
                 s_o[sq] = xi1[0]; s_o[kStage + sq] = xi1[1]; s_o[2 * kStage + sq] = xi1[2];
             };
             // Most particles cross no support boundary in a step: they deposit
@@ -638,6 +656,7 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
     if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(nslow, (unsigned long long)n);
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int t = list[k];
+        if (p.cell[t] < 0) continue;
         int cx, cy, cz;
         unpack_cell(p.cell[t], cx, cy, cz);
         float xi0[3] = {p.ox[t], p.oy[t], p.oz[t]};
@@ -669,7 +688,9 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
         rebin(xi1[1], cy, a.g.n[1]);
         rebin(xi1[2], cz, a.g.n[2]);
         reflect(cx, xi1[0], u[0], a.mirror);
-        p.cell[t] = pack_cell(cx, cy, cz);
+        int32_t cw = pack_cell(cx, cy, cz);
+        if (a.esc > 0.0 && (double)cx + (double)xi1[0] < a.esc && u[0] < 0.0f) cw |= kDeadBit;
+        p.cell[t] = cw;
         p.ox[t] = xi1[0]; p.oy[t] = xi1[1]; p.oz[t] = xi1[2];
         p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
     }
@@ -702,8 +723,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
     if (e0 != cudaSuccess) return e0;
     for (int s = 0; s < c.nspecies; ++s) {
         const Species &S = c.sp[s];
-        if (S.n == 0) continue;
-        if (!S.sorted) return cudaErrorInvalidConfiguration;
+        if (S.n == 0 || !S.sorted) continue;   // never sorted (only injected into): all of it is the tail
         sid[T.ns] = s;
         TiledSpecies &t = T.sp[T.ns++];
         t.p = MixedParticles{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
@@ -720,13 +740,15 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         t.lane_shift = sh;
         for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.drift_dt);
     }
-    if (T.ns == 0) return cudaSuccess;
     T.status = c.d_status;
     T.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
     T.mirror = c.mirror;
+    T.esc = c.escape_now;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
     static bool attr_done[2][4] = {{false}};
+    cudaError_t e = cudaSuccess;
+    if (T.ns > 0) {
 #define PP_T(O, PU)                                                                                         \
     do {                                                                                                    \
         if (!attr_done[PU][O]) {                                                                            \
@@ -743,9 +765,9 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         if (o == 1) PP_T(1, PP_VAY); else if (o == 2) PP_T(2, PP_VAY); else PP_T(3, PP_VAY);
     }
 #undef PP_T
-    ++c.nlaunch;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // the left-out particles of every species, on a fixed grid (count read on the device)
     for (int k = 0; k < T.ns; ++k) {
         const Species &S = c.sp[sid[k]];
@@ -762,7 +784,166 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    // particles injected since the sort (or into a never-sorted species): through the global mesh
+    for (int s = 0; s < c.nspecies; ++s) {
+        const Species &S = c.sp[s];
+        const int64_t first = S.sorted ? S.nsorted : 0;
+        if (S.n <= first) continue;
+        StepArgs<float> a = step_args<float>(c, s);
+        a.off = first;
+        a.n = S.n - first;
+        MixedParticles p{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+        unsigned blocks = (unsigned)((a.n + 255) / 256);
+#define PP_L(O, PU) k_particles_mixed<O, PU><<<blocks, 256, 0, c.st>>>(a, p)
+        if (pu == PP_BORIS) {
+            if (o == 1) PP_L(1, PP_BORIS); else if (o == 2) PP_L(2, PP_BORIS); else PP_L(3, PP_BORIS);
+        } else {
+            if (o == 1) PP_L(1, PP_VAY); else if (o == 2) PP_L(2, PP_VAY); else PP_L(3, PP_VAY);
+        }
+#undef PP_L
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Injection of inflow particles (Sec. II "Sliding window and injection of
+// particles").  Draws come from the counter-based Philox4x32-10 generator of
+// Salmon, Moraes, Dror & Shaw (SC'11): ten rounds of the bijection
+//   (x0, x1, x2, x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)),
+// M0 = 0xD2511F53, M1 = 0xCD9E8D57, the key advanced by 0x9E3779B9, 0xBB67AE85
+// between rounds.  Particle i of a batch takes counter (i, 0, step, stream)
+// under the 64-bit seed; each 32-bit word r gives the uniform (r + 1/2) 2^-32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t (&x)[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * x[0], hi0 = __umulhi(0xD2511F53u, x[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * x[2], hi1 = __umulhi(0xCD9E8D57u, x[2]);
+        const uint32_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+        x[0] = y0; x[1] = lo1; x[2] = y2; x[3] = lo0;
+    }
+}
+
+__device__ __forceinline__ void uniforms4(uint64_t seed, uint32_t i, uint32_t step, uint32_t stream, double (&u)[4]) {
+    uint32_t x[4] = {i, 0u, step, stream};
+    philox4x32_10(x, (uint32_t)seed, (uint32_t)(seed >> 32));
+#pragma unroll
+    for (int m = 0; m < 4; ++m) u[m] = ((double)x[m] + 0.5) * (1.0 / 4294967296.0);
+}
+
+struct InjectArgs {
+    int64_t off, count;        // first slot, number of particles
+    uint64_t seed;
+    uint32_t step, pstream, vstream;
+    double thick;              // slab thickness in x (physical)
+    double ly, lz;             // box lengths in y and z
+    double h[3];               // cell sizes
+    int n[3];                  // mesh cells
+    double u[3], u_th;         // drift proper velocity, thermal spread
+    int mixed;
+};
+
+// Particle i: position (thick u0, Ly u1, Lz u2) from stream pstream, proper
+// velocity drift + u_th (three Box-Muller normals) from stream vstream.
+__global__ void k_inject(InjectArgs a, Fp64Particles p64, MixedParticles pm) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.count) return;
+    double U[4], V[4];
+    uniforms4(a.seed, (uint32_t)i, a.step, a.pstream, U);
+    uniforms4(a.seed, (uint32_t)i, a.step, a.vstream, V);
+    const double X[3] = {a.thick * U[0], a.ly * U[1], a.lz * U[2]};
+    const double r0 = sqrt(-2.0 * log(V[0])), r1 = sqrt(-2.0 * log(V[2]));
+    const double g[3] = {r0 * cos(2.0 * M_PI * V[1]), r0 * sin(2.0 * M_PI * V[1]), r1 * cos(2.0 * M_PI * V[3])};
+    const int64_t q = a.off + i;
+    double xi[3];
+    int cell[3];
+    float o[3];
+    for (int d = 0; d < 3; ++d) {
+        double v = X[d] / a.h[d];
+        if (v >= (double)a.n[d]) v -= (double)a.n[d];
+        xi[d] = v;
+        int ci = (int)floor(v);
+        float of = (float)(v - ci);
+        if (of >= 1.0f) { of = 0.0f; ci += 1; }
+        if (ci >= a.n[d]) ci -= a.n[d];
+        cell[d] = ci;
+        o[d] = of;
+    }
+    const double u0 = a.u[0] + a.u_th * g[0], u1 = a.u[1] + a.u_th * g[1], u2 = a.u[2] + a.u_th * g[2];
+    if (a.mixed) {
+        pm.cell[q] = pack_cell(cell[0], cell[1], cell[2]);
+        pm.ox[q] = o[0]; pm.oy[q] = o[1]; pm.oz[q] = o[2];
+        pm.ux[q] = (float)u0; pm.uy[q] = (float)u1; pm.uz[q] = (float)u2;
+    } else {
+        p64.x[q] = xi[0]; p64.y[q] = xi[1]; p64.z[q] = xi[2];
+        p64.ux[q] = u0; p64.uy[q] = u1; p64.uz[q] = u2;
+    }
+}
+
+cudaError_t launch_inject(Ctx &c, int s, int64_t off, int64_t count, uint32_t step, uint32_t pstream, double thick) {
+    if (count <= 0) return cudaSuccess;
+    Species &S = c.sp[s];
+    const Ctx::Injector &I = c.inj[s];
+    InjectArgs a;
+    a.off = off;
+    a.count = count;
+    a.seed = I.seed;
+    a.step = step;
+    a.pstream = pstream;
+    a.vstream = pstream + 1u + (uint32_t)s;
+    a.thick = thick;
+    a.ly = c.g.n[1] * c.d.dy;
+    a.lz = c.g.n[2] * c.d.dz;
+    a.h[0] = c.d.dx; a.h[1] = c.d.dy; a.h[2] = c.d.dz;
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = c.g.n[d];
+        a.u[d] = I.u[d];
+    }
+    a.u_th = I.u_th;
+    a.mixed = c.fp64 ? 0 : 1;
+    Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
+    MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+    k_inject<<<(unsigned)((count + 255) / 256), 256, 0, c.st>>>(a, p64, pm);
+    ++c.nlaunch;
+    return cudaGetLastError();
+}
+
+// Sliding-window shift of the particles: every live particle moves one cell
+// up in x; one that ends above the top wall (x > nw cells) leaves.
+__global__ void k_window_particles(int64_t n, int nw, Fp64Particles p64, MixedParticles pm, int mixed) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    if (mixed) {
+        int32_t cw = pm.cell[t];
+        if (cw < 0) return;
+        int cx, cy, cz;
+        unpack_cell(cw, cx, cy, cz);
+        ++cx;
+        cw = pack_cell(cx, cy, cz);
+        if (cx > nw || (cx == nw && pm.ox[t] > 0.0f)) cw |= kDeadBit;
+        pm.cell[t] = cw;
+    } else {
+        double x = p64.x[t];
+        if (x < 0.0) return;
+        x += 1.0;
+        p64.x[t] = x > (double)nw ? kDeadX : x;
+    }
+}
+
+cudaError_t launch_window_particles(Ctx &c, int s) {
+    Species &S = c.sp[s];
+    if (S.n == 0) return cudaSuccess;
+    Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
+    MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+    k_window_particles<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, c.mirror, p64, pm, c.fp64 ? 0 : 1);
+    ++c.nlaunch;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -782,12 +963,15 @@ struct RhoAcc {
 // (cell-sorted) array, so the lanes of a warp sit in distinct cells and their
 // FP64 atomics do not pile onto the same nodes.
 template <int O>
-__global__ void k_rho(Geom g, double qw, int64_t n, Fp64Particles p64, MixedParticles pm, int mixed, double *rho) {
+__global__ void k_rho(Geom g, double qw, int64_t n, int64_t off, Fp64Particles p64, MixedParticles pm, int mixed,
+                      double *rho) {
     int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t n32 = (n + 31) / 32;
     if (tt >= n32 * 32) return;
     int64_t t = (tt & 31) * n32 + (tt >> 5);
     if (t >= n) return;
+    t += off;
+    if (mixed ? pm.cell[t] < 0 : p64.x[t] < 0.0) return;   // left the box
     RhoAcc acc{g, rho, 0, 0, 0};
     double xi[3];
     if (mixed) {
@@ -837,6 +1021,7 @@ __global__ void __launch_bounds__(128) k_rho_cells(Geom g, RhoCellGeom kg, int64
     for (int t = b; t < e; ++t) {
         int cx, cy, cz;
         double xi[3];
+        if (mixed ? pm.cell[t] < 0 : p64.x[t] < 0.0) continue;   // left the box
         if (mixed) {
             unpack_cell(pm.cell[t], cx, cy, cz);
             xi[0] = pm.ox[t]; xi[1] = pm.oy[t]; xi[2] = pm.oz[t];
@@ -909,12 +1094,14 @@ cudaError_t launch_rho(Ctx &c) {
 #undef PP_R
             ++c.nlaunch;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            continue;
         }
-        unsigned blocks = (unsigned)(((S.n + 31) / 32 * 32 + 255) / 256);
-        if (c.d.shape_order == 1) k_rho<1><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);
-        else if (c.d.shape_order == 2) k_rho<2><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);
-        else k_rho<3><<<blocks, 256, 0, c.st>>>(c.g, qw, S.n, p64, pm, mixed, c.rho);
+        // every particle of an unsorted species, or the unsorted tail (injected since the sort)
+        const int64_t off = S.sorted ? S.nsorted : 0, cnt = S.n - off;
+        if (cnt <= 0) continue;
+        unsigned blocks = (unsigned)(((cnt + 31) / 32 * 32 + 255) / 256);
+        if (c.d.shape_order == 1) k_rho<1><<<blocks, 256, 0, c.st>>>(c.g, qw, cnt, off, p64, pm, mixed, c.rho);
+        else if (c.d.shape_order == 2) k_rho<2><<<blocks, 256, 0, c.st>>>(c.g, qw, cnt, off, p64, pm, mixed, c.rho);
+        else k_rho<3><<<blocks, 256, 0, c.st>>>(c.g, qw, cnt, off, p64, pm, mixed, c.rho);
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -928,6 +1115,7 @@ __global__ void k_kinetic(int64_t n, Fp64Particles p64, MixedParticles pm, int m
     double acc = 0.0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         double u0, u1, u2;
+        if (mixed ? pm.cell[t] < 0 : p64.x[t] < 0.0) continue;   // left the box
         if (mixed) { u0 = pm.ux[t]; u1 = pm.uy[t]; u2 = pm.uz[t]; }
         else { u0 = p64.ux[t]; u1 = p64.uy[t]; u2 = p64.uz[t]; }
         double u2s = u0 * u0 + u1 * u1 + u2 * u2;

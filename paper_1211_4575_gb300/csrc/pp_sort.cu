@@ -20,6 +20,7 @@ struct KeyGeom {
     int T[3];
     int nt[3];
     int64_t tile_vol;
+    int32_t dead;   // key of a particle that left the box: after every cell's keys
 };
 
 __device__ __forceinline__ int32_t cell_key(const KeyGeom &k, int x, int y, int z) {
@@ -52,6 +53,11 @@ __global__ void k_keys_fp64(KeyGeom kg, int64_t n, const double *x, const double
                             int32_t *counts) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    if (x[t] < 0.0) {   // left the box
+        keys[t] = kg.dead;
+        aggregated_add(counts, kg.dead);
+        return;
+    }
     int cx = (int)floor(x[t]), cy = (int)floor(y[t]), cz = (int)floor(z[t]);
     cx = min(max(cx, 0), kg.n[0] - 1);
     cy = min(max(cy, 0), kg.n[1] - 1);
@@ -67,6 +73,11 @@ __global__ void k_keys_mixed(KeyGeom kg, int64_t n, const int32_t *cell, const f
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     int32_t c = cell[t];
+    if (c < 0) {   // left the box
+        keys[t] = kg.dead;
+        aggregated_add(counts, kg.dead);
+        return;
+    }
     int oct = (ox[t] >= 0.5f ? 1 : 0) | (oy[t] >= 0.5f ? 2 : 0) | (oz[t] >= 0.5f ? 4 : 0);
     int32_t key = cell_key(kg, c & 1023, (c >> 10) & 1023, (c >> 20) & 1023) * kSubKeys + oct;
     keys[t] = key;
@@ -176,6 +187,7 @@ static KeyGeom key_geom(const Ctx &c) {
         k.nt[a] = c.ntile[a];
     }
     k.tile_vol = (int64_t)c.tile[0] * c.tile[1] * c.tile[2];
+    k.dead = (int32_t)c.nkeys;
     return k;
 }
 
@@ -191,12 +203,19 @@ cudaError_t sort_setup(Ctx &c) {
     return cudaMalloc(&c.scan_tmp, c.scan_tmp_bytes);
 }
 
+// Particles that left the box sort after every cell (key nkeys); when the
+// species may hold some, the live count cell_start[nkeys] is read back (a
+// synchronisation) and becomes the species' count, which drops them.
 cudaError_t launch_sort(Ctx &c, int s) {
     Species &S = c.sp[s];
     S.sorted = true;
     cudaError_t e = cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
     if (e != cudaSuccess) return e;
-    if (S.n == 0) return cudaMemsetAsync(S.cell_start, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
+    if (S.n == 0) {
+        S.nsorted = 0;
+        S.may_hold_dead = false;
+        return cudaMemsetAsync(S.cell_start, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
+    }
     KeyGeom kg = key_geom(c);
     unsigned blocks = (unsigned)((S.n + 255) / 256);
     if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
@@ -231,6 +250,14 @@ cudaError_t launch_sort(Ctx &c, int s) {
         S.alt = old;
         S.bind(false);
     }
+    if (S.may_hold_dead) {
+        e = cudaMemcpyAsync(c.h_count, S.cell_start + c.nkeys, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+        if (e != cudaSuccess) return e;
+        S.n = *c.h_count;
+        S.may_hold_dead = false;
+    }
+    S.nsorted = S.n;
     return cudaSuccess;
 }
 

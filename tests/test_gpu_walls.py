@@ -192,3 +192,115 @@ def test_walls_arguments_and_checkpoint(pp, tmp_path):
     Ea, _, _ = a.fields()
     Eb, _, _ = b.fields()
     assert max(H.rel_err(Eb[k], Ea[k]) for k in range(3)) <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# Open lower end, injectors and sliding window
+# --------------------------------------------------------------------------
+
+def _boundary_pair(pp, orc, L, precision, mode=0, window=0.0, steps=6, shape=3, inj=True, open_end=True):
+    gpu, osim = _pair(pp, orc, L, precision, shape, mode=mode, gpu_kw=dict(capacity_extra=4000))
+    # a second, positive species so that the inflow is neutral
+    sp = L.species[0]
+    e = np.zeros(0)
+    sid_g = gpu.add_species(-sp["q"], sp["m"], sp["w"], 4000)
+    sid_o = osim.add_species(-sp["q"], sp["m"], sp["w"], e, e, e, e, e, e)
+    assert sid_g == sid_o == 1
+    if open_end:
+        gpu.set_open_boundary(6, 0.2, 2.0)
+        osim.set_open_boundary(6, 0.2, 2.0)
+    if inj:
+        for sid in (0, 1):
+            gpu.set_injector(sid, 1.5, (0.8, 0.1, -0.05), 0.05, 77)
+            osim.set_injector(sid, 1.5, (0.8, 0.1, -0.05), 0.05, 77)
+    if window:
+        gpu.set_sliding_window(window)
+        osim.set_window(window)
+    gpu.step(steps)
+    osim.step(steps)
+    return gpu, osim
+
+
+def _compare_all(gpu, osim, L, nsp, tol_f, tol_x, tol_u):
+    assert gpu.diagnostics()["status"] == 0
+    for s in range(nsp):
+        p = gpu.particles(s)
+        o = osim.particles(s)
+        assert len(p["x"]) == len(o["x"]), (s, len(p["x"]), len(o["x"]))
+        assert p["x"].min() >= 0.0 and p["x"].max() <= L.n[0] * L.d[0]
+        dpos, du = H.particle_errors(p, o, _box(L))
+        assert dpos <= tol_x and du <= tol_u, (s, dpos, du)
+    fe = H.field_errors(gpu, osim)
+    for k, v in fe.items():
+        assert v <= tol_f, (k, v, fe)
+
+
+def test_open_end_and_injector_fp64_parity(pp, orc):
+    """Open lower end (6-cell layer, escape 2 cells) with neutral injection of
+    two species, fast random particles that reach the open end, random fields,
+    six steps: counts equal, FP64 to 1e-12 against the oracle."""
+    L = _load(seed=181)
+    gpu, osim = _boundary_pair(pp, orc, L, pp.PP_FP64)
+    assert osim.counts[1] > 0 and osim.counts[0] != len(L.species[0]["x"])
+    _compare_all(gpu, osim, L, 2, 1e-12, 1e-12, 1e-12)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_open_end_and_injector_mixed_parity(pp, orc, mode):
+    """The same in the mixed form, global (1) and tiled (2, injected particles
+    in the unsorted tail, escaped ones skipped until the next sort)."""
+    L = _load((12, 16, 16), seed=182)
+    gpu, osim = _boundary_pair(pp, orc, L, pp.PP_MIXED32, mode=mode)
+    _compare_all(gpu, osim, L, 2, 3e-5, 2e-6, 2e-6)
+
+
+@pytest.mark.parametrize("precision,mode", [(0, 0), (1, 2)])
+def test_sliding_window_parity(pp, orc, precision, mode):
+    """Window at v = 0.6 (a shift every few steps) with the open end and the
+    injectors filling each new layer, ten steps: FP64 to 1e-12, mixed tiled to
+    its tolerance."""
+    L = _load((12, 16, 16), seed=183)
+    gpu, osim = _boundary_pair(pp, orc, L, precision, mode=mode, window=0.6, steps=10)
+    assert osim.shifts >= 2
+    tol = (1e-12, 1e-12, 1e-12) if precision == 0 else (3e-5, 2e-6, 2e-6)
+    _compare_all(gpu, osim, L, 2, *tol)
+
+
+def test_boundary_state_in_checkpoint_and_errors(pp, orc, tmp_path):
+    L = _load((12, 8, 8), count=600, seed=184)
+    a, _ = _boundary_pair(pp, orc, L, pp.PP_FP64, window=0.6, steps=3)
+    path = str(tmp_path / "open.ckpt")
+    a.save(path)
+    b = pp.Simulation.restore(path)
+    for s in (a, b):
+        s.step(4)
+    for sid in (0, 1):
+        pa, pb = a.particles(sid), b.particles(sid)
+        assert len(pa["x"]) == len(pb["x"])
+        dpos, du = H.particle_errors(pb, pa, _box(L))
+        assert dpos <= 1e-12 and du <= 1e-12
+    Ea, _, _ = a.fields()
+    Eb, _, _ = b.fields()
+    assert max(H.rel_err(Eb[k], Ea[k]) for k in range(3)) <= 1e-12
+    # errors
+    per = pp.Simulation((8, 8, 8), (0.5, 0.5, 0.5), 0.2)
+    per.add_species(-1.0, 1.0, 0.1, 10)
+    with pytest.raises(pp.PPError):
+        per.set_open_boundary(4, 0.1, 1.0)
+    with pytest.raises(pp.PPError):
+        per.set_injector(0, 1.0, (0.5, 0, 0))
+    with pytest.raises(pp.PPError):
+        per.set_sliding_window(0.5)
+    w = pp.Simulation((8, 8, 8), (0.5, 0.5, 0.5), 0.2, boundary_x=pp.PP_BOUNDARY_WALLS)
+    sid = w.add_species(-1.0, 1.0, 0.1, 10)
+    for args in ((9, 0.1, 1.0), (4, 1.5, 1.0), (4, 0.1, -1.0), (4, 0.1, 1.0, 64)):
+        with pytest.raises(pp.PPError):
+            w.set_open_boundary(*args)
+    with pytest.raises(pp.PPError):
+        w.set_injector(sid, 1.0, (-0.5, 0, 0))
+    with pytest.raises(pp.PPError):
+        w.set_sliding_window(1.0)
+    # an injection beyond the capacity fails the step
+    w.set_injector(sid, 4.0, (0.9, 0, 0))
+    with pytest.raises(pp.PPError):
+        w.step(3)
