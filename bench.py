@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -70,9 +71,10 @@ def args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["thermal", "weibel", "beam"], default="thermal",
+    ap.add_argument("--workload", choices=["thermal", "weibel", "beam", "shock"], default="thermal",
                     help="thermal / weibel: n^3 pair plasma; beam: cold Gamma=10 beam through an electron-ion "
-                         "background on 2n x n x n")
+                         "background on 2n x n x n; shock: the same beam on 2n x n x n between walls, fed "
+                         "through an open end and reflected by the far wall")
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--ppc", type=int, default=None,
                     help="macro-particles per cell per species (per population for beam); default 32, beam 16")
@@ -104,11 +106,15 @@ def args():
 
 
 def workload_grid(a, edge):
-    return (2 * edge, edge, edge) if a.workload == "beam" else (edge, edge, edge)
+    return (2 * edge, edge, edge) if a.workload in ("beam", "shock") else (edge, edge, edge)
+
+
+# open end of the shock workload: 20-cell outflow layer, particles leave 10 cells out
+SHOCK_LAYER, SHOCK_DAMPING, SHOCK_ESCAPE = 20, 0.2, 10.0
 
 
 def workload_dt(a):
-    if a.workload == "beam":   # dx = 0.5; the explicit solver's limit there is 0.233
+    if a.workload in ("beam", "shock"):   # dx = 0.5; the explicit solver's limit there is 0.233
         return 0.2 if a.field_solver == "explicit" else 0.25
     return 0.04 if a.field_solver == "explicit" else 0.05
 
@@ -118,6 +124,10 @@ def make_load(a, edge, seed_offset=0):
     n = workload_grid(a, edge)
     if a.workload == "beam":
         L = pp_synth.beam_background(n=n, ppc=a.ppc, seed=1214 + seed_offset)
+        L.dt = workload_dt(a)
+        return L
+    if a.workload == "shock":
+        L = pp_synth.wall_beam(n=n, ppc=a.ppc, seed=1218 + seed_offset)
         L.dt = workload_dt(a)
         return L
     if a.workload == "thermal":
@@ -140,6 +150,12 @@ def workload_name(a, nparticles):
         head = (f"cold Gamma=10 beam through an electron-ion background (m_i/m_e=25, u_th=0.01c), "
                 f"{nx}x{ny}x{nz} cells, dx=0.5, dt={workload_dt(a):g}, {a.ppc} per cell per species per population "
                 f"({nparticles} particles)")
+    elif a.workload == "shock":
+        head = (f"wall shock: cold Gamma=10 electron-ion beam (m_i/m_e=25) between reflecting walls, "
+                f"{nx}x{ny}x{nz} cells (mesh {2 * nx}x{ny}x{nz} mirror-extended), dx=0.5, dt={workload_dt(a):g}, "
+                f"{a.ppc} per cell per species (about {nparticles} particles), fed through an open end at x=0 "
+                f"({SHOCK_LAYER}-cell outflow layer, damping {SHOCK_DAMPING:g}, escape {SHOCK_ESCAPE:g} cells) "
+                f"by a neutral Philox injector and reflected by the wall at x=L")
     else:
         kind = "thermal pair plasma u_th=0.1c (numerical heating)" if a.workload == "thermal" else \
             "Weibel counter-streaming pair beams +-0.5c, u_th=0.1c"
@@ -223,29 +239,48 @@ def replica_value(particles_per_rank, world, steps, max_ms):
     return particles_per_rank * world * steps / (max_ms * 1e-3)
 
 
+def shock_inflow_room(a, L, steps):
+    """Slots the injectors of the shock workload fill in `steps` steps, per species."""
+    ny, nz = L.n[1], L.n[2]
+    u = L.params["u_drift"]
+    rate = a.ppc * ny * nz * (u / math.sqrt(1.0 + u * u)) * L.dt / L.d[0]
+    return int(math.ceil(rate * (steps + 2))) + 64
+
+
 def oracle_rate(a, steps, warmup=0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    same physics and per-cell loading on a sample_n^3 periodic box."""
+    same physics and per-cell loading on a sample_n^3 periodic box (for the
+    shock: a (sample_n, sample_n/2, sample_n/2) box between walls with its open
+    end and injectors, the oracle's virtual images included in its cost)."""
     import oracle
     import pp_synth
-    L = make_load(a, a.sample_n)
+    shock = a.workload == "shock"
+    L = make_load(a, a.sample_n // 2 if shock else a.sample_n)
     oracle.build()
-    sim = oracle.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6,
-                            relax_max_iter=200, integrator=a.integrator,
-                            field_solver=oracle.EXPLICIT if a.field_solver == "explicit" else oracle.IMPLICIT,
-                            current_mode=oracle.DIRECT if a.current == "direct" else oracle.CHARGE_CONSERVING,
-                            filter_passes=a.filter, filter_interval=1)
+    kw = dict(field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6, relax_max_iter=200, integrator=a.integrator,
+              field_solver=oracle.EXPLICIT if a.field_solver == "explicit" else oracle.IMPLICIT,
+              current_mode=oracle.DIRECT if a.current == "direct" else oracle.CHARGE_CONSERVING,
+              filter_passes=a.filter, filter_interval=1)
+    sim = oracle.WallSimulation(L.n, L.d, L.dt, **kw) if shock else oracle.Simulation(L.n, L.d, L.dt, **kw)
     for s in L.species:
         sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"], rad=a.radiation)
+    if shock:
+        sim.set_open_boundary(min(SHOCK_LAYER, L.n[0] // 2), SHOCK_DAMPING, min(SHOCK_ESCAPE, L.n[0] / 4))
+        for sid in range(len(L.species)):
+            sim.set_injector(sid, a.ppc, (L.params["u_drift"], 0.0, 0.0), 0.0, L.params["seed"])
     if warmup:
         sim.step(warmup)
+    n0 = sum(sim.counts) if shock else L.n_particles
     t0 = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t0
-    sample = (f"{'x'.join(str(v) for v in L.n)} cells, {a.ppc} per cell per species"
-              f"{' per population' if a.workload == 'beam' else ''} = {L.n_particles} particles, "
+    nmean = (n0 + sum(sim.counts)) / 2 if shock else L.n_particles
+    sample = (f"{'x'.join(str(v) for v in L.n)} cells{' between walls' if shock else ''}, "
+              f"{a.ppc} per cell per species"
+              f"{' per population' if a.workload == 'beam' else ''} = {L.n_particles} particles"
+              f"{' at the start, about ' + str(int(nmean)) + ' over the timed steps (the oracle also steps their mirror images)' if shock else ''}, "
               f"{steps} steps, same per-cell load and parameters as the workload, single-threaded C")
-    return L.n_particles * steps / dt, sample, dt
+    return nmean * steps / dt, sample, dt
 
 
 def run_reference(a):
@@ -288,24 +323,39 @@ def run_gpu(a):
     mode = {"auto": pp.PP_DEPOSIT_AUTO, "global": pp.PP_DEPOSIT_GLOBAL, "tiled": pp.PP_DEPOSIT_TILED}[a.deposit]
     stream = torch.cuda.current_stream()
 
+    shock = a.workload == "shock"
+
     def make():
         s = pp.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, pusher=pp.PP_VAY,
                           precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=100, relax_tol=1e-6,
-                          deposit_mode=mode, stream=stream.cuda_stream)
+                          deposit_mode=mode, stream=stream.cuda_stream,
+                          boundary_x=pp.PP_BOUNDARY_WALLS if shock else pp.PP_BOUNDARY_PERIODIC)
         s.set_integrator(a.integrator)
         s.set_field_solver(pp.PP_FIELD_EXPLICIT if a.field_solver == "explicit" else pp.PP_FIELD_IMPLICIT)
         s.set_current_deposit(pp.PP_CURRENT_DIRECT if a.current == "direct" else pp.PP_CURRENT_CONSERVING)
         s.set_divergence_filter(a.filter, 1)
         return s
 
+    # the shock's inflow: room for every step's injection, then the open end and the injectors
+    extra = shock_inflow_room(a, L, a.warmup + a.steps) if shock else 0
+
+    def open_end(s):
+        if shock:
+            s.set_open_boundary(SHOCK_LAYER, SHOCK_DAMPING, SHOCK_ESCAPE)
+            for sid in range(len(L.species)):
+                s.set_injector(sid, a.ppc, (L.params["u_drift"], 0.0, 0.0), 0.0, L.params["seed"])
+
     sim = make()
     for s in L.species:
-        sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+        sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]) + extra)
         sim.set_radiative_cooling(sid, a.radiation)
         sim.load_particles(sid, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    open_end(sim)
     for _ in range(a.warmup):
         sim.step(1)
     sim.sync()
+    if shock:   # particles enter and leave: count the mean load of the timed steps
+        n_start = sum(sim.count(sid) for sid in range(len(L.species)))
 
     # ---- device-resident timed region ----
     sim.profile_enable(True)
@@ -326,6 +376,8 @@ def run_gpu(a):
     prof = sim.profile_read()
     sim.profile_enable(False)
     sim.sync()
+    if shock:
+        npart = (n_start + sum(sim.count(sid) for sid in range(len(L.species)))) // 2
     ms = reduce_max(ms, dist, "cuda")
     total_particles = npart * world
     value = replica_value(npart, world, a.steps, ms)
@@ -352,9 +404,10 @@ def run_gpu(a):
         t0 = time.perf_counter()
         sim2 = make()
         for s, p in zip(L.species, pinned):
-            sid = sim2.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+            sid = sim2.add_species(s["q"], s["m"], s["w"], len(s["x"]) + extra)
             sim2.set_radiative_cooling(sid, a.radiation)
             sim2.load_particles(sid, *[p[k].numpy() for k in ("x", "y", "z", "ux", "uy", "uz")])
+        open_end(sim2)
         sim2.step(a.steps)
         d2 = sim2.diagnostics()
         t1 = time.perf_counter()
@@ -392,6 +445,9 @@ def run_gpu(a):
         "clocks": clk,
         "phases_ms_per_step": {k: prof[k] / a.steps for k in ("particle_ms", "current_ms", "field_ms", "sort_ms")},
         "diag": {"status": diag["status"], "gauss_drift_rel": diag["gauss_drift_max"] / max(diag["rho_max"], 1e-300),
+                 "gauss_drift_max": diag["gauss_drift_max"], "rho_max": diag["rho_max"],
+                 # every workload loads a charge density of 1 per sign (electrons: -1)
+                 "gauss_drift_vs_species_density": diag["gauss_drift_max"],
                  "relax_residual": diag["relax_residual"], "relax_iters": diag["relax_iters"]},
     }
     print(json.dumps(line), flush=True)

@@ -398,7 +398,9 @@ __device__ __forceinline__ int min_image(int d, int n) {
     return d;
 }
 
-template <int O, int PUSH>
+// BND: walls (reflection) and particles that leave (skip, escape); a separate
+// instantiation so that periodic runs carry none of their tests.
+template <int O, int PUSH, bool BND>
 __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_constant__ TiledArgs T) {
     extern __shared__ float smem[];
     float *F = smem;
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 const int q = 32 * (warp + kWarps * r) + lane;
                 if (q >= cn) continue;
                 const int sq = q + (q >> 5);
-                if (s_cell[sq] < 0) {   // left the box: kept as it is until the next sort
+                if (BND && s_cell[sq] < 0) {   // left the box: kept as it is until the next sort
                     s_d[sq] = __int_as_float(0x7fc00000);
                     continue;
                 }
@@ -555,9 +557,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 rebin(xi1[0], cx, g.n[0]);
                 rebin(xi1[1], cy, g.n[1]);
                 rebin(xi1[2], cz, g.n[2]);
-                if (T.mirror) reflect(cx, xi1[0], s_u[sq], T.mirror);
-                int32_t cw = pack_cell(cx, cy, cz);
-                if (T.esc > 0.0 && (double)cx + (double)xi1[0] < T.esc && s_u[sq] < 0.0f) cw |= kDeadBit;
+                int32_t cw;
+                if constexpr (BND) {
+                    reflect(cx, xi1[0], s_u[sq], T.mirror);
+                    cw = pack_cell(cx, cy, cz);
+                    if (T.esc > 0.0 && (double)cx + (double)xi1[0] < T.esc && s_u[sq] < 0.0f) cw |= kDeadBit;
+                } else {
+                    cw = pack_cell(cx, cy, cz);
+                }
                 s_cell[sq] = cw;
                 s_o[sq] = xi1[0]; s_o[kStage + sq] = xi1[1]; s_o[2 * kStage + sq] = xi1[2];
             };
@@ -746,18 +753,23 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
     T.esc = c.escape_now;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
-    static bool attr_done[2][4] = {{false}};
+    static bool attr_done[2][2][4] = {{{false}}};
+    const bool bnd = c.mirror != 0;
     cudaError_t e = cudaSuccess;
     if (T.ns > 0) {
-#define PP_T(O, PU)                                                                                         \
+#define PP_TB(O, PU, BD)                                                                                    \
     do {                                                                                                    \
-        if (!attr_done[PU][O]) {                                                                            \
-            cudaError_t e_ = cudaFuncSetAttribute(k_particles_tiled<O, PU>,                                 \
+        if (!attr_done[BD][PU][O]) {                                                                        \
+            cudaError_t e_ = cudaFuncSetAttribute(k_particles_tiled<O, PU, BD>,                             \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTiledSmem); \
             if (e_ != cudaSuccess) return e_;                                                               \
-            attr_done[PU][O] = true;                                                                        \
+            attr_done[BD][PU][O] = true;                                                                    \
         }                                                                                                   \
-        k_particles_tiled<O, PU><<<blocks, kThreads, kTiledSmem, c.st>>>(T);                                \
+        k_particles_tiled<O, PU, BD><<<blocks, kThreads, kTiledSmem, c.st>>>(T);                            \
+    } while (0)
+#define PP_T(O, PU)                                                                                         \
+    do {                                                                                                    \
+        if (bnd) PP_TB(O, PU, true); else PP_TB(O, PU, false);                                              \
     } while (0)
     if (pu == PP_BORIS) {
         if (o == 1) PP_T(1, PP_BORIS); else if (o == 2) PP_T(2, PP_BORIS); else PP_T(3, PP_BORIS);
@@ -765,6 +777,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
         if (o == 1) PP_T(1, PP_VAY); else if (o == 2) PP_T(2, PP_VAY); else PP_T(3, PP_VAY);
     }
 #undef PP_T
+#undef PP_TB
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -163,6 +163,19 @@ def beam_background(n=(256, 128, 128), seed=1214, ppc=16, gamma_b=10.0, u_th_bg=
     return L
 
 
+def wall_beam(n=(256, 128, 128), seed=1218, ppc=32, gamma_b=10.0, mass_ratio=25.0, cells=None) -> Load:
+    """The beam of the wall-shock setup: a cold Gamma = 10 electron-ion beam
+    (m_i/m_e = 25) along +x filling a box between walls, ppc macro-particles
+    per cell per species, dx = 0.5, dt = 0.25.  The inflow through the open
+    end continues it: params hold the drift proper velocity and the seed."""
+    beta = math.sqrt(1.0 - 1.0 / (gamma_b * gamma_b))
+    pops = [Population(ppc, 1.0, beta, 0.0, boost=True)]
+    L = pair_plasma(n, (0.5, 0.5, 0.5), 0.25, pops, seed, masses=(1.0, mass_ratio), cells=cells)
+    L.params = dict(workload="wall-shock", shape_order=3, field_order=6, alpha=0.55, gamma_b=gamma_b,
+                    u_drift=math.sqrt(gamma_b * gamma_b - 1.0), ppc=ppc, seed=seed)
+    return L
+
+
 def single_particle(n, d, dt, x, u, q=-1.0, m=1.0, w=1.0) -> Load:
     """One macro-particle (used by the deposit pins and the edge cases)."""
     arr = lambda v: np.array([float(v)])
