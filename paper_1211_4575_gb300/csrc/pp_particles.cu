@@ -299,8 +299,12 @@ cudaError_t launch_particles_mixed_global(Ctx &c, int s) {
 // ---------------------------------------------------------------------------
 constexpr int kTile = 8;                       // tile edge (cells)
 constexpr int kTileCells = kTile * kTile * kTile;
+// 1024 threads: 32 warps per SM (one CTA fits, by shared memory) at 64
+// registers a thread with no spills; the kernel waits on shared-memory latency,
+// and twice the warps of a 512-thread CTA hide more of it (64^3 thermal PCS:
+// 3.53 -> 3.39 ms; the Weibel variant, with more queued deposits: 4.10 -> 3.77 ms).
 #ifndef PP_TILED_THREADS
-#define PP_TILED_THREADS 512
+#define PP_TILED_THREADS 1024
 #endif
 constexpr int kThreads = PP_TILED_THREADS;     // threads per tile CTA
 constexpr int kWarps = kThreads / 32;
@@ -596,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
             }
             __syncthreads();
             // The queue: groups of three warps take 32 particles per round, one
-            // current component per warp (warp 15 rests), so that the pass lasts
+            // current component per warp (warps past the last group rest), so that the pass lasts
             // about a third of a deposit and no warp diverges over components.
             const int nq = *nqueue;
             const int group = warp / 3, comp = warp - 3 * group;
