@@ -1,7 +1,8 @@
 """The bounds-checked build (-DPP_CHECKED): every particle-kernel index into
 the mesh or the shared-memory windows is tested against its array.  On the
 cases of tests/checked_cases.py (the tiled kernel with its drift fallback, the
-FP64 global kernels for every shape, the direct current, the 4th-order step)
+FP64 global kernels for every shape, the direct current, the 4th-order step,
+walls with an open end, an injector and a sliding window)
 it must report no violation and give the normal build's fields."""
 import json
 import os
