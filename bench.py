@@ -40,13 +40,13 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # sort (its key sets the particle order the kernel streams) and the part of
 # pp_particles.cu that holds the particle kernels (up to its charge-density
 # section).
-PROFILED_BYTES_PER_PARTICLE = 901.271040e6 / 16777216
+PROFILED_BYTES_PER_PARTICLE = 901.909504e6 / 16777216
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 _HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "cbb895123efa8f3252ff1cb8882f1e24bcc350214df43a96c7b177a64e9f3307",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "cd803c585dfd58b2b48107b461c5b79ce07b701c6300d987b84ef6c30cf506a1",
-    "paper_1211_4575_gb300/csrc/pp_sort.cu": "504fa77f0cf5c710b397512493380b8b75448c917235096f104992b782818ec3",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "1e70a977a3e75b1e36ed64d8662e872c650e0ff7ecb07692209923a04eb443eb",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "643a48f3cec37d301be2db1853792dc3ef6c269944bb793e18bc1b1ae96f6b0b",
+    "paper_1211_4575_gb300/csrc/pp_sort.cu": "8ae278e854810bdf3db42a7069642a62f7c7a0c1cddf9bd8d09dca831784555a",
 }
 
 
