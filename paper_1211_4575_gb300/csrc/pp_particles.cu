@@ -1083,6 +1083,102 @@ __global__ void __launch_bounds__(128) k_rho_cells(Geom g, RhoCellGeom kg, int64
                 if (acc[k][j][i] != A(0)) out.addRho(ST + i, ST + j, ST + k, qw * (double)acc[k][j][i]);
 }
 
+// Mixed form, one CTA per sort tile, one thread per cell: each thread sums its
+// cell's particles into an FP32 frame of NF^3 nodes in registers (as
+// k_rho_cells), the frames go to shared memory, and each node of the tile's
+// window (the tile plus the frames' reach) adds up the frames that cover it,
+// in FP64, before one global atomic.  Global atomics per tile: the window's
+// nodes instead of NF^3 per cell.
+// A particle that left its sorted cell, deposited on its own (kept out of line
+// so that its registers do not add to the frame loop's).
+template <int O>
+__device__ __noinline__ void rho_direct(Geom g, double *rho, int cx, int cy, int cz, double x0, double x1, double x2,
+                                        double qw) {
+    RhoAcc acc1{g, rho, cx, cy, cz};
+    double xi[3] = {x0, x1, x2};
+    deposit_rho<O, double>(acc1, xi, qw);
+}
+
+template <int O>
+__global__ void __launch_bounds__(512) k_rho_tile(Geom g, RhoCellGeom kg, const int32_t *cell_start, double qw,
+                                                  MixedParticles pm, double *rho) {
+    constexpr bool odd = (O % 2) == 1;
+    constexpr int NF = odd ? O + 1 : O + 2;         // frame nodes per axis
+    constexpr int ST = odd ? -(O - 1) / 2 : -O / 2; // frame start relative to the cell
+    constexpr int F3 = NF * NF * NF, FP = F3 + 1;   // frame size; padded pitch (distinct banks per cell)
+    extern __shared__ float fr[];
+    const int tile = blockIdx.x, loc = threadIdx.x;
+    const int T0 = kg.T[0], T1 = kg.T[1], T2 = kg.T[2];
+    const int lx = loc % T0, ly = (loc / T0) % T1, lz = loc / (T0 * T1);
+    const int ox = (tile % kg.nt[0]) * T0, oy = ((tile / kg.nt[0]) % kg.nt[1]) * T1,
+              oz = (tile / (kg.nt[0] * kg.nt[1])) * T2;
+    const int c0 = ox + lx, c1 = oy + ly, c2 = oz + lz;
+    const int64_t key = (int64_t)tile * kg.tile_vol + loc;
+    const int b = cell_start[key * kSubKeys], e = cell_start[(key + 1) * kSubKeys];
+    float acc[NF][NF][NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+#pragma unroll
+            for (int i = 0; i < NF; ++i) acc[k][j][i] = 0.0f;
+    for (int t = b; t < e; ++t) {
+        const int32_t cw = pm.cell[t];
+        if (cw < 0) continue;   // left the box
+        int cx, cy, cz;
+        unpack_cell(cw, cx, cy, cz);
+        if (cx != c0 || cy != c1 || cz != c2) continue;   // left its sorted cell: second pass
+        const float xi[3] = {pm.ox[t], pm.oy[t], pm.oz[t]};
+        float w[3][NF];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float ws[O + 1];
+            const int sh = support<O, float>(xi[a], false, ws) - ST;   // 0, or 1 for even orders
+#pragma unroll
+            for (int m = 0; m < NF; ++m) w[a][m] = (m - sh >= 0 && m - sh <= O) ? ws[m - sh] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < NF; ++k)
+#pragma unroll
+            for (int j = 0; j < NF; ++j) {
+                const float wjk = w[1][j] * w[2][k];
+#pragma unroll
+                for (int i = 0; i < NF; ++i) acc[k][j][i] += w[0][i] * wjk;
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+#pragma unroll
+            for (int i = 0; i < NF; ++i) fr[loc * FP + (k * NF + j) * NF + i] = acc[k][j][i];
+    for (int t = b; t < e; ++t) {   // particles that left their sorted cell, added directly
+        const int32_t cw = pm.cell[t];
+        if (cw < 0) continue;
+        int cx, cy, cz;
+        unpack_cell(cw, cx, cy, cz);
+        if (cx != c0 || cy != c1 || cz != c2) rho_direct<O>(g, rho, cx, cy, cz, pm.ox[t], pm.oy[t], pm.oz[t], qw);
+    }
+    __syncthreads();
+    // window node (wx, wy, wz) is mesh node (ox + ST + wx, ...); cell l of the
+    // tile reaches it with frame index w - l
+    const int W0 = T0 + NF - 1, W1 = T1 + NF - 1, W2 = T2 + NF - 1;
+    for (int nd = threadIdx.x; nd < W0 * W1 * W2; nd += blockDim.x) {
+        const int wx = nd % W0, wy = (nd / W0) % W1, wz = nd / (W0 * W1);
+        double sum = 0.0;
+        for (int k = max(0, wz - T2 + 1); k <= min(NF - 1, wz); ++k)
+            for (int j = max(0, wy - T1 + 1); j <= min(NF - 1, wy); ++j)
+                for (int i = max(0, wx - T0 + 1); i <= min(NF - 1, wx); ++i) {
+                    const int cell = ((wz - k) * T1 + (wy - j)) * T0 + (wx - i);
+                    sum += (double)fr[cell * FP + (k * NF + j) * NF + i];
+                }
+        if (sum != 0.0) {
+            RhoAcc out{g, rho, ox + ST, oy + ST, oz + ST};
+            out.addRho(wx, wy, wz, qw * sum);
+        }
+    }
+}
+
 cudaError_t launch_rho(Ctx &c) {
     cudaError_t e = cudaMemsetAsync(c.rho, 0, sizeof(double) * c.g.cells(), c.st);
     if (e != cudaSuccess) return e;
@@ -1103,12 +1199,27 @@ cudaError_t launch_rho(Ctx &c) {
             int64_t ncell = c.nkeys / kSubKeys;
             unsigned kb = (unsigned)((ncell + 127) / 128);
 #define PP_R(O, A) k_rho_cells<O, A><<<kb, 128, 0, c.st>>>(c.g, kg, ncell, S.cell_start, qw, p64, pm, mixed, c.rho)
+#define PP_T(O)                                                                                            \
+    do {                                                                                                   \
+        constexpr int nf = (O % 2) ? O + 1 : O + 2;                                                       \
+        const size_t sm = sizeof(float) * (size_t)kg.tile_vol * (nf * nf * nf + 1);                        \
+        static bool attr = false;                                                                          \
+        if (!attr) {                                                                                       \
+            cudaError_t e_ = cudaFuncSetAttribute(k_rho_tile<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                  (int)(sizeof(float) * 512 * (nf * nf * nf + 1)));        \
+            if (e_ != cudaSuccess) return e_;                                                              \
+            attr = true;                                                                                   \
+        }                                                                                                  \
+        k_rho_tile<O><<<(unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]), kg.tile_vol, sm, c.st>>>(       \
+            c.g, kg, S.cell_start, qw, pm, c.rho);                                                         \
+    } while (0)
             if (mixed) {
-                if (c.d.shape_order == 1) PP_R(1, float); else if (c.d.shape_order == 2) PP_R(2, float); else PP_R(3, float);
+                if (c.d.shape_order == 1) PP_T(1); else if (c.d.shape_order == 2) PP_T(2); else PP_T(3);
             } else {
                 if (c.d.shape_order == 1) PP_R(1, double); else if (c.d.shape_order == 2) PP_R(2, double); else PP_R(3, double);
             }
 #undef PP_R
+#undef PP_T
             ++c.nlaunch;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

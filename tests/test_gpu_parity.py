@@ -268,3 +268,23 @@ def test_mixed_tiled_drift_fallback(pp, orc):
     Eg, Bg, Jg = glob.fields()
     assert max(H.rel_err(Et[a], Eg[a]) for a in range(3)) <= 1e-4
     assert max(H.rel_err(Jt[a], Jg[a]) for a in range(3)) <= 1e-4
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("n", [(20, 12, 9), (6, 5, 4), (24, 16, 16)])
+def test_mixed_rho_against_oracle(pp, orc, shape, n):
+    """The mixed form's charge density (eq:rho2, per-tile frames summed in
+    shared memory) against the oracle's FP64 deposit of the same positions:
+    tiles of every size (padded, smaller than 8, exact), and particles that
+    left their sorted cell (three steps without a re-sort).  FP32 weights:
+    5e-6 of max|rho|."""
+    L = pp_synth.random_particles(n, (0.5, 0.4, 0.45), 0.2, 3001, seed=40 + shape, u_scale=1.0)
+    gpu = H.gpu_sim(pp, L, pp.PP_MIXED32, shape, sort_interval=0)
+    gpu.step(3)
+    rho = gpu.rho()
+    p = gpu.particles(0)
+    s = L.species[0]
+    o = orc.Simulation(L.n, L.d, L.dt, shape_order=shape)
+    o.add_species(s["q"], s["m"], s["w"], p["x"], p["y"], p["z"], p["ux"], p["uy"], p["uz"])
+    ro = o.rho()
+    assert np.abs(rho - ro).max() <= 5e-6 * np.abs(ro).max()
