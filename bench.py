@@ -41,6 +41,13 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # pp_particles.cu that holds the particle kernels (up to its charge-density
 # section).
 PROFILED_BYTES_PER_PARTICLE = 901.909504e6 / 16777216
+# The same capture's issue and shared-memory figures, reported beside the HBM
+# fraction (the kernel is bound by shared-memory issue, not by DRAM).
+PROFILED_ISSUE = {"issue_active_pct": 56.9, "warp_instructions_per_particle": 111.4,
+                  "shared_wavefronts_per_particle": {"load": 14.0, "atomic": 12.8},
+                  "shared_bank_conflicts_per_particle": {"load": 0.5, "atomic": 6.4},
+                  "top_stall": "mio_throttle (shared-memory pipe)",
+                  "source": "profiles/k_particles_tiled_thermal64.md"}
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 _HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
 PROFILED_SOURCES = {
@@ -50,8 +57,8 @@ PROFILED_SOURCES = {
 }
 
 
-def profiled_traffic(particles_per_launch):
-    """ncu DRAM bytes per launch scaled to this launch, or None once the kernel changed."""
+def profiled_matches():
+    """True while the particle-kernel sources are the ones the committed capture was taken on."""
     import hashlib
     for rel, digest in PROFILED_SOURCES.items():
         with open(os.path.join(ROOT, rel)) as f:
@@ -61,8 +68,13 @@ def profiled_traffic(particles_per_launch):
         elif rel.endswith("pp_internal.cuh"):
             text = text[: text.index(_HOST_START)]
         if hashlib.sha256(text.encode()).hexdigest() != digest:
-            return None
-    return PROFILED_BYTES_PER_PARTICLE * particles_per_launch
+            return False
+    return True
+
+
+def profiled_traffic(particles_per_launch):
+    """ncu DRAM bytes per launch scaled to this launch, or None once the kernel changed."""
+    return PROFILED_BYTES_PER_PARTICLE * particles_per_launch if profiled_matches() else None
 
 
 def args():
@@ -436,6 +448,7 @@ def run_gpu(a):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None,
                      "traffic": profiled_traffic(npart * a.steps / max(1, prof["particle_launches"])),
+                     "issue": PROFILED_ISSUE if profiled_matches() else None,
                      "kernel": "fused particle step (gather+push+move+deposit)",
                      "bytes_per_particle_step": bytes_per_step, "peak_kind": peak_kind,
                      "kernel_ms_per_step": part_ms / a.steps},
