@@ -344,11 +344,28 @@ def mirror_x(f: np.ndarray, half: bool, sign: float) -> np.ndarray:
     return sign * f[..., idx]
 
 
-def wall_symmetrise(F, kind: str):
+def wall_parity(kind: str, comp: int, axis: int):
+    """(staggered along the normal, sign) of component comp of E, B or J across
+    a wall with normal `axis`: E_a and J_a are staggered along a, B_b along
+    every axis but b; staggered components are odd, the others even.  For
+    axis 0 this is WALL_PARITY."""
+    half = (comp == axis) if kind in ("E", "J") else (comp != axis)
+    return half, (-1.0 if half else 1.0)
+
+
+def mirror(f: np.ndarray, axis: int, half: bool, sign: float) -> np.ndarray:
+    """mirror_x along mesh axis `axis` (0 = x, the last array axis)."""
+    return np.moveaxis(mirror_x(np.moveaxis(np.asarray(f, dtype=np.float64), 2 - axis, -1), half, sign), -1, 2 - axis)
+
+
+def wall_symmetrise(F, kind: str, axes=(0,)):
     """Projection of three mesh arrays of the extended box onto the mirror-
-    symmetric state of the table above: f -> (f + P f(mirror)) / 2."""
-    return [0.5 * (np.asarray(F[a], dtype=np.float64) + mirror_x(np.asarray(F[a], dtype=np.float64), *WALL_PARITY[kind][a]))
-            for a in range(3)]
+    symmetric state, f -> (f + P f(mirror)) / 2, across each walled axis in turn
+    (the projections commute)."""
+    out = [np.asarray(F[a], dtype=np.float64) for a in range(3)]
+    for ax in axes:
+        out = [0.5 * (out[a] + mirror(out[a], ax, *wall_parity(kind, a, ax))) for a in range(3)]
+    return out
 
 
 def philox4x32(ctr, key):
@@ -384,18 +401,26 @@ TRANSVERSE = (1 << 1) | (1 << 2) | (1 << 4) | (1 << 5)
 
 
 class WallSimulation:
-    """Reflecting walls in x at 0 and L = n[0] d[0] (periodic in y and z): the
-    periodic oracle on the mirror-extended box of 2 n[0] cells, with every
-    particle's virtual image loaded as a particle.  Mesh arrays (fields,
-    J, rho) are those of the extended box, shape (nz, ny, 2 nx).  Energies,
-    charge and kinetic energy in diagnostics() are those of the physical box
-    [0, L] (half the extended box's sums)."""
+    """Reflecting walls at 0 and L_a = n[a] d[a] on each axis a with walls[a]
+    (x only by default; the others periodic): the periodic oracle on the
+    mirror-extended box (2 n[a] cells on each walled axis), with every
+    particle's virtual images (one per subset of the walled axes) loaded as
+    particles.  Mesh arrays (fields, J, rho) are those of the extended box.
+    Energies, charge and kinetic energy in diagnostics() are those of the
+    physical box (the extended box's sums over 2^k, k walled axes).  The open
+    end, the injector and the window act on x and need walls on x."""
 
-    def __init__(self, n, d, dt, **kw):
+    def __init__(self, n, d, dt, walls=(True, False, False), **kw):
+        self.walls = tuple(bool(w) for w in walls)
+        self.axes = [a for a in range(3) if self.walls[a]]
+        if not self.axes:
+            raise ValueError("at least one walled axis")
+        self.Ls = [n[a] * float(d[a]) for a in range(3)]
+        ext = tuple(2 * n[a] if self.walls[a] else n[a] for a in range(3))
         nx, ny, nz = n
         self.nx = int(nx)
         self.L = nx * float(d[0])
-        self.sim = Simulation((2 * nx, ny, nz), d, dt, **kw)
+        self.sim = Simulation(ext, d, dt, **kw)
         self.counts: list[int] = []
         self.d = tuple(float(v) for v in d)
         self.dt = float(dt)
@@ -428,54 +453,62 @@ class WallSimulation:
         return [self.particles(s) for s in range(len(self.counts))]
 
     def add_species(self, q, m, w, x, y, z, ux, uy, uz, rad=0.0) -> int:
-        x = np.asarray(x, dtype=np.float64)
-        if np.any(x < 0.0) or np.any(x > self.L):
-            raise ValueError("positions must lie between the walls")
-        ux = np.asarray(ux, dtype=np.float64)
-        image = np.where(x > 0.0, 2.0 * self.L - x, 0.0)
-        cat = np.concatenate
-        self.sim.add_species(q, m, w, cat([x, image]), cat([y, y]), cat([z, z]), cat([ux, -ux]), cat([uy, uy]),
-                             cat([uz, uz]), rad=rad)
-        self.counts.append(len(x))
-        return len(self.counts) - 1
+        phys = {k: np.asarray(v, dtype=np.float64).copy()
+                for k, v in dict(x=x, y=y, z=z, ux=ux, uy=uy, uz=uz).items()}
+        for a in self.axes:
+            p = phys["xyz"[a]]
+            if np.any(p < 0.0) or np.any(p > self.Ls[a]):
+                raise ValueError("positions must lie between the walls")
+        self.sim.add_species(q, m, w, *[np.zeros(0)] * 6, rad=rad)
+        self.counts.append(0)
+        sid = len(self.counts) - 1
+        self._set_pairs(sid, phys)
+        return sid
 
     def load_fields(self, E, B):
         """Extended-box arrays, projected onto the mirror-symmetric state."""
-        self.sim.load_fields(wall_symmetrise(E, "E"), wall_symmetrise(B, "B"))
+        self.sim.load_fields(wall_symmetrise(E, "E", self.axes), wall_symmetrise(B, "B", self.axes))
 
     # -- open lower end, injector, sliding window (readings R22-R24) ---------
     def set_open_boundary(self, cells: int, damping: float, escape: float, components: int = TRANSVERSE):
         """Outflow layer of `cells` cells at x = 0 (the other wall stays)."""
+        if not self.walls[0]:
+            raise ValueError("the open end needs walls on x")
         self.open = dict(cells=int(cells), damping=float(damping), escape=float(escape), mask=int(components))
 
     def set_injector(self, sid: int, ppc: float, u, u_th: float, seed: int):
         """Inflow through x = 0 of species sid: ppc particles per cell, drift
         proper velocity u (u[0] > 0), thermal spread u_th, Philox seed."""
+        if not self.walls[0]:
+            raise ValueError("the injector needs walls on x")
         self.injectors[sid] = dict(ppc=float(ppc), u=np.asarray(u, dtype=np.float64), u_th=float(u_th),
                                    seed=int(seed), k0=self.nstep)
 
     def set_window(self, v: float):
         """Sliding window at speed v against x (content moves one cell up)."""
+        if not self.walls[0]:
+            raise ValueError("the window needs walls on x")
         self.window = dict(v=float(v), k0=self.nstep)
 
-    def _pairs(self, sid):
-        s = self.sim.species[sid]
-        n = self.counts[sid]
-        return s, n, s["x"][:n] <= self.L
-
     def _set_pairs(self, sid, phys: dict, keep=None):
-        """Replace species sid by the given physical particles and their images."""
+        """Replace species sid by the given physical particles and their images:
+        copy s (s = 0 .. 2^k - 1) mirrors the walled axes whose bit is set in s,
+        x_a -> 2 L_a - x_a and u_a -> -u_a; copy 0 is the particles themselves."""
         if keep is not None:
             phys = {k: v[keep] for k, v in phys.items()}
-        x = phys["x"]
-        image = np.where(x > 0.0, 2.0 * self.L - x, 0.0)
+        copies = []
+        for sub in range(1 << len(self.axes)):
+            c = {k: v.copy() for k, v in phys.items()}
+            for bit, a in enumerate(self.axes):
+                if (sub >> bit) & 1:
+                    p = c["xyz"[a]]
+                    c["xyz"[a]] = np.where(p > 0.0, 2.0 * self.Ls[a] - p, 0.0)
+                    c["u" + "xyz"[a]] = -c["u" + "xyz"[a]]
+            copies.append(c)
         s = self.sim.species[sid]
-        cat = np.concatenate
-        s["x"] = cat([x, image])
-        s["ux"] = cat([phys["ux"], -phys["ux"]])
-        for k in ("y", "z", "uy", "uz"):
-            s[k] = cat([phys[k], phys[k]])
-        self.counts[sid] = len(x)
+        for k in ("x", "y", "z", "ux", "uy", "uz"):
+            s[k] = np.concatenate([c[k] for c in copies])
+        self.counts[sid] = len(phys["x"])
 
     def _damp(self):
         o = self.open
@@ -567,13 +600,21 @@ class WallSimulation:
                 self._slide()
 
     def particles(self, sid: int) -> dict:
-        """The member of each (particle, image) pair that lies in [0, L]."""
+        """The member of each particle's set of images that lies between the
+        walls on every walled axis."""
         s = self.sim.species[sid]
         n = self.counts[sid]
-        inside = s["x"][:n] <= self.L
-        out = {}
-        for k in ("x", "y", "z", "ux", "uy", "uz"):
-            out[k] = np.where(inside, s[k][:n], s[k][n:])
+        ncopy = 1 << len(self.axes)
+        out = {k: s[k][:n].copy() for k in ("x", "y", "z", "ux", "uy", "uz")}
+        found = np.zeros(n, dtype=bool)
+        for c in range(ncopy):
+            blk = slice(c * n, (c + 1) * n)
+            inside = ~found
+            for a in self.axes:
+                inside &= s["xyz"[a]][blk] <= self.Ls[a]
+            for k in out:
+                out[k] = np.where(inside, s[k][blk], out[k])
+            found |= inside
         return out
 
     def rho(self) -> np.ndarray:
@@ -582,5 +623,5 @@ class WallSimulation:
     def diagnostics(self) -> dict:
         d = self.sim.diagnostics()
         for k in ("energy_E", "energy_B", "energy_Ex", "kinetic", "charge"):
-            d[k] *= 0.5
+            d[k] *= 0.5 ** len(self.axes)
         return d

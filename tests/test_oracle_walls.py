@@ -312,3 +312,83 @@ def test_window_shifts_content_and_adds_a_layer(orc):
     xs = np.sort(pp_["x"] + d[0])
     xs = xs[xs <= n[0] * d[0]]
     assert np.abs(np.sort(pw["x"]) - xs).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Walls on y and z (and on several axes at once)
+# --------------------------------------------------------------------------
+
+def test_wall_parity_table_for_every_normal(orc):
+    """The generic table reduces to the paper's for the x normal, and for any
+    normal a the staggered components (E_a, J_a; B_b for b != a) are odd."""
+    for kind in ("E", "B", "J"):
+        for comp in range(3):
+            assert orc.wall_parity(kind, comp, 0) == orc.WALL_PARITY[kind][comp]
+    assert orc.wall_parity("E", 1, 1) == (True, -1.0) and orc.wall_parity("B", 1, 1) == (False, 1.0)
+    assert orc.wall_parity("B", 0, 2) == (True, -1.0) and orc.wall_parity("J", 0, 2) == (False, 1.0)
+
+
+def test_free_particle_bounces_in_a_closed_box(orc):
+    """Walls on all three axes: each coordinate of a light particle in empty
+    fields follows its own folded straight path, with that velocity component
+    reversed on its odd legs."""
+    n, d, dt = (8, 6, 4), (0.5, 0.5, 0.5), 0.2
+    Ls = np.array([n[a] * d[a] for a in range(3)])
+    x0 = np.array([[2.7, 1.1, 0.6], [0.3, 2.2, 1.7]])
+    u0 = np.array([[1.5, -0.9, 0.7], [-0.4, 1.2, -1.1]])
+    sim = orc.WallSimulation(n, d, dt, walls=(True, True, True), shape_order=2)
+    sim.add_species(-1.0, 1.0, 1e-13, x0[:, 0], x0[:, 1], x0[:, 2], u0[:, 0], u0[:, 1], u0[:, 2])
+    v = u0 / np.sqrt(1.0 + (u0 ** 2).sum(1))[:, None]
+    for k in (10, 25, 40):
+        sim.step(k - sim.nstep)
+        p = sim.particles(0)
+        for a in range(3):
+            s = np.mod(x0[:, a] + k * dt * v[:, a], 2 * Ls[a])
+            xe = np.where(s <= Ls[a], s, 2 * Ls[a] - s)
+            ue = np.where(s <= Ls[a], u0[:, a], -u0[:, a])
+            assert np.abs(p["xyz"[a]] - xe).max() < 1e-9, (k, a)
+            assert np.abs(p["u" + "xyz"[a]] - ue).max() < 1e-9, (k, a)
+
+
+@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (True, True, True)])
+def test_mirror_symmetry_kept_for_other_walls(orc, walls):
+    """Random particles and fields between walls on y, on z, or on all three
+    axes, three steps: every component keeps the parity of its wall normal
+    across every walled axis (to round-off)."""
+    n, d, dt = (8, 6, 6), (0.5, 0.45, 0.4), 0.2
+    L = pp_synth.random_particles(n, d, dt, 300, seed=61, u_scale=0.5)
+    s = L.species[0]
+    sim = orc.WallSimulation(n, d, dt, walls=walls, shape_order=3)
+    sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    ext = tuple(2 * n[a] if walls[a] else n[a] for a in range(3))
+    E, B = pp_synth.random_fields(ext, 62, 0.05)
+    sim.load_fields(E, B)
+    sim.step(3)
+    for kind, F in (("E", sim.E), ("B", sim.B), ("J", sim.J)):
+        for ax in range(3):
+            if not walls[ax]:
+                continue
+            for c in range(3):
+                err = np.abs(F[c] - orc.mirror(F[c], ax, *orc.wall_parity(kind, c, ax))).max()
+                assert err <= 1e-12 * max(np.abs(F[c]).max(), 1e-300), (kind, c, ax, err)
+    q = s["q"] * s["w"] * len(s["x"]) * d[0] * d[1] * d[2]
+    assert sim.diagnostics()["charge"] == pytest.approx(q, rel=1e-12)
+
+
+def test_folding_rules_on_y(orc):
+    """The paper's folding rules with the y normal (rho, J_x, J_z added across
+    the wall, J_y subtracted) reproduce the images' deposit."""
+    n, d, dt = (6, 8, 6), (0.5, 0.45, 0.4), 0.2
+    L = pp_synth.random_particles(n, d, dt, 400, seed=63, u_scale=0.6)
+    s = L.species[0]
+    walls = orc.WallSimulation(n, d, dt, walls=(False, True, False), shape_order=3)
+    walls.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    alone = orc.Simulation((n[0], 2 * n[1], n[2]), d, dt, shape_order=3)
+    alone.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    rho = walls.rho()
+    assert np.abs(alone.rho() + orc.mirror(alone.rho(), 1, False, 1.0) - rho).max() <= 1e-13 * np.abs(rho).max()
+    walls.sim.deposit()
+    alone.deposit()
+    for c in range(3):
+        jf = alone.J[c] + orc.mirror(alone.J[c], 1, *orc.wall_parity("J", c, 1))
+        assert np.abs(jf - walls.J[c]).max() <= 1e-12 * np.abs(walls.J[c]).max(), c
