@@ -90,20 +90,23 @@ typedef struct pp_ctx pp_ctx;
  * still creates the context (the paper reports instability below 0.525).
  *
  * boundary_x = PP_BOUNDARY_WALLS puts reflecting walls at x = 0 and
- * x = L = nx*dx (Sec. II "Boundary conditions"; y and z stay periodic).  The
+ * x = L = nx*dx (Sec. II "Boundary conditions"); boundary_y and boundary_z do
+ * the same on y and z, on any set of axes (the others stay periodic).  The
  * walls sit on integer (charge-density) nodes.  A particle that crosses a wall
  * deposits its current as if streaming freely, its virtual mirror image
- * deposits the mirrored current (rho and J_y, J_z added across the wall, J_x
- * subtracted), and only then is it reflected: x -> 2 x_b - x, u_x -> -u_x.  The
- * fields keep the paper's parities across each wall: E_x, B_y, B_z (staggered
- * in x) odd, E_y, E_z, B_x even.  The library holds the mesh as the
- * mirror-extended periodic box of 2*nx cells in x, whose second half is the
- * mirror image of the first, and every mesh array of the ABI (pp_load_fields,
- * pp_get_fields, pp_get_rho) has that shape: 2*nx*ny*nz values, x fastest.
- * pp_load_fields projects its arrays onto the mirror-symmetric state (each
- * value and its image replaced by their parity-signed mean).  Particle
- * positions stay physical: x in [0, L].  Needs 2*nx <= 1023 (and 2*nx a
- * multiple of 8 for the tiled deposit). */
+ * deposits the mirrored current (rho and the components along the wall added
+ * across it, the normal component subtracted), and only then is it reflected:
+ * x_a -> 2 x_b - x_a, u_a -> -u_a.  The fields keep the paper's parities
+ * across each wall: components staggered along its normal a (E_a; B_b, b != a)
+ * odd, the others even.  The library holds the mesh as the mirror-extended
+ * periodic box, 2*n_a cells on each walled axis a, whose added half is the
+ * mirror image of the physical one, and every mesh array of the ABI
+ * (pp_load_fields, pp_get_fields, pp_get_rho) has that shape (e.g.
+ * 2*nx*ny*nz values, x fastest, with walls on x).  pp_load_fields projects
+ * its arrays onto the mirror-symmetric state (each value and its image
+ * replaced by their parity-signed mean).  Particle positions stay physical:
+ * x_a in [0, L_a] on a walled axis.  Needs 2*n_a <= 1023 (and a multiple of 8
+ * for the tiled deposit). */
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz;
@@ -120,6 +123,8 @@ typedef struct {
     int deposit_mode;     /* PP_DEPOSIT_*                                         */
     void *stream;         /* cudaStream_t                                          */
     int boundary_x;       /* PP_BOUNDARY_PERIODIC or PP_BOUNDARY_WALLS             */
+    int boundary_y;       /* the same for y and z (walls on any set of axes)      */
+    int boundary_z;
 } pp_grid_desc;
 
 /* One particle species: charge q, mass m, and w = number density represented
@@ -132,9 +137,9 @@ typedef struct {
 
 /* FP64 global diagnostics (Sec. III eq:gauss, eq:divb, eq:rho2; Sec. VIII
  * field-energy series).  dV = dx*dy*dz.  Between walls the field energies and
- * the charge are those of the physical box [0, L] (half the sums over the
- * mirror-extended mesh); maxima are taken over the extended mesh, which holds
- * the same values twice. */
+ * the charge are those of the physical box (the sums over the mirror-extended
+ * mesh over 2^k, k walled axes); maxima are taken over the extended mesh,
+ * which holds the same values 2^k times. */
 typedef struct {
     int64_t step;              /* steps taken since pp_init_grid                 */
     double time;               /* step * dt                                       */
@@ -313,9 +318,9 @@ int pp_set_sliding_window(pp_ctx *ctx, double v);
  * velocities ux,uy,uz = gamma*v at t - dt/2.  Six FP64 arrays of n values,
  * host memory (on_device = 0) or device memory (on_device = 1); page-locked
  * host arrays are read in place by the device, pageable ones are staged.
- * Between walls (PP_BOUNDARY_WALLS) x must lie in [0, nx*dx].
+ * On an axis between walls (PP_BOUNDARY_WALLS) x_a must lie in [0, n_a*d_a].
  * Errors: PP_ENOMEM if the count would exceed the capacity, PP_ENAN if a
- * value is not finite, PP_EINVAL for an x outside the walls (nothing is
+ * value is not finite, PP_EINVAL for a position outside the walls (nothing is
  * appended then).  Loading re-sorts the
  * species by cell and resets the Gauss reference G_0 of pp_diagnostics (taken
  * from the loaded state before the next step or diagnostics). */

@@ -51,7 +51,8 @@ class GridDesc(C.Structure):
                 ("c", C.c_double), ("eps0", C.c_double), ("field_order", C.c_int), ("alpha", C.c_double),
                 ("shape_order", C.c_int), ("pusher", C.c_int), ("precision", C.c_int),
                 ("sort_interval", C.c_int), ("relax_max_iter", C.c_int), ("relax_tol", C.c_double),
-                ("deposit_mode", C.c_int), ("stream", C.c_void_p), ("boundary_x", C.c_int)]
+                ("deposit_mode", C.c_int), ("stream", C.c_void_p), ("boundary_x", C.c_int),
+                ("boundary_y", C.c_int), ("boundary_z", C.c_int)]
 
 
 class SpeciesDesc(C.Structure):
@@ -188,10 +189,11 @@ class Simulation:
 
     def __init__(self, n, d, dt, field_order=6, alpha=0.55, shape_order=3, pusher=PP_VAY, precision=PP_FP64,
                  sort_interval=20, relax_max_iter=200, relax_tol=1e-6, deposit_mode=PP_DEPOSIT_AUTO, stream=None,
-                 boundary_x=PP_BOUNDARY_PERIODIC, _handle=None):
-        """boundary_x = PP_BOUNDARY_WALLS: reflecting walls at x = 0 and n[0] d[0];
-        mesh arrays (fields(), rho(), load_fields()) then span the mirror-extended
-        box, shape (nz, ny, 2 nx)."""
+                 boundary_x=PP_BOUNDARY_PERIODIC, boundary_y=PP_BOUNDARY_PERIODIC, boundary_z=PP_BOUNDARY_PERIODIC,
+                 _handle=None):
+        """boundary_a = PP_BOUNDARY_WALLS: reflecting walls at 0 and n[a] d[a] on
+        axis a; mesh arrays (fields(), rho(), load_fields()) then span the
+        mirror-extended box, twice the cells on each walled axis."""
         self._ctx = C.c_void_p()
         if _handle is not None:
             self._ctx = _handle
@@ -200,11 +202,13 @@ class Simulation:
                          field_order=field_order, alpha=alpha, shape_order=shape_order, pusher=pusher,
                          precision=precision, sort_interval=sort_interval, relax_max_iter=relax_max_iter,
                          relax_tol=relax_tol, deposit_mode=deposit_mode,
-                         stream=stream if stream is not None else _current_stream(), boundary_x=boundary_x)
+                         stream=stream if stream is not None else _current_stream(), boundary_x=boundary_x,
+                         boundary_y=boundary_y, boundary_z=boundary_z)
             rc = lib().pp_init_grid(C.byref(self._ctx), C.byref(g))
             _check(rc, self._ctx if self._ctx.value else None)
         self.n = tuple(n)
-        self.walls = boundary_x == PP_BOUNDARY_WALLS
+        self.wall_axes = tuple(b == PP_BOUNDARY_WALLS for b in (boundary_x, boundary_y, boundary_z))
+        self.walls = self.wall_axes[0]
         self.nspecies = 0
 
     # -- lifecycle --------------------------------------------------------
@@ -331,9 +335,9 @@ class Simulation:
 
     @property
     def mesh_shape(self):
-        """(nz, ny, nx) of the mesh arrays; nx doubled between walls."""
-        nx, ny, nz = self.n
-        return (nz, ny, 2 * nx if self.walls else nx)
+        """(nz, ny, nx) of the mesh arrays; doubled on each walled axis."""
+        m = [2 * self.n[a] if self.wall_axes[a] else self.n[a] for a in range(3)]
+        return (m[2], m[1], m[0])
 
     def _mesh(self):
         return np.zeros(self.mesh_shape)
@@ -384,7 +388,8 @@ class Simulation:
         sim._ctx = h
         g, ns = sim.grid()
         sim.n = (g.nx, g.ny, g.nz)
-        sim.walls = g.boundary_x == PP_BOUNDARY_WALLS
+        sim.wall_axes = tuple(b == PP_BOUNDARY_WALLS for b in (g.boundary_x, g.boundary_y, g.boundary_z))
+        sim.walls = sim.wall_axes[0]
         sim.nspecies = ns
         return sim
 

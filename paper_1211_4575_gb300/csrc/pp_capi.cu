@@ -186,17 +186,22 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     Ctx *c = nullptr;
     if (!out || !d) return fail(c, PP_EINVAL, "pp_init_grid: NULL argument");
     *out = nullptr;
-    if (d->boundary_x != PP_BOUNDARY_PERIODIC && d->boundary_x != PP_BOUNDARY_WALLS)
-        return fail(c, PP_EINVAL, "unknown boundary_x %d", d->boundary_x);
-    const bool walls = d->boundary_x == PP_BOUNDARY_WALLS;
-    // between walls the mesh is the mirror-extended box: 2 nx cells in x
-    int n[3] = {walls ? 2 * d->nx : d->nx, d->ny, d->nz};
+    const int bnd[3] = {d->boundary_x, d->boundary_y, d->boundary_z};
+    const int nphys[3] = {d->nx, d->ny, d->nz};
+    bool walls[3];
+    int n[3];   // mesh cells: the mirror-extended box (twice the cells) on walled axes
+    for (int a = 0; a < 3; ++a) {
+        if (bnd[a] != PP_BOUNDARY_PERIODIC && bnd[a] != PP_BOUNDARY_WALLS)
+            return fail(c, PP_EINVAL, "unknown boundary %d on axis %d", bnd[a], a);
+        walls[a] = bnd[a] == PP_BOUNDARY_WALLS;
+        if (nphys[a] < 1) return fail(c, PP_EINVAL, "grid size %d on axis %d below 1", nphys[a], a);
+        n[a] = walls[a] ? 2 * nphys[a] : nphys[a];
+    }
     double h[3] = {d->dx, d->dy, d->dz};
-    if (walls && d->nx < 1) return fail(c, PP_EINVAL, "grid size %d on axis 0 below 1", d->nx);
     for (int a = 0; a < 3; ++a) {
         if (n[a] < 1 || n[a] > 1023)
             return fail(c, PP_EINVAL, "grid size %d on axis %d outside [1, 1023]%s", n[a], a,
-                        walls && a == 0 ? " (between walls the mesh holds 2 nx cells in x)" : "");
+                        walls[a] ? " (between walls the mesh holds twice the cells)" : "");
         if (!(h[a] > 0.0)) return fail(c, PP_EINVAL, "cell size on axis %d must be > 0", a);
         if (!(d->dt > 0.0) || !(d->dt / h[a] < 1.0))
             return fail(c, PP_EINVAL, "need 0 < c dt / d < 1 on every axis (axis %d: %g)", a, d->dt / h[a]);
@@ -222,7 +227,7 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
         return fail(c, PP_EINVAL, "the tiled deposit exists for PP_MIXED32 only");
     if (d->deposit_mode == PP_DEPOSIT_TILED && (n[0] % 8 || n[1] % 8 || n[2] % 8))
         return fail(c, PP_EINVAL, "the tiled deposit needs every mesh size to be a multiple of 8%s",
-                    walls ? " (2 nx between walls)" : "");
+                    (walls[0] || walls[1] || walls[2]) ? " (twice the cells on a walled axis)" : "");
 
     pp_ctx *p = new (std::nothrow) pp_ctx();
     if (!p) return fail(c, PP_ENOMEM, "host allocation failed");
@@ -231,7 +236,7 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     c->st = (cudaStream_t)d->stream;
     c->fp64 = d->precision == PP_FP64;
     c->rsz = c->fp64 ? 8 : 4;
-    c->mirror = walls ? d->nx : 0;
+    for (int a = 0; a < 3; ++a) c->wall[a] = walls[a] ? nphys[a] : 0;
     for (int a = 0; a < 3; ++a) {
         c->g.n[a] = n[a];
         c->g.P[a] = n[a] + 2 * kGhost;
@@ -441,8 +446,7 @@ extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x,
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle load: %s", cudaGetErrorString(e));
         else if (*c->h_status & 1) rc = fail(c, PP_ENAN, "non-finite particle value: nothing appended");
-        else if (*c->h_status) rc = fail(c, PP_EINVAL, "particle x outside the walls [0, %g]: nothing appended",
-                                         c->mirror * c->d.dx);
+        else if (*c->h_status) rc = fail(c, PP_EINVAL, "particle position outside the walls: nothing appended");
         cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
     }
     if (stage) {
@@ -651,7 +655,7 @@ extern "C" int pp_sort(pp_ctx *p) {
 // Open end, injectors or a sliding window: steps change the particle count on
 // the host and synchronise at sorts, so they run eagerly.
 static bool boundary_dynamic(const Ctx *c) {
-    if (!c->mirror) return false;
+    if (!c->wall[0]) return false;
     if (c->open.cells > 0 || c->window.v > 0.0) return true;
     for (int s = 0; s < c->nspecies; ++s)
         if (c->inj[s].ppc > 0.0) return true;
@@ -681,7 +685,7 @@ static int boundary_step(Ctx *c) {
         CU(launch_damp(*c));
         c->filtered_after_solve = true;   // B moved since the solve: its residual no longer measures it
     }
-    const double ny = c->g.n[1], nz = c->g.n[2];
+    const double ny = c->d.ny, nz = c->d.nz;   // the physical box
     for (int s = 0; s < c->nspecies; ++s) {
         const Ctx::Injector &I = c->inj[s];
         if (!(I.ppc > 0.0)) continue;
@@ -730,7 +734,7 @@ static int step_body(Ctx *c, bool sort, bool filter) {
     }
     int r = PP_OK;
     // the open end takes outgoing particles at the end of a full step
-    const double esc = (c->mirror && c->open.cells > 0) ? c->open.escape : 0.0;
+    const double esc = (c->wall[0] && c->open.cells > 0) ? c->open.escape : 0.0;
     if (esc > 0.0)
         for (int s = 0; s < c->nspecies; ++s) c->sp[s].may_hold_dead = true;
     if (c->order == 4) {
@@ -929,10 +933,10 @@ extern "C" int pp_set_divergence_filter(pp_ctx *p, int passes, int interval) {
 extern "C" int pp_set_open_boundary(pp_ctx *p, int cells, double damping, double escape, int components) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
-    if (!c->mirror) return fail(c, PP_EINVAL, "an open end needs boundary_x = PP_BOUNDARY_WALLS");
-    if (cells < 0 || cells > c->mirror) return fail(c, PP_EINVAL, "layer of %d cells outside [0, nx]", cells);
+    if (!c->wall[0]) return fail(c, PP_EINVAL, "an open end needs boundary_x = PP_BOUNDARY_WALLS");
+    if (cells < 0 || cells > c->wall[0]) return fail(c, PP_EINVAL, "layer of %d cells outside [0, nx]", cells);
     if (!(damping >= 0.0 && damping <= 1.0)) return fail(c, PP_EINVAL, "damping must lie in [0, 1]");
-    if (!(escape >= 0.0 && escape <= (double)c->mirror)) return fail(c, PP_EINVAL, "escape must lie in [0, nx]");
+    if (!(escape >= 0.0 && escape <= (double)c->wall[0])) return fail(c, PP_EINVAL, "escape must lie in [0, nx]");
     if (components < 0 || components > 63) return fail(c, PP_EINVAL, "components is a 6-bit mask");
     c->open.cells = cells;
     c->open.damping = damping;
@@ -945,7 +949,7 @@ extern "C" int pp_set_open_boundary(pp_ctx *p, int cells, double damping, double
 extern "C" int pp_set_injector(pp_ctx *p, int sid, double ppc, const double u[3], double u_th, uint64_t seed) {
     Ctx *c = p;
     if (!c || !u) return fail(c, PP_EINVAL, "pp_set_injector: NULL argument");
-    if (!c->mirror) return fail(c, PP_EINVAL, "an injector needs boundary_x = PP_BOUNDARY_WALLS");
+    if (!c->wall[0]) return fail(c, PP_EINVAL, "an injector needs boundary_x = PP_BOUNDARY_WALLS");
     if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
     if (!(ppc >= 0.0 && ppc < 1e6) || !(u_th >= 0.0 && u_th < 1e6) || !isfinite(u[0]) || !isfinite(u[1]) ||
         !isfinite(u[2]))
@@ -964,7 +968,7 @@ extern "C" int pp_set_injector(pp_ctx *p, int sid, double ppc, const double u[3]
 extern "C" int pp_set_sliding_window(pp_ctx *p, double v) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
-    if (!c->mirror) return fail(c, PP_EINVAL, "a sliding window needs boundary_x = PP_BOUNDARY_WALLS");
+    if (!c->wall[0]) return fail(c, PP_EINVAL, "a sliding window needs boundary_x = PP_BOUNDARY_WALLS");
     if (!(v >= 0.0 && v < 1.0)) return fail(c, PP_EINVAL, "window speed must lie in [0, c)");
     c->window.v = v;
     c->window.k0 = c->step;
@@ -1066,7 +1070,8 @@ extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
     CU(cudaMemcpyAsync(kin, c->d_out + 16, sizeof(double) * PP_MAX_SPECIES, cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
     double dV = c->d.dx * c->d.dy * c->d.dz;
-    const double box = c->mirror ? 0.5 : 1.0;   // between walls: the physical half of the extended mesh
+    // between walls: the physical part of the extended mesh (half per walled axis)
+    const double box = (c->wall[0] ? 0.5 : 1.0) * (c->wall[1] ? 0.5 : 1.0) * (c->wall[2] ? 0.5 : 1.0);
     out->step = c->step;
     out->time = c->step * c->d.dt;
     out->energy_E = mesh[0] * dV * box;
@@ -1172,7 +1177,7 @@ extern "C" int pp_get_particles(pp_ctx *p, int sid, double *x, double *y, double
 // Format 2 adds each species' radiative-cooling coefficient, format 3 the
 // integrator order, format 4 the field solver, format 5 the current deposit
 // and the divergence filter; older files restore with the defaults.
-static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '7'};
+static const char kMagic[8] = {'P', 'P', 'G', 'B', '3', '0', '0', '8'};
 
 extern "C" int pp_save(pp_ctx *p, const char *path) {
     Ctx *c = p;
@@ -1225,10 +1230,13 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
     int64_t step = 0;
     int ns = 0;
     int order = 2, solver = PP_FIELD_IMPLICIT, cmode = PP_CURRENT_CONSERVING, fpasses = 0, finterval = 1;
-    // formats 1-5 wrote the descriptor without its last member (boundary_x)
+    // formats 1-5 wrote the descriptor up to boundary_x, formats 6-7 up to boundary_y
     memset(&d, 0, sizeof d);
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '7' &&
-              fread(&d, magic[7] >= '6' ? sizeof d : offsetof(pp_grid_desc, boundary_x), 1, f) == 1 &&
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 7) == 0 && magic[7] >= '1' && magic[7] <= '8' &&
+              fread(&d, magic[7] >= '8' ? sizeof d
+                                        : (magic[7] >= '6' ? offsetof(pp_grid_desc, boundary_y)
+                                                           : offsetof(pp_grid_desc, boundary_x)),
+                    1, f) == 1 &&
               fread(&step, sizeof step, 1, f) == 1 && fread(&ns, sizeof ns, 1, f) == 1 && ns >= 0 &&
               ns <= PP_MAX_SPECIES && (magic[7] < '3' || fread(&order, sizeof order, 1, f) == 1) &&
               (magic[7] < '4' || fread(&solver, sizeof solver, 1, f) == 1) &&
@@ -1270,7 +1278,7 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
         Ctx::OpenEnd open;
         Ctx::Window window;
         ok = fread(&open, sizeof open, 1, f) == 1 && fread(&window, sizeof window, 1, f) == 1;
-        if (ok && c->mirror) {   // validated through the setters, then the run's state taken over
+        if (ok && c->wall[0]) {   // validated through the setters, then the run's state taken over
             rc = pp_set_open_boundary(p, open.cells, open.damping, open.escape, open.mask);
             if (rc == PP_OK) rc = pp_set_sliding_window(p, window.v);
             c->window = window;
@@ -1278,7 +1286,7 @@ extern "C" int pp_restore(pp_ctx **out, const char *path, void *stream) {
         for (int s = 0; s < ns && ok && rc == PP_OK; ++s) {
             Ctx::Injector I;
             ok = fread(&I, sizeof I, 1, f) == 1;
-            if (ok && c->mirror) {
+            if (ok && c->wall[0]) {
                 rc = pp_set_injector(p, s, I.ppc, I.u, I.u_th, I.seed);
                 c->inj[s] = I;
             }

@@ -520,9 +520,11 @@ struct Ctx {
     int field_solver = 0;    // PP_FIELD_IMPLICIT or PP_FIELD_EXPLICIT
     bool g0_pending = false; // a load changed rho or E: take the Gauss reference before the next use
     int current_mode = 0;    // PP_CURRENT_CONSERVING or PP_CURRENT_DIRECT
-    // Reflecting walls at x = 0 and x = mirror (cells): the mesh is the
-    // mirror-extended box, g.n[0] = 2 * mirror.  0 = periodic in x.
-    int mirror = 0;
+    // Reflecting walls at 0 and wall[a] (cells) on axis a: the mesh is the
+    // mirror-extended box there, g.n[a] = 2 * wall[a].  0 = periodic.  The open
+    // end, the injectors and the window act on x and need wall[0].
+    int wall[3] = {0, 0, 0};
+    bool any_wall() const { return wall[0] || wall[1] || wall[2]; }
     // Open lower end between walls (outflow layer, escape), injectors and the
     // sliding window (Sec. II "Boundary conditions", "Sliding window and
     // injection of particles").

@@ -85,18 +85,19 @@ cudaError_t launch_zero_J(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------
-// Reflecting walls (Sec. II "Boundary conditions").  Between walls the mesh is
-// the mirror-extended box of n0 = 2 nx cells in x, the walls on the integer
-// nodes 0 and nx.  Along x, integer node i has the image (n0 - i) mod n0 and
-// half node i+1/2 (index i) the image index n0 - 1 - i.  Components staggered
-// in x are odd across a wall and the others even: component 0 of E and J,
-// components 1 and 2 of B.
+// Reflecting walls (Sec. II "Boundary conditions").  On a walled axis a the
+// mesh is the mirror-extended box of n0 = 2 n_a cells, the walls on the
+// integer nodes 0 and n_a.  Along a, integer node i has the image
+// (n0 - i) mod n0 and half node i+1/2 (index i) the image index n0 - 1 - i.
+// Components staggered along a are odd across the wall and the others even:
+// E_a and J_a, and every B_b with b != a.  Walls on several axes fold one axis
+// after the other (the images of images are the corner images).
 //
 // avg = 0 (a deposit): the virtual images contribute the mirror of what the
 // particles deposited, f(i) <- f(i) + P f(m(i)), and the image node receives
 // P times that sum; a wall node, its own image, doubles.  avg = 1 (a load):
 // f(i) <- (f(i) + P f(m(i))) / 2 on both nodes of the pair.  One thread per
-// pair: i in [0, nx] along a row (odd components stop at nx - 1).
+// pair: i in [0, n_a] along a row (odd components stop at n_a - 1).
 // ---------------------------------------------------------------------------
 struct PaddedIndex {
     Geom g;
@@ -109,24 +110,32 @@ struct CompactIndex {
     }
 };
 
+// Pairs along the wall normal `ax` (walls at 0 and nw cells), over the mesh
+// extents ne of the other two axes: thread (i, p, r) holds the row position i
+// along ax and the coordinates p, r along axes ax+1, ax+2 (mod 3).
 template <typename R, class Ix>
-__global__ void k_mirror(Ix ix, int nx, int ny, int nz, R *F0, R *F1, R *F2, int odd_mask, int avg) {
+__global__ void k_mirror(Ix ix, int ax, int nw, int nb, int nc, R *F0, R *F1, R *F2, int odd_mask, int avg) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int comp = blockIdx.y;
-    if (t >= (int64_t)(nx + 1) * ny * nz) return;
-    const int i = (int)(t % (nx + 1));
-    const int64_t r = t / (nx + 1);
-    const int j = (int)(r % ny), k = (int)(r / ny);
+    if (t >= (int64_t)(nw + 1) * nb * nc) return;
+    const int i = (int)(t % (nw + 1));
+    const int64_t r = t / (nw + 1);
+    const int pb = (int)(r % nb), pc = (int)(r / nb);
     const bool odd = (odd_mask >> comp) & 1;
     int m;
     if (odd) {
-        if (i == nx) return;
-        m = 2 * nx - 1 - i;
+        if (i == nw) return;
+        m = 2 * nw - 1 - i;
     } else {
-        m = i == 0 ? 0 : 2 * nx - i;
+        m = i == 0 ? 0 : 2 * nw - i;
     }
+    int q[3], qm[3];
+    q[ax] = i;
+    qm[ax] = m;
+    q[(ax + 1) % 3] = qm[(ax + 1) % 3] = pb;
+    q[(ax + 2) % 3] = qm[(ax + 2) % 3] = pc;
     R *F = comp == 0 ? F0 : (comp == 1 ? F1 : F2);
-    const int64_t a = ix(i, j, k), b = ix(m, j, k);
+    const int64_t a = ix(q[0], q[1], q[2]), b = ix(qm[0], qm[1], qm[2]);
     const R P = odd ? R(-1) : R(1);
     R v = F[a] + P * F[b];
     if (avg) v *= R(0.5);
@@ -134,36 +143,46 @@ __global__ void k_mirror(Ix ix, int nx, int ny, int nz, R *F0, R *F1, R *F2, int
     if (b != a) F[b] = P * v;
 }
 
+// Components odd across a wall with normal ax: E_ax and J_ax (staggered along
+// it); for B every component but B_ax.
+static inline int odd_mask(bool bfield, int ax) { return bfield ? (7 & ~(1 << ax)) : (1 << ax); }
+
+template <typename R, class Ix>
+static cudaError_t mirror_axes(Ctx &c, Ix ix, R *F0, R *F1, R *F2, int ncomp, int bfield_or_rho, int avg) {
+    for (int ax = 0; ax < 3; ++ax) {
+        const int nw = c.wall[ax];
+        if (!nw) continue;
+        const int nb = c.g.n[(ax + 1) % 3], nc = c.g.n[(ax + 2) % 3];
+        const int mask = bfield_or_rho < 0 ? 0 : odd_mask(bfield_or_rho == 1, ax);
+        dim3 grid((unsigned)(((int64_t)(nw + 1) * nb * nc + 255) / 256), (unsigned)ncomp);
+        k_mirror<R, Ix><<<grid, 256, 0, c.st>>>(ix, ax, nw, nb, nc, F0, F1, F2, mask, avg);
+        ++c.nlaunch;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <typename R>
-static cudaError_t mirror_padded(Ctx &c, void *const F[3], int odd_mask, int avg) {
-    const int nx = c.mirror, ny = c.g.n[1], nz = c.g.n[2];
-    dim3 grid((unsigned)(((int64_t)(nx + 1) * ny * nz + 255) / 256), 3);
-    k_mirror<R, PaddedIndex><<<grid, 256, 0, c.st>>>(PaddedIndex{c.g}, nx, ny, nz, (R *)F[0], (R *)F[1], (R *)F[2],
-                                                     odd_mask, avg);
-    ++c.nlaunch;
-    return cudaGetLastError();
+static cudaError_t mirror_padded(Ctx &c, void *const F[3], int bfield, int avg) {
+    return mirror_axes<R, PaddedIndex>(c, PaddedIndex{c.g}, (R *)F[0], (R *)F[1], (R *)F[2], 3, bfield, avg);
 }
 
 cudaError_t launch_mirror_J(Ctx &c) {
-    if (!c.mirror) return cudaSuccess;
-    return c.fp64 ? mirror_padded<double>(c, c.J, 1, 0) : mirror_padded<float>(c, c.J, 1, 0);
+    if (!c.any_wall()) return cudaSuccess;
+    return c.fp64 ? mirror_padded<double>(c, c.J, 0, 0) : mirror_padded<float>(c, c.J, 0, 0);
 }
 
 cudaError_t launch_mirror_fields(Ctx &c) {
-    if (!c.mirror) return cudaSuccess;
-    cudaError_t e = c.fp64 ? mirror_padded<double>(c, c.E, 1, 1) : mirror_padded<float>(c, c.E, 1, 1);
+    if (!c.any_wall()) return cudaSuccess;
+    cudaError_t e = c.fp64 ? mirror_padded<double>(c, c.E, 0, 1) : mirror_padded<float>(c, c.E, 0, 1);
     if (e != cudaSuccess) return e;
-    return c.fp64 ? mirror_padded<double>(c, c.B, 6, 1) : mirror_padded<float>(c, c.B, 6, 1);
+    return c.fp64 ? mirror_padded<double>(c, c.B, 1, 1) : mirror_padded<float>(c, c.B, 1, 1);
 }
 
 cudaError_t launch_mirror_rho(Ctx &c, double *rho) {
-    if (!c.mirror) return cudaSuccess;
-    const int nx = c.mirror, ny = c.g.n[1], nz = c.g.n[2];
-    dim3 grid((unsigned)(((int64_t)(nx + 1) * ny * nz + 255) / 256), 1);
-    k_mirror<double, CompactIndex><<<grid, 256, 0, c.st>>>(CompactIndex{c.g.n[0], c.g.n[1]}, nx, ny, nz, rho, rho, rho,
-                                                            0, 0);
-    ++c.nlaunch;
-    return cudaGetLastError();
+    if (!c.any_wall()) return cudaSuccess;
+    return mirror_axes<double, CompactIndex>(c, CompactIndex{c.g.n[0], c.g.n[1]}, rho, rho, rho, 1, -1, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -209,7 +228,7 @@ static cudaError_t damp_impl(Ctx &c) {
 }
 
 cudaError_t launch_damp(Ctx &c) {
-    if (!c.mirror || c.open.cells <= 0 || !c.open.mask) return cudaSuccess;
+    if (!c.wall[0] || c.open.cells <= 0 || !c.open.mask) return cudaSuccess;
     return c.fp64 ? damp_impl<double>(c) : damp_impl<float>(c);
 }
 
@@ -249,7 +268,7 @@ static cudaError_t window_fields_impl(Ctx &c) {
     void **S[2] = {c.Xa, c.Xb};
     const int odd[2] = {1, 6};
     for (int f = 0; f < 2; ++f) {
-        k_window_fields<R><<<grid, 256, 0, c.st>>>(c.g, c.mirror, (const R *)F[f][0], (const R *)F[f][1],
+        k_window_fields<R><<<grid, 256, 0, c.st>>>(c.g, c.wall[0], (const R *)F[f][0], (const R *)F[f][1],
                                                    (const R *)F[f][2], (R *)S[f][0], (R *)S[f][1], (R *)S[f][2],
                                                    odd[f]);
         ++c.nlaunch;
@@ -265,7 +284,7 @@ static cudaError_t window_fields_impl(Ctx &c) {
 }
 
 cudaError_t launch_window_fields(Ctx &c) {
-    if (!c.mirror) return cudaSuccess;
+    if (!c.wall[0]) return cudaSuccess;
     return c.fp64 ? window_fields_impl<double>(c) : window_fields_impl<float>(c);
 }
 

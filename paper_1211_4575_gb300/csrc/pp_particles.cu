@@ -49,7 +49,7 @@ struct StepArgs {
     int64_t n;
     int *status;
     int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
-    int mirror;                  // walls at x = 0 and x = mirror cells; 0 = periodic
+    int wall[3];                 // walls at 0 and wall[a] cells on axis a; 0 = periodic
     double esc;                  // open end: outgoing particles below x = esc cells leave; 0 = off
     int64_t off;                 // first particle of the launch
 };
@@ -63,12 +63,12 @@ struct MixedParticles {
     float *ox, *oy, *oz, *ux, *uy, *uz;
 };
 
-// Reflecting walls at x = 0 and x = nw cells (Sec. II "Boundary conditions"),
-// applied after the particle deposited its step as if streaming freely: a
-// particle that ended the move beyond a wall (in (nw, 2 nw) of the
-// mirror-extended box, which the periodic wrap also gives for x < 0) is
-// replaced by its virtual image, x -> 2 nw - x and u_x -> -u_x.  nw = 0: no
-// walls.
+// Reflecting walls at 0 and nw cells on one axis (Sec. II "Boundary
+// conditions"), applied after the particle deposited its step as if streaming
+// freely: a particle that ended the move beyond a wall (in (nw, 2 nw) of the
+// mirror-extended box, which the periodic wrap also gives below 0) is replaced
+// by its virtual image, x -> 2 nw - x and u -> -u along that axis.  nw = 0: no
+// walls on the axis.
 __device__ __forceinline__ void reflect(double &xi, double &ux, int nw) {
     if (nw && xi > (double)nw) {
         xi = 2.0 * (double)nw - xi;
@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
         if (v >= L) v -= L;
         xi1[d] = v;
     }
-    reflect(xi1[0], u[0], a.mirror);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) reflect(xi1[d], u[d], a.wall[d]);
     if (a.esc > 0.0 && xi1[0] < a.esc && u[0] < 0.0) xi1[0] = kDeadX;   // out through the open end
     p.x[t] = xi1[0]; p.y[t] = xi1[1]; p.z[t] = xi1[2];
     p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
@@ -201,7 +202,9 @@ __global__ void __launch_bounds__(256) k_particles_mixed(StepArgs<float> a, Mixe
     rebin(xi1[0], cx, a.g.n[0]);
     rebin(xi1[1], cy, a.g.n[1]);
     rebin(xi1[2], cz, a.g.n[2]);
-    reflect(cx, xi1[0], u[0], a.mirror);
+    reflect(cx, xi1[0], u[0], a.wall[0]);
+    reflect(cy, xi1[1], u[1], a.wall[1]);
+    reflect(cz, xi1[2], u[2], a.wall[2]);
     int32_t cw = pack_cell(cx, cy, cz);
     if (a.esc > 0.0 && (double)cx + (double)xi1[0] < a.esc && u[0] < 0.0f) cw |= kDeadBit;
     p.cell[t] = cw;
@@ -229,7 +232,7 @@ static StepArgs<R> step_args(Ctx &c, int s) {
     a.n = S.n;
     a.status = c.d_status;
     a.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
-    a.mirror = c.mirror;
+    for (int d = 0; d < 3; ++d) a.wall[d] = c.wall[d];
     a.esc = c.escape_now;
     a.off = 0;
     return a;
@@ -392,7 +395,7 @@ struct TiledArgs {
     TiledSpecies sp[kMaxTiledSpecies];
     int *status;
     int direct;                  // 1: direct current eq:jj2; 0: charge-conserving
-    int mirror;                  // walls at x = 0 and x = mirror cells; 0 = periodic
+    int wall[3];                 // walls at 0 and wall[a] cells on axis a; 0 = periodic
     double esc;                  // open end: outgoing particles below x = esc cells leave; 0 = off
 };
 
@@ -563,7 +566,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
                 rebin(xi1[2], cz, g.n[2]);
                 int32_t cw;
                 if constexpr (BND) {
-                    reflect(cx, xi1[0], s_u[sq], T.mirror);
+                    reflect(cx, xi1[0], s_u[sq], T.wall[0]);
+                    reflect(cy, xi1[1], s_u[kStage + sq], T.wall[1]);
+                    reflect(cz, xi1[2], s_u[2 * kStage + sq], T.wall[2]);
                     cw = pack_cell(cx, cy, cz);
                     if (T.esc > 0.0 && (double)cx + (double)xi1[0] < T.esc && s_u[sq] < 0.0f) cw |= kDeadBit;
                 } else {
@@ -698,7 +703,9 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
         rebin(xi1[0], cx, a.g.n[0]);
         rebin(xi1[1], cy, a.g.n[1]);
         rebin(xi1[2], cz, a.g.n[2]);
-        reflect(cx, xi1[0], u[0], a.mirror);
+        reflect(cx, xi1[0], u[0], a.wall[0]);
+        reflect(cy, xi1[1], u[1], a.wall[1]);
+        reflect(cz, xi1[2], u[2], a.wall[2]);
         int32_t cw = pack_cell(cx, cy, cz);
         if (a.esc > 0.0 && (double)cx + (double)xi1[0] < a.esc && u[0] < 0.0f) cw |= kDeadBit;
         p.cell[t] = cw;
@@ -753,12 +760,12 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
     }
     T.status = c.d_status;
     T.direct = c.current_mode == PP_CURRENT_DIRECT ? 1 : 0;
-    T.mirror = c.mirror;
+    for (int d = 0; d < 3; ++d) T.wall[d] = c.wall[d];
     T.esc = c.escape_now;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
     static bool attr_done[2][2][4] = {{{false}}};
-    const bool bnd = c.mirror != 0;
+    const bool bnd = c.any_wall();
     cudaError_t e = cudaSuccess;
     if (T.ns > 0) {
 #define PP_TB(O, PU, BD)                                                                                    \
@@ -915,8 +922,8 @@ cudaError_t launch_inject(Ctx &c, int s, int64_t off, int64_t count, uint32_t st
     a.pstream = pstream;
     a.vstream = pstream + 1u + (uint32_t)s;
     a.thick = thick;
-    a.ly = c.g.n[1] * c.d.dy;
-    a.lz = c.g.n[2] * c.d.dz;
+    a.ly = c.d.ny * c.d.dy;   // the physical box (the mesh is doubled on walled axes)
+    a.lz = c.d.nz * c.d.dz;
     a.h[0] = c.d.dx; a.h[1] = c.d.dy; a.h[2] = c.d.dz;
     for (int d = 0; d < 3; ++d) {
         a.n[d] = c.g.n[d];
@@ -958,7 +965,7 @@ cudaError_t launch_window_particles(Ctx &c, int s) {
     if (S.n == 0) return cudaSuccess;
     Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
-    k_window_particles<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, c.mirror, p64, pm, c.fp64 ? 0 : 1);
+    k_window_particles<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, c.wall[0], p64, pm, c.fp64 ? 0 : 1);
     ++c.nlaunch;
     return cudaGetLastError();
 }
@@ -1287,7 +1294,7 @@ cudaError_t launch_kinetic(Ctx &c, double *out) {
 __global__ void k_convert_in(int64_t n, int64_t off, const double *x, const double *y, const double *z,
                              const double *ux, const double *uy, const double *uz, double hx, double hy,
                              double hz, int nx, int ny, int nz, int mixed, Fp64Particles p64, MixedParticles pm,
-                             int *bad, double wall) {
+                             int *bad, double wx, double wy, double wz) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     double in[3] = {x[t], y[t], z[t]};
@@ -1296,10 +1303,12 @@ __global__ void k_convert_in(int64_t n, int64_t off, const double *x, const doub
         atomicOr(bad, 1);
         return;
     }
-    if (wall > 0.0 && !(in[0] >= 0.0 && in[0] <= wall)) {   // between walls: x in [0, L]
-        atomicOr(bad, 2);
-        return;
-    }
+    const double wl[3] = {wx, wy, wz};   // walls at 0 and L_a on axes with L_a > 0
+    for (int d = 0; d < 3; ++d)
+        if (wl[d] > 0.0 && !(in[d] >= 0.0 && in[d] <= wl[d])) {
+            atomicOr(bad, 2);
+            return;
+        }
     double h[3] = {hx, hy, hz};
     int N[3] = {nx, ny, nz};
     double xi[3];
@@ -1337,7 +1346,8 @@ cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const doubl
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_convert_in<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(n, off, x, y, z, ux, uy, uz, c.d.dx, c.d.dy, c.d.dz,
                                                                c.g.n[0], c.g.n[1], c.g.n[2], c.fp64 ? 0 : 1, p64, pm,
-                                                               bad, c.mirror ? c.mirror * c.d.dx : 0.0);
+                                                               bad, c.wall[0] * c.d.dx, c.wall[1] * c.d.dy,
+                                                               c.wall[2] * c.d.dz);
     ++c.nlaunch;
     return cudaGetLastError();
 }

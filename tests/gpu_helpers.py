@@ -6,12 +6,14 @@ import numpy as np
 
 
 def gpu_sim(pp, L, precision, shape_order, field_order=6, alpha=0.55, pusher=0, relax_tol=None, sort_interval=20,
-            deposit_mode=0, capacity_extra=0, relax_max_iter=400, stream=None, boundary_x=0):
+            deposit_mode=0, capacity_extra=0, relax_max_iter=400, stream=None, boundary_x=0, boundary_y=0,
+            boundary_z=0):
     if relax_tol is None:
         relax_tol = 1e-14 if precision == pp.PP_FP64 else 1e-6
     sim = pp.Simulation(L.n, L.d, L.dt, field_order=field_order, alpha=alpha, shape_order=shape_order, pusher=pusher,
                         precision=precision, sort_interval=sort_interval, relax_max_iter=relax_max_iter,
-                        relax_tol=relax_tol, deposit_mode=deposit_mode, stream=stream, boundary_x=boundary_x)
+                        relax_tol=relax_tol, deposit_mode=deposit_mode, stream=stream, boundary_x=boundary_x,
+                        boundary_y=boundary_y, boundary_z=boundary_z)
     for s in L.species:
         sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]) + capacity_extra)
         if len(s["x"]):

@@ -27,31 +27,35 @@ def pp():
     return m
 
 
-def _pair(pp, orc, L, precision, shape, pusher=0, mode=0, fields_seed=31, gpu_kw=None, orc_kw=None, setup=None):
-    gpu = H.gpu_sim(pp, L, precision, shape, pusher=pusher, deposit_mode=mode, boundary_x=pp.PP_BOUNDARY_WALLS,
-                    **(gpu_kw or {}))
+def _pair(pp, orc, L, precision, shape, pusher=0, mode=0, fields_seed=31, gpu_kw=None, orc_kw=None, setup=None,
+          walls=(True, False, False)):
+    W = pp.PP_BOUNDARY_WALLS
+    gpu = H.gpu_sim(pp, L, precision, shape, pusher=pusher, deposit_mode=mode, boundary_x=W if walls[0] else 0,
+                    boundary_y=W if walls[1] else 0, boundary_z=W if walls[2] else 0, **(gpu_kw or {}))
     if setup:
         setup(gpu)
-    osim = orc.WallSimulation(L.n, L.d, L.dt, shape_order=shape, pusher=pusher, relax_tol=1e-14, relax_max_iter=2000,
-                              **(orc_kw or {}))
+    osim = orc.WallSimulation(L.n, L.d, L.dt, walls=walls, shape_order=shape, pusher=pusher, relax_tol=1e-14,
+                              relax_max_iter=2000, **(orc_kw or {}))
     for s in L.species:
         osim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
-    E, B = pp_synth.random_fields((2 * L.n[0], L.n[1], L.n[2]), fields_seed, 0.05)
+    E, B = pp_synth.random_fields(tuple(2 * L.n[a] if walls[a] else L.n[a] for a in range(3)), fields_seed, 0.05)
     gpu.load_fields(E, B)
     osim.load_fields(E, B)
     return gpu, osim
 
 
-def _box(L):
-    return (2 * L.n[0] * L.d[0], L.n[1] * L.d[1], L.n[2] * L.d[2])
+def _box(L, walls=(True, False, False)):
+    return tuple((2 if walls[a] else 1) * L.n[a] * L.d[a] for a in range(3))
 
 
-def _compare(gpu, osim, L, tol_f, tol_x, tol_u):
+def _compare(gpu, osim, L, tol_f, tol_x, tol_u, walls=(True, False, False)):
     assert gpu.diagnostics()["status"] == 0
     for s in range(len(L.species)):
         p = gpu.particles(s)
-        assert p["x"].min() >= 0.0 and p["x"].max() <= L.n[0] * L.d[0]
-        dpos, du = H.particle_errors(p, osim.particles(s), _box(L))
+        for a in range(3):
+            if walls[a]:
+                assert p["xyz"[a]].min() >= 0.0 and p["xyz"[a]].max() <= L.n[a] * L.d[a]
+        dpos, du = H.particle_errors(p, osim.particles(s), _box(L, walls))
         assert dpos <= tol_x and du <= tol_u, (s, dpos, du)
     fe = H.field_errors(gpu, osim)
     for k, v in fe.items():
@@ -304,3 +308,74 @@ def test_boundary_state_in_checkpoint_and_errors(pp, orc, tmp_path):
     w.set_injector(sid, 4.0, (0.9, 0, 0))
     with pytest.raises(pp.PPError):
         w.step(3)
+
+
+# --------------------------------------------------------------------------
+# Walls on y and z, and on all three axes
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("walls", [(False, True, False), (False, False, True), (True, True, True)])
+def test_other_walls_fp64_parity(pp, orc, walls):
+    """Walls on y, on z, or on every axis (a closed box), random fast particles
+    in unsymmetrised random fields, four steps: FP64 to 1e-12."""
+    L = _load((10, 12, 9), seed=190 + sum(walls) + 2 * walls[2])
+    gpu, osim = _pair(pp, orc, L, pp.PP_FP64, 3, walls=walls)
+    gpu.step(4)
+    osim.step(4)
+    _compare(gpu, osim, L, 1e-12, 1e-12, 1e-12, walls)
+
+
+@pytest.mark.parametrize("walls", [(False, True, False), (True, True, True)])
+def test_other_walls_mixed_tiled_parity(pp, orc, walls):
+    """The tiled kernel with walls on y and in a closed box (meshes of 16 on
+    walled axes): mixed tolerances."""
+    L = _load((8, 8, 16) if walls[0] else (16, 8, 16), seed=195 + sum(walls))
+    gpu, osim = _pair(pp, orc, L, pp.PP_MIXED32, 3, mode=2, walls=walls)
+    gpu.step(3)
+    osim.step(3)
+    _compare(gpu, osim, L, 3e-5, 2e-6, 2e-6, walls)
+
+
+def test_open_end_with_walls_on_y(pp, orc):
+    """The open x end and the injectors in a box that also has walls on y:
+    FP64 to 1e-12 with equal counts."""
+    L = _load((10, 12, 9), count=1500, seed=198)
+    walls = (True, True, False)
+    gpu, osim = _pair(pp, orc, L, pp.PP_FP64, 3, walls=walls, gpu_kw=dict(capacity_extra=4000))
+    e = np.zeros(0)
+    sp = L.species[0]
+    gpu.add_species(-sp["q"], sp["m"], sp["w"], 4000)
+    osim.add_species(-sp["q"], sp["m"], sp["w"], e, e, e, e, e, e)
+    gpu.set_open_boundary(6, 0.2, 2.0)
+    osim.set_open_boundary(6, 0.2, 2.0)
+    for sid in (0, 1):
+        gpu.set_injector(sid, 1.5, (0.8, 0.1, -0.05), 0.05, 78)
+        osim.set_injector(sid, 1.5, (0.8, 0.1, -0.05), 0.05, 78)
+    gpu.step(6)
+    osim.step(6)
+    for sid in (0, 1):
+        assert len(gpu.particles(sid)["x"]) == len(osim.particles(sid)["x"])
+    _compare(gpu, osim, L, 1e-12, 1e-12, 1e-12, walls)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_free_particle_in_a_closed_box_on_gpu(pp, precision):
+    n, d, dt = (8, 8, 8), (0.5, 0.5, 0.5), 0.2
+    Ls = np.array([n[a] * d[a] for a in range(3)])
+    W = pp.PP_BOUNDARY_WALLS
+    sim = pp.Simulation(n, d, dt, shape_order=2, precision=precision, boundary_x=W, boundary_y=W, boundary_z=W,
+                        relax_tol=1e-14 if precision == 0 else 1e-6)
+    assert sim.mesh_shape == (16, 16, 16)
+    x0 = np.array([2.7, 1.1, 0.6])
+    u0 = np.array([1.5, -0.9, 0.7])
+    sid = sim.add_species(-1.0, 1.0, 1e-13, 1)
+    sim.load_particles(sid, *[np.array([v]) for v in x0], *[np.array([v]) for v in u0])
+    v = u0 / np.sqrt(1.0 + (u0 ** 2).sum())
+    sim.step(40)
+    p = sim.particles(sid)
+    tol = 1e-9 if precision == 0 else 1e-4
+    for a in range(3):
+        s_ = np.mod(x0[a] + 40 * dt * v[a], 2 * Ls[a])
+        xe = s_ if s_ <= Ls[a] else 2 * Ls[a] - s_
+        ue = u0[a] if s_ <= Ls[a] else -u0[a]
+        assert abs(p["xyz"[a]][0] - xe) < tol and abs(p["u" + "xyz"[a]][0] - ue) < tol, a
