@@ -42,12 +42,13 @@ def run_cases():
     sim.set_integrator(4)
     sim.step(3)
     out["tiled_step4"] = (sim.diagnostics()["status"], _fields(sim))
-    # walls with an open end, an injector and a sliding window through the tiled
-    # kernel: reflections, particles that leave, the unsorted tail, window shifts
+    # walls on x and y with an open end, an injector and a sliding window through
+    # the tiled kernel: reflections, particles that leave, the unsorted tail,
+    # window shifts
     L = pp_synth.random_particles((16, 16, 16), (0.5, 0.5, 0.5), 0.25, 4000, seed=78, u_scale=0.8)
     sim = H.gpu_sim(pp, L, pp.PP_MIXED32, 3, deposit_mode=2, sort_interval=4, capacity_extra=6000,
-                    boundary_x=pp.PP_BOUNDARY_WALLS)
-    sim.load_fields(*pp_synth.random_fields((32, 16, 16), 4, 0.02))
+                    boundary_x=pp.PP_BOUNDARY_WALLS, boundary_y=pp.PP_BOUNDARY_WALLS)
+    sim.load_fields(*pp_synth.random_fields((32, 32, 16), 4, 0.02))
     sim.set_open_boundary(4, 0.2, 1.5)
     sim.set_injector(0, 1.0, (0.8, 0.0, 0.0), 0.1, 5)
     sim.set_sliding_window(0.5)
