@@ -379,3 +379,29 @@ def test_free_particle_in_a_closed_box_on_gpu(pp, precision):
         xe = s_ if s_ <= Ls[a] else 2 * Ls[a] - s_
         ue = u0[a] if s_ <= Ls[a] else -u0[a]
         assert abs(p["xyz"[a]][0] - xe) < tol and abs(p["u" + "xyz"[a]][0] - ue) < tol, a
+
+
+def test_walls_step_graphs_and_eager_boundary_steps(pp, orc):
+    """Closed walls step through captured graphs like eagerly (FP64 1e-12);
+    with an open end the steps run eagerly even when graphs are enabled."""
+    import torch
+    L = _load((10, 12, 9), count=1200, seed=199)
+    sims = []
+    for graphs in (False, True):
+        st = torch.cuda.Stream()
+        g = H.gpu_sim(pp, L, pp.PP_FP64, 3, sort_interval=3, stream=st.cuda_stream, boundary_x=pp.PP_BOUNDARY_WALLS,
+                      boundary_y=pp.PP_BOUNDARY_WALLS)
+        g._keep = st
+        if graphs:
+            g.set_graphs(True)
+        g.step(8)
+        sims.append(g)
+    E0, B0, _ = sims[0].fields()
+    E1, B1, _ = sims[1].fields()
+    assert max(H.rel_err(E1[a], E0[a]) for a in range(3)) <= 1e-12
+    assert max(H.rel_err(B1[a], B0[a]) for a in range(3)) <= 1e-12
+    cap, rep = sims[1].graph_stats()
+    assert cap + rep == 8 and rep >= 4, (cap, rep)
+    sims[1].set_open_boundary(4, 0.1, 1.0)
+    sims[1].step(3)
+    assert sims[1].graph_stats() == (cap, rep)   # eager: no capture, no replay
