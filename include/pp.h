@@ -90,7 +90,7 @@ typedef struct pp_ctx pp_ctx;
  * still creates the context (the paper reports instability below 0.525).
  *
  * boundary_x = PP_BOUNDARY_WALLS puts reflecting walls at x = 0 and
- * x = L = nx*dx (Sec. II "Boundary conditions"); boundary_y and boundary_z do
+ * x = L = nx*dx (Sec. V "Boundary conditions"); boundary_y and boundary_z do
  * the same on y and z, on any set of axes (the others stay periodic).  The
  * walls sit on integer (charge-density) nodes.  A particle that crosses a wall
  * deposits its current as if streaming freely, its virtual mirror image
@@ -269,7 +269,7 @@ int pp_set_current_deposit(pp_ctx *ctx, int mode);
 int pp_set_divergence_filter(pp_ctx *ctx, int passes, int interval);
 
 /* ---- open end, injector and sliding window (PP_BOUNDARY_WALLS only) -------
- * Sec. II "Boundary conditions" (outflow) and "Sliding window and injection
+ * Sec. V "Boundary conditions" (outflow) and "Sliding window and injection
  * of particles".  The upper wall at x = L stays a reflecting wall; the lower
  * end x = 0 becomes open.  pp_step applies them after each full step, in this
  * order: damping of the layer, injection, window shift (the particles that

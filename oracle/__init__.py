@@ -314,7 +314,7 @@ class Simulation:
 
 
 # ---------------------------------------------------------------------------
-# Reflecting walls (Sec. II "Boundary conditions"): walls at x = 0 and
+# Reflecting walls (Sec. V "Boundary conditions"): walls at x = 0 and
 # x = L = n_x dx, both on integer (charge-density) nodes.  The paper defines
 # the wall through virtual particles: every particle inside has a mirror
 # image outside, x -> 2 x_b - x with the normal momentum reversed, and the

@@ -73,7 +73,7 @@
  *       eigenvalue of -div grad, which removes the Nyquist-scale error in one
  *       pass and damps every other non-constant mode.  Gauss-Seidel ordering
  *       is sequential; the simultaneous form damps the same error.
- *   R21 Reflecting walls (Sec. II "Boundary conditions") are the virtual-image
+ *   R21 Reflecting walls (Sec. V "Boundary conditions") are the virtual-image
  *       system in the mirror-extended box (oracle/__init__.py, WallSimulation).
  *   R22 The outflow layer (same section): the paper gives no profile.  Each
  *       step the chosen field components are multiplied by
@@ -84,7 +84,7 @@
  *       x; the component set is a parameter.  A particle leaves the box when
  *       a step ends with it moving outward (u_x < 0) closer than `escape`
  *       cells to the open end: until then it deposits like any other.
- *   R23 The injector (Sec. II "Sliding window and injection of particles") is
+ *   R23 The injector (Sec. V "Sliding window and injection of particles") is
  *       fed by Philox4x32-10 draws (Salmon et al., SC'11), counter
  *       (index, 0, step, stream), key = the 64-bit seed.  Per step it adds the
  *       inflow that crossed the open end during the step: floor(k r) -

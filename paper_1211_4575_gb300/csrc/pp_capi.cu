@@ -675,11 +675,10 @@ static double inj_vx(const Ctx::Injector &I) {
     return I.u[0] / sqrt(1.0 + I.u[0] * I.u[0] + I.u[1] * I.u[1] + I.u[2] * I.u[2]);
 }
 
-// What the open end, the injectors and the window do after a step (Sec. II,
-// outflow and injection; readings of the outflow layer, the injector and the
-// window in the header): damp the layer (outgoing particles already left in
-// the particle pass), inject the inflow of the step, and shift the window when
-// it has moved a cell.
+// What the open end, the injectors and the window do after a step (Sec. V,
+// outflow, injection and sliding window): damp the layer (outgoing particles
+// already left in the particle pass), inject the inflow of the step, and shift
+// the window when it has moved a cell.
 static int boundary_step(Ctx *c) {
     if (c->open.cells > 0 && c->open.mask) {
         CU(launch_damp(*c));

@@ -526,7 +526,7 @@ struct Ctx {
     int wall[3] = {0, 0, 0};
     bool any_wall() const { return wall[0] || wall[1] || wall[2]; }
     // Open lower end between walls (outflow layer, escape), injectors and the
-    // sliding window (Sec. II "Boundary conditions", "Sliding window and
+    // sliding window (Sec. V "Boundary conditions", "Sliding window and
     // injection of particles").
     struct OpenEnd {
         int cells = 0;           // damping layer width; 0 = no open end

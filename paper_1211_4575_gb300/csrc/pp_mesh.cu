@@ -85,7 +85,7 @@ cudaError_t launch_zero_J(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------
-// Reflecting walls (Sec. II "Boundary conditions").  On a walled axis a the
+// Reflecting walls (Sec. V "Boundary conditions").  On a walled axis a the
 // mesh is the mirror-extended box of n0 = 2 n_a cells, the walls on the
 // integer nodes 0 and n_a.  Along a, integer node i has the image
 // (n0 - i) mod n0 and half node i+1/2 (index i) the image index n0 - 1 - i.
@@ -186,7 +186,7 @@ cudaError_t launch_mirror_rho(Ctx &c, double *rho) {
 }
 
 // ---------------------------------------------------------------------------
-// Open lower end (Sec. II "Boundary conditions", outflow): each step the
+// Open lower end (Sec. V "Boundary conditions", outflow): each step the
 // chosen components are multiplied by 1 - damping ((cells - d) / cells)^2 at
 // distance d < cells from x = 0, d taken at the component's staggered
 // position, on both sides of that mirror plane so that the extended mesh stays
@@ -233,7 +233,7 @@ cudaError_t launch_damp(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------
-// Sliding window (Sec. II "Sliding window and injection of particles"): the
+// Sliding window (Sec. V "Sliding window and injection of particles"): the
 // content of the box moves one cell up in x.  In the physical half a node takes
 // the value of the node one cell below (zero for the new bottom node); a node
 // of the mirror half takes P times the new value of its image.  Written into

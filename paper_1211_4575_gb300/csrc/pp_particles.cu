@@ -63,7 +63,7 @@ struct MixedParticles {
     float *ox, *oy, *oz, *ux, *uy, *uz;
 };
 
-// Reflecting walls at 0 and nw cells on one axis (Sec. II "Boundary
+// Reflecting walls at 0 and nw cells on one axis (Sec. V "Boundary
 // conditions"), applied after the particle deposited its step as if streaming
 // freely: a particle that ended the move beyond a wall (in (nw, 2 nw) of the
 // mirror-extended box, which the periodic wrap also gives below 0) is replaced
@@ -832,7 +832,7 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------
-// Injection of inflow particles (Sec. II "Sliding window and injection of
+// Injection of inflow particles (Sec. V "Sliding window and injection of
 // particles").  Draws come from the counter-based Philox4x32-10 generator of
 // Salmon, Moraes, Dror & Shaw (SC'11): ten rounds of the bijection
 //   (x0, x1, x2, x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0)),

@@ -1,4 +1,4 @@
-"""GPU parity of the reflecting walls (Sec. II "Boundary conditions",
+"""GPU parity of the reflecting walls (Sec. V "Boundary conditions",
 boundary_x = PP_BOUNDARY_WALLS) against the oracle's virtual-image system.
 
 The library deposits the particles alone, folds the images' share into the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's reflecting walls (Sec. II "Boundary conditions").
+"""Pins of the oracle's reflecting walls (Sec. V "Boundary conditions").
 
 The oracle builds the wall from its definition, virtual mirror images in the
 mirror-extended periodic box.  These tests hold that construction to things
