@@ -51,7 +51,7 @@ PROFILED_ISSUE = {"issue_active_pct": 57.0, "warp_instructions_per_particle": 11
 _KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
 _HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "28c767eaebfff52d17d1053ecdb50d27f9b4076c7fd02d819a38fd8b8503757c",
+    "paper_1211_4575_gb300/csrc/pp_particles.cu": "3285fa49a9cf12f024223f16ec4ccb565f4802fa407807e82e696a22d8cd2b5d",
     "paper_1211_4575_gb300/csrc/pp_internal.cuh": "643a48f3cec37d301be2db1853792dc3ef6c269944bb793e18bc1b1ae96f6b0b",
     "paper_1211_4575_gb300/csrc/pp_sort.cu": "8ae278e854810bdf3db42a7069642a62f7c7a0c1cddf9bd8d09dca831784555a",
 }

@@ -714,6 +714,21 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
     }
 }
 
+// The opt-in dynamic shared memory of a kernel, set once per device (the
+// attribute belongs to the device's context; a bit per device ordinal).  Two
+// threads that race here set the same value.
+template <class K>
+static cudaError_t ensure_smem_attr(K kernel, int bytes, unsigned long long &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done |= bit;
+    return e;
+}
+
 bool tiled_supported(const Ctx &c) {
     if (c.fp64 || c.g.G < kWinLo || c.g.G < kWin - kWinLo - kTile) return false;
     for (int a = 0; a < 3; ++a)
@@ -764,18 +779,14 @@ cudaError_t launch_particles_tiled_all(Ctx &c) {
     T.esc = c.escape_now;
     unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     int o = c.d.shape_order, pu = c.d.pusher;
-    static bool attr_done[2][2][4] = {{{false}}};
+    static unsigned long long attr_done[2][2][4] = {};
     const bool bnd = c.any_wall();
     cudaError_t e = cudaSuccess;
     if (T.ns > 0) {
 #define PP_TB(O, PU, BD)                                                                                    \
     do {                                                                                                    \
-        if (!attr_done[BD][PU][O]) {                                                                        \
-            cudaError_t e_ = cudaFuncSetAttribute(k_particles_tiled<O, PU, BD>,                             \
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTiledSmem); \
-            if (e_ != cudaSuccess) return e_;                                                               \
-            attr_done[BD][PU][O] = true;                                                                    \
-        }                                                                                                   \
+        cudaError_t e_ = ensure_smem_attr(k_particles_tiled<O, PU, BD>, (int)kTiledSmem, attr_done[BD][PU][O]); \
+        if (e_ != cudaSuccess) return e_;                                                                   \
         k_particles_tiled<O, PU, BD><<<blocks, kThreads, kTiledSmem, c.st>>>(T);                            \
     } while (0)
 #define PP_T(O, PU)                                                                                         \
@@ -1210,13 +1221,9 @@ cudaError_t launch_rho(Ctx &c) {
     do {                                                                                                   \
         constexpr int nf = (O % 2) ? O + 1 : O + 2;                                                       \
         const size_t sm = sizeof(float) * (size_t)kg.tile_vol * (nf * nf * nf + 1);                        \
-        static bool attr = false;                                                                          \
-        if (!attr) {                                                                                       \
-            cudaError_t e_ = cudaFuncSetAttribute(k_rho_tile<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                  (int)(sizeof(float) * 512 * (nf * nf * nf + 1)));        \
-            if (e_ != cudaSuccess) return e_;                                                              \
-            attr = true;                                                                                   \
-        }                                                                                                  \
+        static unsigned long long attr = 0;                                                               \
+        cudaError_t e_ = ensure_smem_attr(k_rho_tile<O>, (int)(sizeof(float) * 512 * (nf * nf * nf + 1)), attr); \
+        if (e_ != cudaSuccess) return e_;                                                                  \
         k_rho_tile<O><<<(unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]), kg.tile_vol, sm, c.st>>>(       \
             c.g, kg, S.cell_start, qw, pm, c.rho);                                                         \
     } while (0)
