@@ -34,7 +34,7 @@
  *       sum of Sec. III "Charge conserving current density" is fixed by the
  *       line mean of each particle's compact (2nd-order) current, i.e. by the
  *       first moment of its D rho along the line.
- *   R5  "Successive relaxation" of eq:EllipticB is read as Jacobi iteration.
+ *   R5  The unspecified successive relaxation of eq:EllipticB is read as Jacobi iteration.
  *   R6  Each field component is gathered from its own staggered nodes with the
  *       same weight function as the deposit (eq:pfields, eq:rho2).
  *   R16 Radiative cooling (Sec. "Radiative cooling") is the explicit form the
@@ -66,7 +66,7 @@
  *       staggered nodes (like E), W taken at the middle of the move,
  *       (x^n + x^{n+1})/2, and v = u^{n+1/2}/gamma: J^{n+1/2} without the
  *       high-order current solve, which belongs to the charge-conserving form.
- *   R20 The divergence filter ("Gauss-Seidel filtering" of E, and the
+ *   R20 The divergence filter (the Gauss-Seidel filter of E, and the
  *       periodic filter of E and B of long FP32 runs): each pass is one
  *       simultaneous smoothing step E += tau grad^+(div^- E - rho),
  *       B += tau grad^-(div^+ B), tau = 1 / max(sum_a K_a^2), the largest
@@ -79,7 +79,7 @@
  *       step the chosen field components are multiplied by
  *       1 - damping ((cells - d) / cells)^2 at distance d < cells (in cells,
  *       at the component's own staggered position) from the open end.  The
- *       paper's "perpendicular components" is read as those transverse to the
+ *       paper's perpendicular components are read as those transverse to the
  *       boundary normal (E_y, E_z, B_y, B_z), the fields of waves leaving along
  *       x; the component set is a parameter.  A particle leaves the box when
  *       a step ends with it moving outward (u_x < 0) closer than `escape`

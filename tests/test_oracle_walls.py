@@ -11,6 +11,7 @@ deposit.
 """
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -148,6 +149,26 @@ def test_paper_folding_rules_reproduce_the_images(orc, shape):
 # --------------------------------------------------------------------------
 # Open lower end, injector and sliding window (readings R22-R24)
 # --------------------------------------------------------------------------
+
+def test_philox_known_answers(orc):
+    """orc_philox4x32 against the published known-answer vectors of
+    Philox4x32-10 (tests/golden/philox4x32_10_kat.txt): the all-zero, the
+    all-ones and the pi-digits counter/key.  A swapped multiplier, Weyl
+    constant, output word or round count fails at least one of them."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert list(orc.philox4x32(v[0:4], v[4:6])) == v[6:10], r
+    # orc_draws: draw i is the generator at counter (i, 0, step, stream) under
+    # key (seed low, seed high), each word r mapped to (r + 1/2) 2^-32
+    seed, step, stream = (0x299f31d0 << 32) | 0xa4093822, 0x13198a2e, 0x03707344
+    D = orc.draws(seed, step, stream, 3)
+    for i in range(3):
+        words = orc.philox4x32((i, 0, step, stream), (0xa4093822, 0x299f31d0))
+        assert list(D[i]) == [(w + 0.5) * 2.0 ** -32 for w in words]
+
 
 def test_philox_draws_are_uniform_and_mix(orc):
     """The counter-based generator of the injector: its words are uniform
