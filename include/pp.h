@@ -67,7 +67,17 @@ extern "C" {
                            FP64 global reductions                                 */
 #define PP_DEPOSIT_AUTO 0
 #define PP_DEPOSIT_GLOBAL 1  /* one thread per particle, L2 atomics                */
-#define PP_DEPOSIT_TILED 2   /* cell tiles staged in shared memory (PP_MIXED32)     */
+#define PP_DEPOSIT_TILED 2   /* cell tiles staged in shared memory (PP_MIXED32), cell
+                                sort every sort_interval steps                     */
+#define PP_DEPOSIT_CELLS 3   /* PP_MIXED32: particles sorted by cell at the start of
+                                every particle pass (Sec. III, the sort between the
+                                deposit and the field update of every step); the
+                                current of the particles of one cell that cross no
+                                support boundary is summed in registers, then in an
+                                int32 fixed-point tile window.  Needs the
+                                charge-conserving current and mesh sizes that are
+                                multiples of 8; PP_DEPOSIT_AUTO takes it wherever it
+                                applies                                             */
 
 #define PP_FIELD_IMPLICIT 0  /* de-centred implicit update, eq:EllipticB (default)    */
 #define PP_FIELD_EXPLICIT 1  /* explicit FDTD leap-frog (cold-beam comparison)         */
@@ -352,14 +362,15 @@ int pp_deposit(pp_ctx *ctx, int sid);
 int pp_field_update(pp_ctx *ctx);
 
 /* Stable-order-free counting sort of every species by cell (Sec. III, the
- * per-step sort "according to the cell position"). */
+ * sort by cell position between the deposit and the field update). */
 int pp_sort(pp_ctx *ctx);
 
 /* Change the cell-sort interval (>= 0) and the deposit mode (PP_DEPOSIT_*) of
  * a live context; both take effect from the next step and change only how
  * fast a step runs, not what it computes (the tuning knobs of the
- * autotuner).  PP_EINVAL for values the context cannot use (the tiled
- * deposit needs PP_MIXED32 and grid sizes that are multiples of 8). */
+ * autotuner; with PP_DEPOSIT_CELLS every particle pass sorts, whatever the
+ * interval).  PP_EINVAL for values the context cannot use (the tiled
+ * deposits need PP_MIXED32 and grid sizes that are multiples of 8). */
 int pp_set_tuning(pp_ctx *ctx, int sort_interval, int deposit_mode);
 
 /* Synchronise the context's stream and return the device status word as a
@@ -410,19 +421,60 @@ int pp_save(pp_ctx *ctx, const char *path);
 /* Restore a checkpoint written by pp_save into a new context on `stream`. */
 int pp_restore(pp_ctx **out, const char *path, void *stream);
 
+/* ---- z-slab decomposition of one run over ranks (one GPU each) ------------
+ * Sec. IX: the paper splits a run into domains, moves particles that leave a
+ * domain to its neighbour and exchanges the boundary layers of the fields.
+ * Here every rank holds the whole mesh and the particles of one z-slab; a
+ * step is pp_deposit on every rank, the sum of the ranks' currents
+ * (pp_get_current, an allreduce by the caller's communicator, pp_set_current),
+ * pp_field_update on every rank (identical inputs give identical fields), and
+ * the migration of the particles that left each slab (pp_extract_particles,
+ * the caller's exchange, pp_load_particles on the owner).  The driver is
+ * paper_1211_4575_gb300/parallel.py. */
+
+/* Declare ctx the rank that owns the particles with physical z in
+ * [z_lo, z_hi) of a periodic box (0 <= z_lo < z_hi <= nz*dz).  A rank's charge
+ * density is a share of the run's, so from here on loads do not retake the
+ * Gauss reference of pp_diagnostics.  Errors: PP_EINVAL for walls on z or
+ * bounds outside the box. */
+int pp_set_slab(pp_ctx *ctx, double z_lo, double z_hi);
+
+/* Copy the current J on the mesh (after pp_deposit: this rank's high-order
+ * current) into three FP64 arrays in the mesh layout, device pointers when
+ * on_device = 1 (enqueued on the context's stream; the caller orders its own
+ * work after it), else host arrays (synchronises). */
+int pp_get_current(pp_ctx *ctx, double *const J[3], int on_device);
+
+/* Replace J on the mesh by three FP64 arrays in the mesh layout (e.g. the sum
+ * of every rank's current), ready for pp_field_update; on_device as in
+ * pp_get_current.  Drops the step graphs. */
+int pp_set_current(pp_ctx *ctx, const double *const J[3], int on_device);
+
+/* Remove from species sid every particle whose z lies outside the slab of
+ * pp_set_slab and return their FP64 state (physical x, y, z; proper
+ * velocities) in six arrays of capacity cap (device pointers when
+ * on_device = 1, else host); *n_out receives the count.  Synchronises.
+ * Errors: PP_EINVAL without a slab, PP_ENOMEM when more than cap particles
+ * left (nothing is removed then; *n_out = 0). */
+int pp_extract_particles(pp_ctx *ctx, int sid, int64_t cap, double *x, double *y, double *z, double *ux,
+                         double *uy, double *uz, int on_device, int64_t *n_out);
+
 /* Allocation-free FP64 field energies: out[0] = sum 1/2 |E|^2 dV,
  * out[1] = sum 1/2 |B|^2 dV, out[2] = sum 1/2 E_x^2 dV over an nx*ny*nz mesh,
  * the same sums pp_diagnostics reports.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they
- * need the energies (allocation forbidden after start-up, a CUDA graph being
- * captured, a host that hands over pre-allocated buffers only).
+ * need the energies (loops that forbid allocation after start-up, because an
+ * allocation may block or fail at any time; hosts that own all device memory
+ * and hand over pre-allocated buffers only).
  * E, B: arrays of three DEVICE pointers to nx*ny*nz FP64 values each (the
  * mesh layout above; the caller owns them).  out: DEVICE pointer to three
  * FP64 values, written on `stream` (cudaStream_t, NULL = legacy default).
  * The call allocates nothing: its scratch (1024 x 3 FP64 partial sums, 24 KiB)
  * is a fixed array inside the library, one per device, held until the process
  * exits.  The first call on a device looks that array up (with the device
- * current); make it before any stream capture.  Calls whose kernels overlap
+ * current) and keeps its address; make it before any stream capture.  After
+ * cudaDeviceReset that address is stale: do not call this entry point on a
+ * device the process has reset.  Calls whose kernels overlap
  * on the GPU share the array and race.  Errors: PP_EINVAL for NULL pointers or
  * a mesh of more than 1023^3 cells, PP_ECUDA for a failed lookup or launch;
  * pp_field_energy_noalloc_error() then returns the message (per host thread). */
@@ -453,7 +505,10 @@ int pp_batch_create(pp_batch **out, int64_t budget_bytes, int max_slots);
 
 /* Admit ctx for `steps` steps into a free slot (*slot receives it).
  * PP_EBUSY when no slot is free or the budget would be exceeded (nothing
- * changes then).  Give every admitted context its own stream for overlap. */
+ * changes then); PP_EINVAL for a context that already holds a slot.  Give
+ * every admitted context its own stream for overlap: such a context steps
+ * through captured graphs (pp_set_graphs) while it holds the slot, and gets
+ * its previous setting back when the slot is released. */
 int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot);
 
 /* Enqueue up to max_steps steps of every running slot, one step per slot in
@@ -462,7 +517,9 @@ int pp_batch_advance(pp_batch *b, int max_steps);
 
 /* Non-blocking state of a slot (PP_BATCH_*), and the steps enqueued so far.
  * A slot reported DONE or FAILED is released (its bytes return to the
- * budget); its return value is then the failing step's code. */
+ * budget); its return value is then the failing step's code.  A FAILED slot
+ * is released only after the context's stream has drained (this call then
+ * blocks on it). */
 int pp_batch_poll(pp_batch *b, int slot, int64_t *steps_done, int *state);
 
 /* Bytes admitted and slots in use. */

@@ -32,12 +32,16 @@ VAY, BORIS = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile pp_oracle.c into oracle/_build/liboracle.so (gcc -O2)."""
+    """Compile pp_oracle.c into oracle/_build/liboracle.so (gcc -O2, with
+    OpenMP where gcc has it: the particle loop then runs on set_threads(n)
+    threads, one by default)."""
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
         return _OUT
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     tmp = _OUT + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+        subprocess.check_call(base)
     os.replace(tmp, _OUT)
     return _OUT
 
@@ -94,6 +98,8 @@ def lib():
         L.orc_diagnostics.argtypes = [C.POINTER(Grid), P, P, C.POINTER(Species), C.c_int, C.POINTER(Diag)]
         L.orc_philox4x32.argtypes = [P, P, P]
         L.orc_draws.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, P]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
         _lib = L
     return _lib
 
@@ -375,6 +381,13 @@ def philox4x32(ctr, key):
     o = (C.c_uint32 * 4)()
     lib().orc_philox4x32(C.cast(c, C.c_void_p), C.cast(k, C.c_void_p), C.cast(o, C.c_void_p))
     return tuple(o)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's particle loop (per-thread deposit copies, added
+    after the loop); returns the number in effect (1 without OpenMP).  One by
+    default: the parity tests use the oracle single-threaded."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def draws(seed: int, step: int, stream: int, n: int) -> np.ndarray:

@@ -103,6 +103,9 @@
  *       an injector gets a layer of round(ppc ny nz) particles uniform in
  *       [0, dx) (streams 16 and 17 + species, the shift count as the step).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -678,53 +681,107 @@ static void deposit_direct(const orc_grid *g, double qw, const double xm[3], con
 
 /* Gather, kick by kick_dt (push and cooling; none when kick_dt = 0), drift by
  * g->dt, deposit.  The plain leap-frog step has kick_dt = g->dt. */
+/* One particle of a kick-drift pass: gather, push (kick), move (drift) and
+ * deposit into the given arrays, then its new state. */
+static void advance_particle(const orc_grid *g, double kick_dt, double *E[3], double *B[3], orc_species *P,
+                             int64_t p, const double L[3], double *Drho[3], double *lsum[3], double *J[3])
+{
+    double qmdt = P->q * kick_dt / P->m;
+    double x0[3] = {P->x[p], P->y[p], P->z[p]};
+    double u[3] = {P->ux[p], P->uy[p], P->uz[p]};
+    double um[3] = {u[0], u[1], u[2]};
+    if (kick_dt != 0.0) {
+        double Ep[3], Bp[3];
+        orc_gather(g, E, B, x0, Ep, Bp);
+        if (g->pusher == 1) orc_push_boris(qmdt, Ep, Bp, u);
+        else orc_push_vay(qmdt, Ep, Bp, u);
+        if (P->rad != 0.0) orc_radiate(P->rad, kick_dt, um, u);
+    }
+    double gam = sqrt(1.0 + dot3(u, u));
+    double x1[3];
+    for (int a = 0; a < 3; ++a) x1[a] = x0[a] + g->dt * u[a] / gam;
+    if (g->current_mode == 1) {
+        double xm[3], v[3];
+        for (int a = 0; a < 3; ++a) {
+            xm[a] = 0.5 * (x0[a] + x1[a]);
+            v[a] = u[a] / gam;
+        }
+        deposit_direct(g, P->q * P->w, xm, v, J);
+    } else {
+        orc_deposit_particle(g, P->q, P->w, x0, x1, Drho, lsum);
+    }
+    wrap_pos(&x1[0], L[0]);
+    wrap_pos(&x1[1], L[1]);
+    wrap_pos(&x1[2], L[2]);
+    P->x[p] = x1[0]; P->y[p] = x1[1]; P->z[p] = x1[2];
+    P->ux[p] = u[0]; P->uy[p] = u[1]; P->uz[p] = u[2];
+}
+
+/* Threads of the particle loop: 1 unless set (an OpenMP build only), used
+ * for the all-core timing baseline.  As in the paper's Sec. IX OpenMP level,
+ * each thread deposits into its own copies of the charge-change (or direct
+ * current) and line-sum arrays, and the copies are added after the loop; with
+ * one thread the sums are those of the plain loop, bit for bit. */
+static int orc_threads = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    orc_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    orc_threads = 1;
+#endif
+    return orc_threads;
+}
+
 void orc_particles_kick_drift(const orc_grid *g, double kick_dt, double *E[3], double *B[3], orc_species *sp,
                               int nsp, double *J[3])
 {
     int64_t N = ncells(g);
+    int64_t nl[3];
     double *Drho[3], *lsum[3];
     for (int a = 0; a < 3; ++a) {
         Drho[a] = (double *)calloc((size_t)N, sizeof(double));
         int b = (a + 1) % 3, c = (a + 2) % 3;
-        lsum[a] = (double *)calloc((size_t)g->n[b] * g->n[c], sizeof(double));
+        nl[a] = (int64_t)g->n[b] * g->n[c];
+        lsum[a] = (double *)calloc((size_t)nl[a], sizeof(double));
     }
     double L[3] = {g->n[0] * g->d[0], g->n[1] * g->d[1], g->n[2] * g->d[2]};
     if (g->current_mode == 1)
         for (int a = 0; a < 3; ++a) memset(J[a], 0, sizeof(double) * (size_t)N);
+    const int nt = orc_threads;
+    /* per-thread copies: Drho (or J for the direct current) and lsum */
+    double **tbuf = (double **)calloc((size_t)nt * 6, sizeof(double *));
+    for (int t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) {
+            tbuf[6 * t + a] = (double *)calloc((size_t)N, sizeof(double));
+            tbuf[6 * t + 3 + a] = (double *)calloc((size_t)nl[a], sizeof(double));
+        }
     for (int s = 0; s < nsp; ++s) {
         orc_species *P = &sp[s];
-        double qmdt = P->q * kick_dt / P->m;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(static)
+#endif
         for (int64_t p = 0; p < P->n; ++p) {
-            double x0[3] = {P->x[p], P->y[p], P->z[p]};
-            double u[3] = {P->ux[p], P->uy[p], P->uz[p]};
-            double um[3] = {u[0], u[1], u[2]};
-            if (kick_dt != 0.0) {
-                double Ep[3], Bp[3];
-                orc_gather(g, E, B, x0, Ep, Bp);
-                if (g->pusher == 1) orc_push_boris(qmdt, Ep, Bp, u);
-                else orc_push_vay(qmdt, Ep, Bp, u);
-                if (P->rad != 0.0) orc_radiate(P->rad, kick_dt, um, u);
-            }
-            double gam = sqrt(1.0 + dot3(u, u));
-            double x1[3];
-            for (int a = 0; a < 3; ++a) x1[a] = x0[a] + g->dt * u[a] / gam;
-            if (g->current_mode == 1) {
-                double xm[3], v[3];
-                for (int a = 0; a < 3; ++a) {
-                    xm[a] = 0.5 * (x0[a] + x1[a]);
-                    v[a] = u[a] / gam;
-                }
-                deposit_direct(g, P->q * P->w, xm, v, J);
-            } else {
-                orc_deposit_particle(g, P->q, P->w, x0, x1, Drho, lsum);
-            }
-            wrap_pos(&x1[0], L[0]);
-            wrap_pos(&x1[1], L[1]);
-            wrap_pos(&x1[2], L[2]);
-            P->x[p] = x1[0]; P->y[p] = x1[1]; P->z[p] = x1[2];
-            P->ux[p] = u[0]; P->uy[p] = u[1]; P->uz[p] = u[2];
+            int t = 0;
+#ifdef _OPENMP
+            t = omp_get_thread_num();
+#endif
+            double *dr[3] = {tbuf[6 * t], tbuf[6 * t + 1], tbuf[6 * t + 2]};
+            double *ls[3] = {tbuf[6 * t + 3], tbuf[6 * t + 4], tbuf[6 * t + 5]};
+            advance_particle(g, kick_dt, E, B, P, p, L, dr, ls, dr);
         }
     }
+    for (int t = 0; t < nt; ++t)
+        for (int a = 0; a < 3; ++a) {
+            double *dst = g->current_mode == 1 ? J[a] : Drho[a];
+            for (int64_t i = 0; i < N; ++i) dst[i] += tbuf[6 * t + a][i];
+            for (int64_t i = 0; i < nl[a]; ++i) lsum[a][i] += tbuf[6 * t + 3 + a][i];
+            free(tbuf[6 * t + a]);
+            free(tbuf[6 * t + 3 + a]);
+        }
+    free(tbuf);
     if (g->current_mode != 1) orc_current_from_drho(g, Drho, lsum, J);
     for (int a = 0; a < 3; ++a) { free(Drho[a]); free(lsum[a]); }
 }

@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpp_gb300_checked.so" if os.environ.get
 PP_OK, PP_EINVAL, PP_ENOMEM, PP_EBUSY, PP_ECUDA, PP_ETIMEOUT, PP_ENOCONV, PP_ECFL, PP_ENAN, PP_WSTAB, PP_EBOUNDS = range(11)
 PP_VAY, PP_BORIS = 0, 1
 PP_FP64, PP_MIXED32 = 0, 1
-PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED = 0, 1, 2
+PP_DEPOSIT_AUTO, PP_DEPOSIT_GLOBAL, PP_DEPOSIT_TILED, PP_DEPOSIT_CELLS = 0, 1, 2, 3
 PP_FIELD_IMPLICIT, PP_FIELD_EXPLICIT = 0, 1
 PP_CURRENT_CONSERVING, PP_CURRENT_DIRECT = 0, 1
 PP_BOUNDARY_PERIODIC, PP_BOUNDARY_WALLS = 0, 1
@@ -107,6 +107,11 @@ SIGNATURES = {
     "pp_profile_read": (C.c_int, [_P, C.POINTER(Profile)]),
     "pp_save": (C.c_int, [_P, C.c_char_p]),
     "pp_restore": (C.c_int, [_PP, C.c_char_p, _P]),
+    "pp_set_slab": (C.c_int, [_P, C.c_double, C.c_double]),
+    "pp_get_current": (C.c_int, [_P, _PP, C.c_int]),
+    "pp_set_current": (C.c_int, [_P, _PP, C.c_int]),
+    "pp_extract_particles": (C.c_int, [_P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int,
+                                       C.POINTER(C.c_int64)]),
     "pp_field_energy_noalloc": (C.c_int, [_PP, _PP, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
     "pp_field_energy_noalloc_error": (C.c_char_p, []),
     "pp_device_bytes": (C.c_int64, [_P]),
@@ -364,6 +369,41 @@ class Simulation:
         out = {k: np.zeros(n) for k in ("x", "y", "z", "ux", "uy", "uz")}
         self._c(lib().pp_get_particles(self._ctx, sid, *[out[k].ctypes.data for k in ("x", "y", "z", "ux", "uy", "uz")]))
         return out
+
+    # -- z-slab decomposition (parallel.py) ---------------------------------
+    def set_slab(self, z_lo: float, z_hi: float):
+        self._c(lib().pp_set_slab(self._ctx, float(z_lo), float(z_hi)))
+
+    def get_current(self, out=None):
+        """J on the mesh as three FP64 arrays: numpy (host) by default, or into
+        the given CUDA torch tensors (enqueued on the context's stream)."""
+        if out is not None:
+            ptrs = (C.c_void_p * 3)(*[t.data_ptr() for t in out])
+            self._c(lib().pp_get_current(self._ctx, ptrs, 1))
+            return out
+        J = [self._mesh() for _ in range(3)]
+        self._c(lib().pp_get_current(self._ctx, _ptr_array(J), 0))
+        return J
+
+    def set_current(self, J):
+        """Replace J on the mesh: three FP64 numpy arrays or CUDA torch tensors."""
+        if hasattr(J[0], "is_cuda") and J[0].is_cuda:
+            ptrs = (C.c_void_p * 3)(*[t.data_ptr() for t in J])
+            self._c(lib().pp_set_current(self._ctx, ptrs, 1))
+            return
+        J = [_f64(a) for a in J]
+        self._c(lib().pp_set_current(self._ctx, _ptr_array(J), 0))
+
+    def extract_particles(self, sid: int) -> dict:
+        """Remove and return (host FP64 arrays) the particles of species sid
+        that left the slab."""
+        cap = self.count(sid)
+        out = {k: np.zeros(max(cap, 1)) for k in ("x", "y", "z", "ux", "uy", "uz")}
+        n = C.c_int64(0)
+        self._c(lib().pp_extract_particles(self._ctx, int(sid), cap,
+                                           *[out[k].ctypes.data for k in ("x", "y", "z", "ux", "uy", "uz")],
+                                           0, C.byref(n)))
+        return {k: v[: n.value].copy() for k, v in out.items()}
 
     def device_bytes(self) -> int:
         return int(lib().pp_device_bytes(self._ctx))

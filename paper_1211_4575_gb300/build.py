@@ -41,7 +41,7 @@ def sources():
 
 
 def _stale(lib=LIB) -> bool:
-    if not os.path.exists(lib):
+    if not os.path.exists(lib) or os.environ.get("PP_GB300_NVCC_FLAGS"):
         return True
     t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "pp.h")]
@@ -56,6 +56,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
     os.makedirs(os.path.dirname(lib), exist_ok=True)
     cc = nvcc()
     extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DPP_CHECKED"] if checked else [])
+    # PP_GB300_NVCC_FLAGS: extra nvcc flags, e.g. a kernel's tuning macro (-DPP_CELLS_PIECE=32)
+    extra += os.environ.get("PP_GB300_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")

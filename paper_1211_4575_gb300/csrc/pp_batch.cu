@@ -30,6 +30,7 @@ struct pp_batch {
         size_t bytes = 0;
         cudaEvent_t ev = nullptr;
         bool busy = false;
+        bool graphs_before = false;   // the context's step-graph setting before admission
         int status = PP_OK;
     } *slot = nullptr;
     char err[256] = {0};
@@ -40,6 +41,15 @@ static int bfail(pp_batch *b, int code, const char *msg) {
     return code;
 }
 
+// Return a slot's bytes to the budget and its context to the setting it came
+// with.  Only called once the context's stream holds no more of the slot's work.
+static void release(pp_batch *b, pp_batch::Slot &S) {
+    if (static_cast<Ctx *>(S.ctx)->use_graphs != S.graphs_before) pp_set_graphs(S.ctx, S.graphs_before ? 1 : 0);
+    S.busy = false;
+    S.ctx = nullptr;
+    b->used -= S.bytes;
+}
+
 // Device bytes held by a context (mesh, diagnostics and particle storage).
 extern "C" int64_t pp_device_bytes(pp_ctx *p) {
     if (!p) return 0;
@@ -47,7 +57,7 @@ extern "C" int64_t pp_device_bytes(pp_ctx *p) {
     int64_t bytes = (int64_t)c->g.padded_size() * (int64_t)c->rsz * 21 + 2 * 8 * c->g.cells();
     for (int s = 0; s < c->nspecies; ++s) {
         int64_t per = c->fp64 ? 48 : 28;
-        bytes += 2 * per * c->sp[s].cap + 4 * c->sp[s].cap + 4 * (c->nkeys + 1);
+        bytes += 2 * per * c->sp[s].cap + (c->fp64 ? 4 : 8) * c->sp[s].cap + 4 * (c->nkeys + 1);
     }
     bytes += 4 * (c->nkeys + 1);
     return bytes;
@@ -76,10 +86,15 @@ extern "C" int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot
     for (int q = 0; q < b->nslots; ++q)
         if (!b->slot[q].busy) { k = q; break; }
     if (k < 0) return bfail(b, PP_EBUSY, "no free slot");
+    for (int q = 0; q < b->nslots; ++q)
+        if (b->slot[q].busy && b->slot[q].ctx == ctx)
+            return bfail(b, PP_EINVAL, "pp_batch_admit: the context already holds a slot");
     pp_batch::Slot &S = b->slot[k];
     if (!S.ev && cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming) != cudaSuccess)
         return bfail(b, PP_ECUDA, "event creation failed");
-    // slots step through captured graphs where the context has its own stream
+    // slots step through captured graphs where the context has its own stream;
+    // the previous setting comes back when the slot is released
+    S.graphs_before = static_cast<Ctx *>(ctx)->use_graphs;
     if (static_cast<Ctx *>(ctx)->st) pp_set_graphs(ctx, 1);
     S.ctx = ctx;
     S.left = steps;
@@ -129,10 +144,12 @@ extern "C" int pp_batch_poll(pp_batch *b, int slot, int64_t *steps_done, int *st
     }
     if (steps_done) *steps_done = S.done;
     if (S.status != PP_OK) {
+        // earlier steps of the slot may still run: wait for them before the
+        // memory returns to the budget
         *state = PP_BATCH_FAILED;
         int st = S.status;
-        S.busy = false;
-        b->used -= S.bytes;
+        cudaStreamSynchronize(static_cast<Ctx *>(S.ctx)->st);
+        release(b, S);
         return st;
     }
     if (S.left > 0) {
@@ -144,8 +161,7 @@ extern "C" int pp_batch_poll(pp_batch *b, int slot, int64_t *steps_done, int *st
         *state = PP_BATCH_RUNNING;
         return PP_OK;
     }
-    S.busy = false;
-    b->used -= S.bytes;
+    release(b, S);
     if (e != cudaSuccess) {
         *state = PP_BATCH_FAILED;
         return PP_ECUDA;

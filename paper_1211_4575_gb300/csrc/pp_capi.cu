@@ -222,11 +222,12 @@ extern "C" int pp_init_grid(pp_ctx **out, const pp_grid_desc *d) {
     if (d->precision != PP_FP64 && d->precision != PP_MIXED32) return fail(c, PP_EINVAL, "unknown precision");
     if (d->relax_max_iter < 1 || !(d->relax_tol > 0.0)) return fail(c, PP_EINVAL, "relaxation cap and tolerance must be > 0");
     if (d->sort_interval < 0) return fail(c, PP_EINVAL, "sort_interval must be >= 0");
-    if (d->deposit_mode < 0 || d->deposit_mode > 2) return fail(c, PP_EINVAL, "unknown deposit_mode");
-    if (d->deposit_mode == PP_DEPOSIT_TILED && d->precision != PP_MIXED32)
-        return fail(c, PP_EINVAL, "the tiled deposit exists for PP_MIXED32 only");
-    if (d->deposit_mode == PP_DEPOSIT_TILED && (n[0] % 8 || n[1] % 8 || n[2] % 8))
-        return fail(c, PP_EINVAL, "the tiled deposit needs every mesh size to be a multiple of 8%s",
+    if (d->deposit_mode < 0 || d->deposit_mode > 3) return fail(c, PP_EINVAL, "unknown deposit_mode");
+    const bool tiled_mode = d->deposit_mode == PP_DEPOSIT_TILED || d->deposit_mode == PP_DEPOSIT_CELLS;
+    if (tiled_mode && d->precision != PP_MIXED32)
+        return fail(c, PP_EINVAL, "the tiled deposits exist for PP_MIXED32 only");
+    if (tiled_mode && (n[0] % 8 || n[1] % 8 || n[2] % 8))
+        return fail(c, PP_EINVAL, "the tiled deposits need every mesh size to be a multiple of 8%s",
                     (walls[0] || walls[1] || walls[2]) ? " (twice the cells on a walled axis)" : "");
 
     pp_ctx *p = new (std::nothrow) pp_ctx();
@@ -303,6 +304,7 @@ extern "C" int pp_destroy(pp_ctx *p) {
         cudaFree(c->sp[s].buf);
         cudaFree(c->sp[s].alt);
         cudaFree(c->sp[s].keys);
+        cudaFree(c->sp[s].perm);
         cudaFree(c->sp[s].cell_start);
     }
     cudaFree(c->mesh);
@@ -349,8 +351,9 @@ extern "C" int pp_init_species(pp_ctx *p, const pp_species_desc *sd, int *sid) {
     cudaError_t e1 = cudaMalloc(&S.buf, bytes), e2 = cudaMalloc(&S.alt, bytes);
     cudaError_t e3 = cudaMalloc(&S.keys, sizeof(int32_t) * S.cap);
     cudaError_t e4 = cudaMalloc(&S.cell_start, sizeof(int32_t) * (c->nkeys + 1));
-    if (e1 || e2 || e3 || e4) {
-        cudaFree(S.buf); cudaFree(S.alt); cudaFree(S.keys); cudaFree(S.cell_start);
+    cudaError_t e5 = c->fp64 ? cudaSuccess : cudaMalloc(&S.perm, sizeof(int32_t) * S.cap);
+    if (e1 || e2 || e3 || e4 || e5) {
+        cudaFree(S.buf); cudaFree(S.alt); cudaFree(S.keys); cudaFree(S.cell_start); cudaFree(S.perm);
         S = Species();
         return fail(c, PP_ENOMEM, "species storage of %zu bytes x 2", bytes);
     }
@@ -456,7 +459,7 @@ extern "C" int pp_load_particles(pp_ctx *p, int sid, int64_t n, const double *x,
     if (rc != PP_OK) return rc;
     S.n += n;
     CU(launch_sort(*c, sid));
-    c->g0_pending = true;
+    if (!c->slab) c->g0_pending = true;   // a slab rank's rho is a share: no reference
     return PP_OK;
 }
 
@@ -565,16 +568,40 @@ static cudaError_t prof_collect(Ctx *c) {
 // ---------------------------------------------------------------------------
 // The step
 // ---------------------------------------------------------------------------
+// The per-step sorted kernel (PP_DEPOSIT_CELLS, and PP_DEPOSIT_AUTO where it
+// applies) starts every particle pass from particles sorted by cell (Sec. III:
+// the sort between the deposit and the field update of every step).
+static bool cells_mode(const Ctx *c) {
+    const int m = c->d.deposit_mode;
+    return !c->fp64 && (m == PP_DEPOSIT_CELLS || m == PP_DEPOSIT_AUTO) && cells_supported(*c);
+}
+
 static int particle_phase(Ctx *c, int only) {
     NvtxRange nvtx("pp particle phase");
+    const bool cells = only < 0 && cells_mode(c);
+    if (cells) {
+        bool stale = false;
+        for (int s = 0; s < c->nspecies; ++s) stale = stale || (c->sp[s].n > 0 && !c->sp[s].fresh);
+        if (stale) {
+            CU(prof_mark(c, PH_SORT, true));
+            for (int s = 0; s < c->nspecies; ++s)
+                if (!c->sp[s].fresh) CU(launch_sort(*c, s));
+            CU(prof_mark(c, PH_SORT, false));
+            c->since_sort = 0;
+        }
+    }
     CU(launch_zero_J(*c));
     CU(cudaMemsetAsync(c->d_nslow, 0, sizeof(unsigned long long), c->st));
     CU(prof_mark(c, PH_PARTICLE, true));
     bool all_sorted = true;
     for (int s = 0; s < c->nspecies; ++s) all_sorted = all_sorted && (c->sp[s].sorted || c->sp[s].n == 0);
-    bool tiled = !c->fp64 && (c->d.deposit_mode == PP_DEPOSIT_TILED ||
-                              (c->d.deposit_mode == PP_DEPOSIT_AUTO && tiled_supported(*c) && all_sorted));
-    if (tiled && only < 0) {
+    const int m = c->d.deposit_mode;
+    bool tiled = !c->fp64 && !cells && (m == PP_DEPOSIT_TILED || m == PP_DEPOSIT_CELLS ||
+                                        (m == PP_DEPOSIT_AUTO && tiled_supported(*c) && all_sorted));
+    if (cells) {
+        CU(launch_particles_cells(*c));
+        if (c->prof) ++c->prof_particle_launches;
+    } else if (tiled && only < 0) {
         CU(launch_particles_tiled_all(*c));
         if (c->prof) ++c->prof_particle_launches;
     } else {
@@ -586,6 +613,8 @@ static int particle_phase(Ctx *c, int only) {
             if (c->prof) ++c->prof_particle_launches;
         }
     }
+    for (int s = 0; s < c->nspecies; ++s)
+        if (only < 0 || s == only) c->sp[s].fresh = false;   // the particles moved
     CU(prof_mark(c, PH_PARTICLE, false));
     CU(prof_mark(c, PH_CURRENT, true));
     CU(launch_fold_J(*c));
@@ -764,8 +793,15 @@ static int step_body(Ctx *c, bool sort, bool filter) {
 
 static bool graph_matches(const Ctx *c, const StepGraph &G, bool sort, bool filter) {
     if (!G.valid || G.sort != sort || G.filter != filter || G.J0 != c->J[0]) return false;
-    for (int s = 0; s < c->nspecies; ++s)
+    // freshness, a pending permutation and valid keys change what a step
+    // launches only for the per-step sorted kernel (elsewhere they stay false)
+    const bool cells = cells_mode(c);
+    for (int s = 0; s < c->nspecies; ++s) {
         if (G.buf[s] != c->sp[s].buf || G.sorted[s] != c->sp[s].sorted) return false;
+        if (cells && (G.fresh[s] != c->sp[s].fresh || G.pending[s] != c->sp[s].perm_pending ||
+                      G.keys_valid[s] != c->sp[s].keys_valid))
+            return false;
+    }
     return true;
 }
 
@@ -779,7 +815,12 @@ static void graph_save_after(const Ctx *c, StepGraph &G) {
     for (int s = 0; s < c->nspecies; ++s) {
         G.buf_after[s] = c->sp[s].buf;
         G.alt_after[s] = c->sp[s].alt;
+        G.sorted_after[s] = c->sp[s].sorted;
+        G.fresh_after[s] = c->sp[s].fresh;
+        G.pending_after[s] = c->sp[s].perm_pending;
+        G.keys_valid_after[s] = c->sp[s].keys_valid;
     }
+    G.since_sort_after = c->since_sort;
     G.last_iters = c->last_iters;
     G.last_kk = c->last_kk;
     G.filtered_after_solve = c->filtered_after_solve;
@@ -795,12 +836,16 @@ static void graph_apply_after(Ctx *c, const StepGraph &G) {
         S.buf = G.buf_after[s];
         S.alt = G.alt_after[s];
         S.bind(c->fp64);
-        if (G.sort) S.sorted = true;
+        S.sorted = G.sorted_after[s];
+        S.fresh = G.fresh_after[s];
+        S.perm_pending = G.pending_after[s];
+        S.keys_valid = G.keys_valid_after[s];
+        if (S.sorted) S.nsorted = S.n;   // graph steps neither add nor drop particles
     }
     c->last_iters = G.last_iters;
     c->last_kk = G.last_kk;
     c->filtered_after_solve = G.filtered_after_solve;
-    if (G.sort) c->since_sort = 0;
+    c->since_sort = G.since_sort_after;
 }
 
 // One step through the graph cache: replay the capture that starts from the
@@ -832,12 +877,20 @@ static int step_graph(Ctx *c, bool sort, bool filter) {
     for (int s = 0; s < c->nspecies; ++s) {
         G.buf[s] = c->sp[s].buf;
         G.sorted[s] = c->sp[s].sorted;
+        G.fresh[s] = c->sp[s].fresh;
+        G.pending[s] = c->sp[s].perm_pending;
+        G.keys_valid[s] = c->sp[s].keys_valid;
     }
     // host state before, for a failed capture
     StepGraph before;
     graph_save_after(c, before);
-    bool sorted0[PP_MAX_SPECIES];
-    for (int s = 0; s < c->nspecies; ++s) sorted0[s] = c->sp[s].sorted;
+    bool sorted0[PP_MAX_SPECIES], fresh0[PP_MAX_SPECIES], pending0[PP_MAX_SPECIES], keys0[PP_MAX_SPECIES];
+    for (int s = 0; s < c->nspecies; ++s) {
+        sorted0[s] = c->sp[s].sorted;
+        fresh0[s] = c->sp[s].fresh;
+        pending0[s] = c->sp[s].perm_pending;
+        keys0[s] = c->sp[s].keys_valid;
+    }
     int since0 = c->since_sort;
     int64_t nl0 = c->nlaunch;
     cudaGraph_t graph = nullptr;
@@ -851,7 +904,12 @@ static int step_graph(Ctx *c, bool sort, bool filter) {
         cudaGetLastError();   // clear a capture error
         if (exec) cudaGraphExecDestroy(exec);
         graph_apply_after(c, before);   // undo the pointer swaps of the capture
-        for (int s = 0; s < c->nspecies; ++s) c->sp[s].sorted = sorted0[s];
+        for (int s = 0; s < c->nspecies; ++s) {
+            c->sp[s].sorted = sorted0[s];
+            c->sp[s].fresh = fresh0[s];
+            c->sp[s].perm_pending = pending0[s];
+            c->sp[s].keys_valid = keys0[s];
+        }
         c->since_sort = since0;
         c->nlaunch = nl0;
         G = StepGraph();
@@ -1023,9 +1081,9 @@ extern "C" int pp_set_tuning(pp_ctx *p, int sort_interval, int deposit_mode) {
     Ctx *c = p;
     if (!c) return fail(c, PP_EINVAL, "NULL context");
     if (sort_interval < 0) return fail(c, PP_EINVAL, "sort_interval must be >= 0");
-    if (deposit_mode < 0 || deposit_mode > 2) return fail(c, PP_EINVAL, "unknown deposit_mode");
-    if (deposit_mode == PP_DEPOSIT_TILED && !tiled_supported(*c))
-        return fail(c, PP_EINVAL, "the tiled deposit needs PP_MIXED32 and grid sizes that are multiples of 8");
+    if (deposit_mode < 0 || deposit_mode > 3) return fail(c, PP_EINVAL, "unknown deposit_mode");
+    if ((deposit_mode == PP_DEPOSIT_TILED || deposit_mode == PP_DEPOSIT_CELLS) && !tiled_supported(*c))
+        return fail(c, PP_EINVAL, "the tiled deposits need PP_MIXED32 and grid sizes that are multiples of 8");
     c->d.sort_interval = sort_interval;
     c->d.deposit_mode = deposit_mode;
     graphs_clear(c);
@@ -1117,6 +1175,116 @@ extern "C" int pp_get_fields(pp_ctx *p, double *const E[3], double *const B[3], 
         }
     }
     cudaFree(stage);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// z-slab decomposition (multi-GPU): the current of one rank's particles out
+// and the summed current in, and the particles that left the rank's slab.
+// ---------------------------------------------------------------------------
+extern "C" int pp_get_current(pp_ctx *p, double *const J[3], int on_device) {
+    Ctx *c = p;
+    if (!c || !J || !J[0] || !J[1] || !J[2]) return fail(c, PP_EINVAL, "pp_get_current: NULL argument");
+    const size_t nb = sizeof(double) * (size_t)c->g.cells();
+    if (on_device) {
+        for (int a = 0; a < 3; ++a) CU(to_compact(c, c->J[a], J[a]));
+        return PP_OK;
+    }
+    double *stage = nullptr;
+    CU(cudaMalloc(&stage, nb));
+    int rc = PP_OK;
+    for (int a = 0; a < 3 && rc == PP_OK; ++a) {
+        cudaError_t e = to_compact(c, c->J[a], stage);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(J[a], stage, nb, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "current readback: %s", cudaGetErrorString(e));
+    }
+    cudaFree(stage);
+    return rc;
+}
+
+extern "C" int pp_set_current(pp_ctx *p, const double *const J[3], int on_device) {
+    Ctx *c = p;
+    if (!c || !J || !J[0] || !J[1] || !J[2]) return fail(c, PP_EINVAL, "pp_set_current: NULL argument");
+    graphs_clear(c);
+    const size_t nb = sizeof(double) * (size_t)c->g.cells();
+    if (on_device) {
+        for (int a = 0; a < 3; ++a) CU(to_padded(c, J[a], c->J[a]));
+        return PP_OK;
+    }
+    double *stage = nullptr;
+    CU(cudaMalloc(&stage, nb));
+    int rc = PP_OK;
+    for (int a = 0; a < 3 && rc == PP_OK; ++a) {
+        cudaError_t e = cudaMemcpyAsync(stage, J[a], nb, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = to_padded(c, stage, c->J[a]);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "current upload: %s", cudaGetErrorString(e));
+    }
+    cudaFree(stage);
+    return rc;
+}
+
+extern "C" int pp_set_slab(pp_ctx *p, double z_lo, double z_hi) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (c->wall[2]) return fail(c, PP_EINVAL, "pp_set_slab: z must be periodic");
+    const double Lz = c->g.n[2] * c->d.dz;
+    if (!(z_lo >= 0.0 && z_lo < z_hi && z_hi <= Lz)) return fail(c, PP_EINVAL, "pp_set_slab: need 0 <= z_lo < z_hi <= Lz");
+    c->slab = true;
+    c->slab_lo = z_lo;
+    c->slab_hi = z_hi;
+    return PP_OK;
+}
+
+extern "C" int pp_extract_particles(pp_ctx *p, int sid, int64_t cap, double *x, double *y, double *z, double *ux,
+                                    double *uy, double *uz, int on_device, int64_t *n_out) {
+    Ctx *c = p;
+    if (!c || !n_out || cap < 0) return fail(c, PP_EINVAL, "pp_extract_particles: bad argument");
+    if (sid < 0 || sid >= c->nspecies) return fail(c, PP_EINVAL, "no species %d", sid);
+    if (!c->slab) return fail(c, PP_EINVAL, "pp_extract_particles: no slab set (pp_set_slab)");
+    const double z_lo = c->slab_lo, z_hi = c->slab_hi;
+    double *const dst[6] = {x, y, z, ux, uy, uz};
+    for (int k = 0; k < 6 && cap > 0; ++k)
+        if (!dst[k]) return fail(c, PP_EINVAL, "pp_extract_particles: NULL output array");
+    Species &S = c->sp[sid];
+    *n_out = 0;
+    if (S.n == 0) return PP_OK;
+    graphs_clear(c);
+    unsigned long long *d_count = nullptr;
+    CU(cudaMalloc(&d_count, sizeof(unsigned long long)));
+    double *stage = nullptr;
+    int rc = PP_OK;
+    unsigned long long h_count = 0;
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), c->st);
+    if (e == cudaSuccess) e = launch_extract(*c, sid, z_lo, z_hi, 0, 0, d_count, dst);   // count first
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_count, d_count, sizeof h_count, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle extraction: %s", cudaGetErrorString(e));
+    if (rc == PP_OK && (int64_t)h_count > cap)
+        rc = fail(c, PP_ENOMEM, "pp_extract_particles: %lld particles left the slab, room for %lld",
+                  (long long)h_count, (long long)cap);
+    if (rc == PP_OK && h_count > 0) {
+        double *out[6];
+        if (on_device) {
+            for (int k = 0; k < 6; ++k) out[k] = dst[k];
+        } else if ((e = cudaMalloc(&stage, 6 * sizeof(double) * h_count)) == cudaSuccess) {
+            for (int k = 0; k < 6; ++k) out[k] = stage + (size_t)k * h_count;
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), c->st);
+        if (e == cudaSuccess) e = launch_extract(*c, sid, z_lo, z_hi, 1, (int64_t)h_count, d_count, out);
+        for (int k = 0; k < 6 && e == cudaSuccess && !on_device; ++k)
+            e = cudaMemcpyAsync(dst[k], out[k], sizeof(double) * h_count, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) rc = fail(c, PP_ECUDA, "particle extraction: %s", cudaGetErrorString(e));
+        if (rc == PP_OK) {   // drop them now: the compacting sort reads back the new count
+            S.may_hold_dead = true;
+            if ((e = launch_sort(*c, sid)) != cudaSuccess) rc = fail(c, PP_ECUDA, "compaction: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaFree(stage);
+    cudaFree(d_count);
+    if (rc == PP_OK) *n_out = (int64_t)h_count;
     return rc;
 }
 

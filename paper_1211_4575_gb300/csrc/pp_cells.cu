@@ -1,0 +1,792 @@
+// pp_cells.cu -- the particle step of the mixed form on particles sorted by
+// cell at the start of every step (Sec. III: the paper sorts the particle
+// array by cell position in every step, between the current deposit and the
+// field update, so that steps 1-3 run as one sweep that accumulates the
+// current in small cache-resident buffers).
+//
+// One CTA per 8x8x8 tile of cells.  Because every particle of the tile's sorted
+// range sits in the tile, the E/B window staged in shared memory is the tile
+// plus the stencil reach only (13^3 nodes), and the particles of one cell are
+// consecutive in memory.  Per chunk of up to 4096 particles of one species:
+//
+//  phase 1, one thread per particle (a warp on 32 consecutive particles, i.e.
+//    one or two cells: the gather's shared loads are broadcasts): gather
+//    (eq:pfields), push (Vay / Boris, optional radiative cooling), move; the
+//    new cell, offset and momentum go straight back to the particle arrays
+//    (coalesced); the old offset and the displacement are staged for the
+//    deposit.  A particle whose support start changes on some axis (it
+//    crosses a support boundary) is queued.
+//  pieces: the chunk is cut into pieces of at most 8 consecutive particles
+//    of one deposit group (the particles of one cell, and for even orders of
+//    one octant of it, share their support start on every axis).
+//  phase 2, the charge-conserving current (eq:cc1, eq:jj3, Esirkepov's
+//    decomposition written as the 2nd-order current by a per-particle prefix
+//    sum): one thread per (piece, component) sums the O (O+1)^2 site values
+//    of its particles in registers and adds them to the tile's FP32 current
+//    window with one shared atomic per site (about 48 x 3 per piece instead of
+//    per particle); queued particles take the general form on the union
+//    support, one thread per (particle, component), with shared atomics per
+//    nonzero site.  A warp's 32 items always share the component, so no warp
+//    diverges over the three forms.
+//
+// The current window holds int32 fixed point (native shared integer atomics):
+// each chunk takes its unit from its particles' motion so that no node can
+// overflow, and after the chunk the nodes its cells reach are added into the
+// FP32 mesh (one global atomic per nonzero node).  A piece's sum is FP32 in
+// registers and is rounded to the unit once.
+#include "pp_internal.cuh"
+#include "pp_particle_common.cuh"
+
+namespace pp {
+
+namespace {
+
+constexpr int kT = 8;                            // tile edge (cells)
+constexpr int kTCells = kT * kT * kT;
+constexpr int kRLo = 2, kRHi = 3;                // node reach below / above a cell (gather and deposit, O <= 3)
+constexpr int kW = kT + kRLo + kRHi;             // 13 window nodes per axis
+constexpr int kWVol = kW * kW * kW;              // words per window component
+#ifndef PP_CELLS_THREADS
+#define PP_CELLS_THREADS 512
+#endif
+constexpr int kCT = PP_CELLS_THREADS;            // threads per tile CTA
+constexpr int kCW = kCT / 32;
+// With PP_CELLS_PAIRS=1 the gather's window is stored as pairs (F[n], F[n+1])
+// of consecutive x nodes, so that a 4-node row of a PCS stencil takes two
+// 64-bit shared loads instead of four 32-bit ones (nodes -2 .. 9 of a tile,
+// 12 per axis; the chunk shrinks to 3584 particles to make room).  Measured
+// slower than the plain FP32 window (128^3 thermal PCS: 19.3 against 18.3 ms
+// per step), so the plain window is the default.
+#ifndef PP_CELLS_PAIRS
+#define PP_CELLS_PAIRS 0
+#endif
+constexpr int kWG = kT + kRLo + 2;               // 12 gather window nodes per axis
+constexpr int kWGVol = kWG * kWG * kWG;
+__device__ __forceinline__ int wg(int i, int j, int k) { return i + kWG * (j + kWG * k); }
+#if PP_CELLS_PAIRS
+constexpr size_t kFieldBytes = sizeof(float2) * 6 * kWGVol;
+constexpr int kCC = 3584;                        // particles staged per chunk
+#else
+constexpr size_t kFieldBytes = sizeof(float) * 6 * kWVol;
+constexpr int kCC = 4096;                        // particles staged per chunk
+#endif
+constexpr int kCPer = kCC / kCT;                 // phase-1 particles per thread per chunk
+// Pieces of at most 8 particles: more register sums to add than with 16 or 32,
+// but the deposit items spread evenly over the threads (64^3 thermal PCS:
+// 2.60 ms at 8 or 12, 2.64 at 16, 2.92 at 32).
+#ifndef PP_CELLS_PIECE
+#define PP_CELLS_PIECE 8
+#endif
+constexpr int kPiece = PP_CELLS_PIECE;           // most particles per deposit piece
+// Staged arrays hold one pad word per 16 particles: the lanes of a deposit warp
+// read particles about one piece (16) apart, which unpadded would fall in two
+// banks.
+constexpr int kCS = kCC + kCC / 16;              // words per staged array
+__device__ __forceinline__ int sp(int q) { return q + (q >> 4); }
+constexpr uint16_t kSkip = 0x8000;               // group word flag: not deposited by a piece
+static_assert(kCC % kCT == 0 && kCT % 32 == 0, "chunk must split evenly over the CTA");
+static_assert(kCPer * kCW <= 1024, "piece-count table");
+constexpr int kMisc = 16 + kCPer * kCW;          // queue counters (2), piece count, box (6), totals (3), per-(round, warp) counts
+constexpr size_t kCellsSmem = kFieldBytes + sizeof(float) * (3 * kWVol + 6 * kCS) + sizeof(uint16_t) * (3 * kCC + 2) +
+                              sizeof(int) * kMisc;
+// The current window: an int32 fixed-point window whose unit each chunk takes
+// from its particles' motion, flushed into the FP32 mesh per chunk; or, with
+// PP_CELLS_FIXED=0, an FP32 window of shared FP32 atomics flushed once per
+// tile.  Shared FP32 atomics measured about four times the shared-memory
+// wavefronts of int32 ones here (64^3 thermal PCS: 4.67 against 2.51 ms).
+#ifndef PP_CELLS_FIXED
+#define PP_CELLS_FIXED 1
+#endif
+#if PP_CELLS_FIXED
+using JT = int;
+#else
+using JT = float;
+#endif
+constexpr float kFixedRange = 1073741824.0f;    // 2^30
+__device__ __forceinline__ void jadd(JT *p, float v) {
+#if PP_CELLS_FIXED
+    atomicAdd(p, __float2int_rn(v));
+#else
+    atomicAdd(p, v);
+#endif
+}
+static_assert(kCellsSmem <= 227 * 1024, "tile CTA must fit the opt-in shared memory");
+
+__device__ __forceinline__ int wi(int i, int j, int k) { return i + kW * (j + kW * k); }
+
+// Gather accessor over the staged E/B window (frame = the particle's cell).
+struct CellsFieldAcc {
+    const float *Fw;
+    int base;
+    PP_IF_CHECKED(int wx = 0, wy = 0, wz = 0; int *st = nullptr; mutable int bad = 0;)
+#ifdef PP_CHECKED
+    __device__ __forceinline__ bool inside(int i, int j, int k) const {
+        return wx + i >= 0 && wx + i < kW && wy + j >= 0 && wy + j < kW && wz + k >= 0 && wz + k < kW;
+    }
+    __device__ ~CellsFieldAcc() {
+        if (bad && st) atomicOr(st, ST_BOUNDS);
+    }
+#endif
+    __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
+        PP_IF_CHECKED(if (!inside(i, j, k)) { bad = 1; return 0.0f; })
+        return Fw[(kind * 3 + comp) * kWVol + base + wi(i, j, k)];
+    }
+};
+
+// Gather of one staggered component from the pair window P (eq:pfields):
+// separable triple sum over the (O+1)^3 support starting at window node
+// (i0, j0, k0), x innermost, each row read as 64-bit pairs.
+template <int O>
+__device__ __forceinline__ float gather_pairs(const float2 *P, int i0, int j0, int k0, const float (&wx)[O + 1],
+                                              const float (&wy)[O + 1], const float (&wz)[O + 1]) {
+    const float2 *base = P + wg(i0, j0, k0);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= O; ++k) {
+        float sy = 0.0f;
+#pragma unroll
+        for (int j = 0; j <= O; ++j) {
+            const float2 *row = base + wg(0, j, k);
+            const float2 a = row[0];
+            float sx = wx[0] * a.x + wx[1] * a.y;
+            if constexpr (O >= 2) {
+                const float2 b = row[2];
+                sx += wx[2] * b.x;
+                if constexpr (O >= 3) sx += wx[3] * b.y;
+            }
+            sy += wy[j] * sx;
+        }
+        s += wz[k] * sy;
+    }
+    return s;
+}
+
+// E and B at a particle of the tile cell (rx, ry, rz) with offsets xi, from
+// the pair window (component c at P + c kWGVol: E_x, E_y, E_z, B_x, B_y, B_z).
+template <int O>
+__device__ __forceinline__ void gather_EB_pairs(const float2 *P, int rx, int ry, int rz, const float (&xi)[3],
+                                                float (&E)[3], float (&B)[3] PP_IF_CHECKED(, int *st)) {
+    float wI[3][O + 1], wH[3][O + 1];
+    int iI[3], iH[3];
+    const int r[3] = {rx + kRLo, ry + kRLo, rz + kRLo};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        iI[a] = r[a] + support<O, float>(xi[a], false, wI[a]);
+        iH[a] = r[a] + support<O, float>(xi[a], true, wH[a]);
+    }
+#ifdef PP_CHECKED
+    for (int a = 0; a < 3; ++a)
+        if (iI[a] < 0 || iI[a] + O >= kWG || iH[a] < 0 || iH[a] + O >= kWG) {
+            atomicOr(st, ST_BOUNDS);
+            E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = 0.0f;
+            return;
+        }
+#endif
+    // E_a: half-integer along a; B_a: integer along a, half-integer across
+    E[0] = gather_pairs<O>(P + 0 * kWGVol, iH[0], iI[1], iI[2], wH[0], wI[1], wI[2]);
+    E[1] = gather_pairs<O>(P + 1 * kWGVol, iI[0], iH[1], iI[2], wI[0], wH[1], wI[2]);
+    E[2] = gather_pairs<O>(P + 2 * kWGVol, iI[0], iI[1], iH[2], wI[0], wI[1], wH[2]);
+    B[0] = gather_pairs<O>(P + 3 * kWGVol, iI[0], iH[1], iH[2], wI[0], wH[1], wH[2]);
+    B[1] = gather_pairs<O>(P + 4 * kWGVol, iH[0], iI[1], iH[2], wH[0], wI[1], wH[2]);
+    B[2] = gather_pairs<O>(P + 5 * kWGVol, iH[0], iH[1], iI[2], wH[0], wH[1], wI[2]);
+}
+
+// Current accessor over the FP32 shared window (frame = the particle's cell).
+struct CellsCurrentAcc {
+    JT *J;
+    int base;
+    PP_IF_CHECKED(int wx = 0, wy = 0, wz = 0; int *st = nullptr; mutable int bad = 0;)
+#ifdef PP_CHECKED
+    __device__ __forceinline__ bool inside(int i, int j, int k) const {
+        return wx + i >= 0 && wx + i < kW && wy + j >= 0 && wy + j < kW && wz + k >= 0 && wz + k < kW;
+    }
+    __device__ ~CellsCurrentAcc() {
+        if (bad && st) atomicOr(st, ST_BOUNDS);
+    }
+#endif
+    __device__ __forceinline__ void addJ(int comp, int i, int j, int k, float v) const {
+        PP_IF_CHECKED(if (!inside(i, j, k)) { bad = 1; return; })
+        jadd(J + comp * kWVol + base + wi(i, j, k), v);
+    }
+};
+
+struct CellsSpecies {
+    MixedParticles p;            // read: slot i of the sorted order is p[perm[i]] (p[i] without perm)
+    MixedParticles out;          // written: the new state of slot i, in the sorted order
+    const int32_t *perm;         // pending sort permutation, or null
+    int32_t *keys;               // written: the sort key of each slot's new state
+    const int32_t *cell_start;   // per sort key, tile-major
+    float qmdt;
+    float kdt;                   // radiative cooling K / dt (0 = off)
+    float jscale[3];             // -q w dx_a / dt
+};
+
+struct CellsArgs {
+    Geom g;
+    const float *E[3];
+    const float *B[3];
+    float *J[3];
+    float dtdx[3];
+    int nt[3];
+    int ns;
+    CellsSpecies sp[PP_MAX_SPECIES];
+    int *status;
+    int wall[3];                 // walls at 0 and wall[a] cells on axis a; 0 = periodic
+    double esc;                  // open end: outgoing particles below x = esc cells leave; 0 = off
+    int32_t dead_key;            // sort key of a particle that left: after every cell's keys
+};
+
+// Sort key of a particle in cell (x, y, z) with offsets o (the key of the cell
+// sort: its 8^3 tile in tile order, its cell in the tile, the octant of the
+// cell that holds it), or dead_key for a particle that left.
+__device__ __forceinline__ int32_t sort_key(const CellsArgs &T, int32_t cw, const float (&o)[3]) {
+    if (cw < 0) return T.dead_key;
+    int x, y, z;
+    unpack_cell(cw, x, y, z);
+    const int tile = ((z / kT) * T.nt[1] + y / kT) * T.nt[0] + x / kT;
+    const int cell = ((z % kT) * kT + y % kT) * kT + x % kT;
+    const int oct = (o[0] >= 0.5f ? 1 : 0) | (o[1] >= 0.5f ? 2 : 0) | (o[2] >= 0.5f ? 4 : 0);
+    return (tile * kTCells + cell) * kSubKeys + oct;
+}
+
+__device__ __forceinline__ void store(const CellsArgs &T, const CellsSpecies &S, int64_t i, int32_t cw,
+                                      const float (&o)[3], const float (&u)[3]) {
+    S.out.cell[i] = cw;
+    S.out.ox[i] = o[0]; S.out.oy[i] = o[1]; S.out.oz[i] = o[2];
+    S.out.ux[i] = u[0]; S.out.uy[i] = u[1]; S.out.uz[i] = u[2];
+    S.keys[i] = sort_key(T, cw, o);
+}
+
+// Deposit group of a particle: its cell in the tile, and for even orders the
+// octant of the cell it sits in (the support start on integer nodes is
+// floor(xi - (O-1)/2), which for even O depends on which half of the cell
+// holds xi).
+template <int O>
+__device__ __forceinline__ int group_of(int rx, int ry, int rz, const float (&xi)[3]) {
+    const int cell = rx + kT * (ry + kT * rz);
+    if constexpr (O % 2 == 0) {
+        const int oct = (xi[0] >= 0.5f ? 1 : 0) | (xi[1] >= 0.5f ? 2 : 0) | (xi[2] >= 0.5f ? 4 : 0);
+        return (cell << 3) | oct;
+    } else {
+        return cell;
+    }
+}
+
+// Window coordinates of the group's cell and of its support start.
+template <int O>
+__device__ __forceinline__ void group_frame(int grp, int (&cw)[3], int (&lo)[3]) {
+    const int cell = (O % 2 == 0) ? (grp >> 3) : grp;
+    const int r[3] = {cell & (kT - 1), (cell / kT) & (kT - 1), cell / (kT * kT)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cw[d] = r[d] + kRLo;
+        if constexpr (O % 2 == 0) lo[d] = cw[d] - (O - 2) / 2 - 1 + ((grp >> d) & 1);
+        else lo[d] = cw[d] - (O - 1) / 2;
+    }
+}
+
+// Component A of the current of the piece [s, e): the particles that cross no
+// support boundary (flag clear) share the support start lo, so their
+// O (O+1)^2 site values (those of deposit_esirkepov_inner, site by site) are
+// summed in registers and added once.
+template <int O, int A>
+__device__ __forceinline__ void piece_current(JT *Jw, const float *s_o, const float *s_d, const uint16_t *s_grp,
+                                              int s, int e, float jscale PP_IF_CHECKED(, int *st)) {
+    constexpr int Bx = (A + 1) % 3, Cx = (A + 2) % 3;
+    int cw[3], lo[3];
+    group_frame<O>(s_grp[s] & ~kSkip, cw, lo);
+    float acc[O][O + 1][O + 1];
+#pragma unroll
+    for (int m = 0; m < O; ++m)
+#pragma unroll
+        for (int mb = 0; mb <= O; ++mb)
+#pragma unroll
+            for (int mc = 0; mc <= O; ++mc) acc[m][mb][mc] = 0.0f;
+#pragma unroll 1
+    for (int q = s; q < e; ++q) {
+        if (s_grp[q] & kSkip) continue;
+        float S0[3][O + 1], DS[3][O + 1];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float x0 = s_o[d * kCS + sp(q)];
+            const float x1 = x0 + s_d[d * kCS + sp(q)];
+            float wo[O + 1], wn[O + 1];
+            support<O, float>(x0, false, wo);
+            support<O, float>(x1, false, wn);
+#pragma unroll
+            for (int m = 0; m <= O; ++m) {
+                S0[d][m] = wo[m];
+                DS[d][m] = wn[m] - wo[m];
+            }
+        }
+        // prefix of dS along A (suffix form on the upper faces; the last face is 0)
+        float C[O];
+        float run = 0.0f;
+#pragma unroll
+        for (int m = 0; m < O; ++m) {
+            if (2 * m < O + 1) {
+                run += DS[A][m];
+                C[m] = run * jscale;
+            }
+        }
+        run = 0.0f;
+#pragma unroll
+        for (int m = O - 1; m >= 0; --m) {
+            if (2 * m >= O + 1) {
+                run -= DS[A][m + 1];
+                C[m] = run * jscale;
+            }
+        }
+#pragma unroll
+        for (int mc = 0; mc <= O; ++mc) {
+            const float p = S0[Cx][mc] + 0.5f * DS[Cx][mc];
+            const float h = 0.5f * S0[Cx][mc] + (1.0f / 3.0f) * DS[Cx][mc];
+#pragma unroll
+            for (int mb = 0; mb <= O; ++mb) {
+                const float Y = S0[Bx][mb] * p + DS[Bx][mb] * h;
+#pragma unroll
+                for (int m = 0; m < O; ++m) acc[m][mb][mc] += C[m] * Y;
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < O; ++m)
+#pragma unroll
+        for (int mb = 0; mb <= O; ++mb)
+#pragma unroll
+            for (int mc = 0; mc <= O; ++mc) {
+                int idx[3];
+                idx[A] = lo[A] + m;
+                idx[Bx] = lo[Bx] + mb;
+                idx[Cx] = lo[Cx] + mc;
+#ifdef PP_CHECKED
+                if (idx[0] < 0 || idx[0] >= kW || idx[1] < 0 || idx[1] >= kW || idx[2] < 0 || idx[2] >= kW) {
+                    atomicOr(st, ST_BOUNDS);
+                    continue;
+                }
+#endif
+                jadd(Jw + A * kWVol + wi(idx[0], idx[1], idx[2]), acc[m][mb][mc]);
+            }
+}
+
+// Component A of a queued particle's current: the general form on the union
+// of its old and new supports (O + 2 nodes per axis).
+template <int O, int A>
+__device__ __forceinline__ void queued_current(JT *Jw, const float *s_o, const float *s_d, const uint16_t *s_grp,
+                                               int q, float jscale PP_IF_CHECKED(, int *st)) {
+    int cw[3], lo0[3];
+    group_frame<O>(s_grp[q] & ~kSkip, cw, lo0);
+    float xi0[3], xi1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xi0[d] = s_o[d * kCS + sp(q)];
+        xi1[d] = xi0[d] + s_d[d * kCS + sp(q)];
+    }
+    CellsCurrentAcc acc{Jw, wi(cw[0], cw[1], cw[2])};
+    PP_IF_CHECKED(acc.wx = cw[0]; acc.wy = cw[1]; acc.wz = cw[2]; acc.st = st;)
+    float S0[3][O + 2], DS[3][O + 2];
+    int lo[3];
+    esirkepov_weights<O, float>(xi0, xi1, S0, DS, lo);
+    esirkepov_component<O, float, A>(acc, S0, DS, lo, jscale);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt_() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// BND: walls (reflection) and the open end (escape); a separate instantiation
+// so that periodic runs carry none of their tests.
+template <int O, int PUSH, bool BND>
+__global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constant__ CellsArgs T) {
+    extern __shared__ float smem[];
+    float *F = smem;
+    JT *Jw = (JT *)((char *)smem + kFieldBytes);
+    float *s_o = (float *)(Jw + 3 * kWVol);   // 3 x kCS: offsets at t (frame of the cell)
+    float *s_d = s_o + 3 * kCS;           // 3 x kCS: displacement of the step
+    uint16_t *s_grp = (uint16_t *)(s_d + 3 * kCS);   // deposit group | kSkip
+    uint16_t *s_piece = s_grp + kCC;                  // piece starts (+ the end)
+    uint16_t *s_queue = s_piece + kCC + 2;            // queued particles
+    int *misc = (int *)(s_queue + kCC);   // [0], [1]: queue counters of even / odd chunks; [2]: pieces;
+                                          // [4..9]: fixed point: cell box of the chunk; [10..12]: sum |dxi|
+    int *cnt = misc + 16;                 // piece starts per (round, warp)
+    const Geom &g = T.g;
+    const int tile = blockIdx.x;
+    const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
+    const int ox = tx * kT, oy = ty * kT, oz = tz * kT;
+    const int wx = ox - kRLo, wy = oy - kRLo, wz = oz - kRLo;
+    const int64_t key0 = (int64_t)tile * kTCells * kSubKeys, key1 = key0 + kTCells * kSubKeys;
+    {   // a tile that holds no particle (the mirror half of a box between walls) stages nothing
+        int held = 0;
+        for (int s = 0; s < T.ns; ++s) held |= T.sp[s].cell_start[key1] - T.sp[s].cell_start[key0];
+        if (!held) return;
+    }
+#if PP_CELLS_PAIRS
+    {   // pairs (F[i], F[i+1]) of the gather window; the last x node's pair is never read
+        float2 *P = (float2 *)smem;
+        for (int idx = threadIdx.x; idx < 6 * kWGVol; idx += kCT) {
+            const int comp = idx / kWGVol, r = idx - comp * kWGVol;
+            const int i = r % kWG, j = (r / kWG) % kWG, k = r / (kWG * kWG);
+            const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
+#ifdef PP_CHECKED
+            if (wx + i < -g.G || wx + i + 1 >= g.n[0] + g.G || wy + j < -g.G || wy + j >= g.n[1] + g.G ||
+                wz + k < -g.G || wz + k >= g.n[2] + g.G) {
+                atomicOr(T.status, ST_BOUNDS);
+                P[idx] = make_float2(0.0f, 0.0f);
+                continue;
+            }
+#endif
+            const int64_t at = g.at(wx + i, wy + j, wz + k);
+            P[idx] = make_float2(__ldg(src + at), i + 1 < kWG ? __ldg(src + at + 1) : 0.0f);
+        }
+    }
+#else
+    for (int idx = threadIdx.x; idx < 6 * kWVol; idx += kCT) {
+        const int comp = idx / kWVol, r = idx - comp * kWVol;
+        const int i = r % kW, j = (r / kW) % kW, k = r / (kW * kW);
+        const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
+#ifdef PP_CHECKED
+        if (wx + i < -g.G || wx + i >= g.n[0] + g.G || wy + j < -g.G || wy + j >= g.n[1] + g.G || wz + k < -g.G ||
+            wz + k >= g.n[2] + g.G) {
+            atomicOr(T.status, ST_BOUNDS);
+            F[idx] = 0.0f;
+            continue;
+        }
+#endif
+        F[idx] = __ldg(src + g.at(wx + i, wy + j, wz + k));
+    }
+#endif
+    for (int idx = threadIdx.x; idx < 3 * kWVol; idx += kCT) Jw[idx] = 0;
+    if (threadIdx.x < 2) misc[threadIdx.x] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int par = 0;   // chunk parity: selects the queue counter
+    for (int s = 0; s < T.ns; ++s) {
+        const CellsSpecies &S = T.sp[s];
+        const int tb = S.cell_start[key0], te = S.cell_start[key1];
+        for (int cb = tb; cb < te; cb += kCC, par ^= 1) {
+            const int cn = min(kCC, te - cb);
+            if (threadIdx.x == 0) misc[par ^ 1] = 0;   // the next chunk's counter (last read before the barrier above)
+#if PP_CELLS_FIXED
+            float sum[3] = {0.0f, 0.0f, 0.0f};
+            int blo[3] = {kT, kT, kT}, bhi[3] = {-1, -1, -1};
+#endif
+            // ---- phase 1: gather, push, move; write back; stage the deposit
+            // the particle of the next round is fetched (through the pending
+            // permutation) before the current one is computed, so that its
+            // dependent global loads overlap the gather
+            int32_t n_cw = 0;
+            float n_o[3] = {0.0f, 0.0f, 0.0f}, n_u[3] = {0.0f, 0.0f, 0.0f};
+            auto fetch = [&](int qf) {
+                if (qf >= cn) return;
+                const int64_t i = (int64_t)cb + qf;
+                const int64_t src = S.perm ? (int64_t)S.perm[i] : i;
+                n_cw = S.p.cell[src];
+                n_o[0] = S.p.ox[src]; n_o[1] = S.p.oy[src]; n_o[2] = S.p.oz[src];
+                n_u[0] = S.p.ux[src]; n_u[1] = S.p.uy[src]; n_u[2] = S.p.uz[src];
+            };
+            fetch(threadIdx.x);
+#pragma unroll 1
+            for (int r = 0; r < kCPer; ++r) {
+                const int q = r * kCT + threadIdx.x;
+                if (q >= cn) break;
+                const int64_t idx = (int64_t)cb + q;
+                const int32_t cw0 = n_cw;
+                float xi0[3] = {n_o[0], n_o[1], n_o[2]};
+                float u[3] = {n_u[0], n_u[1], n_u[2]};
+                fetch(q + kCT);
+                int cx, cy, cz;
+                unpack_cell(cw0, cx, cy, cz);
+                const int rx = cx - ox, ry = cy - oy, rz = cz - oz;
+                if ((unsigned)rx >= (unsigned)kT || (unsigned)ry >= (unsigned)kT || (unsigned)rz >= (unsigned)kT) {
+                    // not in its sorted tile: cannot happen after a sort; left unmoved and flagged
+                    atomicOr(T.status, ST_RANGE);
+                    s_grp[q] = kSkip;
+                    store(T, S, idx, cw0, xi0, u);
+                    continue;
+                }
+                const float u0[3] = {u[0], u[1], u[2]};
+                const int grp = group_of<O>(rx, ry, rz, xi0);
+                if (S.qmdt != 0.0f) {   // uniform: no kick, no force
+                    float E[3], B[3];
+#if PP_CELLS_PAIRS
+                    gather_EB_pairs<O>((const float2 *)F, rx, ry, rz, xi0, E, B PP_IF_CHECKED(, T.status));
+#else
+                    CellsFieldAcc facc{F, wi(rx + kRLo, ry + kRLo, rz + kRLo)};
+                    PP_IF_CHECKED(facc.wx = rx + kRLo; facc.wy = ry + kRLo; facc.wz = rz + kRLo; facc.st = T.status;)
+                    gather_EB<O, float>(facc, xi0, E, B);
+#endif
+                    push_particle<PUSH, float>(S.qmdt, S.kdt, E, B, u);
+                }
+                const float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                float dx[3], xi1[3];
+                bool ok = true, cross = false;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    dx[d] = T.dtdx[d] * u[d] * gi;
+                    xi1[d] = xi0[d] + dx[d];
+                    ok = ok && (fabsf(dx[d]) < 1.0f);
+                    cross = cross || floorf(xi0[d] - 0.5f * (O - 1)) != floorf(xi1[d] - 0.5f * (O - 1));
+                }
+                if (!ok) {   // leave the particle unchanged and flag the step
+                    atomicOr(T.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
+                    s_grp[q] = (uint16_t)(grp | kSkip);
+                    store(T, S, idx, cw0, xi0, u0);
+                    continue;
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    s_o[d * kCS + sp(q)] = xi0[d];
+                    s_d[d * kCS + sp(q)] = dx[d];
+                }
+#if PP_CELLS_FIXED
+                sum[0] += fabsf(dx[0]); sum[1] += fabsf(dx[1]); sum[2] += fabsf(dx[2]);
+                blo[0] = min(blo[0], rx); blo[1] = min(blo[1], ry); blo[2] = min(blo[2], rz);
+                bhi[0] = max(bhi[0], rx); bhi[1] = max(bhi[1], ry); bhi[2] = max(bhi[2], rz);
+#endif
+                if (cross) s_queue[atomicAdd(misc + par, 1)] = (uint16_t)q;
+                s_grp[q] = (uint16_t)(cross ? (grp | kSkip) : grp);
+                // the new state, written to the slot (the deposit reads the staged copy)
+                int ncx = cx, ncy = cy, ncz = cz;
+                rebin(xi1[0], ncx, g.n[0]);
+                rebin(xi1[1], ncy, g.n[1]);
+                rebin(xi1[2], ncz, g.n[2]);
+                int32_t cwd;
+                if constexpr (BND) {
+                    reflect(ncx, xi1[0], u[0], T.wall[0]);
+                    reflect(ncy, xi1[1], u[1], T.wall[1]);
+                    reflect(ncz, xi1[2], u[2], T.wall[2]);
+                    cwd = pack_cell(ncx, ncy, ncz);
+                    if (T.esc > 0.0 && (double)ncx + (double)xi1[0] < T.esc && u[0] < 0.0f) cwd |= kDeadBit;
+                } else {
+                    cwd = pack_cell(ncx, ncy, ncz);
+                }
+                store(T, S, idx, cwd, xi1, u);
+            }
+#if PP_CELLS_FIXED
+            if (threadIdx.x < 3) {   // previous chunk's values were last read before the barrier above
+                misc[4 + threadIdx.x] = kT;
+                misc[7 + threadIdx.x] = -1;
+                ((float *)misc)[10 + threadIdx.x] = 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float sd = sum[d];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                const int l = __reduce_min_sync(0xffffffffu, blo[d]), h = __reduce_max_sync(0xffffffffu, bhi[d]);
+                if (lane == 0) {
+                    atomicAdd((float *)misc + 10 + d, sd);
+                    atomicMin(misc + 4 + d, l);
+                    atomicMax(misc + 7 + d, h);
+                }
+            }
+#endif
+            __syncthreads();
+            // ---- pieces: starts at a group change and every kPiece-th particle
+            unsigned ball[kCPer];
+#pragma unroll
+            for (int r = 0; r < kCPer; ++r) {
+                const int q = r * kCT + threadIdx.x;
+                bool st = false;
+                if (q < cn) st = q % kPiece == 0 || ((s_grp[q] ^ s_grp[q - 1]) & ~kSkip) != 0;
+                ball[r] = __ballot_sync(0xffffffffu, st);
+                if (lane == 0) cnt[r * kCW + warp] = __popc(ball[r]);
+            }
+            __syncthreads();
+            if (warp == 0) {   // exclusive scan of the per-(round, warp) counts, in chunk order
+                constexpr int kPerLane = (kCPer * kCW + 31) / 32;
+                int v[kPerLane], sum = 0;
+#pragma unroll
+                for (int m = 0; m < kPerLane; ++m) {
+                    const int k = lane * kPerLane + m;
+                    v[m] = k < kCPer * kCW ? cnt[k] : 0;
+                    sum += v[m];
+                }
+                int incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                int run = incl - sum;
+#pragma unroll
+                for (int m = 0; m < kPerLane; ++m) {
+                    const int k = lane * kPerLane + m;
+                    if (k < kCPer * kCW) cnt[k] = run;
+                    run += v[m];
+                }
+                if (lane == 31) misc[2] = incl;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < kCPer; ++r) {
+                const int q = r * kCT + threadIdx.x;
+                if (ball[r] & (1u << lane)) s_piece[cnt[r * kCW + warp] + __popc(ball[r] & lanemask_lt_())] = (uint16_t)q;
+            }
+            if (threadIdx.x == 0) s_piece[misc[2]] = (uint16_t)cn;
+            __syncthreads();
+            // ---- phase 2: current of the pieces, then of the queued particles; items in
+            // blocks of 96 = 3 components x 32, so that a warp's items share the component
+            const int np = misc[2], nq = misc[par];
+            const int nblk = (np + 31) >> 5, nqb = (nq + 31) >> 5;
+            // current scale: -q w dx_a / dt, times the chunk's fixed-point unit; no
+            // node can receive more than K_O |jscale_a| sum_p (|dxi_a| + 1e-6) from
+            // the chunk (|C Y| <= K_O |dxi_a|, fixed_point_cy_bound), kept below 2^30
+            // units; a piece converts its register sum once, so a node collects at
+            // most one rounding half per piece and per queued particle
+            float jsc[3], unit[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+#if PP_CELLS_FIXED
+                const float bound = fixed_point_cy_bound<O>() * fabsf(S.jscale[d]) *
+                                    (((float *)misc)[10 + d] + 1e-6f * (float)cn) * 1.001f;
+                unit[d] = bound > 0.0f ? kFixedRange / bound : 0.0f;
+#else
+                unit[d] = 1.0f;
+#endif
+                jsc[d] = S.jscale[d] * unit[d];
+            }
+            const int nitems = (nblk + nqb) * 96;
+#pragma unroll 1
+            for (int it = threadIdx.x; it < nitems; it += kCT) {
+                const int blk = it / 96, rr = it - blk * 96, comp = rr >> 5, j = rr & 31;
+                if (blk < nblk) {
+                    const int p = blk * 32 + j;
+                    if (p >= np) continue;
+                    const int ps = s_piece[p], pe = s_piece[p + 1];
+                    if (comp == 0) piece_current<O, 0>(Jw, s_o, s_d, s_grp, ps, pe, jsc[0] PP_IF_CHECKED(, T.status));
+                    else if (comp == 1) piece_current<O, 1>(Jw, s_o, s_d, s_grp, ps, pe, jsc[1] PP_IF_CHECKED(, T.status));
+                    else piece_current<O, 2>(Jw, s_o, s_d, s_grp, ps, pe, jsc[2] PP_IF_CHECKED(, T.status));
+                } else {
+                    const int k = (blk - nblk) * 32 + j;
+                    if (k >= nq) continue;
+                    const int q = s_queue[k];
+                    if (comp == 0) queued_current<O, 0>(Jw, s_o, s_d, s_grp, q, jsc[0] PP_IF_CHECKED(, T.status));
+                    else if (comp == 1) queued_current<O, 1>(Jw, s_o, s_d, s_grp, q, jsc[1] PP_IF_CHECKED(, T.status));
+                    else queued_current<O, 2>(Jw, s_o, s_d, s_grp, q, jsc[2] PP_IF_CHECKED(, T.status));
+                }
+            }
+            __syncthreads();
+#if PP_CELLS_FIXED
+            {   // the window nodes the chunk's cells reach, into the FP32 mesh (and cleared)
+                const int x0 = misc[4], y0 = misc[5], z0 = misc[6];
+                if (misc[7] >= x0) {
+                    const int ex = misc[7] - x0 + kRLo + kRHi + 1, ey = misc[8] - y0 + kRLo + kRHi + 1,
+                              ez = misc[9] - z0 + kRLo + kRHi + 1;
+                    const int vol = ex * ey * ez;
+                    for (int idx = threadIdx.x; idx < 3 * vol; idx += kCT) {
+                        const int comp = idx / vol, r = idx - comp * vol;
+                        const int i = x0 + r % ex, j = y0 + (r / ex) % ey, k = z0 + r / (ex * ey);
+                        JT *w = Jw + comp * kWVol + wi(i, j, k);
+                        const int iv = *w;
+                        if (iv == 0) continue;
+                        *w = 0;
+                        atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), (float)iv / unit[comp]);
+                    }
+                }
+                __syncthreads();
+            }
+#endif
+        }
+    }
+#if !PP_CELLS_FIXED
+    // ---- the tile's current, once into the FP32 mesh
+    for (int idx = threadIdx.x; idx < 3 * kWVol; idx += kCT) {
+        const float v = Jw[idx];
+        if (v == 0.0f) continue;
+        const int comp = idx / kWVol, r = idx - comp * kWVol;
+        const int i = r % kW, j = (r / kW) % kW, k = r / (kW * kW);
+        atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), v);
+    }
+#endif
+}
+
+}  // namespace
+
+bool cells_supported(const Ctx &c) {
+    if (c.fp64 || c.current_mode != PP_CURRENT_CONSERVING || c.g.G < kRLo || c.g.G < kRHi) return false;
+    for (int a = 0; a < 3; ++a)
+        if (c.g.n[a] % kT != 0 || c.tile[a] != kT) return false;
+    return true;
+}
+
+// All species in one launch; every species with particles must have been
+// sorted since its particles last moved (Species::fresh).
+cudaError_t launch_particles_cells(Ctx &c) {
+    if (!cells_supported(c)) return cudaErrorInvalidConfiguration;
+    CellsArgs T;
+    T.g = c.g;
+    const double h[3] = {c.d.dx, c.d.dy, c.d.dz};
+    for (int d = 0; d < 3; ++d) {
+        T.E[d] = (const float *)c.E[d];
+        T.B[d] = (const float *)c.B[d];
+        T.J[d] = (float *)c.J[d];
+        T.dtdx[d] = (float)(c.drift_dt / h[d]);
+        T.nt[d] = c.ntile[d];
+    }
+    T.ns = 0;
+    for (int s = 0; s < c.nspecies; ++s) {
+        const Species &S = c.sp[s];
+        if (S.n == 0) continue;
+        if (!S.fresh) return cudaErrorInvalidValue;
+        CellsSpecies &t = T.sp[T.ns++];
+        t.p = MixedParticles{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+        int32_t *c2 = (int32_t *)S.alt;
+        float *f2 = (float *)(c2 + S.cap);
+        t.out = MixedParticles{c2, f2, f2 + S.cap, f2 + 2 * S.cap, f2 + 3 * S.cap, f2 + 4 * S.cap, f2 + 5 * S.cap};
+        t.perm = S.perm_pending ? S.perm : nullptr;
+        t.keys = S.keys;
+        t.cell_start = S.cell_start;
+        t.qmdt = (float)(S.q * c.kick_dt / S.m);
+        t.kdt = (float)(c.kick_dt != 0.0 ? S.rad / c.kick_dt : 0.0);
+        for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.drift_dt);
+    }
+    if (T.ns == 0) return cudaSuccess;
+    T.status = c.d_status;
+    for (int d = 0; d < 3; ++d) T.wall[d] = c.wall[d];
+    T.esc = c.escape_now;
+    T.dead_key = (int32_t)c.nkeys;
+    const unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
+    const int o = c.d.shape_order, pu = c.d.pusher;
+    const bool bnd = c.any_wall();
+    static unsigned long long attr_done[2][2][4] = {};
+#define PP_CB(O, PU, BD)                                                                                     \
+    do {                                                                                                     \
+        cudaError_t e_ = ensure_smem_attr(k_particles_cells<O, PU, BD>, (int)kCellsSmem, attr_done[BD][PU][O]); \
+        if (e_ != cudaSuccess) return e_;                                                                    \
+        k_particles_cells<O, PU, BD><<<blocks, kCT, kCellsSmem, c.st>>>(T);                                  \
+    } while (0)
+#define PP_C(O, PU)                                                                                          \
+    do {                                                                                                     \
+        if (bnd) PP_CB(O, PU, true); else PP_CB(O, PU, false);                                               \
+    } while (0)
+    if (pu == PP_BORIS) {
+        if (o == 1) PP_C(1, PP_BORIS); else if (o == 2) PP_C(2, PP_BORIS); else PP_C(3, PP_BORIS);
+    } else {
+        if (o == 1) PP_C(1, PP_VAY); else if (o == 2) PP_C(2, PP_VAY); else PP_C(3, PP_VAY);
+    }
+#undef PP_C
+#undef PP_CB
+    ++c.nlaunch;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // every slot of the sorted order now holds its particle's new state in the
+    // other buffer, with its next sort key
+    for (int s = 0; s < c.nspecies; ++s) {
+        Species &S = c.sp[s];
+        if (S.n == 0) continue;
+        void *old = S.buf;
+        S.buf = S.alt;
+        S.alt = old;
+        S.bind(false);
+        S.perm_pending = false;
+        S.keys_valid = true;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace pp

@@ -247,6 +247,21 @@ __device__ __forceinline__ void esirkepov_weights(const R (&xi0)[3], const R (&x
     }
 }
 
+// Fixed-point current windows (the tiled kernels): largest |C[m] Y[mb][mc]| of
+// one particle per unit of its displacement |dxi_a|.  C[m] is a difference of
+// two values of the cumulative sum of W^O over the nodes up to the face, a
+// function of position whose slope is a W^(O-1) value, so |C| <= |dxi_a|
+// max W^(O-1); Y = S0b S0c/3 + S1b S0c/6 + S0b S1c/6 + S1b S1c/3 is a convex
+// combination of products of weights, so 0 <= Y <= (max W^O)^2.  With
+// max W^0 = max W^1 = 1, max W^2 = 3/4 and max W^3 = 2/3 (Sec. II list after
+// eq:weightfunction) the product is 1, 9/16 and 1/3 for O = 1, 2, 3.  The
+// direct current's q w v W W W per unit displacement is at most (max W^O)^3,
+// below the same figure.
+template <int O>
+__host__ __device__ constexpr float fixed_point_cy_bound() {
+    return O == 1 ? 1.0f : (O == 2 ? 0.5625f : 1.0f / 3.0f);
+}
+
 // Component A of the current of one particle from its weights.
 template <int O, typename R, int A, class Acc>
 __device__ __forceinline__ void esirkepov_component(Acc &acc, const R (&S0)[3][O + 2], const R (&DS)[3][O + 2],
@@ -442,6 +457,15 @@ struct Species {
     int32_t *keys = nullptr;  // sort keys
     int32_t *cell_start = nullptr; // offsets per sort key (nkeys + 1), valid after a sort
     bool sorted = false;
+    bool fresh = false;       // sorted since the particles last moved (the per-step sorted kernel needs it)
+    // Per-step sorted kernel: its pass writes every particle's new sort key
+    // (keys_valid), and the sort that follows only builds the permutation
+    // perm (perm_pending: slot i of the sorted order holds particle perm[i]),
+    // which the next pass applies while it reads the particles.  Any other
+    // reader of the particle arrays first applies it (materialize).
+    int32_t *perm = nullptr;
+    bool perm_pending = false;
+    bool keys_valid = false;
     // Point the SoA arrays into buf (the sort swaps buf and alt).
     void bind(bool fp64) {
         if (fp64) {
@@ -466,11 +490,16 @@ struct StepGraph {
     void *J0 = nullptr;
     void *buf[PP_MAX_SPECIES] = {};
     bool sorted[PP_MAX_SPECIES] = {};
+    bool fresh[PP_MAX_SPECIES] = {};
+    bool pending[PP_MAX_SPECIES] = {}, keys_valid[PP_MAX_SPECIES] = {};
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
     bool filter = false;
     void *J_after[3] = {}, *Jt_after[3] = {};
     void *buf_after[PP_MAX_SPECIES] = {}, *alt_after[PP_MAX_SPECIES] = {};
+    bool sorted_after[PP_MAX_SPECIES] = {}, fresh_after[PP_MAX_SPECIES] = {};
+    bool pending_after[PP_MAX_SPECIES] = {}, keys_valid_after[PP_MAX_SPECIES] = {};
+    int since_sort_after = 0;
     int last_iters = 0;
     double last_kk = 0;
     bool filtered_after_solve = false;
@@ -547,6 +576,10 @@ struct Ctx {
         int64_t shifts = 0;
     } window;
     int32_t *h_count = nullptr;  // pinned: live count read back after a compacting sort
+    // z-slab decomposition: this context owns the particles with physical z in
+    // [slab_lo, slab_hi) of a run split over ranks (pp_set_slab)
+    bool slab = false;
+    double slab_lo = 0.0, slab_hi = 0.0;
     double escape_now = 0.0;     // escape distance the particle kernels apply (0: none this pass)
     int filter_passes = 0;   // divergence-filter passes every filter_interval steps
     int filter_interval = 1;
@@ -595,6 +628,8 @@ cudaError_t launch_particles_fp64(Ctx &c, int s);
 cudaError_t launch_particles_mixed_global(Ctx &c, int s);
 cudaError_t launch_particles_tiled_all(Ctx &c);
 bool tiled_supported(const Ctx &c);
+cudaError_t launch_particles_cells(Ctx &c);
+bool cells_supported(const Ctx &c);
 cudaError_t launch_rho(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c, double *out_per_species);
 
@@ -610,6 +645,7 @@ cudaError_t launch_ghost_fill(Ctx &c, void *const src_E[3], void *const src_B[3]
 cudaError_t launch_mesh_diag(Ctx &c, double *host_out /* 9 values */);
 
 cudaError_t launch_sort(Ctx &c, int s);
+cudaError_t materialize(Ctx &c, int s);   // apply a pending sort permutation to the arrays
 cudaError_t launch_damp(Ctx &c);
 cudaError_t launch_inject(Ctx &c, int s, int64_t off, int64_t count, uint32_t step, uint32_t pstream, double thick);
 cudaError_t launch_window_fields(Ctx &c);
@@ -620,5 +656,7 @@ cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const doubl
                               const double *z, const double *ux, const double *uy, const double *uz, int *bad);
 cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, double *ux, double *uy,
                                double *uz);
+cudaError_t launch_extract(Ctx &c, int s, double z_lo, double z_hi, int write, int64_t cap,
+                           unsigned long long *count, double *const out[6]);
 
 }  // namespace pp

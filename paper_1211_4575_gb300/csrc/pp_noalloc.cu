@@ -2,19 +2,22 @@
 // reduction of pp_diagnostics, for callers that cannot allocate device memory.
 //
 // Some callers of this library cannot call cudaMalloc at the point where they
-// need the field energies: code running while a CUDA graph is being captured
-// into a memory pool it does not own, real-time loops that forbid allocation
-// after start-up, or embedding hosts that hand the library pre-allocated
-// device buffers and nothing else.  This variant keeps its scratch (the
+// need the field energies: real-time loops that forbid allocation after
+// start-up (an allocation can block or fail at an arbitrary time), or
+// embedding hosts that own all device memory and hand the library
+// pre-allocated buffers and nothing else.  This variant keeps its scratch (the
 // per-block partial sums of the reduction) in a file-scope __device__ array of
 // fixed size instead of asking for memory.
 //
 // The array is one per device that loads the library and lives until the
 // process exits.  Host code cannot use the array's name as a device address:
 // the first call on a device, with that device current, looks the address up
-// with cudaGetSymbolAddress and caches it; make that first call before any
-// stream capture.  Every call shares the array, so calls whose kernels overlap
-// on the GPU (different streams, or different host threads) race on it.
+// with cudaGetSymbolAddress and caches it per device ordinal; make that first
+// call before any stream capture.  The cached address belongs to the device's
+// context: after cudaDeviceReset it is stale, so a process that resets a
+// device must not call this entry point on that device again.  Every call
+// shares the array, so calls whose kernels overlap on the GPU (different
+// streams, or different host threads) race on it.
 #include <stdio.h>
 
 #include <mutex>

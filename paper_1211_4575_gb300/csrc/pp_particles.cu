@@ -3,6 +3,7 @@
 // form, the charge density of eq:rho2, the kinetic-energy reduction and the
 // FP64 <-> storage conversions of pp_load_particles / pp_get_particles.
 #include "pp_internal.cuh"
+#include "pp_particle_common.cuh"
 
 namespace pp {
 
@@ -54,46 +55,6 @@ struct StepArgs {
     int64_t off;                 // first particle of the launch
 };
 
-struct Fp64Particles {
-    double *x, *y, *z, *ux, *uy, *uz;
-};
-
-struct MixedParticles {
-    int32_t *cell;
-    float *ox, *oy, *oz, *ux, *uy, *uz;
-};
-
-// Reflecting walls at 0 and nw cells on one axis (Sec. V "Boundary
-// conditions"), applied after the particle deposited its step as if streaming
-// freely: a particle that ended the move beyond a wall (in (nw, 2 nw) of the
-// mirror-extended box, which the periodic wrap also gives below 0) is replaced
-// by its virtual image, x -> 2 nw - x and u -> -u along that axis.  nw = 0: no
-// walls on the axis.
-__device__ __forceinline__ void reflect(double &xi, double &ux, int nw) {
-    if (nw && xi > (double)nw) {
-        xi = 2.0 * (double)nw - xi;
-        ux = -ux;
-    }
-}
-// Mixed form: cell cx and offset o in [0, 1).  2 nw - (cx + o) is cell
-// 2 nw - 1 - cx with offset 1 - o, or cell 2 nw - cx when o = 0; an offset
-// that rounds to 1 moves to the cell above.
-__device__ __forceinline__ void reflect(int &cx, float &o, float &ux, int nw) {
-    if (nw && (cx > nw || (cx == nw && o > 0.0f))) {
-        if (o > 0.0f) {
-            cx = 2 * nw - 1 - cx;
-            o = 1.0f - o;
-            if (o >= 1.0f) {
-                o = 0.0f;
-                ++cx;
-            }
-        } else {
-            cx = 2 * nw - cx;
-        }
-        ux = -ux;
-    }
-}
-
 template <int O, int PUSH>
 __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64Particles p) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -138,32 +99,6 @@ __global__ void __launch_bounds__(256) k_particles_fp64(StepArgs<double> a, Fp64
     if (a.esc > 0.0 && xi1[0] < a.esc && u[0] < 0.0) xi1[0] = kDeadX;   // out through the open end
     p.x[t] = xi1[0]; p.y[t] = xi1[1]; p.z[t] = xi1[2];
     p.ux[t] = u[0]; p.uy[t] = u[1]; p.uz[t] = u[2];
-}
-
-__device__ __forceinline__ void unpack_cell(int32_t c, int &x, int &y, int &z) {
-    x = c & 1023;
-    y = (c >> 10) & 1023;
-    z = (c >> 20) & 1023;
-}
-__device__ __forceinline__ int32_t pack_cell(int x, int y, int z) { return x | (y << 10) | (z << 20); }
-
-// Re-bin an offset that moved by less than one cell: offset back into [0,1),
-// cell index shifted and wrapped.  An offset that rounds to exactly 1 after
-// adding 1 belongs to the cell above with offset 0.
-__device__ __forceinline__ void rebin(float &o, int &c, int n) {
-    if (o >= 1.0f) {
-        o -= 1.0f;
-        ++c;
-    } else if (o < 0.0f) {
-        o += 1.0f;
-        --c;
-        if (o >= 1.0f) {
-            o = 0.0f;
-            ++c;
-        }
-    }
-    if (c < 0) c += n;
-    else if (c >= n) c -= n;
 }
 
 template <int O, int PUSH>
@@ -259,6 +194,9 @@ cudaError_t launch_particles_fp64(Ctx &c, int s) {
 cudaError_t launch_particles_mixed_global(Ctx &c, int s) {
     Species &S = c.sp[s];
     if (S.n == 0) return cudaSuccess;
+    cudaError_t em = materialize(c, s);
+    if (em != cudaSuccess) return em;
+    S.keys_valid = false;
     StepArgs<float> a = step_args<float>(c, s);
     MixedParticles p{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     unsigned blocks = (unsigned)((S.n + 255) / 256);
@@ -283,10 +221,9 @@ cudaError_t launch_particles_mixed_global(Ctx &c, int s) {
 // particles flushes, over the box it touched, into the FP32 global mesh.
 //
 // Fixed point, chosen per chunk and per current component a: the chunk is
-// first gathered, pushed and moved; then, with |C| <= |dxi_a| (the prefix of
-// dS is a difference of B-spline cumulative sums, whose slope is at most 1)
-// and |Y| <= 3/2, no node can receive more than
-//     bound_a = 3/2 |jscale_a| sum_p (|dxi_{p,a}| + 1e-6)
+// first gathered, pushed and moved; then, with |C Y| <= K_O |dxi_a|
+// (fixed_point_cy_bound: K_3 = 1/3 for PCS), no node can receive more than
+//     bound_a = K_O |jscale_a| sum_p (|dxi_{p,a}| + 1e-6)
 // (the 1e-6 per particle covers the FP32 rounding of the weights in C)
 // from the chunk, and the unit 2^30 / bound_a keeps every int32 sum below
 // 2^30 (plus at most 1024 rounding halves).  The rounding of a contribution
@@ -543,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_particles_tiled(const __grid_co
             float unit[3], jsc[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                float bound = 1.5f * fabsf(S.jscale[d]) * (tot[d] + 1e-6f * (float)cn) * 1.0001f;
+                float bound = fixed_point_cy_bound<O>() * fabsf(S.jscale[d]) * (tot[d] + 1e-6f * (float)cn) * 1.001f;
                 unit[d] = bound > 0.0f ? kFixedRange / bound : 0.0f;
                 jsc[d] = S.jscale[d] * unit[d];
             }
@@ -714,21 +651,6 @@ __global__ void __launch_bounds__(256) k_particles_listed(StepArgs<float> a, Mix
     }
 }
 
-// The opt-in dynamic shared memory of a kernel, set once per device (the
-// attribute belongs to the device's context; a bit per device ordinal).  Two
-// threads that race here set the same value.
-template <class K>
-static cudaError_t ensure_smem_attr(K kernel, int bytes, unsigned long long &done) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (done & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done |= bit;
-    return e;
-}
-
 bool tiled_supported(const Ctx &c) {
     if (c.fp64 || c.g.G < kWinLo || c.g.G < kWin - kWinLo - kTile) return false;
     for (int a = 0; a < 3; ++a)
@@ -740,6 +662,11 @@ bool tiled_supported(const Ctx &c) {
 // their loop); fails if a species has not been sorted yet.
 cudaError_t launch_particles_tiled_all(Ctx &c) {
     if (!tiled_supported(c)) return cudaErrorInvalidConfiguration;
+    for (int s = 0; s < c.nspecies; ++s) {
+        cudaError_t em = materialize(c, s);
+        if (em != cudaSuccess) return em;
+        c.sp[s].keys_valid = false;
+    }
     TiledArgs T;
     T.g = c.g;
     double h[3] = {c.d.dx, c.d.dy, c.d.dz};
@@ -924,6 +851,9 @@ __global__ void k_inject(InjectArgs a, Fp64Particles p64, MixedParticles pm) {
 cudaError_t launch_inject(Ctx &c, int s, int64_t off, int64_t count, uint32_t step, uint32_t pstream, double thick) {
     if (count <= 0) return cudaSuccess;
     Species &S = c.sp[s];
+    cudaError_t em = materialize(c, s);
+    if (em != cudaSuccess) return em;
+    S.keys_valid = false;
     const Ctx::Injector &I = c.inj[s];
     InjectArgs a;
     a.off = off;
@@ -946,6 +876,7 @@ cudaError_t launch_inject(Ctx &c, int s, int64_t off, int64_t count, uint32_t st
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_inject<<<(unsigned)((count + 255) / 256), 256, 0, c.st>>>(a, p64, pm);
     ++c.nlaunch;
+    S.fresh = false;
     return cudaGetLastError();
 }
 
@@ -974,10 +905,14 @@ __global__ void k_window_particles(int64_t n, int nw, Fp64Particles p64, MixedPa
 cudaError_t launch_window_particles(Ctx &c, int s) {
     Species &S = c.sp[s];
     if (S.n == 0) return cudaSuccess;
+    cudaError_t em = materialize(c, s);
+    if (em != cudaSuccess) return em;
+    S.keys_valid = false;
     Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_window_particles<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, c.wall[0], p64, pm, c.fp64 ? 0 : 1);
     ++c.nlaunch;
+    S.fresh = false;
     return cudaGetLastError();
 }
 
@@ -1198,6 +1133,10 @@ __global__ void __launch_bounds__(512) k_rho_tile(Geom g, RhoCellGeom kg, const 
 }
 
 cudaError_t launch_rho(Ctx &c) {
+    for (int s = 0; s < c.nspecies; ++s) {
+        cudaError_t em = materialize(c, s);
+        if (em != cudaSuccess) return em;
+    }
     cudaError_t e = cudaMemsetAsync(c.rho, 0, sizeof(double) * c.g.cells(), c.st);
     if (e != cudaSuccess) return e;
     for (int s = 0; s < c.nspecies; ++s) {
@@ -1349,6 +1288,9 @@ cudaError_t launch_convert_in(Ctx &c, int s, int64_t off, int64_t n, const doubl
                               const double *z, const double *ux, const double *uy, const double *uz, int *bad) {
     if (n == 0) return cudaSuccess;
     Species &S = c.sp[s];
+    cudaError_t em = materialize(c, s);
+    if (em != cudaSuccess) return em;
+    S.keys_valid = false;
     Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_convert_in<<<(unsigned)((n + 255) / 256), 256, 0, c.st>>>(n, off, x, y, z, ux, uy, uz, c.d.dx, c.d.dy, c.d.dz,
@@ -1379,6 +1321,8 @@ __global__ void k_convert_out(int64_t n, double hx, double hy, double hz, int mi
 cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, double *ux, double *uy, double *uz) {
     Species &S = c.sp[s];
     if (S.n == 0) return cudaSuccess;
+    cudaError_t em = materialize(c, s);
+    if (em != cudaSuccess) return em;
     Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
     MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
     k_convert_out<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, c.d.dx, c.d.dy, c.d.dz, c.fp64 ? 0 : 1,
@@ -1387,5 +1331,56 @@ cudaError_t launch_convert_out(Ctx &c, int s, double *x, double *y, double *z, d
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Particles of a z-slab decomposition that moved out of the slab
+// [z_lo, z_hi) (physical z): counted (write = 0), or written out as FP64
+// physical state and marked as gone (write = 1, the first `cap` of them).
+// ---------------------------------------------------------------------------
+__global__ void k_extract(int64_t n, double hx, double hy, double hz, double z_lo, double z_hi, int mixed, int write,
+                          int64_t cap, Fp64Particles p64, MixedParticles pm, unsigned long long *count, double *x,
+                          double *y, double *z, double *ux, double *uy, double *uz) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double px, py, pz;
+    if (mixed) {
+        const int32_t cw = pm.cell[t];
+        if (cw < 0) return;   // gone already
+        int cx, cy, cz;
+        unpack_cell(cw, cx, cy, cz);
+        px = ((double)cx + (double)pm.ox[t]) * hx;
+        py = ((double)cy + (double)pm.oy[t]) * hy;
+        pz = ((double)cz + (double)pm.oz[t]) * hz;
+    } else {
+        if (p64.x[t] < 0.0) return;
+        px = p64.x[t] * hx; py = p64.y[t] * hy; pz = p64.z[t] * hz;
+    }
+    if (pz >= z_lo && pz < z_hi) return;
+    const unsigned long long slot = atomicAdd(count, 1ull);
+    if (!write || slot >= (unsigned long long)cap) return;
+    x[slot] = px; y[slot] = py; z[slot] = pz;
+    if (mixed) {
+        ux[slot] = pm.ux[t]; uy[slot] = pm.uy[t]; uz[slot] = pm.uz[t];
+        pm.cell[t] |= kDeadBit;
+    } else {
+        ux[slot] = p64.ux[t]; uy[slot] = p64.uy[t]; uz[slot] = p64.uz[t];
+        p64.x[t] = kDeadX;
+    }
+}
+
+cudaError_t launch_extract(Ctx &c, int s, double z_lo, double z_hi, int write, int64_t cap,
+                           unsigned long long *count, double *const out[6]) {
+    Species &S = c.sp[s];
+    if (S.n == 0) return cudaSuccess;
+    cudaError_t em = materialize(c, s);
+    if (em != cudaSuccess) return em;
+    if (write) S.keys_valid = false;
+    Fp64Particles p64{S.x, S.y, S.z, S.ux, S.uy, S.uz};
+    MixedParticles pm{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
+    k_extract<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, c.d.dx, c.d.dy, c.d.dz, z_lo, z_hi,
+                                                               c.fp64 ? 0 : 1, write, cap, p64, pm, count, out[0],
+                                                               out[1], out[2], out[3], out[4], out[5]);
+    ++c.nlaunch;
+    return cudaGetLastError();
+}
 
 }  // namespace pp

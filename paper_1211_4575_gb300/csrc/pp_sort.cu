@@ -1,6 +1,6 @@
 // pp_sort.cu -- counting sort of a species' particle arrays by cell (Sec. III:
-// between the current deposit and the field update the particles are "sorted
-// sequentially according to the cell position" for cache locality).
+// between the current deposit and the field update the paper sorts the
+// particles by their cell, for cache locality).
 //
 // The key of a particle is its cell, numbered tile by tile (tiles of up to
 // 8x8x8 cells, x fastest inside a tile and across tiles), so that the sorted
@@ -179,6 +179,58 @@ __global__ void k_scatter_mixed(int64_t n, const int32_t *keys, int32_t *cursor,
     mv(ux, ux2, t, p); mv(uy, uy2, t, p); mv(uz, uz2, t, p);
 }
 
+// Sort from keys a particle pass already wrote (Species::keys_valid): the
+// histogram of the keys, then, through the per-key cursors, the permutation
+// perm[slot] = particle instead of moving the particles.
+__global__ void k_hist(int64_t n, const int32_t *keys, int32_t *counts) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    aggregated_add(counts, keys[t]);
+}
+
+__global__ void k_perm(int64_t n, const int32_t *keys, int32_t *cursor, int32_t *perm) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    perm[aggregated_add(cursor, keys[t])] = (int32_t)t;
+}
+
+// dst[i] = src[perm[i]] for the seven arrays of the mixed form.
+__global__ void k_apply_perm(int64_t n, const int32_t *perm, const int32_t *cell, const float *ox, const float *oy,
+                             const float *oz, const float *ux, const float *uy, const float *uz, int32_t *cell2,
+                             float *ox2, float *oy2, float *oz2, float *ux2, float *uy2, float *uz2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t t = perm[i];
+    mv(cell, cell2, t, i);
+    mv(ox, ox2, t, i); mv(oy, oy2, t, i); mv(oz, oz2, t, i);
+    mv(ux, ux2, t, i); mv(uy, uy2, t, i); mv(uz, uz2, t, i);
+}
+
+static void swap_buffers(Ctx &c, Species &S) {
+    void *old = S.buf;
+    S.buf = S.alt;
+    S.alt = old;
+    S.bind(c.fp64);
+}
+
+cudaError_t materialize(Ctx &c, int s) {
+    Species &S = c.sp[s];
+    if (!S.perm_pending) return cudaSuccess;
+    S.perm_pending = false;
+    if (S.n == 0) return cudaSuccess;
+    const int64_t cp = S.cap;
+    int32_t *c2 = (int32_t *)S.alt;
+    float *f2 = (float *)(c2 + cp);
+    k_apply_perm<<<(unsigned)((S.n + 255) / 256), 256, 0, c.st>>>(S.n, S.perm, S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy,
+                                                                 S.fuz, c2, f2, f2 + cp, f2 + 2 * cp, f2 + 3 * cp,
+                                                                 f2 + 4 * cp, f2 + 5 * cp);
+    ++c.nlaunch;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    swap_buffers(c, S);
+    return cudaSuccess;
+}
+
 static KeyGeom key_geom(const Ctx &c) {
     KeyGeom k;
     for (int a = 0; a < 3; ++a) {
@@ -209,16 +261,24 @@ cudaError_t sort_setup(Ctx &c) {
 cudaError_t launch_sort(Ctx &c, int s) {
     Species &S = c.sp[s];
     S.sorted = true;
-    cudaError_t e = cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
+    // keys from the last particle pass: no key pass, and a permutation in
+    // place of the scatter; otherwise the arrays are put in order first
+    const bool lazy = S.keys_valid && !S.perm_pending && !c.fp64 && S.n > 0;
+    S.keys_valid = false;
+    cudaError_t e = lazy ? cudaSuccess : materialize(c, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
     if (e != cudaSuccess) return e;
     if (S.n == 0) {
         S.nsorted = 0;
         S.may_hold_dead = false;
+        S.fresh = true;
         return cudaMemsetAsync(S.cell_start, 0, sizeof(int32_t) * (c.nkeys + 1), c.st);
     }
     KeyGeom kg = key_geom(c);
     unsigned blocks = (unsigned)((S.n + 255) / 256);
-    if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
+    if (lazy) k_hist<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts);
+    else if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
     else k_keys_mixed<<<blocks, 256, 0, c.st>>>(kg, S.n, S.cell, S.ox, S.oy, S.oz, S.keys, c.counts);
     ++c.nlaunch;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -226,7 +286,12 @@ cudaError_t launch_sort(Ctx &c, int s) {
     if ((e = scan(c.st, c.counts, S.cell_start, c.nkeys + 1, (int32_t *)c.scan_tmp, c.nlaunch)) != cudaSuccess) return e;
     e = cudaMemcpyAsync(c.counts, S.cell_start, sizeof(int32_t) * (c.nkeys + 1), cudaMemcpyDeviceToDevice, c.st);
     if (e != cudaSuccess) return e;
-    if (c.fp64) {
+    if (lazy) {
+        k_perm<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts, S.perm);
+        ++c.nlaunch;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        S.perm_pending = true;
+    } else if (c.fp64) {
         double *b = (double *)S.alt;
         int64_t cp = S.cap;
         k_scatter_fp64<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts, S.x, S.y, S.z, S.ux, S.uy, S.uz, b, b + cp,
@@ -258,6 +323,7 @@ cudaError_t launch_sort(Ctx &c, int s) {
         S.may_hold_dead = false;
     }
     S.nsorted = S.n;
+    S.fresh = true;
     return cudaSuccess;
 }
 

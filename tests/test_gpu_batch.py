@@ -95,11 +95,12 @@ def test_autotuner_picks_a_candidate_and_keeps_physics(pp):
     L = pp_synth.thermal(n=(16, 16, 16), ppc=8, dx=0.1, dt=0.05, seed=3)
     sim = H.gpu_sim(pp, L, pp.PP_MIXED32, 3)
     best, timings = autotune.autotune(sim, sort_intervals=(2, 4), steps=4, use_cache=False)
-    assert best in timings and len(timings) == 4
+    # the per-step sorted mode once, the tiled and global modes at each interval
+    assert best in timings and len(timings) == 5 and (1, pp.PP_DEPOSIT_CELLS) in timings
     g, _ = sim.grid()
     assert (g.sort_interval, g.deposit_mode) == best
     d = sim.diagnostics()
-    assert d["status"] == 0 and d["step"] == 16
+    assert d["status"] == 0 and d["step"] == 20
     assert d["gauss_drift_max"] <= 2e-5 * d["rho_max"]
     with pytest.raises(pp.PPError):
         H.gpu_sim(pp, pp_synth.thermal(n=(12, 12, 12), ppc=2, dx=0.1, dt=0.05), pp.PP_MIXED32, 3).set_tuning(

@@ -128,11 +128,14 @@ def test_graphs_need_a_stream_and_skip_profiling(pp):
         with pytest.raises(pp.PPError):
             legacy.set_graphs(True)
     sim = _sim(pp, L, pp.PP_MIXED32, 2, True, 0)
-    sim.step(3)            # J and J' alternate: two captures, then a replay
-    assert sim.graph_stats() == (2, 1)
+    # per-step sorted kernel: the first step starts from the load's sort; after
+    # it every step sorts from the keys of the last pass, and J / J' and the two
+    # particle buffers alternate: three captures, then a replay
+    sim.step(4)
+    assert sim.graph_stats() == (3, 1)
     sim.profile_enable(True)
     sim.step(3)
     sim.profile_enable(False)
-    assert sim.graph_stats() == (2, 1)    # profiled steps run eagerly
+    assert sim.graph_stats() == (3, 1)    # profiled steps run eagerly
     sim.step(1)
-    assert sim.graph_stats() == (2, 2)
+    assert sim.graph_stats() == (3, 2)

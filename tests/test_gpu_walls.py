@@ -405,3 +405,50 @@ def test_walls_step_graphs_and_eager_boundary_steps(pp, orc):
     sims[1].set_open_boundary(4, 0.1, 1.0)
     sims[1].step(3)
     assert sims[1].graph_stats() == (cap, rep)   # eager: no capture, no replay
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_injector_draws_equal_the_oracle_generator_bit_for_bit(pp, orc, precision):
+    """The GPU injector's Philox4x32-10 words are the oracle's, bit for bit.
+    With unit cell sizes across x and ny = nz = 4, a particle's y and z are
+    4 (r + 1/2) 2^-32 exactly, so the words r1, r2 of its counter can be read
+    back from them; the set of (r1, r2) over one injection equals the words of
+    orc_draws (seed, step 1, position stream 0) at counters 0 .. count-1.  x is
+    thick u0 to rounding, and the Box-Muller momenta of the velocity stream
+    (1 + species) agree to libm-versus-CUDA rounding.  The oracle's generator itself is pinned to the published
+    known-answer vectors."""
+    seed, ppc, u, u_th = 0x1234_5678_9ABC_DEF0, 20.0, (0.8, 0.1, -0.05), 0.05
+    n, d, dt = (16, 4, 4), (0.5, 1.0, 1.0), 0.2
+    sim = pp.Simulation(n, d, dt, shape_order=3, precision=precision, boundary_x=pp.PP_BOUNDARY_WALLS,
+                        relax_tol=1e-6 if precision else 1e-12, relax_max_iter=400)
+    sid = sim.add_species(-1.0, 1.0, 1e-9, 4096)
+    sim.set_injector(sid, ppc, u, u_th, seed)
+    sim.step(1)
+    p = sim.particles(sid)
+    vx = u[0] / math.sqrt(1.0 + sum(v * v for v in u))
+    count = int(math.floor(ppc * n[1] * n[2] * vx * dt / d[0]))
+    assert len(p["x"]) == count and count > 50
+    D = orc.draws(seed, 1, 0, count)
+    words = np.floor(D * 2.0 ** 32).astype(np.int64)
+    ry = p["y"] * 2.0 ** 30 - 0.5
+    rz = p["z"] * 2.0 ** 30 - 0.5
+    if precision == 0:
+        # FP64 positions: the words themselves
+        assert np.all(ry == np.floor(ry)) and np.all(rz == np.floor(rz))
+        got = sorted(zip(ry.astype(np.int64).tolist(), rz.astype(np.int64).tolist()))
+        want = sorted(zip(words[:, 1].tolist(), words[:, 2].tolist()))
+        assert got == want
+        order = np.lexsort((rz, ry))
+        ref = np.lexsort((words[:, 2], words[:, 1]))
+        thick = vx * dt
+        assert np.abs(p["x"][order] - thick * D[ref, 0]).max() <= 4e-16 * thick
+        # proper velocities: Box-Muller on the draws of the velocity stream 1 + species
+        G = orc.gaussians(orc.draws(seed, 1, 1, count))[ref]
+        for a, k in enumerate(("ux", "uy", "uz")):
+            assert np.abs(p[k][order] - (u[a] + u_th * G[:, a])).max() <= 1e-14
+    else:
+        # mixed form: int32 cell + FP32 offset of the same draws (offset
+        # rounded to FP32, 2^-24 of a cell)
+        got = np.sort(p["y"] + 4.0 * p["z"])
+        want = np.sort(4.0 * D[:, 1] + 16.0 * D[:, 2])
+        assert np.abs(got - want).max() <= 4.0 * 2.0 ** -22

@@ -860,3 +860,32 @@ def test_divergence_filter_converges_by_gradients_only(orc):
     dB = [sim.B[a] - B0[a] for a in range(3)]
     assert max(np.abs(c).max() for c in curl(dE, +1)) < 1e-12 * max(np.abs(x).max() for x in dE)
     assert max(np.abs(c).max() for c in curl(dB, -1)) < 1e-12 * max(np.abs(x).max() for x in dB)
+
+
+def test_threaded_particle_loop_equals_the_plain_one(orc):
+    """The oracle's particle loop on several threads (per-thread copies of the
+    charge change and line sums, added after the loop: the timing baseline's
+    all-core form) gives the single-threaded results to summation order
+    (1e-13), for the charge-conserving and the direct current."""
+    import pp_synth
+    from tests import gpu_helpers as H
+    L = pp_synth.thermal(n=(8, 8, 8), ppc=8, u_th=0.1, dx=0.1, dt=0.05, seed=5)
+    for mode in (orc.CHARGE_CONSERVING, orc.DIRECT):
+        runs = []
+        for nt in (1, 4):
+            orc.set_threads(nt)
+            sim = orc.Simulation(L.n, L.d, L.dt, shape_order=3, relax_tol=1e-14, relax_max_iter=2000,
+                                 current_mode=mode)
+            for s in L.species:
+                sim.add_species(s["q"], s["m"], s["w"], s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+            sim.step(2)
+            runs.append(sim)
+        orc.set_threads(1)
+        for F in ("E", "B", "J"):
+            a, b = getattr(runs[0], F), getattr(runs[1], F)
+            scale = max(np.abs(x).max() for x in a)
+            assert max(np.abs(x - y).max() for x, y in zip(a, b)) <= 1e-13 * scale, (mode, F)
+        for s in range(2):   # the second step's push sees fields that differ at round-off
+            for k in ("x", "ux"):
+                a, b = runs[0].species[s][k], runs[1].species[s][k]
+                assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max(), (mode, s, k)

@@ -1,11 +1,12 @@
 """The allocation-free field-energy entry point (pp_field_energy_noalloc).
 
 Some callers of this library cannot allocate device memory when they need the
-field energies (allocation forbidden after start-up, a graph being captured,
-hosts that only hand over pre-allocated buffers).  This entry point keeps its
-scratch in a fixed array inside the library.  Its results must equal the
-energies pp_diagnostics computes for the same fields, on two calls in a row
-(the second call reuses the array the first one left behind).
+field energies (loops that forbid allocation after start-up, hosts that own
+all device memory and only hand over pre-allocated buffers).  This entry point
+keeps its scratch in a fixed array inside the library.  Its results must equal
+the energies pp_diagnostics computes for the same fields, on two calls in a
+row (the second call reuses the array the first one left behind), and a call
+after the first must leave the device's free memory unchanged.
 
 Kept in a file of its own that pytest collects last.
 """
@@ -56,13 +57,19 @@ def test_noalloc_energies_match_diagnostics_twice(pp):
     stream = torch.cuda.current_stream().cuda_stream
     expect = np.array([d["energy_E"], d["energy_B"], d["energy_Ex"]])
     assert expect.min() > 0.0
+    free = []
     for _ in range(2):
         rc = lib.pp_field_energy_noalloc(pe, pb, L.n[0], L.n[1], L.n[2], dV, out.data_ptr(), stream)
         assert rc == pp.PP_OK, lib.pp_field_energy_noalloc_error()
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         got = out.cpu().numpy()
         assert np.allclose(got, expect, rtol=1e-12, atol=0.0), (got, expect)
         out.fill_(-1.0)
+    torch.cuda.synchronize()
+    free.append(torch.cuda.mem_get_info()[0])
+    # the first call may load the module's code; the second allocates nothing
+    assert free[1] == free[0] and free[2] == free[0], free
     # a different mesh afterwards: the shared scratch carries nothing over
     half = [t[:, :, : L.n[0] // 2].contiguous() for t in Et + Bt]
     pp.field_energy_noalloc(half[:3], half[3:], dV, out)
