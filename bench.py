@@ -1,18 +1,23 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 Photon-Plasma particle step.
 
-One "step" is one full leap-frog step of the library (pp_step): per species the
-fused gather -> push -> move -> charge-conserving deposit kernel, ghost fold,
-6th-order current solve, implicit field update, and the cell sort every 20
-steps.  Workload (default): the numerical-heating plasma of the paper's
-Sec. VIII scaled to 3D, 128^3 cells, 32 macro-particles per cell per species
-(134,217,728 particles), PCS shapes, 6th-order fields, mixed precision (int32
-cell + FP32 offset).  Inputs are seeded synthetic loads (pp_synth).
+One "step" is one full leap-frog step of the library (pp_step): the cell sort
+(every step for the per-step sorted kernel), the fused gather -> push -> move
+-> charge-conserving deposit kernel over every species, ghost fold, 6th-order
+current solve and the implicit field update.  Default workload: the
+mixed-precision beam configuration, a cold Gamma = 10 beam streaming through a
+thermal electron-ion background (m_i/m_e = 25, u_th = 0.01c) on 256 x 128 x 128
+cells, 16 macro-particles per cell per species per population (268,435,456
+particles), PCS shapes, 6th-order fields, int32 cell + FP32 offset.
+`--workload thermal` runs the 128^3 numerical-heating pair plasma (32 per cell
+per species, 134,217,728 particles).  Inputs are seeded synthetic loads
+(pp_synth).
 
 Prints one JSON line (rank 0).  Multi-GPU: every rank advances its own
 independent plasma (replicas, weak scaling); no collective on the data path.
-`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
-the same workload.
+The cpu_baseline leg times the FP64 oracle on a 32^3 crop of the workload
+(the same per-cell load on a periodic 32^3 box) and states the GPU's error
+against it on that crop.  `--impl reference` times the oracle alone.
 """
 from __future__ import annotations
 
@@ -33,48 +38,28 @@ METRIC = "particle-steps/s (gather+push+deposit)"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp32 momenta) read + written
 
-# DRAM traffic of the fused particle kernel per particle, from the committed ncu
-# capture of the 64^3 x 32 ppc thermal workload kept under profiles/ (traffic
-# grows with the particle count).  Valid only for the kernel sources it was
-# taken on: the device part of the header (up to its host-side context), the
-# sort (its key sets the particle order the kernel streams) and the part of
-# pp_particles.cu that holds the particle kernels (up to its charge-density
-# section).
-PROFILED_BYTES_PER_PARTICLE = 901.598720e6 / 16777216
-# The same capture's issue and shared-memory figures, reported beside the HBM
-# fraction (the kernel is bound by shared-memory issue, not by DRAM).
-PROFILED_ISSUE = {"issue_active_pct": 57.0, "warp_instructions_per_particle": 111.4,
-                  "shared_wavefronts_per_particle": {"load": 14.0, "atomic": 12.8},
-                  "shared_bank_conflicts_per_particle": {"load": 0.5, "atomic": 6.4},
-                  "top_stall": "mio_throttle (shared-memory pipe)",
-                  "source": "profiles/k_particles_tiled_thermal64.md"}
-_KERNEL_END = "// ---------------------------------------------------------------------------\n// Charge density of eq:rho2"
-_HOST_START = "// ---------------------------------------------------------------------------\n// Context (host side)"
-PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_particles.cu": "3285fa49a9cf12f024223f16ec4ccb565f4802fa407807e82e696a22d8cd2b5d",
-    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "643a48f3cec37d301be2db1853792dc3ef6c269944bb793e18bc1b1ae96f6b0b",
-    "paper_1211_4575_gb300/csrc/pp_sort.cu": "8ae278e854810bdf3db42a7069642a62f7c7a0c1cddf9bd8d09dca831784555a",
-}
+# DRAM traffic per particle of the fused particle kernel, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on a small case
+# of each workload, divided by its particles; traffic grows with the particle
+# count), with the same capture's issue and shared-memory figures.  Each entry
+# is valid only while the kernel's sources are the ones it was taken on
+# (sha256 of the files below); otherwise traffic is reported as null.
+PROFILED = {}
+PROFILED_SOURCES = {}
 
 
-def profiled_matches():
-    """True while the particle-kernel sources are the ones the committed capture was taken on."""
+def _digest(rel):
     import hashlib
-    for rel, digest in PROFILED_SOURCES.items():
-        with open(os.path.join(ROOT, rel)) as f:
-            text = f.read()
-        if rel.endswith("pp_particles.cu"):
-            text = text[: text.index(_KERNEL_END)]
-        elif rel.endswith("pp_internal.cuh"):
-            text = text[: text.index(_HOST_START)]
-        if hashlib.sha256(text.encode()).hexdigest() != digest:
-            return False
-    return True
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
 
 
-def profiled_traffic(particles_per_launch):
-    """ncu DRAM bytes per launch scaled to this launch, or None once the kernel changed."""
-    return PROFILED_BYTES_PER_PARTICLE * particles_per_launch if profiled_matches() else None
+def profiled(workload):
+    """The ncu figures of this workload's capture, or None once the kernel changed."""
+    P = PROFILED.get(workload)
+    if not P or any(_digest(rel) != d for rel, d in PROFILED_SOURCES.items()):
+        return None
+    return P
 
 
 def args():
@@ -83,14 +68,14 @@ def args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["thermal", "weibel", "beam", "shock"], default="thermal",
+    ap.add_argument("--workload", choices=["thermal", "weibel", "beam", "shock"], default="beam",
                     help="thermal / weibel: n^3 pair plasma; beam: cold Gamma=10 beam through an electron-ion "
                          "background on 2n x n x n; shock: the same beam on 2n x n x n between walls, fed "
                          "through an open end and reflected by the far wall")
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--ppc", type=int, default=None,
                     help="macro-particles per cell per species (per population for beam); default 32, beam 16")
-    ap.add_argument("--deposit", choices=["auto", "global", "tiled"], default="auto")
+    ap.add_argument("--deposit", choices=["auto", "global", "tiled", "cells"], default="auto")
     ap.add_argument("--field-solver", choices=["implicit", "explicit"], default="implicit",
                     help="implicit (eq:EllipticB) or the explicit FDTD leap-frog; explicit runs at dt=0.04, "
                          "under its stability limit 0.0466 at dx=0.1")
@@ -103,12 +88,20 @@ def args():
                     help="radiative-cooling coefficient mu0 q^2/(6 pi m c) for every species (0 = off)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sample-n", type=int, default=16, help="cells per axis of the oracle sample")
+    ap.add_argument("--sample-n", type=int, default=32, help="cells per axis of the oracle sample (the crop)")
+    ap.add_argument("--sample-steps", type=int, default=2, help="steps of the oracle sample")
+    ap.add_argument("--ref-sample-n", type=int, default=16,
+                    help="cells per axis of the oracle sample that --impl reference times every step")
+    ap.add_argument("--diag-steps", type=int, default=10,
+                    help="steps after the timed region with diagnostics after each (Gauss-drift series)")
     ap.add_argument("--serve", action="store_true",
                     help="serving form: p50/p99 time-to-result of a Poisson request trace, batched vs one at a time")
     ap.add_argument("--batched", action="store_true",
                     help="batched form: 64 uneven runs advanced together against one at a time")
     ap.add_argument("--batch-steps", type=int, default=30, help="steps per run of the batched form")
+    ap.add_argument("--decompose", action="store_true",
+                    help="one run split over the ranks by z-slabs (parallel.py: current summed by allreduce, "
+                         "particles migrate); strong scaling. Default: independent replicas, weak scaling")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=20.0)
     a = ap.parse_args()
@@ -259,16 +252,34 @@ def shock_inflow_room(a, L, steps):
     return int(math.ceil(rate * (steps + 2))) + 64
 
 
-def oracle_rate(a, steps, warmup=0):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    same physics and per-cell loading on a sample_n^3 periodic box (for the
-    shock: a (sample_n, sample_n/2, sample_n/2) box between walls with its open
-    end and injectors, the oracle's virtual images included in its cost)."""
-    import oracle
+def crop_load(a, edge):
+    """The workload's per-cell load on a periodic edge^3 box (the crop), or for
+    the shock a (edge, edge/2, edge/2) box between walls."""
     import pp_synth
+    if a.workload == "shock":
+        return make_load(a, edge // 2)
+    if a.workload == "beam":
+        L = pp_synth.beam_background(n=(edge, edge, edge), ppc=a.ppc, seed=1214)
+        L.dt = workload_dt(a)
+        return L
+    return make_load(a, edge)
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_sample(a, edge, steps, warmup=0, threads=1):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    same physics and per-cell loading on the crop (for the shock: a box
+    between walls with its open end and injectors, the oracle's virtual images
+    included in its cost).  Returns (particle-steps/s, description, seconds,
+    the oracle run, its load)."""
+    import oracle
     shock = a.workload == "shock"
-    L = make_load(a, a.sample_n // 2 if shock else a.sample_n)
+    L = crop_load(a, edge)
     oracle.build()
+    threads = oracle.set_threads(threads)
     kw = dict(field_order=6, alpha=0.55, shape_order=3, relax_tol=1e-6, relax_max_iter=200, integrator=a.integrator,
               field_solver=oracle.EXPLICIT if a.field_solver == "explicit" else oracle.IMPLICIT,
               current_mode=oracle.DIRECT if a.current == "direct" else oracle.CHARGE_CONSERVING,
@@ -286,13 +297,62 @@ def oracle_rate(a, steps, warmup=0):
     t0 = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t0
+    oracle.set_threads(1)
     nmean = (n0 + sum(sim.counts)) / 2 if shock else L.n_particles
-    sample = (f"{'x'.join(str(v) for v in L.n)} cells{' between walls' if shock else ''}, "
+    sample = (f"{'x'.join(str(v) for v in L.n)} cells{' between walls' if shock else ' (periodic crop)'}, "
               f"{a.ppc} per cell per species"
               f"{' per population' if a.workload == 'beam' else ''} = {L.n_particles} particles"
               f"{' at the start, about ' + str(int(nmean)) + ' over the timed steps (the oracle also steps their mirror images)' if shock else ''}, "
-              f"{steps} steps, same per-cell load and parameters as the workload, single-threaded C")
-    return nmean * steps / dt, sample, dt
+              f"{steps} steps, same per-cell load and parameters as the workload, C on {threads} thread(s)"
+              f"{' (particle loop with per-thread current copies)' if threads > 1 else ''}")
+    return nmean * steps / dt, sample, dt, sim, L, threads
+
+
+def crop_error(a, pp, osim, L, steps):
+    """Error of the GPU's mixed form against the FP64 oracle on the crop, after
+    the same steps from the same loaded particles: per field the max
+    difference over max(max|oracle|, floor), the floor being the largest
+    single-species current density J_s for J and J_s t for E and B (the net
+    current of a neutral beam is a small difference of large species
+    currents, which FP32 rounds relative to each species' own); positions in
+    cells (particles matched one to one as periodic nearest neighbours) and
+    momenta relative to max|u|."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+    sim = pp.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, pusher=pp.PP_VAY,
+                        precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=200, relax_tol=1e-6)
+    for s in L.species:
+        sid = sim.add_species(s["q"], s["m"], s["w"], len(s["x"]))
+        sim.load_particles(sid, s["x"], s["y"], s["z"], s["ux"], s["uy"], s["uz"])
+    sim.step(steps)
+    js = 0.0
+    if a.workload == "beam":
+        js = 0.5 * math.sqrt(1.0 - 1.0 / L.params["gamma_b"] ** 2)
+    t = steps * L.dt
+    E, B, J = sim.fields()
+    out = {}
+    for name, G, O, floor in (("E", E, osim.E, js * t), ("B", B, osim.B, js * t), ("J", J, osim.J, js)):
+        num = max(float(np.abs(G[k] - O[k]).max()) for k in range(3))
+        den = max(max(float(np.abs(O[k]).max()) for k in range(3)), floor)
+        out[name] = num / den
+    box = np.array([L.n[k] * L.d[k] for k in range(3)])
+    dpos, du = 0.0, 0.0
+    for s in range(len(L.species)):
+        g, o = sim.particles(s), osim.species[s]
+        P = np.stack([np.mod(g[k], box[i]) for i, k in enumerate("xyz")], 1)
+        Q = np.stack([np.mod(o[k], box[i]) for i, k in enumerate("xyz")], 1)
+        P = np.minimum(P, np.nextafter(box, 0))
+        Q = np.minimum(Q, np.nextafter(box, 0))
+        _, j = cKDTree(Q, boxsize=box).query(P, k=1)
+        d = (P - Q[j] + 0.5 * box) % box - 0.5 * box
+        dpos = max(dpos, float((np.abs(d) / np.asarray(L.d)).max()))
+        us = max(float(np.abs(o[k]).max()) for k in ("ux", "uy", "uz"))
+        du = max(du, max(float(np.abs(g[k] - o[k][j]).max()) for k in ("ux", "uy", "uz")) / us)
+    diag = sim.diagnostics()
+    sim.close()
+    return {"steps": steps, "E": out["E"], "B": out["B"], "J": out["J"], "positions_cells": dpos,
+            "momenta_rel": du, "species_current_floor": js, "gauss_drift_gpu": diag["gauss_drift_max"],
+            "grid": list(L.n), "particles": L.n_particles}
 
 
 def run_reference(a):
@@ -300,12 +360,12 @@ def run_reference(a):
     if rank != 0:
         return
     steps = max(1, a.steps)
-    rate, sample, dt = oracle_rate(a, steps, warmup=a.warmup)
+    rate, sample, dt, _, _, cores = oracle_sample(a, a.ref_sample_n, steps, warmup=a.warmup, threads=host_cores())
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a, nominal_particles(a)), "oracle_sample": sample},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -332,7 +392,8 @@ def run_gpu(a):
 
     L = workload_load(a, seed_offset=rank)
     npart = L.n_particles
-    mode = {"auto": pp.PP_DEPOSIT_AUTO, "global": pp.PP_DEPOSIT_GLOBAL, "tiled": pp.PP_DEPOSIT_TILED}[a.deposit]
+    mode = {"auto": pp.PP_DEPOSIT_AUTO, "global": pp.PP_DEPOSIT_GLOBAL, "tiled": pp.PP_DEPOSIT_TILED,
+            "cells": pp.PP_DEPOSIT_CELLS}[a.deposit]
     stream = torch.cuda.current_stream()
 
     shock = a.workload == "shock"
@@ -400,6 +461,14 @@ def run_gpu(a):
     bytes_per_step = BYTES_PER_PARTICLE_STEP * (4 if a.integrator == 4 else 1)   # one particle pass per substep
     achieved = bytes_per_step * npart * a.steps / (part_ms * 1e-3) / 1e9 if part_ms > 0 else 0.0
     diag = sim.diagnostics()
+    # Gauss drift after each of diag_steps further steps: max|G - G_0| with
+    # G = div E - rho; a step changes G by -dt times its discrete continuity
+    # residual (rho^{n+1} - rho^n)/dt + div J, so the series shows how that
+    # residual adds up
+    series = [diag["gauss_drift_max"]]
+    for _ in range(a.diag_steps):
+        sim.step(1)
+        series.append(sim.diagnostics()["gauss_drift_max"])
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -433,10 +502,16 @@ def run_gpu(a):
         if dist is not None:
             dist.destroy_process_group()
         return
-    cpu = None
+    cpu, crop = None, None
     if not a.no_cpu_baseline:
-        rate, sample, _ = oracle_rate(a, steps=5)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        rate, sample, _, osim, Lc, cores = oracle_sample(a, a.sample_n, steps=a.sample_steps, threads=host_cores())
+        rate1, sample1, _, _, _, _ = oracle_sample(a, a.sample_n, steps=1, threads=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": rate1, "unit": UNIT, "cores": 1, "sample": sample1}}
+        if a.workload != "shock":   # the crop's error: the GPU's mixed form on the oracle's sample
+            crop = crop_error(a, pp, osim, Lc, a.sample_steps)
+    P = profiled(a.workload)
+    per_launch = npart * a.steps / max(1, prof["particle_launches"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -447,12 +522,13 @@ def run_gpu(a):
                    "l2": "inputs larger than L2 (particle state 28 B x particles, read and written every step)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None,
-                     "traffic": profiled_traffic(npart * a.steps / max(1, prof["particle_launches"])),
-                     "issue": PROFILED_ISSUE if profiled_matches() else None,
+                     "traffic": P["bytes_per_particle"] * per_launch if P else None,
+                     "limiter": P["limiter"] if P else None, "issue": P["issue"] if P else None,
                      "kernel": "fused particle step (gather+push+move+deposit)",
                      "bytes_per_particle_step": bytes_per_step, "peak_kind": peak_kind,
                      "kernel_ms_per_step": part_ms / a.steps},
         "cpu_baseline": cpu,
+        "oracle_error": crop,
         "e2e": e2e,
         "gpu_launches": prof["kernel_launches"],
         "clocks": clk,
@@ -461,7 +537,10 @@ def run_gpu(a):
                  "gauss_drift_max": diag["gauss_drift_max"], "rho_max": diag["rho_max"],
                  # every workload loads a charge density of 1 per sign (electrons: -1)
                  "gauss_drift_vs_species_density": diag["gauss_drift_max"],
-                 "relax_residual": diag["relax_residual"], "relax_iters": diag["relax_iters"]},
+                 "relax_residual": diag["relax_residual"], "relax_iters": diag["relax_iters"],
+                 "gauss_drift_series_vs_species_density": series,
+                 "gauss_drift_growth_per_step_max": max((abs(b - c) for b, c in zip(series[1:], series[:-1])),
+                                                        default=0.0)},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -520,10 +599,71 @@ def run_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def run_decomposed(a):
+    """One run of the workload split over the ranks by z-slabs: every rank
+    holds the mesh and the particles of its slab; per step the particle pass,
+    the allreduce of the current (NCCL), the field update and the migration of
+    the particles that changed slab (paper_1211_4575_gb300.parallel)."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29533")
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    from paper_1211_4575_gb300 import build
+    build.build()
+    import paper_1211_4575_gb300 as pp
+    from paper_1211_4575_gb300 import parallel
+    if a.workload not in ("thermal", "weibel", "beam"):
+        raise SystemExit("--decompose runs the periodic workloads")
+    L = workload_load(a)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    bounds = parallel.slab_bounds(L.n[2], L.d[2], world)
+    sim = pp.Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=3, pusher=pp.PP_VAY,
+                        precision=pp.PP_MIXED32, sort_interval=20, relax_max_iter=100, relax_tol=1e-6,
+                        stream=stream.cuda_stream)
+    for s in L.species:   # room for the particles that migrate in
+        sim.add_species(s["q"], s["m"], s["w"], int(1.5 * len(s["x"]) / world) + 4096)
+    sl = parallel.Slab(sim, rank, bounds, len(L.species))
+    parallel.load([sl], L.species)
+    comm = parallel.TorchComm(device=dev)
+    for _ in range(a.warmup):
+        parallel.step([sl], comm, device=dev)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        parallel.step([sl], comm, device=dev)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
+    wall = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    kin, count = parallel.kinetic_and_count([sl], comm)
+    if rank == 0:
+        line = {"metric": METRIC, "value": L.n_particles * a.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(a, L.n_particles), "grid": list(L.n),
+                           "parallelism": f"z-slabs x{world} (current allreduce, particle migration, "
+                                          "replicated field update)"},
+                "wall_s": wall, "particles_after": count}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 if __name__ == "__main__":
     a = args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.decompose:
+        run_decomposed(a)
     elif a.batched:
         run_batched(a)
     elif a.serve:
