@@ -499,6 +499,13 @@ typedef struct pp_batch pp_batch;
 /* Device bytes a context holds (mesh, scratch and particle storage). */
 int64_t pp_device_bytes(pp_ctx *ctx);
 
+/* The device bytes of a context that pp_init_grid(desc) and nspecies
+ * pp_init_species calls with the given capacities would create, before any
+ * of it exists (pp_device_bytes of that context returns the same figure): a
+ * server checks a run against its memory budget before building it.  0 for an
+ * invalid argument. */
+int64_t pp_estimate_device_bytes(const pp_grid_desc *desc, int nspecies, const int64_t *capacities);
+
 /* New batch admitting contexts while their device bytes sum to at most
  * budget_bytes, in at most max_slots (1..4096) slots.  PP_EINVAL, PP_ENOMEM. */
 int pp_batch_create(pp_batch **out, int64_t budget_bytes, int max_slots);

@@ -115,6 +115,7 @@ SIGNATURES = {
     "pp_field_energy_noalloc": (C.c_int, [_PP, _PP, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
     "pp_field_energy_noalloc_error": (C.c_char_p, []),
     "pp_device_bytes": (C.c_int64, [_P]),
+    "pp_estimate_device_bytes": (C.c_int64, [C.POINTER(GridDesc), C.c_int, C.POINTER(C.c_int64)]),
     "pp_batch_create": (C.c_int, [_PP, C.c_int64, C.c_int]),
     "pp_batch_admit": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int)]),
     "pp_batch_advance": (C.c_int, [_P, C.c_int]),
@@ -187,6 +188,15 @@ def field_energy_noalloc(E, B, dV, out, stream=None):
                                        stream if stream is not None else _current_stream())
     if rc != PP_OK:
         raise PPError(rc, lib().pp_field_energy_noalloc_error().decode(errors="replace"))
+
+
+def estimate_device_bytes(n, capacities, precision=PP_MIXED32, boundary=(PP_BOUNDARY_PERIODIC,) * 3) -> int:
+    """Device bytes a Simulation of this mesh with species of these capacities
+    will hold once built (pp_estimate_device_bytes), before building it."""
+    g = GridDesc(nx=n[0], ny=n[1], nz=n[2], precision=precision, boundary_x=boundary[0], boundary_y=boundary[1],
+                 boundary_z=boundary[2])
+    caps = (C.c_int64 * max(1, len(capacities)))(*[int(c) for c in capacities])
+    return int(lib().pp_estimate_device_bytes(C.byref(g), len(capacities), caps))
 
 
 class Simulation:

@@ -17,6 +17,7 @@
 #include <new>
 
 #include "pp_ctx.cuh"
+#include "pp_internal.cuh"
 
 using namespace pp;
 
@@ -50,17 +51,50 @@ static void release(pp_batch *b, pp_batch::Slot &S) {
     b->used -= S.bytes;
 }
 
+// Device bytes of a context on a mesh of n cells (the mirror-extended mesh
+// between walls) with the given rounded species capacities: 21 padded mesh
+// arrays, the compact rho and Gauss reference, and per species two particle
+// buffers, the sort keys (and, in the mixed form, the permutation) and the
+// per-key offsets, plus the sort's counters.
+static int64_t context_bytes(const int n[3], bool fp64, int ns, const int64_t *cap) {
+    int64_t padded = 1, cells = 1, nkeys = kSubKeys;
+    for (int a = 0; a < 3; ++a) {
+        padded *= n[a] + 2 * kGhost;
+        cells *= n[a];
+        const int t = n[a] < 8 ? n[a] : 8;
+        nkeys *= (int64_t)((n[a] + t - 1) / t) * t;
+    }
+    int64_t bytes = padded * (fp64 ? 8 : 4) * 21 + 2 * 8 * cells;
+    for (int s = 0; s < ns; ++s) {
+        const int64_t per = fp64 ? 48 : 28;
+        bytes += 2 * per * cap[s] + (fp64 ? 4 : 8) * cap[s] + 4 * (nkeys + 1);
+    }
+    return bytes + 4 * (nkeys + 1);
+}
+
 // Device bytes held by a context (mesh, diagnostics and particle storage).
 extern "C" int64_t pp_device_bytes(pp_ctx *p) {
     if (!p) return 0;
     Ctx *c = p;
-    int64_t bytes = (int64_t)c->g.padded_size() * (int64_t)c->rsz * 21 + 2 * 8 * c->g.cells();
-    for (int s = 0; s < c->nspecies; ++s) {
-        int64_t per = c->fp64 ? 48 : 28;
-        bytes += 2 * per * c->sp[s].cap + (c->fp64 ? 4 : 8) * c->sp[s].cap + 4 * (c->nkeys + 1);
+    int64_t cap[PP_MAX_SPECIES];
+    for (int s = 0; s < c->nspecies; ++s) cap[s] = c->sp[s].cap;
+    return context_bytes(c->g.n, c->fp64, c->nspecies, cap);
+}
+
+extern "C" int64_t pp_estimate_device_bytes(const pp_grid_desc *d, int nspecies, const int64_t *capacities) {
+    if (!d || nspecies < 0 || nspecies > PP_MAX_SPECIES || (nspecies > 0 && !capacities)) return 0;
+    const int bnd[3] = {d->boundary_x, d->boundary_y, d->boundary_z}, nphys[3] = {d->nx, d->ny, d->nz};
+    int n[3];
+    for (int a = 0; a < 3; ++a) {
+        if (nphys[a] < 1) return 0;
+        n[a] = bnd[a] == PP_BOUNDARY_WALLS ? 2 * nphys[a] : nphys[a];
     }
-    bytes += 4 * (c->nkeys + 1);
-    return bytes;
+    int64_t cap[PP_MAX_SPECIES];
+    for (int s = 0; s < nspecies; ++s) {
+        if (capacities[s] < 0) return 0;
+        cap[s] = capacities[s] == 0 ? 64 : (capacities[s] + 63) / 64 * 64;   // as pp_init_species rounds
+    }
+    return context_bytes(n, d->precision == PP_FP64, nspecies, cap);
 }
 
 extern "C" int pp_batch_create(pp_batch **out, int64_t budget_bytes, int max_slots) {

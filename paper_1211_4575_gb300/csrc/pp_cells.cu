@@ -654,15 +654,19 @@ __global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constan
 #pragma unroll 1
             for (int it = threadIdx.x; it < nitems; it += kCT) {
                 const int blk = it / 96, rr = it - blk * 96, comp = rr >> 5, j = rr & 31;
+                // lane j of item block b takes piece (queue entry) j * blocks + b:
+                // consecutive pieces and queue entries often share a cell, and the
+                // cold beams' queued particles of one cell share their sites, so
+                // lanes on consecutive entries would add to the same words
                 if (blk < nblk) {
-                    const int p = blk * 32 + j;
+                    const int p = j * nblk + blk;
                     if (p >= np) continue;
                     const int ps = s_piece[p], pe = s_piece[p + 1];
                     if (comp == 0) piece_current<O, 0>(Jw, s_o, s_d, s_grp, ps, pe, jsc[0] PP_IF_CHECKED(, T.status));
                     else if (comp == 1) piece_current<O, 1>(Jw, s_o, s_d, s_grp, ps, pe, jsc[1] PP_IF_CHECKED(, T.status));
                     else piece_current<O, 2>(Jw, s_o, s_d, s_grp, ps, pe, jsc[2] PP_IF_CHECKED(, T.status));
                 } else {
-                    const int k = (blk - nblk) * 32 + j;
+                    const int k = j * nqb + (blk - nblk);
                     if (k >= nq) continue;
                     const int q = s_queue[k];
                     if (comp == 0) queued_current<O, 0>(Jw, s_o, s_d, s_grp, q, jsc[0] PP_IF_CHECKED(, T.status));

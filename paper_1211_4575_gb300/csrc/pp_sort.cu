@@ -181,17 +181,67 @@ __global__ void k_scatter_mixed(int64_t n, const int32_t *keys, int32_t *cursor,
 
 // Sort from keys a particle pass already wrote (Species::keys_valid): the
 // histogram of the keys, then, through the per-key cursors, the permutation
-// perm[slot] = particle instead of moving the particles.
-__global__ void k_hist(int64_t n, const int32_t *keys, int32_t *counts) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    aggregated_add(counts, keys[t]);
+// perm[slot] = particle instead of moving the particles.  The keys of a block
+// of consecutive particles (in the last sort's order) lie in a short range, so
+// each block counts its keys in shared memory and reserves one run of slots
+// per distinct key with a single global atomic; keys outside the block's
+// window (a particle that left, a far jump) take a global atomic of their own.
+constexpr int kAggThreads = 1024;
+constexpr int kAggWindow = 4096;   // keys counted in shared memory per block
+
+__device__ __forceinline__ int32_t block_min_key(int32_t k, int32_t *sh) {
+    // smallest live key of the block (keys >= sentinel are ignored)
+    int32_t v = k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int32_t w = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0x7fffffff;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = min(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (threadIdx.x == 0) sh[32] = w;
+    }
+    __syncthreads();
+    return sh[32];
 }
 
-__global__ void k_perm(int64_t n, const int32_t *keys, int32_t *cursor, int32_t *perm) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    perm[aggregated_add(cursor, keys[t])] = (int32_t)t;
+__global__ void __launch_bounds__(kAggThreads) k_hist(int64_t n, const int32_t *keys, int32_t *counts) {
+    __shared__ int32_t cnt[kAggWindow];
+    __shared__ int32_t red[33];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t key = t < n ? keys[t] : 0x7fffffff;
+    const int32_t k0 = block_min_key(key, red);
+    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    if (t < n) {
+        const int32_t r = key - k0;
+        if (r < kAggWindow) atomicAdd(cnt + r, 1);
+        else atomicAdd(counts + key, 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x)
+        if (cnt[i]) atomicAdd(counts + k0 + i, cnt[i]);
+}
+
+__global__ void __launch_bounds__(kAggThreads) k_perm(int64_t n, const int32_t *keys, int32_t *cursor, int32_t *perm) {
+    __shared__ int32_t cnt[kAggWindow];   // block-local rank counters, then the reserved bases
+    __shared__ int32_t red[33];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t key = t < n ? keys[t] : 0x7fffffff;
+    const int32_t k0 = block_min_key(key, red);
+    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int32_t r = key - k0;
+    const bool local = t < n && r < kAggWindow;
+    int32_t rank = 0;
+    if (local) rank = atomicAdd(cnt + r, 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x)
+        if (cnt[i]) cnt[i] = atomicAdd(cursor + k0 + i, cnt[i]);
+    __syncthreads();
+    if (local) perm[cnt[r] + rank] = (int32_t)t;
+    else if (t < n) perm[atomicAdd(cursor + key, 1)] = (int32_t)t;
 }
 
 // dst[i] = src[perm[i]] for the seven arrays of the mixed form.
@@ -277,7 +327,8 @@ cudaError_t launch_sort(Ctx &c, int s) {
     }
     KeyGeom kg = key_geom(c);
     unsigned blocks = (unsigned)((S.n + 255) / 256);
-    if (lazy) k_hist<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts);
+    const unsigned ablocks = (unsigned)((S.n + kAggThreads - 1) / kAggThreads);
+    if (lazy) k_hist<<<ablocks, kAggThreads, 0, c.st>>>(S.n, S.keys, c.counts);
     else if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
     else k_keys_mixed<<<blocks, 256, 0, c.st>>>(kg, S.n, S.cell, S.ox, S.oy, S.oz, S.keys, c.counts);
     ++c.nlaunch;
@@ -287,7 +338,7 @@ cudaError_t launch_sort(Ctx &c, int s) {
     e = cudaMemcpyAsync(c.counts, S.cell_start, sizeof(int32_t) * (c.nkeys + 1), cudaMemcpyDeviceToDevice, c.st);
     if (e != cudaSuccess) return e;
     if (lazy) {
-        k_perm<<<blocks, 256, 0, c.st>>>(S.n, S.keys, c.counts, S.perm);
+        k_perm<<<ablocks, kAggThreads, 0, c.st>>>(S.n, S.keys, c.counts, S.perm);
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         S.perm_pending = true;

@@ -12,7 +12,7 @@ import time
 
 import numpy as np
 
-from . import PP_BATCH_DONE, PP_BATCH_FAILED, PP_MIXED32, Batch, PPError, Simulation
+from . import PP_BATCH_DONE, PP_BATCH_FAILED, PP_MIXED32, Batch, PPError, Simulation, estimate_device_bytes
 
 
 def _build(req, precision, stream):
@@ -47,10 +47,17 @@ def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, k
         now = time.perf_counter() - t0
         while pending and pending[0].get("arrival", 0.0) <= now:
             req = pending[0]
+            # admit by the run's device bytes, known before anything is built:
+            # a run that does not fit waits, unbuilt, until a slot's memory returns
+            import pp_synth
+            need = estimate_device_bytes((req["n"],) * 3, pp_synth.run_counts(req), precision)
+            used, nact = batch.used()
+            if used + need > budget_bytes or nact >= max_slots:
+                break
             stream = torch.cuda.Stream()
             sim, npart = _build(req, precision, stream.cuda_stream)
             slot = batch.admit(sim, req["steps"])
-            if slot is None:          # full: retry once capacity frees up
+            if slot is None:          # cannot happen after the check above; keep the request
                 sim.close()
                 break
             pending.pop(0)

@@ -251,6 +251,52 @@ def quiet_two_stream(nx=32, ntr=2, dx=0.25, dt=0.125, ppc=8, beta=0.2, mode=2, e
     return L
 
 
+def quiet_weibel(ny=32, ntr=8, dx=0.25, dt=0.1, ppc=4, beta=0.5, mode=2, eps=1e-6) -> Load:
+    """Noise-free (quiet-start) cold filamentation (Weibel) load: four co-located
+    populations (electrons and positrons of a +beta and a -beta beam along x,
+    density 1/2 each) on a regular lattice, ppc per cell along y and one per
+    cell in x and z, on ntr x ny x ntr cells, with a seeded velocity
+    perturbation eps*sin(k y) on the +beta electrons (a current modulation
+    across the beams), k = 2*pi*mode/(ny*dx).  Uniform along the beams and
+    along z, the problem is one-dimensional in y; the charge density starts
+    exactly at zero."""
+    Ly = ny * dx
+    G = 1.0 / math.sqrt(1.0 - beta * beta)
+    j = np.arange(ny).repeat(ppc)
+    s = np.tile(np.arange(ppc), ny)
+    y1 = (j + (s + 0.5) / ppc) * dx
+    xs, ys, zs = [], [], []
+    for k in range(ntr):
+        for i in range(ntr):
+            ys.append(y1)
+            xs.append(np.full(y1.size, (i + 0.5) * dx))
+            zs.append(np.full(y1.size, (k + 0.5) * dx))
+    x = np.concatenate(xs); y = np.concatenate(ys); z = np.concatenate(zs)
+    ky = 2.0 * np.pi * mode / Ly
+    pert = eps * np.sin(ky * y)
+    zero = np.zeros_like(x)
+    w = 0.5 / ppc
+    species = []
+    for q in (-1.0, 1.0):
+        for sgn in (+1.0, -1.0):
+            ux = sgn * G * beta + (pert if (q < 0 and sgn > 0) else 0.0)
+            species.append(dict(q=q, m=1.0, w=w, x=x.copy(), y=y.copy(), z=z.copy(),
+                                ux=np.asarray(ux, dtype=np.float64) + zero, uy=zero.copy(), uz=zero.copy()))
+    L = Load(n=(ntr, ny, ntr), d=(dx, dx, dx), dt=dt, species=species)
+    L.params = dict(workload="quiet-weibel", beta=beta, mode=mode, k=ky)
+    return L
+
+
+def heating_plasma(n=(32, 32, 32), ppc=8, u_th=0.1, mass_ratio=16.0, dx=0.1, dt=0.05, seed=1219) -> Load:
+    """The numerical-heating set-up (Sec. VIII) in 3D: electrons and ions of
+    mass ratio 16 at rest, both with thermal proper velocity u_th per component,
+    ten cells per skin depth, ppc per cell per species (pair-co-located)."""
+    pops = [Population(ppc, 1.0, 0.0, u_th)]
+    L = pair_plasma(n, (dx, dx, dx), dt, pops, seed, masses=(1.0, mass_ratio))
+    L.params = dict(workload="heating", ppc=ppc, u_th=u_th, mass_ratio=mass_ratio)
+    return L
+
+
 # --------------------------------------------------------------------------
 # Independent-run workloads of the batched and served forms.
 # --------------------------------------------------------------------------
@@ -268,6 +314,12 @@ def run_load(req) -> Load:
     L = pair_plasma(n, (dx, dx, dx), 0.5 * dx, pops, req["seed"], masses=masses)
     L.params = dict(workload=req["kind"], shape_order=req.get("shape", 3), field_order=6, alpha=0.55)
     return L
+
+
+def run_counts(req) -> list:
+    """Particles per species of the load run_load(req) builds (without building it)."""
+    ppc = max(2, int(req["ppc"]) // 2 * 2)
+    return [int(req["n"]) ** 3 * ppc] * 2
 
 
 def batched_runs(n_runs=64, seed=1215, edges=tuple(range(16, 97, 8)), ppc=(8, 64), steps=300):

@@ -65,6 +65,9 @@ def test_admission_by_budget_and_slots(pp):
     a, b, c = make(), make(), make()
     need = a.device_bytes()
     assert need > 0
+    # the estimate a server takes before building equals what the built run holds
+    assert pp.estimate_device_bytes(L.n, [len(s["x"]) for s in L.species], pp.PP_MIXED32) == need
+    assert pp.estimate_device_bytes(L.n, pp_synth.run_counts(_requests()[0]), pp.PP_MIXED32) == need
     batch = pp.Batch(int(2.5 * need), max_slots=8)
     sa = batch.admit(a, 3)
     sb = batch.admit(b, 1)

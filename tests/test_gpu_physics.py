@@ -6,6 +6,10 @@
   the cold closed form.
 * The noisy 16^3 two-stream load: the E_x energy series of the FP64 GPU path
   follows the oracle's step by step.
+* Filamentation (Weibel, the config-2 variant's instability): the magnetic
+  energy growth rate of the GPU path on a quiet start is within 2% of the
+  oracle's, in FP64 and in the mixed form (the oracle is pinned to the
+  cold-fluid dispersion relation).
 * A relativistic beam (Gamma = 10) through an electron-ion background
   (m_i/m_e = 25): the mixed form against the oracle on a small periodic box
   with the beam-background per-cell load.
@@ -53,6 +57,37 @@ def test_two_stream_growth_rate_gpu_within_2pct_of_oracle(pp, orc, precision, ep
     assert ng >= 30 and no >= 30
     assert rg == pytest.approx(ro, rel=0.02)
     assert rg == pytest.approx(theory.cold_two_stream(L.params["k"], 0.2), rel=0.03)
+
+
+_WEIBEL_ORACLE = {}
+
+
+def _weibel_oracle_rate(orc, L, nst):
+    if "rate" not in _WEIBEL_ORACLE:
+        osim = H.oracle_sim(orc, L, 2, relax_tol=1e-13)
+        Wo = _series(osim, nst, lambda s: s.diagnostics()["energy_B"])
+        _WEIBEL_ORACLE["rate"] = theory.fit_growth(np.arange(1, nst + 1) * L.dt, Wo)
+    return _WEIBEL_ORACLE["rate"]
+
+
+@pytest.mark.parametrize("precision,eps", [(0, 1e-6), (1, 1e-4)])
+def test_weibel_growth_rate_gpu_within_2pct_of_oracle(pp, orc, precision, eps):
+    """Quiet cold +-0.5c pair beams with a seeded transverse current mode on
+    8 x 32 x 8 cells (the mixed form runs the per-step sorted kernel): the
+    growth rate of the magnetic energy, GPU against oracle.  The mixed form
+    starts from a larger seed so that its linear phase clears FP32 noise."""
+    L = pp_synth.quiet_weibel(eps=eps)
+    nst = 240
+    gpu = H.gpu_sim(pp, L, precision, 2, relax_tol=1e-12 if precision == 0 else 1e-6)
+    Wg = _series(gpu, nst, lambda s: s.diagnostics()["energy_B"])
+    t = np.arange(1, nst + 1) * L.dt
+    rg, ng = theory.fit_growth(t, Wg)
+    Lo = pp_synth.quiet_weibel(eps=eps)
+    ro, no = _weibel_oracle_rate(orc, Lo, nst) if eps == 1e-6 else theory.fit_growth(
+        t, _series(H.oracle_sim(orc, Lo, 2, relax_tol=1e-13), nst, lambda s: s.diagnostics()["energy_B"]))
+    assert ng >= 20 and no >= 20, (ng, no)
+    assert rg == pytest.approx(ro, rel=0.02), (rg, ro)
+    assert gpu.diagnostics()["status"] == 0
 
 
 def test_noisy_two_stream_energy_series_fp64(pp, orc):
