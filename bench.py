@@ -102,8 +102,9 @@ def args():
     ap.add_argument("--decompose", action="store_true",
                     help="one run split over the ranks by z-slabs (parallel.py: current summed by allreduce, "
                          "particles migrate); strong scaling. Default: independent replicas, weak scaling")
-    ap.add_argument("--requests", type=int, default=48)
-    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--requests", type=int, default=12)
+    ap.add_argument("--rate", type=float, default=0.07, help="mean arrivals per second of the serving trace")
+    ap.add_argument("--serve-scale", choices=["c5", "reduced"], default="c5")
     a = ap.parse_args()
     if a.ppc is None:
         a.ppc = 16 if a.workload == "beam" else 32
@@ -548,26 +549,37 @@ def run_gpu(a):
 
 
 def run_serve(a):
-    """Serving form on a reduced Poisson trace (same distributions as the
-    serving config, edges 16..48 and 20..100 steps so that it ends in minutes):
-    continuous batching through pp_batch_* against the same requests run one
-    at a time."""
-    import torch
+    """Serving form: a Poisson trace of independent two-stream / Weibel runs
+    served by continuous batching through pp_batch_* (admission by device
+    bytes, every run resident, steps overlapping on the GPU), against the same
+    requests run one at a time.  Default trace: the serving configuration's
+    distributions (edges 32..192, 8..32 ppc per species, pair or m_i/m_e = 25,
+    200..1000 steps) at a sub-saturating rate; `--serve-scale reduced` takes
+    edges 16..48 and 20..100 steps instead."""
     import pp_synth
     from paper_1211_4575_gb300 import build
     build.build()
     from paper_1211_4575_gb300 import serving
-    trace = pp_synth.serving_trace(n_requests=a.requests, rate=a.rate, edges=(16, 24, 32, 40, 48), steps=(20, 100))
-    warm = [dict(r, arrival=0.0, steps=2) for r in trace[:2]]
+    if a.serve_scale == "c5":
+        edges, steps, desc = tuple(range(32, 193, 16)), (200, 1000), "edges 32..192, 200..1000 steps"
+        budget, slots = 200 << 30, 8
+    else:
+        edges, steps, desc = (16, 24, 32, 40, 48), (20, 100), "edges 16..48, 20..100 steps"
+        budget, slots = 64 << 30, 32
+    trace = pp_synth.serving_trace(n_requests=a.requests, rate=a.rate, edges=edges, steps=steps)
+    warm = [dict(r, arrival=0.0, steps=2, n=32) for r in trace[:2]]
     serving.sequential(warm)
     seq, _ = serving.sequential(trace)
-    bat, _ = serving.serve(trace, budget_bytes=64 << 30, max_slots=32, chunk=4)
+    bat, _ = serving.serve(trace, budget_bytes=budget, max_slots=slots, chunk=4)
+    work = sum(r["n"] ** 3 * max(2, r["ppc"] // 2 * 2) * 2 * r["steps"] for r in trace)
     line = {"metric": "serving p50/p99 time-to-result", "value": bat["p99_s"], "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"{a.requests} Poisson arrivals at {a.rate}/s of two-stream/Weibel runs, "
-                                   "edges 16..48, 8..32 ppc per species, pair or m_i/m_e=25, 20..100 steps, "
-                                   "mixed precision, PCS; budget 64 GiB, 32 slots"},
-               "batched": bat, "sequential": seq}
+                                   f"{desc}, 8..32 ppc per species, pair or m_i/m_e=25, mixed precision, PCS; "
+                                   f"budget {budget >> 30} GiB, {slots} slots; loads built by 4 host worker threads "
+                                   "in both forms; time to result from arrival to the end of the last step",
+                       "offered_particle_steps": work},
+            "batched": bat, "sequential": seq}
     print(json.dumps(line), flush=True)
 
 
@@ -588,14 +600,16 @@ def run_batched(a):
     seq = serving.one_at_a_time(built)
     eager = serving.batched(built, budget_bytes=160 << 30, max_slots=64, chunk=4, graphs=False)
     bat = serving.batched(built, budget_bytes=160 << 30, max_slots=64, chunk=4, graphs=True)
+    fused = serving.batched(built, budget_bytes=160 << 30, max_slots=64, chunk=4, graphs=False, fused=True)
     for _, sim, _, _ in built:
         sim.close()
-    line = {"metric": "particle-steps/s (gather+push+deposit)", "value": bat["particle_steps_per_s"],
+    best = max((fused, bat, eager), key=lambda r: r["particle_steps_per_s"])
+    line = {"metric": "particle-steps/s (gather+push+deposit)", "value": best["particle_steps_per_s"],
             "unit": "particle-steps/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"64 independent two-stream pair runs, edges 16..96, 8..64 ppc per species, "
                                    f"drift 0.05..0.5c, u_th 0.01..0.1c, TSC or PCS, {a.batch_steps} steps each, "
                                    "mixed precision, loads resident before timing; 64 slots, one stream each"},
-            "batched_graphs": bat, "batched_eager": eager, "one_at_a_time": seq}
+            "batched_fused": fused, "batched_graphs": bat, "batched_eager": eager, "one_at_a_time": seq}
     print(json.dumps(line), flush=True)
 
 

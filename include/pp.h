@@ -522,6 +522,18 @@ int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot);
  * turn, then record each slot's completion event.  Does not synchronise. */
 int pp_batch_advance(pp_batch *b, int max_steps);
 
+/* Fused rounds (enable = 1): each round of pp_batch_advance then takes one
+ * step of every running slot with the particle kernels of all of them in one
+ * persistent launch per group of runs that share shape order, pusher and
+ * boundary kind: persistent CTAs, one per SM, take the (run, tile) work items
+ * of the group from a device counter, largest runs first; each slot's sort
+ * before it and its current solve and field update after it run on the slot's
+ * own stream.  Applies while every running slot steps through the per-step
+ * sorted kernel as a leap-frog step with no open end, injector, window or
+ * profiling; otherwise rounds take the per-slot path.  Results equal those of
+ * the per-slot path.  Creates the batch's own stream. */
+int pp_batch_set_fused(pp_batch *b, int enable);
+
 /* Non-blocking state of a slot (PP_BATCH_*), and the steps enqueued so far.
  * A slot reported DONE or FAILED is released (its bytes return to the
  * budget); its return value is then the failing step's code.  A FAILED slot

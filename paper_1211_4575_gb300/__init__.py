@@ -119,6 +119,7 @@ SIGNATURES = {
     "pp_batch_create": (C.c_int, [_PP, C.c_int64, C.c_int]),
     "pp_batch_admit": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int)]),
     "pp_batch_advance": (C.c_int, [_P, C.c_int]),
+    "pp_batch_set_fused": (C.c_int, [_P, C.c_int]),
     "pp_batch_poll": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "pp_batch_used": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "pp_batch_last_error": (C.c_char_p, [_P]),
@@ -470,6 +471,13 @@ class Batch:
         if rc != PP_OK:
             raise PPError(rc, lib().pp_batch_last_error(self._b).decode(errors="replace"))
         return slot.value
+
+    def set_fused(self, enable: bool = True):
+        """Fused rounds: the particle kernels of all running slots as one
+        persistent launch per group of compatible runs."""
+        rc = lib().pp_batch_set_fused(self._b, 1 if enable else 0)
+        if rc != PP_OK:
+            raise PPError(rc, lib().pp_batch_last_error(self._b).decode(errors="replace"))
 
     def advance(self, max_steps: int):
         rc = lib().pp_batch_advance(self._b, int(max_steps))

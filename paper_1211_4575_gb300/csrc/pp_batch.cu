@@ -30,10 +30,24 @@ struct pp_batch {
         int64_t done = 0;       // steps enqueued
         size_t bytes = 0;
         cudaEvent_t ev = nullptr;
+        cudaEvent_t pre = nullptr;    // fused rounds: the slot's work before the shared launch
         bool busy = false;
         bool graphs_before = false;   // the context's step-graph setting before admission
         int status = PP_OK;
     } *slot = nullptr;
+    // fused rounds (pp_batch_set_fused): one persistent particle launch per group
+    // of compatible slots on the batch's own stream
+    bool fused = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t join = nullptr;
+    int nsm = 0;
+    static constexpr int kGroups = 16;   // cells_batch_key values
+    CellsBatchScratch scr[kGroups];
+    void *h_args[2][kGroups] = {}, *h_items[2][kGroups] = {};   // pinned, by round parity
+    size_t h_args_cap[2][kGroups] = {}, h_items_cap[2][kGroups] = {};
+    cudaEvent_t h_done[2][kGroups] = {};  // the copies from h_*[parity][group] have run
+    int64_t rounds = 0;
+    int64_t fused_launches = 0;
     char err[256] = {0};
 };
 
@@ -141,8 +155,150 @@ extern "C" int pp_batch_admit(pp_batch *b, pp_ctx *ctx, int64_t steps, int *slot
     return PP_OK;
 }
 
+// Device and pinned host room for a group's argument blocks and work items.
+static cudaError_t ensure_room(pp_batch *b, int par, int grp, size_t abytes, size_t ibytes) {
+    CellsBatchScratch &S = b->scr[grp];
+    cudaError_t e = cudaSuccess;
+    if (abytes > S.args_cap) {
+        if (S.args) cudaFree(S.args);
+        S.args = nullptr;
+        S.args_cap = 0;
+        if ((e = cudaMalloc(&S.args, abytes * 2)) != cudaSuccess) return e;
+        S.args_cap = abytes * 2;
+    }
+    if (ibytes > S.items_cap) {
+        if (S.items) cudaFree(S.items);
+        S.items = nullptr;
+        S.items_cap = 0;
+        if ((e = cudaMalloc(&S.items, ibytes * 2)) != cudaSuccess) return e;
+        S.items_cap = ibytes * 2;
+    }
+    if (!S.next && (e = cudaMalloc(&S.next, sizeof(int))) != cudaSuccess) return e;
+    if (abytes > b->h_args_cap[par][grp]) {
+        if (b->h_args[par][grp]) cudaFreeHost(b->h_args[par][grp]);
+        b->h_args[par][grp] = nullptr;
+        b->h_args_cap[par][grp] = 0;
+        if ((e = cudaHostAlloc(&b->h_args[par][grp], abytes * 2, cudaHostAllocDefault)) != cudaSuccess) return e;
+        b->h_args_cap[par][grp] = abytes * 2;
+    }
+    if (ibytes > b->h_items_cap[par][grp]) {
+        if (b->h_items[par][grp]) cudaFreeHost(b->h_items[par][grp]);
+        b->h_items[par][grp] = nullptr;
+        b->h_items_cap[par][grp] = 0;
+        if ((e = cudaHostAlloc(&b->h_items[par][grp], ibytes * 2, cudaHostAllocDefault)) != cudaSuccess) return e;
+        b->h_items_cap[par][grp] = ibytes * 2;
+    }
+    if (!b->h_done[par][grp] && (e = cudaEventCreateWithFlags(&b->h_done[par][grp], cudaEventDisableTiming)) !=
+                                     cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+// One fused round: every running slot's step, with the particle kernels of
+// all of them as one persistent launch per group of compatible slots.
+// Returns false (nothing enqueued) when a running slot cannot be fused.
+static bool fused_round(pp_batch *b) {
+    Ctx *run[4096];
+    int qs[4096], n = 0;
+    for (int q = 0; q < b->nslots; ++q) {
+        pp_batch::Slot &S = b->slot[q];
+        if (!S.busy || S.left <= 0 || S.status != PP_OK) continue;
+        Ctx *c = S.ctx;
+        if (!batch_fusable(c) || !c->st || cells_batch_key(*c) >= pp_batch::kGroups) return false;
+        run[n] = c;
+        qs[n++] = q;
+    }
+    if (n == 0) return false;
+    // before the shared launch: each slot's sort and cleared current, on its stream
+    int ok[4096];
+    for (int k = 0; k < n; ++k) {
+        pp_batch::Slot &S = b->slot[qs[k]];
+        int rc = batch_step_pre(run[k]);
+        if (rc == PP_OK && cudaEventRecord(S.pre, run[k]->st) != cudaSuccess) rc = PP_ECUDA;
+        if (rc == PP_OK && cudaStreamWaitEvent(b->st, S.pre, 0) != cudaSuccess) rc = PP_ECUDA;
+        ok[k] = rc == PP_OK;
+        if (rc != PP_OK) S.status = rc;
+    }
+    // the shared launches, one per group
+    const int par = (int)(b->rounds & 1);
+    for (int grp = 0; grp < pp_batch::kGroups; ++grp) {
+        Ctx *g[4096];
+        int m = 0;
+        int64_t tiles = 0;
+        for (int k = 0; k < n; ++k)
+            if (ok[k] && cells_batch_key(*run[k]) == grp) {
+                g[m++] = run[k];
+                tiles += (int64_t)run[k]->ntile[0] * run[k]->ntile[1] * run[k]->ntile[2];
+            }
+        if (m == 0) continue;
+        cudaError_t e = ensure_room(b, par, grp, cells_args_bytes() * m, sizeof(int2) * tiles);
+        // the pinned buffers of this parity were last read by the copies of two rounds ago
+        if (e == cudaSuccess) e = cudaEventSynchronize(b->h_done[par][grp]);
+        if (e == cudaSuccess)
+            e = launch_particles_cells_batch(g, m, b->st, b->scr[grp], b->h_args[par][grp], b->h_items[par][grp],
+                                             b->nsm);
+        if (e == cudaSuccess) e = cudaEventRecord(b->h_done[par][grp], b->st);
+        ++b->fused_launches;
+        if (e != cudaSuccess) {
+            snprintf(b->err, sizeof b->err, "fused particle launch: %s", cudaGetErrorString(e));
+            for (int k = 0; k < n; ++k)
+                if (ok[k] && cells_batch_key(*run[k]) == grp) {
+                    b->slot[qs[k]].status = PP_ECUDA;
+                    ok[k] = 0;
+                }
+        }
+    }
+    cudaEventRecord(b->join, b->st);
+    // after it: each slot's current solve and field update, on its stream
+    for (int k = 0; k < n; ++k) {
+        if (!ok[k]) continue;
+        pp_batch::Slot &S = b->slot[qs[k]];
+        int rc = cudaStreamWaitEvent(run[k]->st, b->join, 0) == cudaSuccess ? batch_step_post(run[k]) : PP_ECUDA;
+        if (rc != PP_OK) {
+            S.status = rc;
+            continue;
+        }
+        --S.left;
+        ++S.done;
+    }
+    ++b->rounds;
+    return true;
+}
+
+extern "C" int pp_batch_set_fused(pp_batch *b, int enable) {
+    if (!b) return PP_EINVAL;
+    if (enable && !b->st) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+            return bfail(b, PP_ECUDA, "pp_batch_set_fused: stream or event creation failed");
+        for (int q = 0; q < b->nslots; ++q)
+            if (!b->slot[q].pre && cudaEventCreateWithFlags(&b->slot[q].pre, cudaEventDisableTiming) != cudaSuccess)
+                return bfail(b, PP_ECUDA, "pp_batch_set_fused: event creation failed");
+    }
+    b->fused = enable != 0;
+    return PP_OK;
+}
+
 extern "C" int pp_batch_advance(pp_batch *b, int max_steps) {
     if (!b || max_steps < 0) return bfail(b, PP_EINVAL, "pp_batch_advance: bad argument");
+    if (b->fused) {
+        int r = 0;
+        for (; r < max_steps; ++r)
+            if (!fused_round(b)) break;
+        if (r < max_steps) {   // nothing fusable left running: the per-slot path takes the rest
+            max_steps -= r;
+        } else {
+            for (int q = 0; q < b->nslots; ++q) {
+                pp_batch::Slot &S = b->slot[q];
+                if (S.busy && cudaEventRecord(S.ev, static_cast<Ctx *>(S.ctx)->st) != cudaSuccess)
+                    S.status = PP_ECUDA;
+            }
+            return PP_OK;
+        }
+    }
     // one step per slot per round, so that slots interleave on the device
     for (int r = 0; r < max_steps; ++r) {
         bool any = false;
@@ -219,8 +375,23 @@ extern "C" const char *pp_batch_last_error(const pp_batch *b) { return b ? b->er
 
 extern "C" int pp_batch_destroy(pp_batch *b) {
     if (!b) return PP_OK;
-    for (int q = 0; q < b->nslots; ++q)
+    if (b->st) cudaStreamSynchronize(b->st);
+    for (int q = 0; q < b->nslots; ++q) {
         if (b->slot[q].ev) cudaEventDestroy(b->slot[q].ev);
+        if (b->slot[q].pre) cudaEventDestroy(b->slot[q].pre);
+    }
+    for (int g = 0; g < pp_batch::kGroups; ++g) {
+        cudaFree(b->scr[g].args);
+        cudaFree(b->scr[g].items);
+        cudaFree(b->scr[g].next);
+        for (int p = 0; p < 2; ++p) {
+            if (b->h_args[p][g]) cudaFreeHost(b->h_args[p][g]);
+            if (b->h_items[p][g]) cudaFreeHost(b->h_items[p][g]);
+            if (b->h_done[p][g]) cudaEventDestroy(b->h_done[p][g]);
+        }
+    }
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->st) cudaStreamDestroy(b->st);
     delete[] b->slot;
     delete b;
     return PP_OK;

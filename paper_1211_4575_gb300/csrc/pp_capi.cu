@@ -576,9 +576,11 @@ static bool cells_mode(const Ctx *c) {
     return !c->fp64 && (m == PP_DEPOSIT_CELLS || m == PP_DEPOSIT_AUTO) && cells_supported(*c);
 }
 
-static int particle_phase(Ctx *c, int only) {
-    NvtxRange nvtx("pp particle phase");
-    const bool cells = only < 0 && cells_mode(c);
+// The parts of a particle phase around its kernel launch: before it, the
+// per-step sort of the per-step sorted kernel when the particles moved, and
+// the cleared current; after it, the ghost fold, the images' current between
+// walls and the high-order current solve.
+static int particle_pre(Ctx *c, bool cells) {
     if (cells) {
         bool stale = false;
         for (int s = 0; s < c->nspecies; ++s) stale = stale || (c->sp[s].n > 0 && !c->sp[s].fresh);
@@ -593,6 +595,30 @@ static int particle_phase(Ctx *c, int only) {
     CU(launch_zero_J(*c));
     CU(cudaMemsetAsync(c->d_nslow, 0, sizeof(unsigned long long), c->st));
     CU(prof_mark(c, PH_PARTICLE, true));
+    return PP_OK;
+}
+
+static int particle_post(Ctx *c, int only) {
+    for (int s = 0; s < c->nspecies; ++s)
+        if (only < 0 || s == only) c->sp[s].fresh = false;   // the particles moved
+    CU(prof_mark(c, PH_PARTICLE, false));
+    CU(prof_mark(c, PH_CURRENT, true));
+    CU(launch_fold_J(*c));
+    CU(launch_mirror_J(*c));   // between walls: the virtual images' current
+    if (c->current_mode == PP_CURRENT_CONSERVING) CU(launch_current_solve(*c));   // eq:jj2 is final
+    CU(prof_mark(c, PH_CURRENT, false));
+    if (c->prof) ++c->prof_steps;
+    if (c->prof && c->prof_n > 4096) {
+        CU(cudaStreamSynchronize(c->st));
+        CU(prof_collect(c));
+    }
+    return PP_OK;
+}
+
+static int particle_phase(Ctx *c, int only) {
+    NvtxRange nvtx("pp particle phase");
+    const bool cells = only < 0 && cells_mode(c);
+    if (int r = particle_pre(c, cells)) return r;
     bool all_sorted = true;
     for (int s = 0; s < c->nspecies; ++s) all_sorted = all_sorted && (c->sp[s].sorted || c->sp[s].n == 0);
     const int m = c->d.deposit_mode;
@@ -613,20 +639,7 @@ static int particle_phase(Ctx *c, int only) {
             if (c->prof) ++c->prof_particle_launches;
         }
     }
-    for (int s = 0; s < c->nspecies; ++s)
-        if (only < 0 || s == only) c->sp[s].fresh = false;   // the particles moved
-    CU(prof_mark(c, PH_PARTICLE, false));
-    CU(prof_mark(c, PH_CURRENT, true));
-    CU(launch_fold_J(*c));
-    CU(launch_mirror_J(*c));   // between walls: the virtual images' current
-    if (c->current_mode == PP_CURRENT_CONSERVING) CU(launch_current_solve(*c));   // eq:jj2 is final
-    CU(prof_mark(c, PH_CURRENT, false));
-    if (c->prof) ++c->prof_steps;
-    if (c->prof && c->prof_n > 4096) {
-        CU(cudaStreamSynchronize(c->st));
-        CU(prof_collect(c));
-    }
-    return PP_OK;
+    return particle_post(c, only);
 }
 
 static int field_phase(Ctx *c) {
@@ -942,6 +955,44 @@ extern "C" int pp_step(pp_ctx *p, int nsteps) {
     }
     return PP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched form: a step split around a particle kernel launched for many
+// contexts at once (pp_batch.cu).  Only contexts that step as one leap-frog
+// step through the per-step sorted kernel, with no open end, injector or
+// window and no profiling, take this path.
+// ---------------------------------------------------------------------------
+namespace pp {
+
+bool batch_fusable(const Ctx *c) {
+    return cells_mode(c) && c->order == 2 && !boundary_dynamic(c) && !c->prof;
+}
+
+int batch_step_pre(Ctx *c) {
+    if (int r = ensure_gauss_reference(c)) return r;
+    const bool sort = c->d.sort_interval > 0 && c->since_sort >= c->d.sort_interval;
+    if (sort) {
+        if (int r = pp_sort(static_cast<pp_ctx *>(c))) return r;
+    }
+    c->kick_dt = c->drift_dt = c->d.dt;
+    c->escape_now = 0.0;
+    return particle_pre(c, true);
+}
+
+int batch_step_post(Ctx *c) {
+    int r = particle_post(c, -1);
+    if (r == PP_OK) r = field_phase(c);
+    if (r == PP_OK && c->filter_passes > 0 && (c->step + 1) % c->filter_interval == 0) {
+        CU(launch_divergence_filter(*c));
+    }
+    if (r == PP_OK) {
+        ++c->step;
+        ++c->since_sort;
+    }
+    return r;
+}
+
+}  // namespace pp
 
 extern "C" int pp_set_field_solver(pp_ctx *p, int solver) {
     Ctx *c = p;

@@ -65,11 +65,16 @@ constexpr int kWGVol = kWG * kWG * kWG;
 __device__ __forceinline__ int wg(int i, int j, int k) { return i + kWG * (j + kWG * k); }
 #if PP_CELLS_PAIRS
 constexpr size_t kFieldBytes = sizeof(float2) * 6 * kWGVol;
-constexpr int kCC = 3584;                        // particles staged per chunk
+#ifndef PP_CELLS_CHUNK
+#define PP_CELLS_CHUNK 3584
+#endif
 #else
 constexpr size_t kFieldBytes = sizeof(float) * 6 * kWVol;
-constexpr int kCC = 4096;                        // particles staged per chunk
+#ifndef PP_CELLS_CHUNK
+#define PP_CELLS_CHUNK 4096
 #endif
+#endif
+constexpr int kCC = PP_CELLS_CHUNK;              // particles staged per chunk
 constexpr int kCPer = kCC / kCT;                 // phase-1 particles per thread per chunk
 // Pieces of at most 8 particles: more register sums to add than with 16 or 32,
 // but the deposit items spread evenly over the threads (64^3 thermal PCS:
@@ -398,9 +403,11 @@ __device__ __forceinline__ unsigned lanemask_lt_() {
 
 // BND: walls (reflection) and the open end (escape); a separate instantiation
 // so that periodic runs carry none of their tests.
+// One tile of one run: the whole particle step of the tile's particles (all
+// species), its current added into the run's mesh.  Called by every thread
+// of the CTA; smem is the CTA's dynamic shared memory.
 template <int O, int PUSH, bool BND>
-__global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constant__ CellsArgs T) {
-    extern __shared__ float smem[];
+__device__ __forceinline__ void cells_tile(const CellsArgs &T, const int tile, float *smem) {
     float *F = smem;
     JT *Jw = (JT *)((char *)smem + kFieldBytes);
     float *s_o = (float *)(Jw + 3 * kWVol);   // 3 x kCS: offsets at t (frame of the cell)
@@ -412,7 +419,6 @@ __global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constan
                                           // [4..9]: fixed point: cell box of the chunk; [10..12]: sum |dxi|
     int *cnt = misc + 16;                 // piece starts per (round, warp)
     const Geom &g = T.g;
-    const int tile = blockIdx.x;
     const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
     const int ox = tx * kT, oy = ty * kT, oz = tz * kT;
     const int wx = ox - kRLo, wy = oy - kRLo, wz = oz - kRLo;
@@ -709,6 +715,33 @@ __global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constan
 #endif
 }
 
+template <int O, int PUSH, bool BND>
+__global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constant__ CellsArgs T) {
+    extern __shared__ float smem[];
+    cells_tile<O, PUSH, BND>(T, blockIdx.x, smem);
+}
+
+// Batched form: the tiles of many runs as (run, tile) work items, taken in
+// order by persistent CTAs from a device counter (the items come sorted by
+// run size, largest first, so that the last items are short).  Every run's
+// arguments sit in device memory.
+template <int O, int PUSH, bool BND>
+__global__ void __launch_bounds__(kCT, 1) k_particles_cells_multi(const CellsArgs *args, const int2 *items,
+                                                                 int nitems, int *next) {
+    extern __shared__ float smem[];
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(next, 1);
+        __syncthreads();
+        const int w = item;
+        __syncthreads();   // every thread has read it before thread 0 takes the next
+        if (w >= nitems) return;
+        const int2 it = items[w];
+        cells_tile<O, PUSH, BND>(args[it.x], it.y, smem);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 bool cells_supported(const Ctx &c) {
@@ -718,11 +751,8 @@ bool cells_supported(const Ctx &c) {
     return true;
 }
 
-// All species in one launch; every species with particles must have been
-// sorted since its particles last moved (Species::fresh).
-cudaError_t launch_particles_cells(Ctx &c) {
-    if (!cells_supported(c)) return cudaErrorInvalidConfiguration;
-    CellsArgs T;
+// The argument block of one context: false when no species holds particles.
+static bool cells_args(const Ctx &c, CellsArgs &T) {
     T.g = c.g;
     const double h[3] = {c.d.dx, c.d.dy, c.d.dz};
     for (int d = 0; d < 3; ++d) {
@@ -736,7 +766,6 @@ cudaError_t launch_particles_cells(Ctx &c) {
     for (int s = 0; s < c.nspecies; ++s) {
         const Species &S = c.sp[s];
         if (S.n == 0) continue;
-        if (!S.fresh) return cudaErrorInvalidValue;
         CellsSpecies &t = T.sp[T.ns++];
         t.p = MixedParticles{S.cell, S.ox, S.oy, S.oz, S.fux, S.fuy, S.fuz};
         int32_t *c2 = (int32_t *)S.alt;
@@ -749,18 +778,53 @@ cudaError_t launch_particles_cells(Ctx &c) {
         t.kdt = (float)(c.kick_dt != 0.0 ? S.rad / c.kick_dt : 0.0);
         for (int d = 0; d < 3; ++d) t.jscale[d] = (float)(-S.q * S.w * h[d] / c.drift_dt);
     }
-    if (T.ns == 0) return cudaSuccess;
     T.status = c.d_status;
     for (int d = 0; d < 3; ++d) T.wall[d] = c.wall[d];
     T.esc = c.escape_now;
     T.dead_key = (int32_t)c.nkeys;
+    return T.ns > 0;
+}
+
+static bool cells_ready(const Ctx &c) {
+    for (int s = 0; s < c.nspecies; ++s)
+        if (c.sp[s].n > 0 && !c.sp[s].fresh) return false;
+    return true;
+}
+
+// After the launch: every slot of the sorted order holds its particle's new
+// state in the other buffer, with its next sort key.
+static void cells_after(Ctx &c) {
+    for (int s = 0; s < c.nspecies; ++s) {
+        Species &S = c.sp[s];
+        if (S.n == 0) continue;
+        void *old = S.buf;
+        S.buf = S.alt;
+        S.alt = old;
+        S.bind(false);
+        S.perm_pending = false;
+        S.keys_valid = true;
+    }
+}
+
+template <class K>
+static cudaError_t smem_attr(K kernel, unsigned long long &done) {
+    return ensure_smem_attr(kernel, (int)kCellsSmem, done);
+}
+
+// All species in one launch; every species with particles must have been
+// sorted since its particles last moved (Species::fresh).
+cudaError_t launch_particles_cells(Ctx &c) {
+    if (!cells_supported(c)) return cudaErrorInvalidConfiguration;
+    if (!cells_ready(c)) return cudaErrorInvalidValue;
+    CellsArgs T;
+    if (!cells_args(c, T)) return cudaSuccess;
     const unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     const int o = c.d.shape_order, pu = c.d.pusher;
     const bool bnd = c.any_wall();
     static unsigned long long attr_done[2][2][4] = {};
 #define PP_CB(O, PU, BD)                                                                                     \
     do {                                                                                                     \
-        cudaError_t e_ = ensure_smem_attr(k_particles_cells<O, PU, BD>, (int)kCellsSmem, attr_done[BD][PU][O]); \
+        cudaError_t e_ = smem_attr(k_particles_cells<O, PU, BD>, attr_done[BD][PU][O]);                      \
         if (e_ != cudaSuccess) return e_;                                                                    \
         k_particles_cells<O, PU, BD><<<blocks, kCT, kCellsSmem, c.st>>>(T);                                  \
     } while (0)
@@ -778,17 +842,81 @@ cudaError_t launch_particles_cells(Ctx &c) {
     ++c.nlaunch;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // every slot of the sorted order now holds its particle's new state in the
-    // other buffer, with its next sort key
-    for (int s = 0; s < c.nspecies; ++s) {
-        Species &S = c.sp[s];
-        if (S.n == 0) continue;
-        void *old = S.buf;
-        S.buf = S.alt;
-        S.alt = old;
-        S.bind(false);
-        S.perm_pending = false;
-        S.keys_valid = true;
+    cells_after(c);
+    return cudaSuccess;
+}
+
+size_t cells_args_bytes() { return sizeof(CellsArgs); }
+
+int cells_batch_key(const Ctx &c) { return c.d.shape_order * 4 + c.d.pusher * 2 + (c.any_wall() ? 1 : 0); }
+
+// The tiles of n contexts with one cells_batch_key in one persistent launch of
+// nsm CTAs on st.  host_args / host_items: pinned host memory of at least
+// n * cells_args_bytes() and (sum of tiles) * 8 bytes, copied to the device
+// scratch on st (the caller keeps them unchanged until the copy has run).
+cudaError_t launch_particles_cells_batch(Ctx *const *ctxs, int n, cudaStream_t st, CellsBatchScratch &scr,
+                                         void *host_args, void *host_items, int nsm) {
+    if (n <= 0) return cudaSuccess;
+    CellsArgs *A = (CellsArgs *)host_args;
+    int2 *items = (int2 *)host_items;
+    // runs with particles, largest first: their tiles become the first items
+    int order[4096], m = 0;
+    for (int k = 0; k < n && m < 4096; ++k) {
+        Ctx &c = *ctxs[k];
+        if (!cells_supported(c) || !cells_ready(c)) return cudaErrorInvalidValue;
+        if (cells_args(c, A[m])) order[m++] = k;
+    }
+    int64_t ntot = 0;
+    for (int a = 0; a < m; ++a) {   // insertion sort by tile count, descending
+        for (int b = a; b > 0; --b) {
+            const Ctx &x = *ctxs[order[b]], &y = *ctxs[order[b - 1]];
+            const int64_t tx = (int64_t)x.ntile[0] * x.ntile[1] * x.ntile[2];
+            const int64_t ty = (int64_t)y.ntile[0] * y.ntile[1] * y.ntile[2];
+            if (tx <= ty) break;
+            const int t = order[b]; order[b] = order[b - 1]; order[b - 1] = t;
+            CellsArgs u = A[b]; A[b] = A[b - 1]; A[b - 1] = u;
+        }
+    }
+    for (int a = 0; a < m; ++a) {
+        const Ctx &c = *ctxs[order[a]];
+        const int tiles = c.ntile[0] * c.ntile[1] * c.ntile[2];
+        for (int t = 0; t < tiles; ++t) items[ntot++] = make_int2(a, t);
+    }
+    if (m == 0) return cudaSuccess;
+    const size_t abytes = sizeof(CellsArgs) * (size_t)m, ibytes = sizeof(int2) * (size_t)ntot;
+    if (abytes > scr.args_cap || ibytes > scr.items_cap) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemcpyAsync(scr.args, A, abytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scr.items, items, ibytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scr.next, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const Ctx &c0 = *ctxs[order[0]];
+    const int o = c0.d.shape_order, pu = c0.d.pusher;
+    const bool bnd = c0.any_wall();
+    const unsigned grid = (unsigned)(nsm < ntot ? nsm : ntot);
+    static unsigned long long attr_done[2][2][4] = {};
+#define PP_MB(O, PU, BD)                                                                                     \
+    do {                                                                                                     \
+        cudaError_t e_ = smem_attr(k_particles_cells_multi<O, PU, BD>, attr_done[BD][PU][O]);                \
+        if (e_ != cudaSuccess) return e_;                                                                    \
+        k_particles_cells_multi<O, PU, BD><<<grid, kCT, kCellsSmem, st>>>(                                   \
+            (const CellsArgs *)scr.args, (const int2 *)scr.items, (int)ntot, scr.next);                      \
+    } while (0)
+#define PP_M(O, PU)                                                                                          \
+    do {                                                                                                     \
+        if (bnd) PP_MB(O, PU, true); else PP_MB(O, PU, false);                                               \
+    } while (0)
+    if (pu == PP_BORIS) {
+        if (o == 1) PP_M(1, PP_BORIS); else if (o == 2) PP_M(2, PP_BORIS); else PP_M(3, PP_BORIS);
+    } else {
+        if (o == 1) PP_M(1, PP_VAY); else if (o == 2) PP_M(2, PP_VAY); else PP_M(3, PP_VAY);
+    }
+#undef PP_M
+#undef PP_MB
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int a = 0; a < m; ++a) {
+        Ctx &c = *ctxs[order[a]];
+        ++c.nlaunch;
+        cells_after(c);
     }
     return cudaSuccess;
 }

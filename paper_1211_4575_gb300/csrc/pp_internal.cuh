@@ -630,6 +630,21 @@ cudaError_t launch_particles_tiled_all(Ctx &c);
 bool tiled_supported(const Ctx &c);
 cudaError_t launch_particles_cells(Ctx &c);
 bool cells_supported(const Ctx &c);
+// batched form: one launch over the tiles of many contexts (same shape order,
+// pusher and boundary kind); scratch = device memory the caller owns
+struct CellsBatchScratch {
+    void *args = nullptr;   // per context argument block
+    void *items = nullptr;  // (context, tile) work items
+    int *next = nullptr;    // work counter
+    size_t args_cap = 0, items_cap = 0;
+};
+int cells_batch_key(const Ctx &c);   // contexts with equal keys can share a launch
+cudaError_t launch_particles_cells_batch(Ctx *const *ctxs, int n, cudaStream_t st, CellsBatchScratch &scr,
+                                         void *host_args, void *host_items, int nsm);
+size_t cells_args_bytes();
+bool batch_fusable(const Ctx *c);
+int batch_step_pre(Ctx *c);
+int batch_step_post(Ctx *c);
 cudaError_t launch_rho(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c, double *out_per_species);
 

@@ -15,9 +15,16 @@ import numpy as np
 from . import PP_BATCH_DONE, PP_BATCH_FAILED, PP_MIXED32, Batch, PPError, Simulation, estimate_device_bytes
 
 
-def _build(req, precision, stream):
+def _make_load(req):
     import pp_synth
-    L = pp_synth.run_load(req)
+    return pp_synth.run_load(req)
+
+
+def _build(req, precision, stream, L=None):
+    """The run of a request on the device: its seeded load (built here unless
+    given), a context on `stream`, the particles uploaded."""
+    if L is None:
+        L = _make_load(req)
     sim = Simulation(L.n, L.d, L.dt, field_order=6, alpha=0.55, shape_order=req.get("shape", 3),
                      precision=precision, sort_interval=20, relax_max_iter=100,
                      relax_tol=1e-6 if precision == PP_MIXED32 else 1e-12, stream=stream)
@@ -27,6 +34,36 @@ def _build(req, precision, stream):
     return sim, L.n_particles
 
 
+class _Loads:
+    """Host worker threads that build the seeded loads of arrived requests
+    (the server's input preparation), at most `ahead` at a time, in arrival
+    order; both the batched and the one-at-a-time server use it."""
+
+    def __init__(self, workers=4, ahead=4):
+        from concurrent.futures import ThreadPoolExecutor
+        self.pool = ThreadPoolExecutor(max_workers=workers)
+        self.ahead = ahead
+        self.fut = {}
+
+    def feed(self, pending, now):
+        for req in pending:
+            if len(self.fut) >= self.ahead or req.get("arrival", 0.0) > now:
+                break
+            key = id(req)
+            if key not in self.fut:
+                self.fut[key] = self.pool.submit(_make_load, req)
+
+    def ready(self, req):
+        f = self.fut.get(id(req))
+        return f is not None and f.done()
+
+    def take(self, req):
+        return self.fut.pop(id(req)).result()
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+
 def _summary(lat, work, makespan):
     lat = np.asarray(lat, dtype=float)
     return {"requests": int(lat.size), "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
@@ -34,28 +71,34 @@ def _summary(lat, work, makespan):
             "particle_steps_per_s": work / makespan if makespan > 0 else None}
 
 
-def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, keep=False):
+def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, keep=False, loaders=4, fused=False):
     """Continuous batching.  Returns (summary, per-request results); with keep
-    the finished Simulations are returned too (for comparisons)."""
+    the finished Simulations are returned too (for comparisons).  fused: the
+    batch's fused rounds (one persistent particle launch per round)."""
     import torch
+    import pp_synth
     pending = sorted(requests, key=lambda r: r.get("arrival", 0.0))
     batch = Batch(budget_bytes, max_slots)
+    if fused:
+        batch.set_fused(True)
+    loads = _Loads(workers=loaders, ahead=loaders)
     active = {}
     lat, work, results = [], 0, []
     t0 = time.perf_counter()
     while pending or active:
         now = time.perf_counter() - t0
-        while pending and pending[0].get("arrival", 0.0) <= now:
+        loads.feed(pending, now)
+        while pending and pending[0].get("arrival", 0.0) <= now and loads.ready(pending[0]):
             req = pending[0]
-            # admit by the run's device bytes, known before anything is built:
-            # a run that does not fit waits, unbuilt, until a slot's memory returns
-            import pp_synth
+            # admit by the run's device bytes, known before anything is built on
+            # the device: a run that does not fit waits until a slot's memory returns
             need = estimate_device_bytes((req["n"],) * 3, pp_synth.run_counts(req), precision)
             used, nact = batch.used()
             if used + need > budget_bytes or nact >= max_slots:
                 break
             stream = torch.cuda.Stream()
-            sim, npart = _build(req, precision, stream.cuda_stream)
+            sim, npart = _build(req, precision, stream.cuda_stream, loads.take(req))
+            loads.feed(pending[1:], now)
             slot = batch.admit(sim, req["steps"])
             if slot is None:          # cannot happen after the check above; keep the request
                 sim.close()
@@ -64,7 +107,7 @@ def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, k
             active[slot] = (req, sim, npart, stream)
         if not active:
             if pending:
-                time.sleep(max(0.0, min(0.01, pending[0].get("arrival", 0.0) - now)))
+                time.sleep(max(0.001, min(0.01, pending[0].get("arrival", 0.0) - now)))
             continue
         batch.advance(chunk)
         for slot in list(active):
@@ -81,21 +124,28 @@ def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, k
                     sim.close()
     makespan = time.perf_counter() - t0
     batch.close()
+    loads.close()
     return _summary(lat, work, makespan), results
 
 
-def sequential(requests, precision=PP_MIXED32, keep=False):
-    """The same requests one at a time, in arrival order, on one stream."""
+def sequential(requests, precision=PP_MIXED32, keep=False, loaders=4):
+    """The same requests one at a time, in arrival order, on one stream (loads
+    prepared by the same host workers as the batched server)."""
     import torch
     pending = sorted(requests, key=lambda r: r.get("arrival", 0.0))
+    loads = _Loads(workers=loaders, ahead=loaders)
     lat, work, results = [], 0, []
     stream = torch.cuda.current_stream().cuda_stream
     t0 = time.perf_counter()
-    for req in pending:
-        now = time.perf_counter() - t0
-        if req.get("arrival", 0.0) > now:
-            time.sleep(req["arrival"] - now)
-        sim, npart = _build(req, precision, stream)
+    for i, req in enumerate(pending):
+        while True:
+            now = time.perf_counter() - t0
+            loads.feed(pending[i:], now)
+            if req.get("arrival", 0.0) <= now and loads.ready(req):
+                break
+            time.sleep(0.002)
+        sim, npart = _build(req, precision, stream, loads.take(req))
+        loads.feed(pending[i + 1:], time.perf_counter() - t0)
         sim.step(req["steps"])
         sim.sync()
         t = time.perf_counter() - t0
@@ -105,6 +155,7 @@ def sequential(requests, precision=PP_MIXED32, keep=False):
         if not keep:
             sim.close()
     makespan = time.perf_counter() - t0
+    loads.close()
     return _summary(lat, work, makespan), results
 
 
@@ -121,12 +172,16 @@ def build_all(requests, precision=PP_MIXED32):
     return built
 
 
-def batched(built, budget_bytes, max_slots=64, chunk=4, graphs=True):
+def batched(built, budget_bytes, max_slots=64, chunk=4, graphs=True, fused=False):
     """Batched form on runs already resident (build_all): all runs admitted
     into slots as budget and slots allow and advanced together, one stream
     each, each step replayed from a captured CUDA graph unless graphs=False,
-    until every run has taken its steps.  Summary of the timed region."""
+    or (fused) with the particle kernels of all runs as one persistent launch
+    per round, until every run has taken its steps.  Summary of the timed
+    region."""
     batch = Batch(budget_bytes, max_slots)
+    if fused:
+        batch.set_fused(True)
     waiting = list(built)
     active = {}
     lat, work = [], 0

@@ -51,6 +51,32 @@ def test_each_result_same_alone_and_in_the_mix(pp, precision, tol):
         ref.close()
 
 
+def test_fused_rounds_same_as_alone(pp):
+    """Fused rounds (one persistent particle launch over the tiles of every
+    running slot, PCS and TSC runs in two groups): each result equals the run
+    alone to the mixed form's round-off (the flush of a tile's current into
+    the mesh is an FP32 atomic sum, order-dependent)."""
+    from paper_1211_4575_gb300 import serving
+    reqs = [dict(r, n=((r["n"] + 7) // 8) * 8) for r in _requests()]   # meshes of multiples of 8
+    alone, ra = serving.sequential(reqs, precision=pp.PP_MIXED32, keep=True)
+    mixed, rm = serving.serve(reqs, budget_bytes=8 << 30, max_slots=4, chunk=2, precision=pp.PP_MIXED32, keep=True,
+                              fused=True)
+    assert mixed["requests"] == 3
+    by_seed = {r["seed"]: s for r, s in ra}
+    for req, sim in rm:
+        ref = by_seed[req["seed"]]
+        E1, B1, _ = sim.fields()
+        E0, B0, _ = ref.fields()
+        assert max(H.rel_err(E1[a], E0[a]) for a in range(3)) <= 5e-5
+        assert max(H.rel_err(B1[a], B0[a]) for a in range(3)) <= 5e-5
+        for s in range(2):
+            dpos, du = H.particle_errors(sim.particles(s), ref.particles(s), tuple(req["n"] * 0.5 for _ in range(3)))
+            assert dpos <= 5e-5 and du <= 5e-5
+        assert sim.diagnostics()["step"] == ref.diagnostics()["step"] == req["steps"]
+        sim.close()
+        ref.close()
+
+
 def test_admission_by_budget_and_slots(pp):
     import pp_synth
     L = pp_synth.run_load(_requests()[0])

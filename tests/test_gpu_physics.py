@@ -10,6 +10,10 @@
   energy growth rate of the GPU path on a quiet start is within 2% of the
   oracle's, in FP64 and in the mixed form (the oracle is pinned to the
   cold-fluid dispersion relation).
+* Numerical heating (Sec. VIII): an electron-ion plasma at rest (mass ratio
+  16, v_th = 0.1c for both, ten cells per skin depth) heats its electrons at
+  a rate proportional to 1/ppc on the GPU (8, 16 and 32 per cell per species),
+  and the GPU's rate at the smallest size agrees with the oracle's.
 * A relativistic beam (Gamma = 10) through an electron-ion background
   (m_i/m_e = 25): the mixed form against the oracle on a small periodic box
   with the beam-background per-cell load.
@@ -88,6 +92,58 @@ def test_weibel_growth_rate_gpu_within_2pct_of_oracle(pp, orc, precision, eps):
     assert ng >= 20 and no >= 20, (ng, no)
     assert rg == pytest.approx(ro, rel=0.02), (rg, ro)
     assert gpu.diagnostics()["status"] == 0
+
+
+def _electron_kinetic_gpu(sim):
+    return sim.diagnostics()["kinetic"][0]
+
+
+def _electron_kinetic_oracle(sim):
+    # sum over the electrons of w m (gamma - 1) dV (the kinetic energy pp_diagnostics reports)
+    s = sim.species[0]
+    g = np.sqrt(1.0 + s["ux"] ** 2 + s["uy"] ** 2 + s["uz"] ** 2)
+    dV = float(np.prod([sim.g.d[a] for a in range(3)]))
+    return s["w"] * s["m"] * float((g - 1.0).sum()) * dV
+
+
+def _heating_slope(sim, steps, every=10, ke_of=_electron_kinetic_gpu):
+    """Least-squares slope, per step, of the electron kinetic energy over its
+    initial value (the heating rate)."""
+    ke = []
+    for _ in range(steps // every):
+        sim.step(every)
+        ke.append(ke_of(sim))
+    ke = np.array(ke)
+    t = np.arange(1, len(ke) + 1) * every
+    return np.polyfit(t, ke / ke[0], 1)[0]
+
+
+def test_numerical_heating_scales_as_one_over_ppc(pp, orc):
+    """Mixed form (the per-step sorted kernel) on 32^3 cells: the electron
+    heating rate halves when the particles per cell double (8 -> 16 -> 32),
+    each ratio within 25% of 2; at 16^3 x 8 ppc the GPU's rate is within 25%
+    of the oracle's (FP64, same seeded particles; heating is a statistical
+    property of the noise, so the two runs agree in rate, not step by step)."""
+    rates = {}
+    for ppc in (8, 16, 32):
+        L = pp_synth.heating_plasma(n=(32, 32, 32), ppc=ppc)
+        sim = H.gpu_sim(pp, L, pp.PP_MIXED32, 3)
+        rates[ppc] = _heating_slope(sim, 400)
+        assert sim.diagnostics()["status"] == 0
+    assert rates[8] > 0.0
+    assert rates[8] / rates[16] == pytest.approx(2.0, rel=0.25), rates
+    assert rates[16] / rates[32] == pytest.approx(2.0, rel=0.25), rates
+    L = pp_synth.heating_plasma(n=(16, 16, 16), ppc=8)
+    gpu = H.gpu_sim(pp, L, pp.PP_MIXED32, 3)
+    rg = _heating_slope(gpu, 300)
+    import os
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        osim = H.oracle_sim(orc, L, 3, relax_tol=1e-10)
+        ro = _heating_slope(osim, 300, ke_of=_electron_kinetic_oracle)
+    finally:
+        orc.set_threads(1)
+    assert rg == pytest.approx(ro, rel=0.25), (rg, ro)
 
 
 def test_noisy_two_stream_energy_series_fp64(pp, orc):
