@@ -377,6 +377,20 @@ int pp_set_tuning(pp_ctx *ctx, int sort_interval, int deposit_mode);
  * PP_* code (PP_ECFL, PP_ENAN, PP_ENOCONV, ...; PP_OK when clean).  Clears it. */
 int pp_sync(pp_ctx *ctx);
 
+/* Check of the bounded device-side wait.  The per-step sorted kernel
+ * (PP_DEPOSIT_CELLS) stages each tile's E/B window into shared memory with TMA
+ * tensor copies that complete on an mbarrier; every thread's wait on it gives
+ * up after one second, records PP_ETIMEOUT in the device status word and
+ * stops its CTA (later tiles see the status and stop too), so that no wait can
+ * hold the GPU.  This call runs that same wait in one CTA on the context's
+ * stream with a limit of limit_ns nanoseconds (1 .. 10^10): with deliver != 0
+ * the barrier's phase completes and the call returns PP_OK; with deliver == 0
+ * the phase waits for 16 bytes that no copy delivers, the wait runs out and
+ * the call returns PP_ETIMEOUT (after about 2 limit_ns: the timed-out CTA
+ * waits once more, bounded, for copies in flight).  The context stays
+ * usable.  PP_EINVAL for a limit outside the range. */
+int pp_check_bounded_wait(pp_ctx *ctx, int deliver, long long limit_ns);
+
 /* Global FP64 diagnostics into *out (synchronises). */
 int pp_diagnostics(pp_ctx *ctx, pp_diag *out);
 

@@ -96,6 +96,7 @@ SIGNATURES = {
     "pp_field_update": (C.c_int, [_P]),
     "pp_sort": (C.c_int, [_P]),
     "pp_sync": (C.c_int, [_P]),
+    "pp_check_bounded_wait": (C.c_int, [_P, C.c_int, C.c_longlong]),
     "pp_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "pp_diagnostics": (C.c_int, [_P, C.POINTER(Diag)]),
     "pp_get_fields": (C.c_int, [_P, _PP, _PP, _PP]),
@@ -337,6 +338,13 @@ class Simulation:
 
     def sync(self):
         self._c(lib().pp_sync(self._ctx))
+
+    def check_bounded_wait(self, deliver: bool, limit_ns: int) -> int:
+        """Run the particle kernel's bounded staging wait once on the
+        context's stream (pp_check_bounded_wait): PP_OK when its barrier
+        phase completes (deliver), PP_ETIMEOUT when it waits for bytes that
+        never come and the limit runs out."""
+        return int(lib().pp_check_bounded_wait(self._ctx, 1 if deliver else 0, int(limit_ns)))
 
     def set_tuning(self, sort_interval: int, deposit_mode: int):
         self._c(lib().pp_set_tuning(self._ctx, int(sort_interval), int(deposit_mode)))

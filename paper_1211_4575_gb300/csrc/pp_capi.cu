@@ -16,6 +16,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "pp_ctx.cuh"
+#include "pp_tma.cuh"
 
 // NVTX range over a host scope: each phase of a step shows up by name in a
 // profiler timeline (ncu --nvtx, Nsight Systems).
@@ -1143,6 +1144,7 @@ extern "C" int pp_set_tuning(pp_ctx *p, int sort_interval, int deposit_mode) {
 
 static int status_code(int bits) {
     if (bits & ST_BOUNDS) return PP_EBOUNDS;
+    if (bits & ST_TIMEOUT) return PP_ETIMEOUT;
     if (bits & ST_NAN) return PP_ENAN;
     if (bits & ST_CFL) return PP_ECFL;
     if (bits & ST_NOCONV) return PP_ENOCONV;
@@ -1157,7 +1159,7 @@ extern "C" int pp_sync(pp_ctx *p) {
     CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st));
     CU(cudaStreamSynchronize(c->st));
     int code = status_code(*c->h_status);
-    if (code) return fail(c, code, "device status 0x%x (NaN=1, CFL=2, relaxation=4, range=8)", *c->h_status);
+    if (code) return fail(c, code, "device status 0x%x (NaN=1, CFL=2, relaxation=4, range=8, bounds=16, timeout=32)", *c->h_status);
     return PP_OK;
 }
 
@@ -1227,6 +1229,16 @@ extern "C" int pp_get_fields(pp_ctx *p, double *const E[3], double *const B[3], 
     }
     cudaFree(stage);
     return rc;
+}
+
+extern "C" int pp_check_bounded_wait(pp_ctx *p, int deliver, long long limit_ns) {
+    Ctx *c = p;
+    if (!c) return fail(c, PP_EINVAL, "NULL context");
+    if (limit_ns < 1 || limit_ns > 10000000000ll) return fail(c, PP_EINVAL, "limit_ns %lld outside 1 .. 1e10", limit_ns);
+    int rc = pp_sync(p);   // earlier work's status first
+    if (rc != PP_OK) return rc;
+    CU(launch_wait_check(c->st, c->d_status, deliver, (uint64_t)limit_ns));
+    return pp_sync(p);
 }
 
 // ---------------------------------------------------------------------------

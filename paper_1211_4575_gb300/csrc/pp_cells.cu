@@ -6,8 +6,11 @@
 //
 // One CTA per 8x8x8 tile of cells.  Because every particle of the tile's sorted
 // range sits in the tile, the E/B window staged in shared memory is the tile
-// plus the stencil reach only (13^3 nodes), and the particles of one cell are
-// consecutive in memory.  Per chunk of up to 4096 particles of one species:
+// plus the gather's reach only (12^3 nodes per component, copied by six TMA
+// tensor copies that complete on an mbarrier whose wait is bounded in time),
+// the current window the tile plus the deposit's reach (13^3 nodes), and the
+// particles of one cell are consecutive in memory.  Per chunk of up to 4096
+// particles of one species:
 //
 //  phase 1, one thread per particle (a warp on 32 consecutive particles, i.e.
 //    one or two cells: the gather's shared loads are broadcasts): gather
@@ -36,6 +39,7 @@
 // registers and is rounded to the unit once.
 #include "pp_internal.cuh"
 #include "pp_particle_common.cuh"
+#include "pp_tma.cuh"
 
 namespace pp {
 
@@ -51,28 +55,22 @@ constexpr int kWVol = kW * kW * kW;              // words per window component
 #endif
 constexpr int kCT = PP_CELLS_THREADS;            // threads per tile CTA
 constexpr int kCW = kCT / 32;
-// With PP_CELLS_PAIRS=1 the gather's window is stored as pairs (F[n], F[n+1])
-// of consecutive x nodes, so that a 4-node row of a PCS stencil takes two
-// 64-bit shared loads instead of four 32-bit ones (nodes -2 .. 9 of a tile,
-// 12 per axis; the chunk shrinks to 3584 particles to make room).  Measured
-// slower than the plain FP32 window (128^3 thermal PCS: 19.3 against 18.3 ms
-// per step), so the plain window is the default.
-#ifndef PP_CELLS_PAIRS
-#define PP_CELLS_PAIRS 0
-#endif
-constexpr int kWG = kT + kRLo + 2;               // 12 gather window nodes per axis
-constexpr int kWGVol = kWG * kWG * kWG;
-__device__ __forceinline__ int wg(int i, int j, int k) { return i + kWG * (j + kWG * k); }
-#if PP_CELLS_PAIRS
-constexpr size_t kFieldBytes = sizeof(float2) * 6 * kWGVol;
-#ifndef PP_CELLS_CHUNK
-#define PP_CELLS_CHUNK 3584
-#endif
-#else
-constexpr size_t kFieldBytes = sizeof(float) * 6 * kWVol;
+// The E/B window the gather reads: nodes -2 .. 9 of the tile on each axis
+// (a PCS support reaches two nodes either side of a particle's cell), one box
+// of kWG^3 nodes per component copied by one TMA tensor copy (rows of 48
+// bytes, a multiple of 16 as the copy requires), the six components kFComp
+// words apart (128-byte aligned), then a 128-byte slot for the mbarrier the
+// copies complete on.  The current window keeps kW nodes per axis: a particle
+// that moves to the next cell deposits one node further up.
+constexpr int kWG = kT + kRLo + 2;                             // 12
+constexpr int kFComp = (kWG * kWG * kWG + 31) / 32 * 32;       // 1728 words
+constexpr uint32_t kFBoxBytes = sizeof(float) * kWG * kWG * kWG;  // 6912 bytes per component
+constexpr size_t kFieldBytes = sizeof(float) * 6 * kFComp + 128;
+__device__ __forceinline__ int fi(int i, int j, int k) { return i + kWG * (j + kWG * k); }
+// A staging wait that has not completed after this long gives up (ST_TIMEOUT).
+constexpr uint64_t kStageWaitNs = 1000000000ull;
 #ifndef PP_CELLS_CHUNK
 #define PP_CELLS_CHUNK 4096
-#endif
 #endif
 constexpr int kCC = PP_CELLS_CHUNK;              // particles staged per chunk
 constexpr int kCPer = kCC / kCT;                 // phase-1 particles per thread per chunk
@@ -126,7 +124,7 @@ struct CellsFieldAcc {
     PP_IF_CHECKED(int wx = 0, wy = 0, wz = 0; int *st = nullptr; mutable int bad = 0;)
 #ifdef PP_CHECKED
     __device__ __forceinline__ bool inside(int i, int j, int k) const {
-        return wx + i >= 0 && wx + i < kW && wy + j >= 0 && wy + j < kW && wz + k >= 0 && wz + k < kW;
+        return wx + i >= 0 && wx + i < kWG && wy + j >= 0 && wy + j < kWG && wz + k >= 0 && wz + k < kWG;
     }
     __device__ ~CellsFieldAcc() {
         if (bad && st) atomicOr(st, ST_BOUNDS);
@@ -134,67 +132,9 @@ struct CellsFieldAcc {
 #endif
     __device__ __forceinline__ float F(int kind, int comp, int i, int j, int k) const {
         PP_IF_CHECKED(if (!inside(i, j, k)) { bad = 1; return 0.0f; })
-        return Fw[(kind * 3 + comp) * kWVol + base + wi(i, j, k)];
+        return Fw[(kind * 3 + comp) * kFComp + base + fi(i, j, k)];
     }
 };
-
-// Gather of one staggered component from the pair window P (eq:pfields):
-// separable triple sum over the (O+1)^3 support starting at window node
-// (i0, j0, k0), x innermost, each row read as 64-bit pairs.
-template <int O>
-__device__ __forceinline__ float gather_pairs(const float2 *P, int i0, int j0, int k0, const float (&wx)[O + 1],
-                                              const float (&wy)[O + 1], const float (&wz)[O + 1]) {
-    const float2 *base = P + wg(i0, j0, k0);
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k <= O; ++k) {
-        float sy = 0.0f;
-#pragma unroll
-        for (int j = 0; j <= O; ++j) {
-            const float2 *row = base + wg(0, j, k);
-            const float2 a = row[0];
-            float sx = wx[0] * a.x + wx[1] * a.y;
-            if constexpr (O >= 2) {
-                const float2 b = row[2];
-                sx += wx[2] * b.x;
-                if constexpr (O >= 3) sx += wx[3] * b.y;
-            }
-            sy += wy[j] * sx;
-        }
-        s += wz[k] * sy;
-    }
-    return s;
-}
-
-// E and B at a particle of the tile cell (rx, ry, rz) with offsets xi, from
-// the pair window (component c at P + c kWGVol: E_x, E_y, E_z, B_x, B_y, B_z).
-template <int O>
-__device__ __forceinline__ void gather_EB_pairs(const float2 *P, int rx, int ry, int rz, const float (&xi)[3],
-                                                float (&E)[3], float (&B)[3] PP_IF_CHECKED(, int *st)) {
-    float wI[3][O + 1], wH[3][O + 1];
-    int iI[3], iH[3];
-    const int r[3] = {rx + kRLo, ry + kRLo, rz + kRLo};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        iI[a] = r[a] + support<O, float>(xi[a], false, wI[a]);
-        iH[a] = r[a] + support<O, float>(xi[a], true, wH[a]);
-    }
-#ifdef PP_CHECKED
-    for (int a = 0; a < 3; ++a)
-        if (iI[a] < 0 || iI[a] + O >= kWG || iH[a] < 0 || iH[a] + O >= kWG) {
-            atomicOr(st, ST_BOUNDS);
-            E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = 0.0f;
-            return;
-        }
-#endif
-    // E_a: half-integer along a; B_a: integer along a, half-integer across
-    E[0] = gather_pairs<O>(P + 0 * kWGVol, iH[0], iI[1], iI[2], wH[0], wI[1], wI[2]);
-    E[1] = gather_pairs<O>(P + 1 * kWGVol, iI[0], iH[1], iI[2], wI[0], wH[1], wI[2]);
-    E[2] = gather_pairs<O>(P + 2 * kWGVol, iI[0], iI[1], iH[2], wI[0], wI[1], wH[2]);
-    B[0] = gather_pairs<O>(P + 3 * kWGVol, iI[0], iH[1], iH[2], wI[0], wH[1], wH[2]);
-    B[1] = gather_pairs<O>(P + 4 * kWGVol, iH[0], iI[1], iH[2], wH[0], wI[1], wH[2]);
-    B[2] = gather_pairs<O>(P + 5 * kWGVol, iH[0], iH[1], iI[2], wH[0], wH[1], wI[2]);
-}
 
 // Current accessor over the FP32 shared window (frame = the particle's cell).
 struct CellsCurrentAcc {
@@ -227,6 +167,7 @@ struct CellsSpecies {
 };
 
 struct CellsArgs {
+    CUtensorMap tmap[6];         // E_x, E_y, E_z, B_x, B_y, B_z: boxes of kWG^3 nodes
     Geom g;
     const float *E[3];
     const float *B[3];
@@ -406,9 +347,13 @@ __device__ __forceinline__ unsigned lanemask_lt_() {
 // One tile of one run: the whole particle step of the tile's particles (all
 // species), its current added into the run's mesh.  Called by every thread
 // of the CTA; smem is the CTA's dynamic shared memory.
-template <int O, int PUSH, bool BND>
-__device__ __forceinline__ void cells_tile(const CellsArgs &T, const int tile, float *smem) {
+// Returns false when the CTA must stop: a staging wait ran out (here or in
+// another CTA, ST_TIMEOUT).  phase: parity of the CTA's staging mbarrier, which
+// the kernel initialised.  GMAPS: the tensor maps sit in global memory.
+template <int O, int PUSH, bool BND, bool GMAPS>
+__device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, float *smem, uint32_t &phase) {
     float *F = smem;
+    uint64_t *bar = (uint64_t *)((char *)smem + kFieldBytes - 128);
     JT *Jw = (JT *)((char *)smem + kFieldBytes);
     float *s_o = (float *)(Jw + 3 * kWVol);   // 3 x kCS: offsets at t (frame of the cell)
     float *s_d = s_o + 3 * kCS;           // 3 x kCS: displacement of the step
@@ -426,46 +371,37 @@ __device__ __forceinline__ void cells_tile(const CellsArgs &T, const int tile, f
     {   // a tile that holds no particle (the mirror half of a box between walls) stages nothing
         int held = 0;
         for (int s = 0; s < T.ns; ++s) held |= T.sp[s].cell_start[key1] - T.sp[s].cell_start[key0];
-        if (!held) return;
+        if (!held) return true;
     }
-#if PP_CELLS_PAIRS
-    {   // pairs (F[i], F[i+1]) of the gather window; the last x node's pair is never read
-        float2 *P = (float2 *)smem;
-        for (int idx = threadIdx.x; idx < 6 * kWGVol; idx += kCT) {
-            const int comp = idx / kWGVol, r = idx - comp * kWGVol;
-            const int i = r % kWG, j = (r / kWG) % kWG, k = r / (kWG * kWG);
-            const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
-#ifdef PP_CHECKED
-            if (wx + i < -g.G || wx + i + 1 >= g.n[0] + g.G || wy + j < -g.G || wy + j >= g.n[1] + g.G ||
-                wz + k < -g.G || wz + k >= g.n[2] + g.G) {
-                atomicOr(T.status, ST_BOUNDS);
-                P[idx] = make_float2(0.0f, 0.0f);
-                continue;
+    // ---- the E/B window by six TMA tensor copies (array coordinates of the
+    // window's first node; the host checked that every tile's box lies inside
+    // the padded arrays with an aligned x; rechecked here, uniformly, so that
+    // no copy can start misaligned or outside)
+    const int x0 = wx + g.G, y0 = wy + g.G, z0 = wz + g.G;
+    if ((x0 & 3) || x0 < 0 || y0 < 0 || z0 < 0 || x0 + kWG > g.P[0] || y0 + kWG > g.P[1] || z0 + kWG > g.P[2]) {
+        if (threadIdx.x == 0) atomicOr(T.status, ST_BOUNDS);
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        misc[0] = misc[1] = 0;
+        // a CTA whose wait ran out stops the others at their next tile
+        misc[3] = (*(volatile int *)T.status & ST_TIMEOUT) != 0;
+        if (misc[3]) {
+            mbar_arrive(bar);
+        } else {
+            fence_proxy_async_smem();   // the previous tile's reads of F come before the copies' writes
+            mbar_arrive_expect(bar, 6 * kFBoxBytes);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                if (GMAPS) fence_tensormap_acquire(&T.tmap[c]);
+                tma_load_3d(F + c * kFComp, &T.tmap[c], x0, y0, z0, bar);
             }
-#endif
-            const int64_t at = g.at(wx + i, wy + j, wz + k);
-            P[idx] = make_float2(__ldg(src + at), i + 1 < kWG ? __ldg(src + at + 1) : 0.0f);
         }
     }
-#else
-    for (int idx = threadIdx.x; idx < 6 * kWVol; idx += kCT) {
-        const int comp = idx / kWVol, r = idx - comp * kWVol;
-        const int i = r % kW, j = (r / kW) % kW, k = r / (kW * kW);
-        const float *src = comp < 3 ? T.E[comp] : T.B[comp - 3];
-#ifdef PP_CHECKED
-        if (wx + i < -g.G || wx + i >= g.n[0] + g.G || wy + j < -g.G || wy + j >= g.n[1] + g.G || wz + k < -g.G ||
-            wz + k >= g.n[2] + g.G) {
-            atomicOr(T.status, ST_BOUNDS);
-            F[idx] = 0.0f;
-            continue;
-        }
-#endif
-        F[idx] = __ldg(src + g.at(wx + i, wy + j, wz + k));
-    }
-#endif
     for (int idx = threadIdx.x; idx < 3 * kWVol; idx += kCT) Jw[idx] = 0;
-    if (threadIdx.x < 2) misc[threadIdx.x] = 0;
-    __syncthreads();
+    if (!cta_wait_bounded(bar, phase, kStageWaitNs, T.status)) return false;
+    phase ^= 1;
+    if (misc[3]) return false;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int par = 0;   // chunk parity: selects the queue counter
@@ -517,13 +453,9 @@ __device__ __forceinline__ void cells_tile(const CellsArgs &T, const int tile, f
                 const int grp = group_of<O>(rx, ry, rz, xi0);
                 if (S.qmdt != 0.0f) {   // uniform: no kick, no force
                     float E[3], B[3];
-#if PP_CELLS_PAIRS
-                    gather_EB_pairs<O>((const float2 *)F, rx, ry, rz, xi0, E, B PP_IF_CHECKED(, T.status));
-#else
-                    CellsFieldAcc facc{F, wi(rx + kRLo, ry + kRLo, rz + kRLo)};
+                    CellsFieldAcc facc{F, fi(rx + kRLo, ry + kRLo, rz + kRLo)};
                     PP_IF_CHECKED(facc.wx = rx + kRLo; facc.wy = ry + kRLo; facc.wz = rz + kRLo; facc.st = T.status;)
                     gather_EB<O, float>(facc, xi0, E, B);
-#endif
                     push_particle<PUSH, float>(S.qmdt, S.kdt, E, B, u);
                 }
                 const float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -713,46 +645,71 @@ __device__ __forceinline__ void cells_tile(const CellsArgs &T, const int tile, f
         atomicAdd(T.J[comp] + g.at(wx + i, wy + j, wz + k), v);
     }
 #endif
+    return true;
+}
+
+// Dynamic shared memory starts 128-byte aligned (the TMA destinations); the
+// kernels check it and stop (ST_BOUNDS) otherwise.
+__device__ __forceinline__ bool smem_aligned(const float *smem, int *status) {
+    if ((smem_addr(smem) & 127) == 0) return true;
+    if (threadIdx.x == 0) atomicOr(status, ST_BOUNDS);
+    return false;
 }
 
 template <int O, int PUSH, bool BND>
 __global__ void __launch_bounds__(kCT, 1) k_particles_cells(const __grid_constant__ CellsArgs T) {
-    extern __shared__ float smem[];
-    cells_tile<O, PUSH, BND>(T, blockIdx.x, smem);
+    extern __shared__ __align__(128) float smem[];
+    if (!smem_aligned(smem, T.status)) return;
+    uint64_t *bar = (uint64_t *)((char *)smem + kFieldBytes - 128);
+    if (threadIdx.x == 0) mbar_init(bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    cells_tile<O, PUSH, BND, false>(T, blockIdx.x, smem, phase);
 }
 
 // Batched form: the tiles of many runs as (run, tile) work items, taken in
 // order by persistent CTAs from a device counter (the items come sorted by
 // run size, largest first, so that the last items are short).  Every run's
-// arguments sit in device memory.
+// arguments, tensor maps included, sit in device memory.
 template <int O, int PUSH, bool BND>
 __global__ void __launch_bounds__(kCT, 1) k_particles_cells_multi(const CellsArgs *args, const int2 *items,
-                                                                 int nitems, int *next) {
-    extern __shared__ float smem[];
-    __shared__ int item;
+                                                                 int nitems, int *next, int *status) {
+    extern __shared__ __align__(128) float smem[];
+    if (!smem_aligned(smem, status)) return;
+    uint64_t *bar = (uint64_t *)((char *)smem + kFieldBytes - 128);
+    int *item = (int *)(bar + 2);
+    if (threadIdx.x == 0) mbar_init(bar);
+    uint32_t phase = 0;
     for (;;) {
-        if (threadIdx.x == 0) item = atomicAdd(next, 1);
+        if (threadIdx.x == 0) *item = atomicAdd(next, 1);
         __syncthreads();
-        const int w = item;
+        const int w = *item;
         __syncthreads();   // every thread has read it before thread 0 takes the next
         if (w >= nitems) return;
         const int2 it = items[w];
-        cells_tile<O, PUSH, BND>(args[it.x], it.y, smem);
+        if (!cells_tile<O, PUSH, BND, true>(args[it.x], it.y, smem, phase)) return;
         __syncthreads();
     }
 }
 
 }  // namespace
 
+// Besides the tile shape: every tile's TMA box starts at an x that is a
+// multiple of 4 nodes (G - kRLo is, and tile origins are multiples of 8) and
+// ends inside the padded row (G >= kWG - kT - kRLo), with rows of a multiple
+// of 16 bytes.
 bool cells_supported(const Ctx &c) {
     if (c.fp64 || c.current_mode != PP_CURRENT_CONSERVING || c.g.G < kRLo || c.g.G < kRHi) return false;
+    if ((c.g.G - kRLo) % 4 != 0 || c.g.G < kWG - kT - kRLo || c.g.P[0] % 4 != 0) return false;
     for (int a = 0; a < 3; ++a)
         if (c.g.n[a] % kT != 0 || c.tile[a] != kT) return false;
     return true;
 }
 
-// The argument block of one context: false when no species holds particles.
-static bool cells_args(const Ctx &c, CellsArgs &T) {
+// The argument block of one context, with the tensor maps of its E and B
+// arrays; any = false when no species holds particles.
+static cudaError_t cells_args(const Ctx &c, CellsArgs &T, bool &any) {
+    any = false;
     T.g = c.g;
     const double h[3] = {c.d.dx, c.d.dy, c.d.dz};
     for (int d = 0; d < 3; ++d) {
@@ -761,6 +718,11 @@ static bool cells_args(const Ctx &c, CellsArgs &T) {
         T.J[d] = (float *)c.J[d];
         T.dtdx[d] = (float)(c.drift_dt / h[d]);
         T.nt[d] = c.ntile[d];
+    }
+    const int box[3] = {kWG, kWG, kWG};
+    for (int comp = 0; comp < 6; ++comp) {
+        cudaError_t e = encode_box_map(&T.tmap[comp], comp < 3 ? T.E[comp] : T.B[comp - 3], c.g.P, box);
+        if (e != cudaSuccess) return e;
     }
     T.ns = 0;
     for (int s = 0; s < c.nspecies; ++s) {
@@ -782,7 +744,8 @@ static bool cells_args(const Ctx &c, CellsArgs &T) {
     for (int d = 0; d < 3; ++d) T.wall[d] = c.wall[d];
     T.esc = c.escape_now;
     T.dead_key = (int32_t)c.nkeys;
-    return T.ns > 0;
+    any = T.ns > 0;
+    return cudaSuccess;
 }
 
 static bool cells_ready(const Ctx &c) {
@@ -817,7 +780,9 @@ cudaError_t launch_particles_cells(Ctx &c) {
     if (!cells_supported(c)) return cudaErrorInvalidConfiguration;
     if (!cells_ready(c)) return cudaErrorInvalidValue;
     CellsArgs T;
-    if (!cells_args(c, T)) return cudaSuccess;
+    bool any = false;
+    cudaError_t ea = cells_args(c, T, any);
+    if (ea != cudaSuccess || !any) return ea;
     const unsigned blocks = (unsigned)(c.ntile[0] * c.ntile[1] * c.ntile[2]);
     const int o = c.d.shape_order, pu = c.d.pusher;
     const bool bnd = c.any_wall();
@@ -864,7 +829,10 @@ cudaError_t launch_particles_cells_batch(Ctx *const *ctxs, int n, cudaStream_t s
     for (int k = 0; k < n && m < 4096; ++k) {
         Ctx &c = *ctxs[k];
         if (!cells_supported(c) || !cells_ready(c)) return cudaErrorInvalidValue;
-        if (cells_args(c, A[m])) order[m++] = k;
+        bool any = false;
+        cudaError_t ea = cells_args(c, A[m], any);
+        if (ea != cudaSuccess) return ea;
+        if (any) order[m++] = k;
     }
     int64_t ntot = 0;
     for (int a = 0; a < m; ++a) {   // insertion sort by tile count, descending
@@ -899,7 +867,7 @@ cudaError_t launch_particles_cells_batch(Ctx *const *ctxs, int n, cudaStream_t s
         cudaError_t e_ = smem_attr(k_particles_cells_multi<O, PU, BD>, attr_done[BD][PU][O]);                \
         if (e_ != cudaSuccess) return e_;                                                                    \
         k_particles_cells_multi<O, PU, BD><<<grid, kCT, kCellsSmem, st>>>(                                   \
-            (const CellsArgs *)scr.args, (const int2 *)scr.items, (int)ntot, scr.next);                      \
+            (const CellsArgs *)scr.args, (const int2 *)scr.items, (int)ntot, scr.next, c0.d_status);         \
     } while (0)
 #define PP_M(O, PU)                                                                                          \
     do {                                                                                                     \

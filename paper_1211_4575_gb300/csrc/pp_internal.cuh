@@ -17,8 +17,11 @@ namespace pp {
 // x fastest.  Interior index (i,j,k) in [0,n) maps to the padded offset below.
 // ---------------------------------------------------------------------------
 constexpr int kSubKeys = 8;  // sort sub-keys per cell: the octant of the particle inside it
-constexpr int kGhost = 5;   // covers the deposit reach of a particle sorted up to
-                            // two cells outside its tile plus the PCS support
+// Ghost layers per side: 5 cover the deposit reach of a particle sorted up to
+// two cells outside its tile plus the PCS support; the sixth makes the padded
+// row (n + 12 nodes) a multiple of 16 bytes in FP32 for every n that is a
+// multiple of 8, as the TMA tensor maps of the per-step kernel require.
+constexpr int kGhost = 6;
 
 struct Geom {
     int n[3];     // interior cells
@@ -45,7 +48,7 @@ __host__ __device__ __forceinline__ int wrap(int i, int n) {
 }
 
 // Device status bits (collected into one word, mapped to PP_* on the host).
-enum : int { ST_NAN = 1, ST_CFL = 2, ST_NOCONV = 4, ST_RANGE = 8, ST_BOUNDS = 16 };
+enum : int { ST_NAN = 1, ST_CFL = 2, ST_NOCONV = 4, ST_RANGE = 8, ST_BOUNDS = 16, ST_TIMEOUT = 32 };
 
 // Checked build (-DPP_CHECKED): the particle kernels test every mesh and
 // shared-memory index against its array; a violation sets ST_BOUNDS in the

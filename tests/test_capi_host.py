@@ -90,13 +90,13 @@ def test_batch_create_validation_without_gpu(built):
 
 def test_device_bytes_estimate_is_host_only_arithmetic():
     """pp_estimate_device_bytes needs no device: 21 padded mesh arrays (ghost
-    width 5), FP64 rho and Gauss reference, per species two particle buffers
+    width 6), FP64 rho and Gauss reference, per species two particle buffers
     of the rounded capacity, keys and permutation, per-key offsets and the
     sort counters (8 octant keys per tile-padded cell)."""
     import paper_1211_4575_gb300 as pp
     n, caps = (16, 24, 8), [1000, 0]
     got = pp.estimate_device_bytes(n, caps, pp.PP_MIXED32)
-    padded = (16 + 10) * (24 + 10) * (8 + 10)
+    padded = (16 + 12) * (24 + 12) * (8 + 12)
     cells = 16 * 24 * 8
     nkeys = 8 * 16 * 24 * 8
     rounded = [1024, 64]
@@ -104,7 +104,7 @@ def test_device_bytes_estimate_is_host_only_arithmetic():
     assert got == expect
     # walls on x double the mesh along x; FP64 particles are 48 B and carry no permutation
     got64 = pp.estimate_device_bytes(n, [64], pp.PP_FP64, (pp.PP_BOUNDARY_WALLS, 0, 0))
-    padded64 = (32 + 10) * (24 + 10) * (8 + 10)
+    padded64 = (32 + 12) * (24 + 12) * (8 + 12)
     nk64 = 8 * 32 * 24 * 8
     assert got64 == padded64 * 8 * 21 + 16 * 32 * 24 * 8 + 2 * 48 * 64 + 4 * 64 + 4 * (nk64 + 1) + 4 * (nk64 + 1)
     assert pp.estimate_device_bytes(n, [-1]) == 0

@@ -59,3 +59,40 @@ def test_capacity_and_species_limits(pp):
     with pytest.raises(pp.PPError) as ei:
         sim.load_particles(0, *[np.zeros(2)] * 6)
     assert ei.value.code == pp.PP_ENOMEM
+
+
+def test_staging_wait_runs_out_into_etimeout_and_context_survives(pp):
+    """The per-step sorted kernel stages each tile's E/B window with TMA tensor
+    copies and waits on an mbarrier for at most a second.  The same bounded
+    wait run once on a barrier whose phase completes returns PP_OK; on one
+    that waits for 16 bytes no copy delivers it runs out and returns
+    PP_ETIMEOUT after about twice its limit (the CTA waits once more for
+    copies in flight), with no fault: the context then steps on as one that
+    never met the timeout."""
+    import time
+    L = pp_synth.thermal(n=(16, 16, 16), ppc=4, seed=31)
+    a = H.gpu_sim(pp, L, pp.PP_MIXED32, 3, deposit_mode=pp.PP_DEPOSIT_CELLS)
+    b = H.gpu_sim(pp, L, pp.PP_MIXED32, 3, deposit_mode=pp.PP_DEPOSIT_CELLS)
+    a.step(1)
+    b.step(1)
+    assert a.check_bounded_wait(True, 1_000_000) == pp.PP_OK
+    t0 = time.perf_counter()
+    rc = a.check_bounded_wait(False, 5_000_000)
+    dt = time.perf_counter() - t0
+    assert rc == pp.PP_ETIMEOUT
+    assert 0.009 <= dt < 5.0
+    assert a.check_bounded_wait(True, 1_000_000) == pp.PP_OK   # the status word was cleared
+    assert a.check_bounded_wait(False, 0) == pp.PP_EINVAL
+    a.step(3)
+    b.step(3)
+    a.sync()
+    b.sync()
+    for s in range(2):
+        pa, pb = a.particles(s), b.particles(s)
+        assert a.count(s) == b.count(s) == len(L.species[s]["x"])
+        for k in ("ux", "uy", "uz"):
+            np.testing.assert_allclose(np.sort(pa[k]), np.sort(pb[k]), rtol=0, atol=1e-5)
+    da, db = a.diagnostics(), b.diagnostics()
+    assert da["status"] == pp.PP_OK
+    ea, eb = da["energy_E"] + da["energy_B"], db["energy_E"] + db["energy_B"]
+    assert abs(ea - eb) <= 1e-4 * abs(eb)
