@@ -181,67 +181,100 @@ __global__ void k_scatter_mixed(int64_t n, const int32_t *keys, int32_t *cursor,
 
 // Sort from keys a particle pass already wrote (Species::keys_valid): the
 // histogram of the keys, then, through the per-key cursors, the permutation
-// perm[slot] = particle instead of moving the particles.  The keys of a block
-// of consecutive particles (in the last sort's order) lie in a short range, so
-// each block counts its keys in shared memory and reserves one run of slots
-// per distinct key with a single global atomic; keys outside the block's
-// window (a particle that left, a far jump) take a global atomic of their own.
+// perm[slot] = particle instead of moving the particles.  The keys sit in the
+// last sort's slot order and each particle moved at most a cell, so the keys
+// of a block of consecutive slots lie in a short range: each block counts its
+// kAggSpan keys in a shared window and reserves one run of slots per distinct
+// key with a single global atomic; keys outside the window (a particle that
+// left, a far jump) take a global atomic of their own.  The window starts
+// kAggMargin keys below the median of the block's first three keys (robust to
+// one of them having jumped), which leaves room for particles that moved down
+// a cell in z.
 constexpr int kAggThreads = 1024;
-constexpr int kAggWindow = 4096;   // keys counted in shared memory per block
+constexpr int kAggPer = 8;                          // keys per thread
+constexpr int kAggSpan = kAggThreads * kAggPer;     // keys per block
+constexpr int kAggWindow = 8192;                    // window of keys counted in shared memory
+constexpr int kAggMargin = 1024;
+constexpr int32_t kNoKey = 0x7fffffff;
 
-__device__ __forceinline__ int32_t block_min_key(int32_t k, int32_t *sh) {
-    // smallest live key of the block (keys >= sentinel are ignored)
-    int32_t v = k;
+// The kAggPer keys of this thread: two runs of four consecutive slots, each
+// one 16-byte load when whole (slot of key 4h + m: base + 4 h kAggThreads + 4 tid + m).
+__device__ __forceinline__ void load_keys(const int32_t *keys, int64_t n, int64_t base, int32_t (&k)[kAggPer]) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int32_t w = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0x7fffffff;
+    for (int h = 0; h < kAggPer / 4; ++h) {
+        const int64_t q = base + (int64_t)h * 4 * kAggThreads + 4 * threadIdx.x;
+        if (q + 3 < n) {
+            const int4 v = __ldg(reinterpret_cast<const int4 *>(keys + q));
+            k[4 * h] = v.x;
+            k[4 * h + 1] = v.y;
+            k[4 * h + 2] = v.z;
+            k[4 * h + 3] = v.w;
+        } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w = min(w, __shfl_xor_sync(0xffffffffu, w, o));
-        if (threadIdx.x == 0) sh[32] = w;
+            for (int m = 0; m < 4; ++m) k[4 * h + m] = q + m < n ? keys[q + m] : kNoKey;
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t key_slot(int64_t base, int i) {
+    return base + (int64_t)(i >> 2) * 4 * kAggThreads + 4 * threadIdx.x + (i & 3);
+}
+
+// First key of the block's window (same value in every thread).
+__device__ __forceinline__ int32_t window_start(const int32_t *keys, int64_t n, int64_t base, int32_t *sh) {
+    if (threadIdx.x == 0) {
+        const int32_t a = keys[base], b = base + 1 < n ? keys[base + 1] : a, c = base + 2 < n ? keys[base + 2] : a;
+        const int32_t med = max(min(a, b), min(max(a, b), c));
+        sh[0] = med - kAggMargin;
     }
     __syncthreads();
-    return sh[32];
+    return sh[0];
 }
 
 __global__ void __launch_bounds__(kAggThreads) k_hist(int64_t n, const int32_t *keys, int32_t *counts) {
     __shared__ int32_t cnt[kAggWindow];
-    __shared__ int32_t red[33];
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t key = t < n ? keys[t] : 0x7fffffff;
-    const int32_t k0 = block_min_key(key, red);
-    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    if (t < n) {
-        const int32_t r = key - k0;
-        if (r < kAggWindow) atomicAdd(cnt + r, 1);
-        else atomicAdd(counts + key, 1);
+    __shared__ int32_t k0s;
+    const int64_t base = (int64_t)blockIdx.x * kAggSpan;
+    int32_t k[kAggPer];
+    load_keys(keys, n, base, k);
+    for (int i = threadIdx.x; i < kAggWindow; i += kAggThreads) cnt[i] = 0;
+    const int32_t k0 = window_start(keys, n, base, &k0s);
+#pragma unroll
+    for (int i = 0; i < kAggPer; ++i) {
+        if (k[i] == kNoKey) continue;
+        const uint32_t r = (uint32_t)k[i] - (uint32_t)k0;
+        if (r < (uint32_t)kAggWindow) atomicAdd(cnt + r, 1);
+        else atomicAdd(counts + k[i], 1);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x)
+    for (int i = threadIdx.x; i < kAggWindow; i += kAggThreads)
         if (cnt[i]) atomicAdd(counts + k0 + i, cnt[i]);
 }
 
 __global__ void __launch_bounds__(kAggThreads) k_perm(int64_t n, const int32_t *keys, int32_t *cursor, int32_t *perm) {
     __shared__ int32_t cnt[kAggWindow];   // block-local rank counters, then the reserved bases
-    __shared__ int32_t red[33];
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t key = t < n ? keys[t] : 0x7fffffff;
-    const int32_t k0 = block_min_key(key, red);
-    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x) cnt[i] = 0;
+    __shared__ int32_t k0s;
+    const int64_t base = (int64_t)blockIdx.x * kAggSpan;
+    int32_t k[kAggPer], rank[kAggPer];
+    load_keys(keys, n, base, k);
+    for (int i = threadIdx.x; i < kAggWindow; i += kAggThreads) cnt[i] = 0;
+    const int32_t k0 = window_start(keys, n, base, &k0s);
+#pragma unroll
+    for (int i = 0; i < kAggPer; ++i) {
+        const uint32_t r = (uint32_t)k[i] - (uint32_t)k0;
+        rank[i] = (k[i] != kNoKey && r < (uint32_t)kAggWindow) ? atomicAdd(cnt + r, 1) : -1;
+    }
     __syncthreads();
-    const int32_t r = key - k0;
-    const bool local = t < n && r < kAggWindow;
-    int32_t rank = 0;
-    if (local) rank = atomicAdd(cnt + r, 1);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kAggWindow; i += blockDim.x)
+    for (int i = threadIdx.x; i < kAggWindow; i += kAggThreads)
         if (cnt[i]) cnt[i] = atomicAdd(cursor + k0 + i, cnt[i]);
     __syncthreads();
-    if (local) perm[cnt[r] + rank] = (int32_t)t;
-    else if (t < n) perm[atomicAdd(cursor + key, 1)] = (int32_t)t;
+#pragma unroll
+    for (int i = 0; i < kAggPer; ++i) {
+        if (k[i] == kNoKey) continue;
+        const int32_t slot =
+            rank[i] >= 0 ? cnt[(uint32_t)k[i] - (uint32_t)k0] + rank[i] : atomicAdd(cursor + k[i], 1);
+        perm[slot] = (int32_t)key_slot(base, i);
+    }
 }
 
 // dst[i] = src[perm[i]] for the seven arrays of the mixed form.
@@ -327,7 +360,7 @@ cudaError_t launch_sort(Ctx &c, int s) {
     }
     KeyGeom kg = key_geom(c);
     unsigned blocks = (unsigned)((S.n + 255) / 256);
-    const unsigned ablocks = (unsigned)((S.n + kAggThreads - 1) / kAggThreads);
+    const unsigned ablocks = (unsigned)((S.n + kAggSpan - 1) / kAggSpan);
     if (lazy) k_hist<<<ablocks, kAggThreads, 0, c.st>>>(S.n, S.keys, c.counts);
     else if (c.fp64) k_keys_fp64<<<blocks, 256, 0, c.st>>>(kg, S.n, S.x, S.y, S.z, S.keys, c.counts);
     else k_keys_mixed<<<blocks, 256, 0, c.st>>>(kg, S.n, S.cell, S.ox, S.oy, S.oz, S.keys, c.counts);
