@@ -501,42 +501,105 @@ __global__ void k_rhs_lin(Geom g, FieldCoef k, Vec3<R> E, Vec3<R> B, Vec3<R> J, 
     }
 }
 
-// k_cheb on an iterate X with valid ghost layers; writes the new iterate with
-// its ghost images (so the next sweep reads it the same way).
-template <typename R>
-__global__ void k_cheb_lin(Geom g, FieldCoef k, Vec3<R> X, Vec3<R> Xp, Vec3<R> Rh, R *O0, R *O1, R *O2, R kk, R c1,
-                           R c2) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n[0]) return;
-    int j = blockIdx.y, kz = blockIdx.z;
-    NbLin<R> nl = nb_lin<R>(g, i, j, kz);
-    R *out[3] = {O0, O1, O2};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        R x = X.p[a][nl.q];
-        R r = Rh.p[a][nl.q] - x + kk * nl.lap(X.p[a], k);
-        R xp = Xp.p[a][nl.q];
-        store_periodic(out[a], g, i, j, kz, x + c1 * (x - xp) + c2 * r);
-    }
-}
+// One Chebyshev sweep (Saad's three-term form, see field_update_impl), plane by
+// plane: r = rhs - X + kk L X, X_new = X + c1 (X - X_prev) + c2 r, with each
+// component's 31-point Laplacian (NbLin::lap, the same sums in the same order) read
+// from a shared xy plane (the block's 32 x 8 nodes and 5 nodes of halo on each
+// side) and a register column of the 11 z nodes around the plane.  A block
+// marches through kChebZ planes of one component, so every node of X comes
+// from L2 or HBM about three times (column, halo, chunk start) instead of 31.
+// Planes per block: 8 measured best (C3 beam field update 2.62 ms per step
+// against 2.68 at 16 and 2.91 at 32; 3.80 for the node-per-thread sweep that
+// read every neighbour through L1/L2).
+#ifndef PP_CHEB_Z
+#define PP_CHEB_Z 8
+#endif
+constexpr int kChebBX = 32, kChebBY = 8, kChebZ = PP_CHEB_Z, kChebR = 5;
 
-// One Chebyshev semi-iteration step for (1 - kk L) x = rhs:
-// x_new = x + c1 (x - x_prev) + c2 (rhs - x + kk L x); x_new may alias x_prev.
 template <typename R>
-__global__ void k_cheb(Geom g, FieldCoef k, Vec3<R> X, Vec3<R> Xp, Vec3<R> Rh, R *O0, R *O1, R *O2, R kk, R c1,
-                       R c2) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.cells()) return;
-    Nb<R> nb{g, {0, 0, 0}};
-    unflatten(t, g, nb.c[0], nb.c[1], nb.c[2]);
-    int64_t q = g.at(nb.c[0], nb.c[1], nb.c[2]);
-    R *out[3] = {O0, O1, O2};
+__global__ void __launch_bounds__(kChebBX *kChebBY) k_cheb_plane(Geom g, FieldCoef k, Vec3<R> X, Vec3<R> Xp, Vec3<R> Rh,
+                                                                 R *O0, R *O1, R *O2, R kk, R c1, R c2, int nzc) {
+    __shared__ R pl[kChebBY + 2 * kChebR][kChebBX + 2 * kChebR];
+    const int tx = threadIdx.x % kChebBX, ty = threadIdx.x / kChebBX;
+    const int x0 = blockIdx.x * kChebBX, y0 = blockIdx.y * kChebBY;
+    const int a = blockIdx.z / nzc, zc = blockIdx.z - a * nzc;
+    const int z0 = zc * kChebZ, z1 = min(g.n[2], z0 + kChebZ);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool mine = i < g.n[0] && j < g.n[1];
+    // the component's arrays, selected without indexing the parameter arrays
+    // at run time (which would copy them to local memory)
+    const R *f = a == 0 ? X.p[0] : (a == 1 ? X.p[1] : X.p[2]);
+    const R *fp = a == 0 ? Xp.p[0] : (a == 1 ? Xp.p[1] : Xp.p[2]);
+    const R *rh = a == 0 ? Rh.p[0] : (a == 1 ? Rh.p[1] : Rh.p[2]);
+    R *out = a == 0 ? O0 : (a == 1 ? O1 : O2);
+    // a node inside the padded array (every node a computed node reads is)
+    auto val = [&](int x, int y, int z) -> R {
+        return (x >= -g.G && x < g.n[0] + g.G && y >= -g.G && y < g.n[1] + g.G) ? f[g.at(x, y, z)] : R(0);
+    };
+    R col[2 * kChebR + 1];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        R x = X.p[a][q];
-        R r = Rh.p[a][q] - x + kk * nb.lap(X.p[a], k);
-        R xp = Xp.p[a][q];
-        out[a][q] = x + c1 * (x - xp) + c2 * r;
+    for (int m = 0; m < 2 * kChebR + 1; ++m) col[m] = val(i, j, z0 - kChebR + m);
+    R lp[kChebR + 1];
+#pragma unroll
+    for (int o = 0; o <= kChebR; ++o) lp[o] = (R)k.lap[o];
+    const R ih2x = (R)k.ih2[0], ih2y = (R)k.ih2[1], ih2z = (R)k.ih2[2];
+    // the next plane's halo nodes, rhs and previous iterate are loaded one
+    // plane ahead, so that their latency overlaps the current plane's work
+    R hx0 = R(0), hx1 = R(0), hy0 = R(0), hy1 = R(0), rhn = R(0), xpn = R(0);
+    auto fetch = [&](int z) {
+        if (tx < kChebR) {
+            hx0 = val(x0 + tx - kChebR, j, z);
+            hx1 = val(x0 + kChebBX + tx, j, z);
+        }
+        if (ty < kChebR) {
+            hy0 = val(i, y0 + ty - kChebR, z);
+            hy1 = val(i, y0 + kChebBY + ty, z);
+        }
+        if (mine) {
+            const int64_t q = g.at(i, j, z);
+            rhn = rh[q];
+            xpn = fp[q];
+        }
+    };
+    fetch(z0);
+    for (int z = z0; z < z1; ++z) {
+        pl[ty + kChebR][tx + kChebR] = col[kChebR];
+        if (tx < kChebR) {
+            pl[ty + kChebR][tx] = hx0;
+            pl[ty + kChebR][tx + kChebBX + kChebR] = hx1;
+        }
+        if (ty < kChebR) {
+            pl[ty][tx + kChebR] = hy0;
+            pl[ty + kChebBY + kChebR][tx + kChebR] = hy1;
+        }
+        const R rhz = rhn, xpz = xpn;
+        __syncthreads();
+        if (z + 1 < z1) fetch(z + 1);
+        if (mine) {
+            const R center = col[kChebR];
+            R v = R(0);
+            R sa = lp[0] * center;
+#pragma unroll
+            for (int o = 1; o <= kChebR; ++o)
+                sa += lp[o] * (pl[ty + kChebR][tx + kChebR + o] + pl[ty + kChebR][tx + kChebR - o]);
+            v += sa * ih2x;
+            sa = lp[0] * center;
+#pragma unroll
+            for (int o = 1; o <= kChebR; ++o)
+                sa += lp[o] * (pl[ty + kChebR + o][tx + kChebR] + pl[ty + kChebR - o][tx + kChebR]);
+            v += sa * ih2y;
+            sa = lp[0] * center;
+#pragma unroll
+            for (int o = 1; o <= kChebR; ++o) sa += lp[o] * (col[kChebR + o] + col[kChebR - o]);
+            v += sa * ih2z;
+            const R x = center;
+            const R r = rhz - x + kk * v;
+            store_periodic(out, g, i, j, z, x + c1 * (x - xpz) + c2 * r);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 2 * kChebR; ++m) col[m] = col[m + 1];
+        if (z + 1 < z1) col[2 * kChebR] = val(i, j, z + 1 + kChebR);
     }
 }
 
@@ -641,6 +704,9 @@ static cudaError_t field_update_impl(Ctx &c) {
     // Chebyshev semi-iteration on the spectrum [1, lmax] of the SPD operator,
     // starting from B^n (Saad, Iterative Methods, Alg. 12.1 in 3-term form).
     double theta = ch.theta, delta = ch.delta;
+    const int nzc = (g.n[2] + kChebZ - 1) / kChebZ;
+    const dim3 pg((unsigned)((g.n[0] + kChebBX - 1) / kChebBX), (unsigned)((g.n[1] + kChebBY - 1) / kChebBY),
+                  (unsigned)(3 * nzc));
     void **cur = c.B, **prev = c.B;
     void **bufs[2] = {c.Xa, c.Xb};
     int nb = 0;
@@ -660,8 +726,9 @@ static cudaError_t field_update_impl(Ctx &c) {
         // output: a scratch buffer that is neither cur nor (when prev is B) B
         void **out = (prev == c.B || prev == cur) ? bufs[nb] : prev;
         if (out == cur) out = bufs[1 - nb];
-        k_cheb_lin<R><<<cg, kCellThreads, 0, c.st>>>(g, k, v3<R>(cur), v3<R>(prev), v3<R>(c.R), (R *)out[0],
-                                                     (R *)out[1], (R *)out[2], (R)kk, (R)c1, (R)c2);
+        k_cheb_plane<R><<<pg, kChebBX * kChebBY, 0, c.st>>>(g, k, v3<R>(cur), v3<R>(prev), v3<R>(c.R),
+                                                             (R *)out[0], (R *)out[1], (R *)out[2], (R)kk, (R)c1,
+                                                             (R)c2, nzc);
         ++c.nlaunch;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         prev = cur;
