@@ -379,7 +379,7 @@ extern "C" int pp_set_radiative_cooling(pp_ctx *p, int sid, double coef) {
 // ---------------------------------------------------------------------------
 static int refresh_gauss_reference(Ctx *c) {
     double tmp[16];
-    CU(launch_rho(*c));
+    CU(launch_rho(*c, true));
     c->have_G0 = false;
     CU(launch_mesh_diag(*c, tmp));
     CU(cudaStreamSynchronize(c->st));
@@ -1174,7 +1174,7 @@ extern "C" int pp_diagnostics(pp_ctx *p, pp_diag *out) {
     double mesh[16], kin[PP_MAX_SPECIES];
     unsigned long long nslow = 0;
     CU(cudaMemcpyAsync(&nslow, c->d_nslow, sizeof nslow, cudaMemcpyDeviceToHost, c->st));
-    CU(launch_rho(*c));
+    CU(launch_rho(*c, true));
     CU(launch_kinetic(*c, c->d_out + 16));
     CU(launch_mesh_diag(*c, mesh));
     CU(cudaMemcpyAsync(kin, c->d_out + 16, sizeof(double) * PP_MAX_SPECIES, cudaMemcpyDeviceToHost, c->st));
@@ -1354,7 +1354,7 @@ extern "C" int pp_extract_particles(pp_ctx *p, int sid, int64_t cap, double *x, 
 extern "C" int pp_get_rho(pp_ctx *p, double *rho) {
     Ctx *c = p;
     if (!c || !rho) return fail(c, PP_EINVAL, "pp_get_rho: NULL argument");
-    CU(launch_rho(*c));
+    CU(launch_rho(*c, true));
     CU(cudaMemcpyAsync(rho, c->rho, sizeof(double) * c->g.cells(), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
     return PP_OK;

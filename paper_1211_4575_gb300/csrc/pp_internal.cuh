@@ -648,7 +648,11 @@ size_t cells_args_bytes();
 bool batch_fusable(const Ctx *c);
 int batch_step_pre(Ctx *c);
 int batch_step_post(Ctx *c);
-cudaError_t launch_rho(Ctx &c);
+// sort_first (calls outside a step: diagnostics, the Gauss reference, rho
+// readback): a mixed-form species whose particles are unsorted, or that the
+// per-step sorted kernel left with fresh keys, is sorted first, so that every
+// particle sits in its sorted cell and the tile kernel adds none directly.
+cudaError_t launch_rho(Ctx &c, bool sort_first = false);
 cudaError_t launch_kinetic(Ctx &c, double *out_per_species);
 
 cudaError_t launch_zero_J(Ctx &c);

@@ -1132,8 +1132,13 @@ __global__ void __launch_bounds__(512) k_rho_tile(Geom g, RhoCellGeom kg, const 
     }
 }
 
-cudaError_t launch_rho(Ctx &c) {
+cudaError_t launch_rho(Ctx &c, bool sort_first) {
     for (int s = 0; s < c.nspecies; ++s) {
+        const Species &S = c.sp[s];
+        if (sort_first && !c.fp64 && S.n > 0 && (S.keys_valid || !S.sorted)) {
+            cudaError_t es = launch_sort(c, s);
+            if (es != cudaSuccess) return es;
+        }
         cudaError_t em = materialize(c, s);
         if (em != cudaSuccess) return em;
     }

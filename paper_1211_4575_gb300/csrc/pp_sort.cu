@@ -195,6 +195,7 @@ constexpr int kAggPer = 8;                          // keys per thread
 constexpr int kAggSpan = kAggThreads * kAggPer;     // keys per block
 constexpr int kAggWindow = 8192;                    // window of keys counted in shared memory
 constexpr int kAggMargin = 1024;
+static_assert(kAggWindow % kAggThreads == 0, "window must split evenly over the block");
 constexpr int32_t kNoKey = 0x7fffffff;
 
 // The kAggPer keys of this thread: two runs of four consecutive slots, each
@@ -265,8 +266,14 @@ __global__ void __launch_bounds__(kAggThreads) k_perm(int64_t n, const int32_t *
         rank[i] = (k[i] != kNoKey && r < (uint32_t)kAggWindow) ? atomicAdd(cnt + r, 1) : -1;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kAggWindow; i += kAggThreads)
-        if (cnt[i]) cnt[i] = atomicAdd(cursor + k0 + i, cnt[i]);
+    // one reservation per distinct key; the loop is unrolled so that a
+    // thread's atomics (each waits for its returned base) are all in flight
+#pragma unroll
+    for (int m = 0; m < kAggWindow / kAggThreads; ++m) {
+        const int i = threadIdx.x + m * kAggThreads;
+        const int32_t c = cnt[i];
+        if (c) cnt[i] = atomicAdd(cursor + k0 + i, c);
+    }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kAggPer; ++i) {
