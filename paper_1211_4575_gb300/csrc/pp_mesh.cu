@@ -532,13 +532,23 @@ __global__ void __launch_bounds__(kChebBX *kChebBY) k_cheb_plane(Geom g, FieldCo
     const R *fp = a == 0 ? Xp.p[0] : (a == 1 ? Xp.p[1] : Xp.p[2]);
     const R *rh = a == 0 ? Rh.p[0] : (a == 1 ? Rh.p[1] : Rh.p[2]);
     R *out = a == 0 ? O0 : (a == 1 ? O1 : O2);
-    // a node inside the padded array (every node a computed node reads is)
-    auto val = [&](int x, int y, int z) -> R {
-        return (x >= -g.G && x < g.n[0] + g.G && y >= -g.G && y < g.n[1] + g.G) ? f[g.at(x, y, z)] : R(0);
-    };
+    // Each thread reads at most five x, y positions of the padded array (its
+    // column and up to four halo nodes); their plane-0 offsets and whether
+    // they lie inside the padded array (every node a computed node reads
+    // does) are fixed for the whole march.
+    const int64_t ps = (int64_t)g.P[0] * g.P[1];
+    auto inside = [&](int x, int y) { return x >= -g.G && x < g.n[0] + g.G && y >= -g.G && y < g.n[1] + g.G; };
+    const bool okc = inside(i, j);
+    const int64_t qc = okc ? g.at(i, j, 0) : 0;
+    const bool okx0 = tx < kChebR && inside(x0 + tx - kChebR, j), okx1 = tx < kChebR && inside(x0 + kChebBX + tx, j);
+    const bool oky0 = ty < kChebR && inside(i, y0 + ty - kChebR), oky1 = ty < kChebR && inside(i, y0 + kChebBY + ty);
+    const int64_t qx0 = okx0 ? g.at(x0 + tx - kChebR, j, 0) : 0, qx1 = okx1 ? g.at(x0 + kChebBX + tx, j, 0) : 0;
+    const int64_t qy0 = oky0 ? g.at(i, y0 + ty - kChebR, 0) : 0, qy1 = oky1 ? g.at(i, y0 + kChebBY + ty, 0) : 0;
+    // no periodic image of this column's nodes inside the ghost layers on x or y
+    const bool noimg_xy = i >= g.G && i < g.n[0] - g.G && j >= g.G && j < g.n[1] - g.G;
     R col[2 * kChebR + 1];
 #pragma unroll
-    for (int m = 0; m < 2 * kChebR + 1; ++m) col[m] = val(i, j, z0 - kChebR + m);
+    for (int m = 0; m < 2 * kChebR + 1; ++m) col[m] = okc ? f[qc + (int64_t)(z0 - kChebR + m) * ps] : R(0);
     R lp[kChebR + 1];
 #pragma unroll
     for (int o = 0; o <= kChebR; ++o) lp[o] = (R)k.lap[o];
@@ -547,18 +557,14 @@ __global__ void __launch_bounds__(kChebBX *kChebBY) k_cheb_plane(Geom g, FieldCo
     // plane ahead, so that their latency overlaps the current plane's work
     R hx0 = R(0), hx1 = R(0), hy0 = R(0), hy1 = R(0), rhn = R(0), xpn = R(0);
     auto fetch = [&](int z) {
-        if (tx < kChebR) {
-            hx0 = val(x0 + tx - kChebR, j, z);
-            hx1 = val(x0 + kChebBX + tx, j, z);
-        }
-        if (ty < kChebR) {
-            hy0 = val(i, y0 + ty - kChebR, z);
-            hy1 = val(i, y0 + kChebBY + ty, z);
-        }
+        const int64_t zo = (int64_t)z * ps;
+        if (okx0) hx0 = f[qx0 + zo];
+        if (okx1) hx1 = f[qx1 + zo];
+        if (oky0) hy0 = f[qy0 + zo];
+        if (oky1) hy1 = f[qy1 + zo];
         if (mine) {
-            const int64_t q = g.at(i, j, z);
-            rhn = rh[q];
-            xpn = fp[q];
+            rhn = rh[qc + zo];
+            xpn = fp[qc + zo];
         }
     };
     fetch(z0);
@@ -594,12 +600,16 @@ __global__ void __launch_bounds__(kChebBX *kChebBY) k_cheb_plane(Geom g, FieldCo
             v += sa * ih2z;
             const R x = center;
             const R r = rhz - x + kk * v;
-            store_periodic(out, g, i, j, z, x + c1 * (x - xpz) + c2 * r);
+            const R nv = x + c1 * (x - xpz) + c2 * r;
+            if (noimg_xy && z >= g.G && z < g.n[2] - g.G)
+                out[qc + (int64_t)z * ps] = nv;
+            else
+                store_periodic(out, g, i, j, z, nv);
         }
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < 2 * kChebR; ++m) col[m] = col[m + 1];
-        if (z + 1 < z1) col[2 * kChebR] = val(i, j, z + 1 + kChebR);
+        if (z + 1 < z1 && okc) col[2 * kChebR] = f[qc + (int64_t)(z + 1 + kChebR) * ps];
     }
 }
 
