@@ -38,14 +38,28 @@ METRIC = "particle-steps/s (gather+push+deposit)"
 UNIT = "particle-steps/s"
 BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp32 momenta) read + written
 
-# DRAM traffic per particle of the fused particle kernel, measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on a small case
-# of each workload, divided by its particles; traffic grows with the particle
-# count), with the same capture's issue and shared-memory figures.  Each entry
-# is valid only while the kernel's sources are the ones it was taken on
-# (sha256 of the files below); otherwise traffic is reported as null.
-PROFILED = {}
-PROFILED_SOURCES = {}
+# ncu figures of the per-step sorted particle kernel, per particle, from one
+# capture of one launch on a small case of each workload with the workload's
+# per-cell load (beam: 128x64x64 cells; thermal: 64^3 cells): DRAM traffic
+# (dram__bytes_read.sum + dram__bytes_write.sum; traffic grows with the
+# particle count), warp-instructions (smsp__inst_executed.sum) and the
+# limiter the capture shows.  An entry holds only while the kernel's sources
+# are the ones it was taken on (sha256 below); otherwise the line reports
+# traffic, limiter and issue as null.
+PROFILED = {
+    "beam": {"bytes_per_particle": 64.48, "warp_inst_per_particle": 103.0,
+             "limiter": "instruction issue (59.7 % of issue slots busy; LSU 38.9 %, FMA 31.6 % of peak; "
+                        "DRAM 5.7 %)"},
+    "thermal": {"bytes_per_particle": 66.20, "warp_inst_per_particle": 91.7,
+                "limiter": "instruction issue (60.7 % of issue slots busy; LSU 42.8 %, FMA 33.7 % of peak; "
+                           "DRAM 5.9 %)"},
+}
+PROFILED_SOURCES = {
+    "paper_1211_4575_gb300/csrc/pp_cells.cu": "9d0e804851f4d8e067503aaafffe40a66bad23e76fd9ba08a98b72648a79dc05",
+    "paper_1211_4575_gb300/csrc/pp_internal.cuh": "00cb3fc2fa3f0515a11f11b42e8eb92fa4d4d124135cefaf834886bc46b91cb9",
+    "paper_1211_4575_gb300/csrc/pp_particle_common.cuh": "6805ab903ef2be60e620b6059392d7afd2da3fd0f9a098f8dbf04858b8b05717",
+    "paper_1211_4575_gb300/csrc/pp_tma.cuh": "e0ac1f2401ee66da9f6509e7830a148f7aadb33c4eab9f1a62bf6f1a7995817c",
+}
 
 
 def _digest(rel):
@@ -54,12 +68,34 @@ def _digest(rel):
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def profiled(workload):
-    """The ncu figures of this workload's capture, or None once the kernel changed."""
-    P = PROFILED.get(workload)
-    if not P or any(_digest(rel) != d for rel, d in PROFILED_SOURCES.items()):
+def profiled(a):
+    """The ncu figures of this workload's capture, or None once the kernel
+    changed or the run is not the captured configuration (the per-step sorted
+    kernel at the workload's default per-cell load, leap-frog step, no cooling,
+    the charge-conserving current)."""
+    P = PROFILED.get(a.workload)
+    default_ppc = 16 if a.workload == "beam" else 32
+    if (not P or a.deposit not in ("auto", "cells") or a.ppc != default_ppc or a.integrator != 2 or a.radiation
+            or a.current != "conserving" or a.filter or a.field_solver != "implicit"):
+        return None
+    if not PROFILED_SOURCES or any(_digest(rel) != d for rel, d in PROFILED_SOURCES.items()):
         return None
     return P
+
+
+def issue_roofline(P, particle_steps, part_ms, clk):
+    """Instruction issue of the particle kernel against its ceiling: the
+    captured warp-instructions per particle times the particle-steps, over the
+    kernel's live time, against SMs x 4 schedulers x one warp-instruction per
+    cycle at the SM clock sampled during the timed region."""
+    import torch
+    if not P or part_ms <= 0 or not clk or not clk.get("sm_mhz"):
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    achieved = P["warp_inst_per_particle"] * particle_steps / (part_ms * 1e-3)
+    peak = sms * 4 * clk["sm_mhz"] * 1e6
+    return {"warp_inst_per_particle": P["warp_inst_per_particle"], "achieved": achieved, "peak": peak,
+            "unit": "warp-instructions/s", "frac": achieved / peak, "sms": sms}
 
 
 def args():
@@ -511,7 +547,7 @@ def run_gpu(a):
                "single_core": {"value": rate1, "unit": UNIT, "cores": 1, "sample": sample1}}
         if a.workload != "shock":   # the crop's error: the GPU's mixed form on the oracle's sample
             crop = crop_error(a, pp, osim, Lc, a.sample_steps)
-    P = profiled(a.workload)
+    P = profiled(a)
     per_launch = npart * a.steps / max(1, prof["particle_launches"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -524,7 +560,7 @@ def run_gpu(a):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None,
                      "traffic": P["bytes_per_particle"] * per_launch if P else None,
-                     "limiter": P["limiter"] if P else None, "issue": P["issue"] if P else None,
+                     "limiter": P["limiter"] if P else None, "issue": issue_roofline(P, npart * a.steps, part_ms, clk),
                      "kernel": "fused particle step (gather+push+move+deposit)",
                      "bytes_per_particle_step": bytes_per_step, "peak_kind": peak_kind,
                      "kernel_ms_per_step": part_ms / a.steps},

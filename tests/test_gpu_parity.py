@@ -288,3 +288,25 @@ def test_mixed_rho_against_oracle(pp, orc, shape, n):
     o.add_species(s["q"], s["m"], s["w"], p["x"], p["y"], p["z"], p["ux"], p["uy"], p["uz"])
     ro = o.rho()
     assert np.abs(rho - ro).max() <= 5e-6 * np.abs(ro).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kinetic_energy_against_its_definition(pp, precision):
+    """The kinetic energy reduction (w m dV sum of gamma - 1 per species, FP64)
+    against the plain FP64 sum over the momenta read back from the device,
+    for |u| log-uniform over 1e-4 .. 1e3 (non-relativistic terms, where
+    gamma - 1 ~ u^2 / 2, to ultra-relativistic ones)."""
+    rng = np.random.default_rng(77)
+    n, count = (16, 16, 16), 20000
+    L = pp_synth.random_particles(n, (0.5, 0.5, 0.5), 0.2, count, seed=5)
+    mag = 10.0 ** rng.uniform(-4, 3, count)
+    dirs = rng.normal(size=(3, count))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    sp = L.species[0]
+    sp["ux"], sp["uy"], sp["uz"] = mag * dirs[0], mag * dirs[1], mag * dirs[2]
+    sim = H.gpu_sim(pp, L, precision, 3)
+    p = sim.particles(0)
+    u2 = p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2
+    want = sp["w"] * sp["m"] * 0.125 * np.sum(u2 / (np.sqrt(1.0 + u2) + 1.0))
+    got = sim.diagnostics()["kinetic"][0]
+    assert got == pytest.approx(want, rel=1e-13)
