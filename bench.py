@@ -141,6 +141,9 @@ def args():
     ap.add_argument("--requests", type=int, default=12)
     ap.add_argument("--rate", type=float, default=0.07, help="mean arrivals per second of the serving trace")
     ap.add_argument("--serve-scale", choices=["c5", "reduced"], default="c5")
+    ap.add_argument("--serve-particles", type=int, default=48_000_000,
+                    help="serving: particles the running requests may hold together before the next request "
+                         "waits (0 = no limit)")
     a = ap.parse_args()
     if a.ppc is None:
         a.ppc = 16 if a.workload == "beam" else 32
@@ -606,13 +609,15 @@ def run_serve(a):
     warm = [dict(r, arrival=0.0, steps=2, n=32) for r in trace[:2]]
     serving.sequential(warm)
     seq, _ = serving.sequential(trace)
-    bat, _ = serving.serve(trace, budget_bytes=budget, max_slots=slots, chunk=4)
+    bat, _ = serving.serve(trace, budget_bytes=budget, max_slots=slots, chunk=4,
+                           max_active_particles=a.serve_particles or None)
     work = sum(r["n"] ** 3 * max(2, r["ppc"] // 2 * 2) * 2 * r["steps"] for r in trace)
     line = {"metric": "serving p50/p99 time-to-result", "value": bat["p99_s"], "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"{a.requests} Poisson arrivals at {a.rate}/s of two-stream/Weibel runs, "
                                    f"{desc}, 8..32 ppc per species, pair or m_i/m_e=25, mixed precision, PCS; "
-                                   f"budget {budget >> 30} GiB, {slots} slots; loads built by 4 host worker threads "
+                                   f"budget {budget >> 30} GiB, {slots} slots, "
+                                   f"particle budget {a.serve_particles or 'none'}; loads built by 4 host worker threads "
                                    "in both forms; time to result from arrival to the end of the last step",
                        "offered_particle_steps": work},
             "batched": bat, "sequential": seq}

@@ -71,10 +71,20 @@ def _summary(lat, work, makespan):
             "particle_steps_per_s": work / makespan if makespan > 0 else None}
 
 
-def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, keep=False, loaders=4, fused=False):
+def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, keep=False, loaders=4, fused=False,
+          max_active_particles=None):
     """Continuous batching.  Returns (summary, per-request results); with keep
     the finished Simulations are returned too (for comparisons).  fused: the
-    batch's fused rounds (one persistent particle launch per round)."""
+    batch's fused rounds (one persistent particle launch per round).
+
+    Requests are admitted in arrival order while device memory and slots
+    allow, and, with max_active_particles, while the particles of the running
+    requests plus the next one stay within that budget (a request over it is
+    admitted only onto an idle GPU).  Runs of a few million particles cannot
+    fill the GPU alone and gain most from overlapping; a run that fills it
+    gains nothing from company and would only be slowed by the runs admitted
+    after it, so under the budget the largest requests run as they would one
+    at a time."""
     import torch
     import pp_synth
     pending = sorted(requests, key=lambda r: r.get("arrival", 0.0))
@@ -92,9 +102,13 @@ def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, k
             req = pending[0]
             # admit by the run's device bytes, known before anything is built on
             # the device: a run that does not fit waits until a slot's memory returns
-            need = estimate_device_bytes((req["n"],) * 3, pp_synth.run_counts(req), precision)
+            counts = pp_synth.run_counts(req)
+            need = estimate_device_bytes((req["n"],) * 3, counts, precision)
             used, nact = batch.used()
             if used + need > budget_bytes or nact >= max_slots:
+                break
+            running = sum(v[2] for v in active.values())
+            if max_active_particles is not None and active and running + sum(counts) > max_active_particles:
                 break
             stream = torch.cuda.Stream()
             sim, npart = _build(req, precision, stream.cuda_stream, loads.take(req))
