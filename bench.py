@@ -139,7 +139,7 @@ def args():
                     help="one run split over the ranks by z-slabs (parallel.py: current summed by allreduce, "
                          "particles migrate); strong scaling. Default: independent replicas, weak scaling")
     ap.add_argument("--requests", type=int, default=12)
-    ap.add_argument("--rate", type=float, default=0.07, help="mean arrivals per second of the serving trace")
+    ap.add_argument("--rate", type=float, default=0.3, help="mean arrivals per second of the serving trace")
     ap.add_argument("--serve-scale", choices=["c5", "reduced"], default="c5")
     ap.add_argument("--serve-particles", type=int, default=48_000_000,
                     help="serving: particles the running requests may hold together before the next request "
