@@ -590,11 +590,12 @@ def run_gpu(a):
 def run_serve(a):
     """Serving form: a Poisson trace of independent two-stream / Weibel runs
     served by continuous batching through pp_batch_* (admission by device
-    bytes, every run resident, steps overlapping on the GPU), against the same
-    requests run one at a time.  Default trace: the serving configuration's
-    distributions (edges 32..192, 8..32 ppc per species, pair or m_i/m_e = 25,
-    200..1000 steps) at a sub-saturating rate; `--serve-scale reduced` takes
-    edges 16..48 and 20..100 steps instead."""
+    bytes and by a particle budget, every run resident, steps overlapping on
+    the GPU), against the same requests run one at a time.  Default trace: the
+    serving configuration's distributions (edges 32..192, 8..32 ppc per
+    species, pair or m_i/m_e = 25, 200..1000 steps) at 0.3 arrivals/s, which
+    the GPU just saturates; `--serve-scale reduced` takes edges 16..48 and
+    20..100 steps instead."""
     import pp_synth
     from paper_1211_4575_gb300 import build
     build.build()
