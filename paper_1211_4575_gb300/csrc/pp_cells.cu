@@ -18,19 +18,24 @@
 //    new cell, offset and momentum go straight back to the particle arrays
 //    (coalesced); the old offset and the displacement are staged for the
 //    deposit.  A particle whose support start changes on some axis (it
-//    crosses a support boundary) is queued.
+//    crosses a support boundary) is queued, with the axis and direction of
+//    the change.
 //  pieces: the chunk is cut into pieces of at most 8 consecutive particles
 //    of one deposit group (the particles of one cell, and for even orders of
-//    one octant of it, share their support start on every axis).
+//    one octant of it, share their support start on every axis); the queue
+//    (in chunk order) into crossing pieces of at most 8 consecutive entries
+//    of one group that change their support start on the same single axis
+//    in the same direction (so they share the union support: a cold beam's
+//    particles of one cell that cross into the next one).
 //  phase 2, the charge-conserving current (eq:cc1, eq:jj3, Esirkepov's
 //    decomposition written as the 2nd-order current by a per-particle prefix
 //    sum): one thread per (piece, component) sums the O (O+1)^2 site values
-//    of its particles in registers and adds them to the tile's FP32 current
+//    of its particles in registers and adds them to the tile's current
 //    window with one shared atomic per site (about 48 x 3 per piece instead of
-//    per particle); queued particles take the general form on the union
-//    support, one thread per (particle, component), with shared atomics per
-//    nonzero site.  A warp's 32 items always share the component, so no warp
-//    diverges over the three forms.
+//    per particle); a crossing piece likewise over its union support (at most
+//    (O+1)^3 sites per component); a particle that crosses on several axes
+//    takes the general union form, with shared atomics per nonzero site.  A
+//    warp's 32 items always share the component.
 //
 // The current window holds int32 fixed point (native shared integer atomics):
 // each chunk takes its unit from its particles' motion so that no node can
@@ -86,11 +91,22 @@ constexpr int kPiece = PP_CELLS_PIECE;           // most particles per deposit p
 // banks.
 constexpr int kCS = kCC + kCC / 16;              // words per staged array
 __device__ __forceinline__ int sp(int q) { return q + (q >> 4); }
-constexpr uint16_t kSkip = 0x8000;               // group word flag: not deposited by a piece
+// Group word of a staged particle: its deposit group (bits 0-11), its
+// crossing signature (bits 12-14: 0 no support start changes; 1 + 2a + up for
+// a change on axis a alone, up when it moves up; 7 for changes on several
+// axes) and kSkip (not deposited by a piece of non-crossing particles).
+constexpr uint16_t kSkip = 0x8000;
+constexpr int kSigShift = 12;
+constexpr uint16_t kGrpMask = 0x0fff, kSigMask = 0x7000;
 static_assert(kCC % kCT == 0 && kCT % 32 == 0, "chunk must split evenly over the CTA");
 static_assert(kCPer * kCW <= 1024, "piece-count table");
-constexpr int kMisc = 16 + kCPer * kCW;          // queue counters (2), piece count, box (6), totals (3), per-(round, warp) counts
-constexpr size_t kCellsSmem = kFieldBytes + sizeof(float) * (3 * kWVol + 6 * kCS) + sizeof(uint16_t) * (3 * kCC + 2) +
+// counts (queue, -, pieces), box (6), totals (3); then four tables of
+// per-(round, warp) counts and the crossing pieces per bucket (4)
+constexpr int kMisc = 20 + 4 * kCPer * kCW;
+// A crossing piece is stored as its first queue entry (12 bits) and its
+// length - 1 (3 bits).
+static_assert(kCC <= 4096 && kPiece <= 8, "crossing-piece word");
+constexpr size_t kCellsSmem = kFieldBytes + sizeof(float) * (3 * kWVol + 6 * kCS) + sizeof(uint16_t) * (4 * kCC + 4) +
                               sizeof(int) * kMisc;
 // The current window: an int32 fixed-point window whose unit each chunk takes
 // from its particles' motion, flushed into the FP32 mesh per chunk; or, with
@@ -240,7 +256,7 @@ __device__ __forceinline__ void piece_current(JT *Jw, const float *s_o, const fl
                                               int s, int e, float jscale PP_IF_CHECKED(, int *st)) {
     constexpr int Bx = (A + 1) % 3, Cx = (A + 2) % 3;
     int cw[3], lo[3];
-    group_frame<O>(s_grp[s] & ~kSkip, cw, lo);
+    group_frame<O>(s_grp[s] & kGrpMask, cw, lo);
     float acc[O][O + 1][O + 1];
 #pragma unroll
     for (int m = 0; m < O; ++m)
@@ -315,13 +331,16 @@ __device__ __forceinline__ void piece_current(JT *Jw, const float *s_o, const fl
             }
 }
 
-// Component A of a queued particle's current: the general form on the union
-// of its old and new supports (O + 2 nodes per axis).
+// Component A of the current of a particle whose support start moves on
+// several axes: the general form on the union of its old and new supports
+// (O + 2 nodes per axis).  Rare (a few particles per thousand even in a hot
+// plasma), so kept out of line: the tile loop's code stays small enough for
+// the instruction cache.
 template <int O, int A>
-__device__ __forceinline__ void queued_current(JT *Jw, const float *s_o, const float *s_d, const uint16_t *s_grp,
+__device__ __noinline__ void queued_current(JT *Jw, const float *s_o, const float *s_d, const uint16_t *s_grp,
                                                int q, float jscale PP_IF_CHECKED(, int *st)) {
     int cw[3], lo0[3];
-    group_frame<O>(s_grp[q] & ~kSkip, cw, lo0);
+    group_frame<O>(s_grp[q] & kGrpMask, cw, lo0);
     float xi0[3], xi1[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -336,10 +355,173 @@ __device__ __forceinline__ void queued_current(JT *Jw, const float *s_o, const f
     esirkepov_component<O, float, A>(acc, S0, DS, lo, jscale);
 }
 
+// Component A of the current of a crossing piece: particles of one deposit
+// group whose support start moves one node along axis XA alone, all in the
+// same direction (up: to the next node), so that they share the union support
+// (O + 2 nodes along XA, O + 1 along the others).  Their site values are those
+// of the general union form (esirkepov_weights + esirkepov_component, site by
+// site the same products; its sites that are zero for such a particle are
+// left out here): NA faces along A (O + 1 when A is the crossing axis, else O,
+// the last face being zero) times the union nodes across.  They are summed in
+// registers over the piece and added once per site.  The work is written in
+// axes rotated so that the crossing axis comes first (rotated axis r is axis
+// (r + XA) mod 3, RA the rotated A), so that one body serves all three
+// crossing axes.
+template <int O, int RA>
+__device__ __forceinline__ void cross_piece(JT *Jw, int A, int XA, const float *s_o, const float *s_d,
+                                            const uint16_t *s_queue, int ks, int ke, int grp, bool up,
+                                            float jscale PP_IF_CHECKED(, int *st)) {
+    constexpr int RB = (RA + 1) % 3, RC = (RA + 2) % 3;
+    constexpr int NA = (RA == 0) ? O + 1 : O;
+    constexpr int NB = (RB == 0) ? O + 2 : O + 1;
+    constexpr int NC = (RC == 0) ? O + 2 : O + 1;
+    int cw[3], lo[3];
+    group_frame<O>(grp, cw, lo);
+    const int p[3] = {XA, XA == 2 ? 0 : XA + 1, XA == 0 ? 2 : XA - 1};   // physical axis of rotated axis r
+    int lr[3], sr[3];   // support start and window stride per rotated axis
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        lr[r] = p[r] == 0 ? lo[0] : (p[r] == 1 ? lo[1] : lo[2]);
+        sr[r] = p[r] == 0 ? 1 : (p[r] == 1 ? kW : kW * kW);
+    }
+    lr[0] -= up ? 0 : 1;   // union start along the crossing axis: the lower of the old and new starts
+    float acc[NA][NB][NC];
+#pragma unroll
+    for (int m = 0; m < NA; ++m)
+#pragma unroll
+        for (int mb = 0; mb < NB; ++mb)
+#pragma unroll
+            for (int mc = 0; mc < NC; ++mc) acc[m][mb][mc] = 0.0f;
+#pragma unroll 1
+    for (int e = ks; e < ke; ++e) {
+        const int q = s_queue[e];
+        float S0[3][O + 2], DS[3][O + 2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float x0 = s_o[p[r] * kCS + sp(q)];
+            const float x1 = x0 + s_d[p[r] * kCS + sp(q)];
+            float wo[O + 1], wn[O + 1];
+            support<O, float>(x0, false, wo);
+            support<O, float>(x1, false, wn);
+            if (r == 0) {   // old weights from the union start (up) or one node above it
+#pragma unroll
+                for (int m = 0; m < O + 2; ++m) {
+                    const float a0 = up ? (m <= O ? wo[m] : 0.0f) : (m >= 1 ? wo[m - 1] : 0.0f);
+                    const float a1 = up ? (m >= 1 ? wn[m - 1] : 0.0f) : (m <= O ? wn[m] : 0.0f);
+                    S0[r][m] = a0;
+                    DS[r][m] = a1 - a0;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m <= O; ++m) {
+                    S0[r][m] = wo[m];
+                    DS[r][m] = wn[m] - wo[m];
+                }
+                S0[r][O + 1] = 0.0f;
+                DS[r][O + 1] = 0.0f;
+            }
+        }
+        // prefix of dS along A on the lower faces, suffix on the upper ones
+        float C[NA];
+        float run = 0.0f;
+#pragma unroll
+        for (int m = 0; m < NA; ++m) {
+            if (2 * m < O + 1) {
+                run += DS[RA][m];
+                C[m] = run * jscale;
+            }
+        }
+        run = 0.0f;
+#pragma unroll
+        for (int m = NA - 1; m >= 0; --m) {
+            if (2 * m >= O + 1) {
+                run -= DS[RA][m + 1];
+                C[m] = run * jscale;
+            }
+        }
+#pragma unroll
+        for (int mc = 0; mc < NC; ++mc) {
+            const float pc = S0[RC][mc] + 0.5f * DS[RC][mc];
+            const float hc = 0.5f * S0[RC][mc] + (1.0f / 3.0f) * DS[RC][mc];
+#pragma unroll
+            for (int mb = 0; mb < NB; ++mb) {
+                const float Y = S0[RB][mb] * pc + DS[RB][mb] * hc;
+#pragma unroll
+                for (int m = 0; m < NA; ++m) acc[m][mb][mc] += C[m] * Y;
+            }
+        }
+    }
+    JT *J = Jw + A * kWVol;
+#pragma unroll
+    for (int m = 0; m < NA; ++m)
+#pragma unroll
+        for (int mb = 0; mb < NB; ++mb)
+#pragma unroll
+            for (int mc = 0; mc < NC; ++mc) {
+#ifdef PP_CHECKED
+                if (lr[RA] + m < 0 || lr[RA] + m >= kW || lr[RB] + mb < 0 || lr[RB] + mb >= kW || lr[RC] + mc < 0 ||
+                    lr[RC] + mc >= kW) {
+                    atomicOr(st, ST_BOUNDS);
+                    continue;
+                }
+#endif
+                jadd(J + (lr[RA] + m) * sr[RA] + (lr[RB] + mb) * sr[RB] + (lr[RC] + mc) * sr[RC], acc[m][mb][mc]);
+            }
+}
+
+// Component A of the current of the crossing piece [ks, ke) of the queue, of
+// bucket xa: the crossing axis (cross_piece), or 3 for a single particle whose
+// support start moves on several axes (the general union form).
+template <int O>
+__device__ __forceinline__ void xpiece_current(JT *Jw, int A, const float *s_o, const float *s_d,
+                                               const uint16_t *s_grp, const uint16_t *s_queue, int ks, int ke, int xa,
+                                               float jscale PP_IF_CHECKED(, int *st)) {
+    if (xa == 3) {
+        if (A == 0) queued_current<O, 0>(Jw, s_o, s_d, s_grp, s_queue[ks], jscale PP_IF_CHECKED(, st));
+        else if (A == 1) queued_current<O, 1>(Jw, s_o, s_d, s_grp, s_queue[ks], jscale PP_IF_CHECKED(, st));
+        else queued_current<O, 2>(Jw, s_o, s_d, s_grp, s_queue[ks], jscale PP_IF_CHECKED(, st));
+        return;
+    }
+    const int g0 = s_grp[s_queue[ks]];
+    const bool up = (((g0 & kSigMask) >> kSigShift) & 1) == 0;   // signature 1 + 2 xa + up
+    const int grp = g0 & kGrpMask;
+    const int ra = A >= xa ? A - xa : A - xa + 3;
+    if (ra == 0) cross_piece<O, 0>(Jw, A, xa, s_o, s_d, s_queue, ks, ke, grp, up, jscale PP_IF_CHECKED(, st));
+    else if (ra == 1) cross_piece<O, 1>(Jw, A, xa, s_o, s_d, s_queue, ks, ke, grp, up, jscale PP_IF_CHECKED(, st));
+    else cross_piece<O, 2>(Jw, A, xa, s_o, s_d, s_queue, ks, ke, grp, up, jscale PP_IF_CHECKED(, st));
+}
+
 __device__ __forceinline__ unsigned lanemask_lt_() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Exclusive scan, in chunk order, of the per-(round, warp) counts
+// c[0 .. kCPer kCW) by one warp; the total goes to *total.
+__device__ __forceinline__ void scan_counts(int *c, int *total, int lane) {
+    constexpr int kPerLane = (kCPer * kCW + 31) / 32;
+    int v[kPerLane], sum = 0;
+#pragma unroll
+    for (int m = 0; m < kPerLane; ++m) {
+        const int k = lane * kPerLane + m;
+        v[m] = k < kCPer * kCW ? c[k] : 0;
+        sum += v[m];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int m = 0; m < kPerLane; ++m) {
+        const int k = lane * kPerLane + m;
+        if (k < kCPer * kCW) c[k] = run;
+        run += v[m];
+    }
+    if (lane == 31) *total = incl;
 }
 
 // BND: walls (reflection) and the open end (escape); a separate instantiation
@@ -357,12 +539,15 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
     JT *Jw = (JT *)((char *)smem + kFieldBytes);
     float *s_o = (float *)(Jw + 3 * kWVol);   // 3 x kCS: offsets at t (frame of the cell)
     float *s_d = s_o + 3 * kCS;           // 3 x kCS: displacement of the step
-    uint16_t *s_grp = (uint16_t *)(s_d + 3 * kCS);   // deposit group | kSkip
+    uint16_t *s_grp = (uint16_t *)(s_d + 3 * kCS);   // group word (deposit group, crossing, kSkip)
     uint16_t *s_piece = s_grp + kCC;                  // piece starts (+ the end)
-    uint16_t *s_queue = s_piece + kCC + 2;            // queued particles
-    int *misc = (int *)(s_queue + kCC);   // [0], [1]: queue counters of even / odd chunks; [2]: pieces;
-                                          // [4..9]: fixed point: cell box of the chunk; [10..12]: sum |dxi|
-    int *cnt = misc + 16;                 // piece starts per (round, warp)
+    uint16_t *s_queue = s_piece + kCC + 2;            // crossing particles, in chunk order
+    uint16_t *s_xpiece = s_queue + kCC;               // crossing pieces by bucket: first entry | (length - 1) << 12
+    int *misc = (int *)(s_xpiece + kCC + 2);   // [0]: queue length; [2]: pieces;
+                                               // [4..9]: fixed point: cell box of the chunk; [10..12]: sum |dxi|
+    int *cnt = misc + 16;                 // starts per (round, warp); four tables
+    int *qcnt = cnt + kCPer * kCW;        // crossing particles per (round, warp)
+    int *xtot = cnt + 4 * kCPer * kCW;    // crossing pieces per bucket
     const Geom &g = T.g;
     const int tx = tile % T.nt[0], ty = (tile / T.nt[0]) % T.nt[1], tz = tile / (T.nt[0] * T.nt[1]);
     const int ox = tx * kT, oy = ty * kT, oz = tz * kT;
@@ -383,7 +568,6 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
         return true;
     }
     if (threadIdx.x == 0) {
-        misc[0] = misc[1] = 0;
         // a CTA whose wait ran out stops the others at their next tile
         misc[3] = (*(volatile int *)T.status & ST_TIMEOUT) != 0;
         if (misc[3]) {
@@ -404,13 +588,11 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
     if (misc[3]) return false;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int par = 0;   // chunk parity: selects the queue counter
     for (int s = 0; s < T.ns; ++s) {
         const CellsSpecies &S = T.sp[s];
         const int tb = S.cell_start[key0], te = S.cell_start[key1];
-        for (int cb = tb; cb < te; cb += kCC, par ^= 1) {
+        for (int cb = tb; cb < te; cb += kCC) {
             const int cn = min(kCC, te - cb);
-            if (threadIdx.x == 0) misc[par ^ 1] = 0;   // the next chunk's counter (last read before the barrier above)
 #if PP_CELLS_FIXED
             float sum[3] = {0.0f, 0.0f, 0.0f};
             int blo[3] = {kT, kT, kT}, bhi[3] = {-1, -1, -1};
@@ -460,13 +642,17 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
                 }
                 const float gi = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 float dx[3], xi1[3];
-                bool ok = true, cross = false;
+                bool ok = true;
+                int ncross = 0, xa = 0;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     dx[d] = T.dtdx[d] * u[d] * gi;
                     xi1[d] = xi0[d] + dx[d];
                     ok = ok && (fabsf(dx[d]) < 1.0f);
-                    cross = cross || floorf(xi0[d] - 0.5f * (O - 1)) != floorf(xi1[d] - 0.5f * (O - 1));
+                    if (floorf(xi0[d] - 0.5f * (O - 1)) != floorf(xi1[d] - 0.5f * (O - 1))) {
+                        ++ncross;
+                        xa = d;
+                    }
                 }
                 if (!ok) {   // leave the particle unchanged and flag the step
                     atomicOr(T.status, isfinite(u[0] + u[1] + u[2]) ? ST_CFL : ST_NAN);
@@ -484,8 +670,10 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
                 blo[0] = min(blo[0], rx); blo[1] = min(blo[1], ry); blo[2] = min(blo[2], rz);
                 bhi[0] = max(bhi[0], rx); bhi[1] = max(bhi[1], ry); bhi[2] = max(bhi[2], rz);
 #endif
-                if (cross) s_queue[atomicAdd(misc + par, 1)] = (uint16_t)q;
-                s_grp[q] = (uint16_t)(cross ? (grp | kSkip) : grp);
+                // crossing signature: the axis and direction of a support start
+                // that moves on one axis alone, 7 when it moves on several
+                const int sig = ncross == 0 ? 0 : (ncross == 1 ? 1 + 2 * xa + (dx[xa] > 0.0f ? 1 : 0) : 7);
+                s_grp[q] = (uint16_t)(grp | (sig << kSigShift) | (ncross ? kSkip : 0));
                 // the new state, written to the slot (the deposit reads the staged copy)
                 int ncx = cx, ncy = cy, ncz = cz;
                 rebin(xi1[0], ncx, g.n[0]);
@@ -524,58 +712,98 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
             }
 #endif
             __syncthreads();
-            // ---- pieces: starts at a group change and every kPiece-th particle
-            unsigned ball[kCPer];
+            // ---- pieces of non-crossing particles: starts at a group change and
+            // every kPiece-th particle; crossing particles into the queue, in chunk
+            // order (both by ballots and a scan of the per-(round, warp) counts)
+            unsigned ball[kCPer], qball[kCPer];
 #pragma unroll
             for (int r = 0; r < kCPer; ++r) {
                 const int q = r * kCT + threadIdx.x;
-                bool st = false;
-                if (q < cn) st = q % kPiece == 0 || ((s_grp[q] ^ s_grp[q - 1]) & ~kSkip) != 0;
+                bool st = false, cr = false;
+                if (q < cn) {
+                    const int gq = s_grp[q];
+                    st = q % kPiece == 0 || ((gq ^ s_grp[q - 1]) & kGrpMask) != 0;
+                    cr = (gq & kSigMask) != 0;
+                }
                 ball[r] = __ballot_sync(0xffffffffu, st);
-                if (lane == 0) cnt[r * kCW + warp] = __popc(ball[r]);
+                qball[r] = __ballot_sync(0xffffffffu, cr);
+                if (lane == 0) {
+                    cnt[r * kCW + warp] = __popc(ball[r]);
+                    qcnt[r * kCW + warp] = __popc(qball[r]);
+                }
             }
             __syncthreads();
-            if (warp == 0) {   // exclusive scan of the per-(round, warp) counts, in chunk order
-                constexpr int kPerLane = (kCPer * kCW + 31) / 32;
-                int v[kPerLane], sum = 0;
-#pragma unroll
-                for (int m = 0; m < kPerLane; ++m) {
-                    const int k = lane * kPerLane + m;
-                    v[m] = k < kCPer * kCW ? cnt[k] : 0;
-                    sum += v[m];
-                }
-                int incl = sum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                int run = incl - sum;
-#pragma unroll
-                for (int m = 0; m < kPerLane; ++m) {
-                    const int k = lane * kPerLane + m;
-                    if (k < kCPer * kCW) cnt[k] = run;
-                    run += v[m];
-                }
-                if (lane == 31) misc[2] = incl;
-            }
+            if (warp == 0) scan_counts(cnt, misc + 2, lane);
+            else if (warp == 1) scan_counts(qcnt, misc + 0, lane);
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < kCPer; ++r) {
                 const int q = r * kCT + threadIdx.x;
-                if (ball[r] & (1u << lane)) s_piece[cnt[r * kCW + warp] + __popc(ball[r] & lanemask_lt_())] = (uint16_t)q;
+                const unsigned below = lanemask_lt_();
+                if (ball[r] & (1u << lane)) s_piece[cnt[r * kCW + warp] + __popc(ball[r] & below)] = (uint16_t)q;
+                if (qball[r] & (1u << lane)) s_queue[qcnt[r * kCW + warp] + __popc(qball[r] & below)] = (uint16_t)q;
             }
             if (threadIdx.x == 0) s_piece[misc[2]] = (uint16_t)cn;
             __syncthreads();
-            // ---- phase 2: current of the pieces, then of the queued particles; items in
+            // ---- crossing pieces over the queue: starts at a change of group or
+            // crossing, at a particle crossing on several axes and after one, and
+            // every kPiece-th entry.  They are listed by bucket (the crossing axis,
+            // or 3 for several axes), so that the 32 items of a warp take one form.
+            const int nq = misc[0];
+            auto xstart = [&](int k) {
+                const int gk = s_grp[s_queue[k]];
+                if (k % kPiece == 0 || (gk & kSigMask) == kSigMask) return true;
+                const int gp = s_grp[s_queue[k - 1]];
+                return (gp & kSigMask) == kSigMask || ((gk ^ gp) & (kGrpMask | kSigMask)) != 0;
+            };
+            int xflag = 0;   // per round: bit 2 start, bits 0-1 bucket
+#pragma unroll
+            for (int r = 0; r < kCPer; ++r) {
+                const int k = r * kCT + threadIdx.x;
+                int f = 0;
+                if (k < nq && xstart(k)) f = 4 | ((((s_grp[s_queue[k]] & kSigMask) >> kSigShift) - 1) >> 1);
+                xflag |= f << (3 * r);
+#pragma unroll
+                for (int bk = 0; bk < 4; ++bk) {
+                    const unsigned m = __ballot_sync(0xffffffffu, f == (4 | bk));
+                    if (lane == 0) cnt[bk * kCPer * kCW + r * kCW + warp] = __popc(m);
+                }
+            }
+            __syncthreads();
+            if (warp < 4) scan_counts(cnt + warp * kCPer * kCW, xtot + warp, lane);
+            __syncthreads();
+            const int xb1 = xtot[0], xb2 = xb1 + xtot[1], xb3 = xb2 + xtot[2];
+#pragma unroll
+            for (int r = 0; r < kCPer; ++r) {
+                const int k = r * kCT + threadIdx.x;
+                const int f = (xflag >> (3 * r)) & 7;
+#pragma unroll
+                for (int bk = 0; bk < 4; ++bk) {
+                    const unsigned m = __ballot_sync(0xffffffffu, f == (4 | bk));
+                    if (f == (4 | bk)) {
+                        int e = k + 1;
+                        while (e < nq && e % kPiece != 0 && !xstart(e)) ++e;
+                        const int base = bk == 0 ? 0 : (bk == 1 ? xb1 : (bk == 2 ? xb2 : xb3));
+                        s_xpiece[base + cnt[bk * kCPer * kCW + r * kCW + warp] + __popc(m & lanemask_lt_())] =
+                            (uint16_t)(k | ((e - k - 1) << 12));
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- phase 2: current of the pieces, then of the crossing pieces; items in
             // blocks of 96 = 3 components x 32, so that a warp's items share the component
-            const int np = misc[2], nq = misc[par];
-            const int nblk = (np + 31) >> 5, nqb = (nq + 31) >> 5;
+            const int np = misc[2];
+            const int nblk = (np + 31) >> 5;
+            // crossing pieces per bucket, their blocks of 32 (scalars: an array
+            // indexed by the bucket would live in local memory)
+            const int xn0 = xtot[0], xn1 = xtot[1], xn2 = xtot[2], xn3 = xtot[3];
+            const int xk0 = (xn0 + 31) >> 5, xk1 = (xn1 + 31) >> 5, xk2 = (xn2 + 31) >> 5, xk3 = (xn3 + 31) >> 5;
             // current scale: -q w dx_a / dt, times the chunk's fixed-point unit; no
             // node can receive more than K_O |jscale_a| sum_p (|dxi_a| + 1e-6) from
             // the chunk (|C Y| <= K_O |dxi_a|, fixed_point_cy_bound), kept below 2^30
-            // units; a piece converts its register sum once, so a node collects at
-            // most one rounding half per piece and per queued particle
+            // units; a piece or crossing piece converts its register sum once, so
+            // a node collects at most one rounding half per piece, per crossing
+            // piece and per particle crossing on several axes
             float jsc[3], unit[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -588,14 +816,13 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
 #endif
                 jsc[d] = S.jscale[d] * unit[d];
             }
-            const int nitems = (nblk + nqb) * 96;
+            const int nitems = (nblk + xk0 + xk1 + xk2 + xk3) * 96;
 #pragma unroll 1
             for (int it = threadIdx.x; it < nitems; it += kCT) {
                 const int blk = it / 96, rr = it - blk * 96, comp = rr >> 5, j = rr & 31;
-                // lane j of item block b takes piece (queue entry) j * blocks + b:
-                // consecutive pieces and queue entries often share a cell, and the
-                // cold beams' queued particles of one cell share their sites, so
-                // lanes on consecutive entries would add to the same words
+                // lane j of item block b takes piece (crossing piece) j * blocks + b:
+                // consecutive pieces often share a cell, so lanes on consecutive
+                // pieces would add to the same words
                 if (blk < nblk) {
                     const int p = j * nblk + blk;
                     if (p >= np) continue;
@@ -603,13 +830,24 @@ __device__ __forceinline__ bool cells_tile(const CellsArgs &T, const int tile, f
                     if (comp == 0) piece_current<O, 0>(Jw, s_o, s_d, s_grp, ps, pe, jsc[0] PP_IF_CHECKED(, T.status));
                     else if (comp == 1) piece_current<O, 1>(Jw, s_o, s_d, s_grp, ps, pe, jsc[1] PP_IF_CHECKED(, T.status));
                     else piece_current<O, 2>(Jw, s_o, s_d, s_grp, ps, pe, jsc[2] PP_IF_CHECKED(, T.status));
-                } else {
-                    const int k = j * nqb + (blk - nblk);
-                    if (k >= nq) continue;
-                    const int q = s_queue[k];
-                    if (comp == 0) queued_current<O, 0>(Jw, s_o, s_d, s_grp, q, jsc[0] PP_IF_CHECKED(, T.status));
-                    else if (comp == 1) queued_current<O, 1>(Jw, s_o, s_d, s_grp, q, jsc[1] PP_IF_CHECKED(, T.status));
-                    else queued_current<O, 2>(Jw, s_o, s_d, s_grp, q, jsc[2] PP_IF_CHECKED(, T.status));
+                } else {   // crossing pieces: the block's bucket, then lane j's piece in it
+                    int bk, lb = blk - nblk, nk, nn, base;
+                    if (lb < xk0) {
+                        bk = 0; nk = xk0; nn = xn0; base = 0;
+                    } else if ((lb -= xk0) < xk1) {
+                        bk = 1; nk = xk1; nn = xn1; base = xn0;
+                    } else if ((lb -= xk1) < xk2) {
+                        bk = 2; nk = xk2; nn = xn2; base = xn0 + xn1;
+                    } else {
+                        lb -= xk2;
+                        bk = 3; nk = xk3; nn = xn3; base = xn0 + xn1 + xn2;
+                    }
+                    const int k = j * nk + lb;
+                    if (k >= nn) continue;
+                    const int v = s_xpiece[base + k];
+                    const int ks = v & 0xfff, ke = ks + (v >> 12) + 1;
+                    const float js = comp == 0 ? jsc[0] : (comp == 1 ? jsc[1] : jsc[2]);
+                    xpiece_current<O>(Jw, comp, s_o, s_d, s_grp, s_queue, ks, ke, bk, js PP_IF_CHECKED(, T.status));
                 }
             }
             __syncthreads();
