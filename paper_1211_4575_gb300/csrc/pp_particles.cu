@@ -1197,23 +1197,6 @@ cudaError_t launch_rho(Ctx &c, bool sort_first) {
 // ---------------------------------------------------------------------------
 // Kinetic energy sum_p w m (gamma - 1) dV (FP64).
 // ---------------------------------------------------------------------------
-// gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), in FP64 but without an FP64 square
-// root or division (both long sequences at this part's FP64 rate): FP32
-// estimates of 1/sqrt(1 + u^2) and of the reciprocal, each refined by two
-// Newton-Raphson steps in FP64 (y <- y (3 - x y^2) / 2, r <- r (2 - d r)),
-// which square the relative error twice, from about 1e-7 to FP64 rounding.
-__device__ __forceinline__ double gamma_minus_one(double u2) {
-    const double x = 1.0 + u2;
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    const double d = x * y + 1.0;   // sqrt(1 + u^2) + 1
-    double r = (double)__frcp_rn((float)d);
-    r = r * (2.0 - d * r);
-    r = r * (2.0 - d * r);
-    return u2 * r;
-}
-
 __global__ void k_kinetic(int64_t n, Fp64Particles p64, MixedParticles pm, int mixed, double scale, double *out) {
     double acc = 0.0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -1221,7 +1204,8 @@ __global__ void k_kinetic(int64_t n, Fp64Particles p64, MixedParticles pm, int m
         if (mixed ? pm.cell[t] < 0 : p64.x[t] < 0.0) continue;   // left the box
         if (mixed) { u0 = pm.ux[t]; u1 = pm.uy[t]; u2 = pm.uz[t]; }
         else { u0 = p64.ux[t]; u1 = p64.uy[t]; u2 = p64.uz[t]; }
-        acc += gamma_minus_one(u0 * u0 + u1 * u1 + u2 * u2);   // gamma - 1 without cancellation
+        double u2s = u0 * u0 + u1 * u1 + u2 * u2;
+        acc += u2s / (sqrt(1.0 + u2s) + 1.0);   // gamma - 1 without cancellation
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     __shared__ double ws[32];
