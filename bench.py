@@ -47,15 +47,15 @@ BYTES_PER_PARTICLE_STEP = 56   # mixed form: (int32 cell + 3 fp32 offsets + 3 fp
 # are the ones it was taken on (sha256 below); otherwise the line reports
 # traffic, limiter and issue as null.
 PROFILED = {
-    "beam": {"bytes_per_particle": 64.48, "warp_inst_per_particle": 103.0,
-             "limiter": "instruction issue (59.7 % of issue slots busy; LSU 38.9 %, FMA 31.6 % of peak; "
-                        "DRAM 5.7 %)"},
-    "thermal": {"bytes_per_particle": 66.20, "warp_inst_per_particle": 91.7,
-                "limiter": "instruction issue (60.7 % of issue slots busy; LSU 42.8 %, FMA 33.7 % of peak; "
-                           "DRAM 5.9 %)"},
+    "beam": {"bytes_per_particle": 64.55, "warp_inst_per_particle": 100.2,
+             "limiter": "instruction issue (63.0 % of issue slots busy; LSU 41.0 %, FMA 37.0 % of peak; "
+                        "DRAM 6.1 %)"},
+    "thermal": {"bytes_per_particle": 66.23, "warp_inst_per_particle": 94.6,
+                "limiter": "instruction issue (57.3 % of issue slots busy; LSU 39.4 %, FMA 32.2 % of peak; "
+                           "DRAM 5.3 %)"},
 }
 PROFILED_SOURCES = {
-    "paper_1211_4575_gb300/csrc/pp_cells.cu": "9d0e804851f4d8e067503aaafffe40a66bad23e76fd9ba08a98b72648a79dc05",
+    "paper_1211_4575_gb300/csrc/pp_cells.cu": "16c7f12cf0f9e413eae8c402bdf089400dd7af4e2ce7593d6ed90713baf03ed6",
     "paper_1211_4575_gb300/csrc/pp_internal.cuh": "00cb3fc2fa3f0515a11f11b42e8eb92fa4d4d124135cefaf834886bc46b91cb9",
     "paper_1211_4575_gb300/csrc/pp_particle_common.cuh": "6805ab903ef2be60e620b6059392d7afd2da3fd0f9a098f8dbf04858b8b05717",
     "paper_1211_4575_gb300/csrc/pp_tma.cuh": "e0ac1f2401ee66da9f6509e7830a148f7aadb33c4eab9f1a62bf6f1a7995817c",
