@@ -72,9 +72,13 @@ extern "C" {
 #define PP_DEPOSIT_CELLS 3   /* PP_MIXED32: particles sorted by cell at the start of
                                 every particle pass (Sec. III, the sort between the
                                 deposit and the field update of every step); the
-                                current of the particles of one cell that cross no
-                                support boundary is summed in registers, then in an
-                                int32 fixed-point tile window.  Needs the
+                                E/B window of each 8^3 tile arrives by TMA tensor
+                                copies (bounded wait, PP_ETIMEOUT); the current of
+                                the particles of one cell that cross no support
+                                boundary, and of those that cross it on the same
+                                single axis in the same direction, is summed in
+                                registers, then in an int32 fixed-point tile
+                                window.  Needs the
                                 charge-conserving current and mesh sizes that are
                                 multiples of 8; PP_DEPOSIT_AUTO takes it wherever it
                                 applies                                             */
