@@ -64,6 +64,20 @@ class _Loads:
         self.pool.shutdown(wait=True)
 
 
+def admissible(used, need, budget_bytes, nact, max_slots, running_particles, req_particles,
+               max_active_particles=None):
+    """Whether the next request in arrival order may enter now: its device
+    bytes fit the budget beside the running requests', a slot is free, and,
+    with a particle budget, the running requests' particles plus its own stay
+    within it (a request over the budget enters only an idle GPU)."""
+    if used + need > budget_bytes or nact >= max_slots:
+        return False
+    if max_active_particles is not None and running_particles > 0 and \
+            running_particles + req_particles > max_active_particles:
+        return False
+    return True
+
+
 def _summary(lat, work, makespan):
     lat = np.asarray(lat, dtype=float)
     return {"requests": int(lat.size), "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
@@ -105,10 +119,8 @@ def serve(requests, budget_bytes, max_slots=16, chunk=8, precision=PP_MIXED32, k
             counts = pp_synth.run_counts(req)
             need = estimate_device_bytes((req["n"],) * 3, counts, precision)
             used, nact = batch.used()
-            if used + need > budget_bytes or nact >= max_slots:
-                break
             running = sum(v[2] for v in active.values())
-            if max_active_particles is not None and active and running + sum(counts) > max_active_particles:
+            if not admissible(used, need, budget_bytes, nact, max_slots, running, sum(counts), max_active_particles):
                 break
             stream = torch.cuda.Stream()
             sim, npart = _build(req, precision, stream.cuda_stream, loads.take(req))
